@@ -1,0 +1,196 @@
+"""Seeded synthetic inputs: material presets, solver presets, periodic Voronoi
+polycrystals, orientations, pre-crack masks and cyclic loading programs.
+
+This module holds none of the method's arithmetic.  It only produces the data
+a run starts from, so the GPU library and the CPU oracle can be fed exactly
+the same inputs.  Units are MPa, mm, s.
+
+The paper's own microstructures are not available (they appear only as
+figures), so seeded periodic Voronoi tessellations with orientations uniform
+on SO(3) stand in for them, with the voxel size of Sec. 4 (0.78 um).
+"""
+import math
+
+import numpy as np
+
+VOXEL_MM = 0.78e-3  # Sec. 4: characteristic voxel length 0.78 um
+
+# Table 1 (CMSX-4) as printed, plus the constants the paper uses without a
+# value: activation volume dV (20 b^3), shear modulus mu (= C44), stored-energy
+# fraction xi_store, initial SSD density (= rho_m).  G_crit = 4 J/m^2 and
+# ell = 2.34 um, ell_Fp = 1.56 um are from Sec. 4.
+_B = 3.5e-7
+PAPER_TABLE1 = {
+    "C11": 250e3, "C12": 161e3, "C44": 129e3, "tau_c0": 350.0, "b": _B, "nu_D": 1e11,
+    "k_B": 1.4e-23, "T": 295.0, "dF": 4.9e-20, "rho_m": 5.0e6, "lambda_h": 150e6,
+    "dV": 20.0 * _B ** 3, "mu": 129e3, "xi_store": 0.05, "rho_ssd0": 5.0e6,
+    "G_crit": 4e-3, "ell": 2.34e-3, "ell_Fp": 1.56e-3, "k_res": 1e-5,
+}
+
+
+def material(preset="baseline", **overrides):
+    """Material dictionary.
+
+    ``paper``: Table 1 exactly.  ``baseline``: Table 1 with the cubic constants
+    C11/C12/C44 = 246.5/147.3/124.7 GPa and ell = ell_Fp = 2 voxels.
+    """
+    m = dict(PAPER_TABLE1)
+    if preset == "baseline":
+        m.update(C11=246.5e3, C12=147.3e3, C44=124.7e3, mu=124.7e3,
+                 ell=2 * VOXEL_MM, ell_Fp=2 * VOXEL_MM)
+    elif preset != "paper":
+        raise ValueError(preset)
+    m.update(overrides)
+    return m
+
+
+def solver_options(preset="paper", **overrides):
+    """Tolerance presets.
+
+    ``paper``: Newton and staggered 5e-3, Krylov 1e-5 (Sec. 3.1-3.2).
+    ``parity64``: tight tolerances for FP64 parity.  ``parity32``: the
+    tightest the FP32-bulk path reaches reliably.
+    """
+    base = {"max_stag": 50, "max_newton": 25, "max_lin": 2000, "max_pf": 500, "max_local": 100,
+            "restart": 30}
+    if preset == "paper":
+        o = dict(tol_stag=5e-3, tol_newton=5e-3, tol_lin=1e-5, tol_pf=1e-5, tol_local=1e-9)
+    elif preset == "parity64":
+        o = dict(tol_stag=1e-9, tol_newton=1e-9, tol_lin=1e-10, tol_pf=1e-11,
+                 tol_local=1e-10)
+    elif preset == "parity32":
+        o = dict(tol_stag=1e-4, tol_newton=1e-4, tol_lin=1e-6, tol_pf=1e-6, tol_local=3e-4)
+    else:
+        raise ValueError(preset)
+    base.update(o)
+    base.update(overrides)
+    return base
+
+
+def random_orientations(rng, n):
+    """Bunge Euler angles uniform on SO(3): phi1, phi2 uniform, cos(Phi) uniform."""
+    phi1 = 2.0 * math.pi * rng.random(n)
+    Phi = np.arccos(np.clip(2.0 * rng.random(n) - 1.0, -1.0, 1.0))
+    phi2 = 2.0 * math.pi * rng.random(n)
+    return np.stack([phi1, Phi, phi2], axis=1)
+
+
+def voronoi(n, n_grains, seed, h=VOXEL_MM):
+    """Periodic Voronoi polycrystal.
+
+    Centres uniform in the periodic box, voxel centres at (i + 1/2) h, grain
+    id = nearest centre under the minimum-image distance.  Returns grain ids
+    as int32 of length n0*n1*n2 (x fastest) and Euler angles (n_grains, 3)
+    drawn from the same seeded stream.
+    """
+    n = tuple(int(x) for x in n)
+    rng = np.random.default_rng(seed)
+    L = np.array(n, dtype=np.float64) * h
+    centres = rng.random((n_grains, 3)) * L
+    euler = random_orientations(rng, n_grains)
+    x = (np.arange(n[0]) + 0.5) * h
+    y = (np.arange(n[1]) + 0.5) * h
+    z = (np.arange(n[2]) + 0.5) * h
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    try:
+        from scipy.spatial import cKDTree
+        tree = cKDTree(centres, boxsize=L)
+        _, idx = tree.query(pts, k=1)
+    except ImportError:  # pragma: no cover - scipy is present on both hosts
+        idx = np.empty(len(pts), dtype=np.int64)
+        for s in range(0, len(pts), 65536):
+            d = pts[s:s + 65536, None, :] - centres[None, :, :]
+            d -= L * np.round(d / L)
+            idx[s:s + 65536] = np.argmin((d * d).sum(-1), axis=1)
+    return idx.astype(np.int32), euler
+
+
+def single_crystal(n, euler=(0.0, 0.0, 0.0)):
+    N = int(np.prod(n))
+    return np.zeros(N, dtype=np.int32), np.array([euler], dtype=np.float64)
+
+
+def precrack_plane(n, x_range, y, value=1.0):
+    """Pre-crack: phase field 1 and plasticity off on a one-voxel-thick plane
+    y = const spanning x in x_range and every z (the paper's soft pre-crack
+    region of Sec. 4.1 with stiffness g(1) = k)."""
+    n0, n1, n2 = n
+    phi = np.zeros((n2, n1, n0))
+    phi[:, y, x_range[0]:x_range[1] + 1] = value
+    mask = (phi > 0).astype(np.uint8)
+    return phi.reshape(-1), mask.reshape(-1)
+
+
+def uniaxial_cycle_program(amplitude, inc_per_cycle, cycles, axis=1, eps_rate=1e-3):
+    """Fully reversed (R = -1) triangle wave 0 -> +a -> 0 -> -a -> 0 per cycle,
+    equal strain steps, dt = |d eps| / eps_rate.  Returns a list of
+    (Fbar_target (9,), dt) with Fbar = I + eps e_axis (x) e_axis."""
+    assert inc_per_cycle % 4 == 0
+    q = inc_per_cycle // 4
+    de = amplitude / q
+    eps = [0.0]
+    for _ in range(cycles):
+        for k in range(1, q + 1):
+            eps.append(k * de)
+        for k in range(q - 1, -q - 1, -1):
+            eps.append(k * de)
+        for k in range(-q + 1, 1):
+            eps.append(k * de)
+    prog = []
+    for i in range(1, len(eps)):
+        F = np.eye(3)
+        F[axis, axis] += eps[i]
+        prog.append((F.reshape(9).copy(), abs(eps[i] - eps[i - 1]) / eps_rate))
+    return prog
+
+
+# The five workloads: grids, grain counts, loading (Sec. 4 shapes).
+CONFIGS = {
+    "sx16": dict(n=(16, 16, 16), grains=1, amplitude=0.005, inc_per_cycle=20, cycles=1,
+                 precrack=True, seed=1001),
+    "poly64": dict(n=(64, 64, 64), grains=50, amplitude=0.006, inc_per_cycle=40, cycles=3,
+                   precrack=False, seed=1002),
+    "poly128": dict(n=(128, 128, 128), grains=200, amplitude=0.007, inc_per_cycle=40,
+                    cycles=10, precrack=False, seed=1003),
+    "batch32": dict(sizes=(32, 48, 64, 96), count=32, grains=(20, 150), amplitude=0.006,
+                    inc_per_cycle=30, cycles=2, seed=2000),
+    "poly256": dict(n=(256, 256, 256), grains=1000, amplitude=0.007, inc_per_cycle=40,
+                    cycles=5, precrack=False, seed=1005),
+}
+
+
+def build_config(name, n_override=None):
+    """Grain ids, Euler angles, phi0, elastic mask and loading for one config.
+
+    ``sx16``'s pre-crack is the plane y = 8, x = 6..9, all z (a 4 x 16 plane
+    at mid-height, one voxel thick), scaled with the grid when ``n_override``
+    is given."""
+    c = CONFIGS[name]
+    n = tuple(n_override) if n_override else c["n"]
+    if c["grains"] == 1:
+        gid, eul = single_crystal(n)
+    else:
+        gid, eul = voronoi(n, c["grains"], c["seed"])
+    phi0 = mask = None
+    if c.get("precrack"):
+        s = n[0] / 16.0
+        x0, x1 = int(round(6 * s)), int(round(10 * s)) - 1
+        phi0, mask = precrack_plane(n, (x0, x1), n[1] // 2)
+    prog = uniaxial_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"])
+    return dict(n=n, h=VOXEL_MM, grain_ids=gid, euler=eul, phi0=phi0, elastic_only=mask,
+                program=prog)
+
+
+def batch_configs(seed=2000, count=32, sizes=(32, 48, 64, 96), grains=(20, 150)):
+    """The batched-RVE workload: ``count`` polycrystals with grids drawn from
+    ``sizes`` (cubes) and grain counts uniform in ``grains``, seed + r each."""
+    out = []
+    for r in range(count):
+        rng = np.random.default_rng(seed + r)
+        s = int(sizes[rng.integers(len(sizes))])
+        g = int(rng.integers(grains[0], grains[1] + 1))
+        gid, eul = voronoi((s, s, s), g, seed + 10000 + r)
+        out.append(dict(n=(s, s, s), h=VOXEL_MM, grain_ids=gid, euler=eul, phi0=None,
+                        elastic_only=None))
+    return out

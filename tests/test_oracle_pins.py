@@ -1,0 +1,558 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by the
+mathematics (closed forms, brute force, library routines, invariants).
+
+Each test names the passage it pins.  None of them compares the oracle with
+itself or retypes one of its formulas: they use an independent route to the
+same number, chosen so that a dropped term, a wrong sign, a transposed operand
+or a mis-scaled frequency fails at least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2304_01125_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+MAT = I.material("baseline")
+H = I.VOXEL_MM
+
+
+def cubic_voigt(m):
+    C = np.zeros((6, 6))
+    C[:3, :3] = m["C12"]
+    for i in range(3):
+        C[i, i] = m["C11"]
+        C[3 + i, 3 + i] = m["C44"]
+    return C
+
+
+def cubic_apply_np(m, E):
+    """S = C : E for the cubic lattice tensor, through the 6x6 Voigt matrix
+    with engineering shear strains (independent of the oracle's routine)."""
+    e = np.array([E[0, 0], E[1, 1], E[2, 2], 2 * E[1, 2], 2 * E[0, 2], 2 * E[0, 1]])
+    s = cubic_voigt(m) @ e
+    return np.array([[s[0], s[5], s[4]], [s[5], s[1], s[3]], [s[4], s[3], s[2]]])
+
+
+# --------------------------------------------------------------------- P6
+@pytest.mark.parametrize("shape", [(4, 4, 4), (3, 3, 3), (6, 6, 6), (1, 1, 48), (1, 96, 1),
+                                   (5, 3, 2)])
+def test_fft_matches_numpy_and_naive_dft(shape):
+    """Sec. 3.1: the DFT of a voxel field computed by an FFT.  The oracle's
+    own FFT equals numpy's FFT and its own naive DFT; inverse is 1/N."""
+    rng = np.random.default_rng(sum(shape))
+    a = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    f = O.fft3d(a, -1)
+    ref = np.fft.fftn(a)
+    tol = 1e-12 * np.abs(ref).max()
+    assert np.abs(f - ref).max() < tol
+    if np.prod(shape) <= 512:
+        assert np.abs(O.fft3d(a, -1, naive=True) - ref).max() < tol
+    assert np.abs(O.fft3d(f, +1) - a).max() < 1e-13 * np.abs(a).max() * 10
+
+
+def test_fft_parseval():
+    rng = np.random.default_rng(0)
+    a = rng.standard_normal((6, 4, 8))
+    f = O.fft3d(a.astype(complex), -1)
+    assert abs((np.abs(f) ** 2).sum() / a.size - (a ** 2).sum()) < 1e-10 * (a ** 2).sum()
+
+
+# --------------------------------------------------------------- tables
+def test_material_preset_is_table1():
+    """Table 1 and Sec. 4 values, from the committed fixture."""
+    t = json.load(open(os.path.join(GOLD, "table1_cmsx4.json")))
+    m = I.material("paper")
+    assert m["C11"] == t["C11_GPa"] * 1e3 and m["C12"] == t["C12_GPa"] * 1e3
+    assert m["C44"] == t["C44_GPa"] * 1e3 and m["tau_c0"] == t["tau_c0_MPa"]
+    assert m["b"] == t["b_mm"] and m["nu_D"] == t["nu_D_per_s"]
+    assert m["k_B"] == t["k_J_per_K"] and m["dF"] == t["dF_J"]
+    assert m["rho_m"] == t["rho_m_per_mm2"] and m["lambda_h"] == t["lambda_per_mm2"]
+    assert m["T"] == t["T_K"] and m["k_res"] == t["k_residual"]
+    assert abs(m["G_crit"] - t["G_crit_J_per_m2"] * 1e-3) < 1e-15  # J/m^2 -> N/mm
+    assert abs(m["ell"] - t["ell_um"] * 1e-3) < 1e-15
+    assert abs(m["ell_Fp"] - t["ell_Fp_um"] * 1e-3) < 1e-15
+    assert abs(I.VOXEL_MM - t["voxel_um"] * 1e-3) < 1e-15
+
+
+def test_fcc_slip_systems():
+    """Sec. 2.1: N_s = 12 FCC {111}<110> systems (textbook set, unordered).
+    A system is identified by its Schmid dyad s (x) n up to sign."""
+    def canon(sv, nv):
+        P = np.outer(sv / np.linalg.norm(sv), nv / np.linalg.norm(nv)).reshape(9)
+        k = np.nonzero(np.abs(P) > 1e-9)[0][0]
+        return tuple(np.round(P * np.sign(P[k]), 9))
+
+    s, n = O.fcc_systems()
+    ref = np.loadtxt(os.path.join(GOLD, "fcc_111_110.txt"))
+    want = {canon(row[3:], row[:3]) for row in ref}
+    got = set()
+    for a in range(12):
+        assert abs(np.linalg.norm(s[a]) - 1) < 1e-15 and abs(np.linalg.norm(n[a]) - 1) < 1e-15
+        assert abs(s[a] @ n[a]) < 1e-15
+        got.add(canon(s[a], n[a]))
+    assert got == want and len(got) == 12
+
+
+def test_euler_rotation_is_bunge():
+    """Bunge z-x-z: (phi1, 0, 0) is a rotation about z; Q is proper orthogonal;
+    Q(phi1, Phi, phi2) composes three elementary rotations."""
+    def rz(a):
+        c, s = np.cos(a), np.sin(a)
+        return np.array([[c, -s, 0], [s, c, 0], [0, 0, 1.0]])
+
+    def rx(a):
+        c, s = np.cos(a), np.sin(a)
+        return np.array([[1.0, 0, 0], [0, c, -s], [0, s, c]])
+
+    e = np.array([0.4, 1.1, -0.7])
+    Q = O.euler_to_Q(e)
+    # active rotation lattice -> sample: Rz(phi1) Rx(Phi) Rz(phi2)
+    assert np.abs(Q - rz(e[0]) @ rx(e[1]) @ rz(e[2])).max() < 1e-15
+    assert abs(np.linalg.det(Q) - 1) < 1e-14
+
+
+# ------------------------------------------------------------------ P2
+def test_elastic_uniaxial_closed_form():
+    """Sec. 2.1 with the elastic reading S = C:E: a [100] crystal under
+    F = I + eps e2 (x) e2 below yield gives E22 = ((1+eps)^2-1)/2,
+    S22 = C11 E22, S11 = S33 = C12 E22, P22 = (1+eps) S22, and the tensile
+    energy of Eq. decMiehe is 1/2 C11 ln(1+eps)^2 (0 in compression)."""
+    for eps in (0.004, -0.004):
+        F = np.eye(3)
+        F[1, 1] += eps
+        r = O.cp_point(MAT, np.eye(3), F, np.eye(3), MAT["rho_ssd0"], 0.0, 1.0)
+        E = ((1 + eps) ** 2 - 1) / 2
+        assert r["fail"] == 0 and np.all(r["dgamma"] == 0)
+        assert abs(r["P"][1, 1] - (1 + eps) * MAT["C11"] * E) < 1e-9
+        assert abs(r["P"][0, 0] - MAT["C12"] * E) < 1e-9
+        assert abs(r["P"][2, 2] - MAT["C12"] * E) < 1e-9
+        assert np.abs(r["P"] - np.diag(np.diag(r["P"]))).max() < 1e-12
+        we = 0.5 * MAT["C11"] * np.log(1 + eps) ** 2 if eps > 0 else 0.0
+        assert abs(r["We_plus"] - we) < 1e-12
+
+
+def test_elastic_rotated_crystal_frame_covariance():
+    """Sec. 2.1: rotating the crystal and the loading together leaves the
+    response unchanged (P rotates with Q)."""
+    rng = np.random.default_rng(5)
+    Q = O.euler_to_Q(rng.random(3) * 3)
+    F0 = np.eye(3) + 1e-3 * rng.standard_normal((3, 3))
+    r0 = O.cp_point(MAT, np.eye(3), F0, np.eye(3), MAT["rho_ssd0"], 0.0, 1.0)
+    r1 = O.cp_point(MAT, Q, Q @ F0 @ Q.T, np.eye(3), MAT["rho_ssd0"], 0.0, 1.0)
+    assert np.abs(Q @ r0["P"] @ Q.T - r1["P"]).max() < 1e-9
+
+
+# ------------------------------------------------------------------ P3
+def _single_slip_case(dt):
+    """A lattice-frame simple shear along system 0 with tau_c between the
+    largest and the second largest trial resolved shear, so only system 0
+    slips."""
+    s, n = O.fcc_systems()
+    Fgrad = 4e-3 * np.outer(s[0], n[0])
+    F = np.eye(3) + Fgrad
+    E = 0.5 * (F.T @ F - np.eye(3))
+    S = cubic_apply_np(MAT, E)
+    tau = np.array([s[a] @ S @ n[a] for a in range(12)])
+    order = np.argsort(-np.abs(tau))
+    assert order[0] == 0
+    tc = 0.5 * (abs(tau[0]) + abs(tau[order[1]]))
+    m = dict(MAT, tau_c0=tc, mu=0.0)  # tau_c = tc exactly
+    return m, F, s, n, tc
+
+
+@pytest.mark.parametrize("dt", [0.05, 1.0, 30.0])
+def test_single_slip_by_bisection(dt):
+    """Eq. flowrule with one active system reduces to one scalar equation
+    dg = dt g0 sinh((tau(dg) - tau_c)/sT), tau(dg) = s.S(dg).n, S = C:E_e,
+    E_e = (Fe^T Fe - I)/2, Fe = F (I - dg s(x)n).  Solved here by bisection."""
+    m, F, s, n, tc = _single_slip_case(dt)
+    kT = m["k_B"] * m["T"]
+    g0 = m["rho_m"] * m["b"] ** 2 * m["nu_D"] * np.exp(-m["dF"] / kT)
+    sT = kT / (m["dV"] * 1e-3)
+    P0 = np.outer(s[0], n[0])
+
+    def tau_of(dg):
+        Fe = F @ (np.eye(3) - dg * P0)
+        S = cubic_apply_np(m, 0.5 * (Fe.T @ Fe - np.eye(3)))
+        return s[0] @ S @ n[0]
+
+    def f(dg):
+        return dg - dt * g0 * np.sinh((tau_of(dg) - tc) / sT)
+
+    lo, hi = 0.0, 0.01
+    assert f(lo) < 0 < f(hi)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if f(mid) < 0:
+            lo = mid
+        else:
+            hi = mid
+    dg_ref = 0.5 * (lo + hi)
+    r = O.cp_point(m, np.eye(3), F, np.eye(3), 0.0, 0.0, dt, tol_local=1e-10)
+    assert r["fail"] == 0
+    assert abs(r["dgamma"][0] - dg_ref) < 1e-12 + 1e-9 * dg_ref
+    assert np.all(r["dgamma"][1:] == 0)
+    assert np.all(np.abs(r["tau"][1:]) <= tc)
+    # plastic work increment and SSD increment of Sec. 2.1/2.3
+    assert abs(r["dWp"] - tau_of(dg_ref) * dg_ref) < 1e-9 * abs(r["dWp"]) + 1e-14
+    Lp = dg_ref * P0
+    assert abs(r["drho_ssd"] - m["lambda_h"] * np.sqrt(2 / 3 * np.sum(Lp * Lp))) < \
+        1e-8 * r["drho_ssd"]
+
+
+def test_slip_rate_limits():
+    """Rate dependence of Eq. flowrule: slip grows with the step and vanishes
+    with it (monotone in dt); a long
+    step relaxes the resolved shear to tau_c + sT*asinh(dg/(dt g0))."""
+    m, F, s, n, tc = _single_slip_case(1.0)
+    dgs = [O.cp_point(m, np.eye(3), F, np.eye(3), 0.0, 0.0, dt)["dgamma"][0]
+           for dt in (1e-30, 1e-12, 1e-3, 1.0)]
+    assert dgs[0] < 1e-15 and all(a < b for a, b in zip(dgs, dgs[1:]))
+    r = O.cp_point(m, np.eye(3), F, np.eye(3), 0.0, 0.0, 1e4)
+    kT = m["k_B"] * m["T"]
+    g0 = m["rho_m"] * m["b"] ** 2 * m["nu_D"] * np.exp(-m["dF"] / kT)
+    sT = kT / (m["dV"] * 1e-3)
+    over = r["tau"][0] - tc
+    assert 0 < over < 1e-3 and abs(over - sT * np.arcsinh(r["dgamma"][0] / (1e4 * g0))) < 1e-9
+
+
+def test_elastic_only_voxel_does_not_slip():
+    """Pre-crack voxels (Sec. 4.1 soft elastic region) never slip."""
+    m, F, s, n, tc = _single_slip_case(1.0)
+    r = O.cp_point(m, np.eye(3), F, np.eye(3), 0.0, 0.0, 1.0, elastic_only=True)
+    assert np.all(r["dgamma"] == 0)
+
+
+# ----------------------------------------------------------------- P11
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_tangent_matches_finite_differences(seed):
+    """Eq. newton needs K = dP/dF (consistent tangent): compare with central
+    differences of P in plastic states (several active systems)."""
+    rng = np.random.default_rng(seed)
+    Q = O.euler_to_Q(rng.random(3) * 3)
+    F = np.eye(3) + 0.004 * rng.standard_normal((3, 3))
+    FpL = np.eye(3) + 0.001 * rng.standard_normal((3, 3))
+    args = (MAT, Q)
+    r = O.cp_point(*args, F, FpL, MAT["rho_ssd0"], 1e5, 1.0, tol_local=1e-10)
+    assert r["fail"] == 0
+    d = 1e-7
+    Kfd = np.zeros((9, 9))
+    for c in range(9):
+        Fp = F.reshape(9).copy()
+        Fm = F.reshape(9).copy()
+        Fp[c] += d
+        Fm[c] -= d
+        Pp = O.cp_point(*args, Fp, FpL, MAT["rho_ssd0"], 1e5, 1.0, tol_local=1e-10,
+                        tangent=False)
+        Pm = O.cp_point(*args, Fm, FpL, MAT["rho_ssd0"], 1e5, 1.0, tol_local=1e-10,
+                        tangent=False)
+        Kfd[:, c] = (Pp["P"] - Pm["P"]).reshape(9) / (2 * d)
+    assert np.abs(r["K"] - Kfd).max() < 1e-6 * np.abs(Kfd).max()
+
+
+def test_local_solve_robust_on_extreme_states():
+    """The local update converges from large trial overstress (many systems
+    active), and its solution satisfies the slip law on every system."""
+    rng = np.random.default_rng(3)
+    kT = MAT["k_B"] * MAT["T"]
+    g0 = MAT["rho_m"] * MAT["b"] ** 2 * MAT["nu_D"] * np.exp(-MAT["dF"] / kT)
+    sT = kT / (MAT["dV"] * 1e-3)
+    for _ in range(60):
+        Q = O.euler_to_Q(I.random_orientations(rng, 1)[0])
+        F = np.eye(3) + 0.01 * rng.standard_normal((3, 3))
+        FpL = np.eye(3) + 0.003 * rng.standard_normal((3, 3))
+        dt = float(rng.choice([0.1, 1.0, 20.0]))
+        r = O.cp_point(MAT, Q, F, FpL, MAT["rho_ssd0"], 1e5, dt, tol_local=1e-9,
+                       tangent=False)
+        assert r["fail"] == 0
+        for a in range(12):
+            over = abs(r["tau"][a]) - r["tau_c"]
+            if r["dgamma"][a] == 0:
+                assert over <= 1e-7
+            else:
+                # slip law (Eq. flowrule) holds to the local tolerance in stress
+                assert np.sign(r["dgamma"][a]) == np.sign(r["tau"][a])
+                inv = sT * np.arcsinh(abs(r["dgamma"][a]) / (dt * g0))
+                assert abs(over - inv) < 1e-8
+
+
+# ----------------------------------------------------------------- P13
+def test_eigen_split_degenerate_and_rotated():
+    """Eq. decMiehe: eps+ from the eigen-decomposition of 1/2 ln(Fe Fe^T),
+    including repeated eigenvalues; the Jacobi routine reproduces a known
+    spectrum in a rotated basis."""
+    a, b = 3e-3, -2e-3
+    Fe = np.diag([1 + a, 1 + a, 1 + b])
+    ep = np.diag([np.log(1 + a), np.log(1 + a), 0.0])
+    we = 0.5 * np.sum(ep * cubic_apply_np(MAT, ep))
+    assert abs(O.we_plus(MAT, Fe) - we) < 1e-12 * we
+    rng = np.random.default_rng(2)
+    R = O.euler_to_Q(rng.random(3) * 3)
+    D = np.array([0.3, 0.3, -1.2])
+    w, V = O.sym_eig3(R @ np.diag(D) @ R.T)
+    assert np.abs(np.sort(w) - np.sort(D)).max() < 1e-14
+    assert np.abs(V @ np.diag(w) @ V.T - R @ np.diag(D) @ R.T).max() < 1e-14
+    assert O.we_plus(MAT, np.diag([1 - a, 1 + b, 1 - a])) == 0.0
+
+
+# ------------------------------------------------------------------ P5
+def test_green_operator_identities():
+    """Eq. precf with Eq. avstiff: M(xi)(xi.K.xi) = I, and the projection
+    Gamma_ijkl = xi_j M_ik xi_l is idempotent under K: Gamma:K:Gamma = Gamma;
+    M = 0 at xi = 0."""
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((9, 9))
+    K = A @ A.T + 9 * np.eye(9)
+    K4 = K.reshape(3, 3, 3, 3)
+    for _ in range(5):
+        xi = rng.standard_normal(3)
+        M = O.green_precond(K, xi)
+        A3 = np.einsum("j,ijkl,l->ik", xi, K4, xi)
+        assert np.abs(M @ A3 - np.eye(3)).max() < 1e-12
+        G = np.einsum("j,ik,l->ijkl", xi, M, xi)
+        GKG = np.einsum("ijab,abcd,cdkl->ijkl", G, K4, G)
+        assert np.abs(GKG - G).max() < 1e-12 * np.abs(G).max()
+    assert np.all(O.green_precond(K, np.zeros(3)) == 0)
+
+
+# ------------------------------------------------------------------ P4
+def _green_1mlap(n, h, ell):
+    """Discrete Green's function of (1 - ell^2 lap) with the spectral
+    Laplacian (-|xi|^2), via numpy's FFT."""
+    k = [2 * np.pi * np.fft.fftfreq(nn, d=h) for nn in n]
+    KX = k[0][None, None, :]
+    KY = k[1][None, :, None]
+    KZ = k[2][:, None, None]
+    ghat = 1.0 / (1.0 + ell ** 2 * (KX ** 2 + KY ** 2 + KZ ** 2))
+    return np.real(np.fft.ifftn(ghat))
+
+
+def test_phase_field_uniform_source():
+    """Eq. phase with uniform S: the Laplacian vanishes, (1+2S) phi = 2S,
+    phi = 2S/(1+2S)."""
+    n = (4, 4, 4)
+    S = np.full(64, 0.37)
+    phi, it, st = O.phase_field(n, H, 2 * H, S, np.zeros(64), np.zeros(64), tol=1e-14)
+    assert st == 0
+    assert np.abs(phi - 2 * 0.37 / (1 + 2 * 0.37)).max() < 1e-13
+
+
+def test_phase_field_point_source_exact():
+    """Eq. phase with S = s0 at one voxel: phi = 2 s0 (1 - phi0) G(x - x0),
+    phi0 = 2 s0 G(0) / (1 + 2 s0 G(0)), G the discrete Green's function of
+    (1 - ell^2 lap) (Eq. precph operator), computed with numpy."""
+    n = (8, 6, 5)
+    N = int(np.prod(n))
+    ell = 2 * H
+    S = np.zeros(N)
+    v0 = 3 + 8 * (2 + 6 * 1)
+    S[v0] = 0.8
+    phi, it, st = O.phase_field(n, H, ell, S, np.zeros(N), np.zeros(N), tol=1e-14)
+    G = _green_1mlap(n, H, ell).reshape(-1)
+    G0 = G[0]
+    phi0 = 2 * 0.8 * G0 / (1 + 2 * 0.8 * G0)
+    Gs = np.roll(G.reshape(n[::-1]), (1, 2, 3), axis=(0, 1, 2)).reshape(-1)
+    want = 2 * 0.8 * (1 - phi0) * Gs
+    assert st == 0 and np.abs(phi - want).max() < 1e-12
+
+
+def test_phase_field_1d_profile_exp():
+    """Eq. strpf 1-D: the Green's function of (1 - ell^2 d2/dx2) on a period L
+    is cosh((L/2 - |x|)/ell) / (2 ell sinh(L/(2 ell))); the spectral solution
+    approaches it as ell/h grows (the exp(-|x|/ell) profile)."""
+    N = 128
+    errs = []
+    for ratio in (2, 4, 8):
+        ell = ratio * H
+        S = np.zeros(N)
+        S[0] = 1e-6  # linear regime: phi = 2 s0 G
+        phi, it, st = O.phase_field((N, 1, 1), H, ell, S, np.zeros(N), np.zeros(N),
+                                    tol=1e-15)
+        x = np.minimum(np.arange(N), N - np.arange(N)) * H
+        L = N * H
+        cont = np.cosh((L / 2 - x) / ell) / (2 * ell * np.sinh(L / (2 * ell)))
+        prof = phi / (2e-6 * (1 - phi[0])) / H  # per unit length
+        errs.append(np.abs(prof - cont).max() / cont.max())
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 0.05
+
+
+def test_phase_field_irreversibility_clamp():
+    """Algorithm 1 clamp: phi_i = max(phi_i, phi_t) pointwise."""
+    n = (4, 4, 4)
+    rng = np.random.default_rng(1)
+    S = rng.random(64) * 0.1
+    phit = np.where(rng.random(64) > 0.7, 0.9, 0.0)
+    phi, it, st = O.phase_field(n, H, 2 * H, S, phit, phit, tol=1e-13)
+    assert np.all(phi >= phit) and np.all(phi < 1)
+    free, _, _ = O.phase_field(n, H, 2 * H, S, phit, np.zeros(64), tol=1e-13)
+    assert np.abs(np.maximum(free, phit) - phi).max() < 1e-12
+
+
+def test_phase_field_zero_drive_keeps_phi_t():
+    n = (4, 4, 4)
+    phit = np.linspace(0, 1, 64)
+    phi, it, st = O.phase_field(n, H, 2 * H, np.zeros(64), phit, phit)
+    assert it == 0 and np.all(phi == phit)
+
+
+# ------------------------------------------------------------ P7 / P8
+def _qfield(N, Q=np.eye(3)):
+    return np.tile(Q.reshape(9), N)
+
+
+def _spectral_grad(n, h, v):
+    """grad of a periodic scalar field with the derivative multiplier i xi,
+    zero on the Nyquist frequency (numpy FFT)."""
+    out = []
+    shape = n[::-1]
+    vh = np.fft.fftn(v.reshape(shape))
+    for d in range(3):
+        k = 2 * np.pi * np.fft.fftfreq(n[d], d=h)
+        if n[d] % 2 == 0:
+            k[n[d] // 2] = 0.0
+        ax = 2 - d
+        shp = [1, 1, 1]
+        shp[ax] = n[d]
+        out.append(np.real(np.fft.ifftn(vh * 1j * k.reshape(shp))).reshape(-1))
+    return out
+
+
+def test_nye_of_compatible_field_vanishes():
+    """Eq. nye1 / nyeindexfourier: the curl of a gradient is zero, so a
+    compatible plastic distortion F_p = I + grad(v) carries no GNDs."""
+    n = (8, 6, 4)
+    N = int(np.prod(n))
+    rng = np.random.default_rng(7)
+    Fp = np.zeros((9, N))
+    for i in range(3):
+        v = rng.standard_normal(N) * 1e-6
+        g = _spectral_grad(n, H, v)
+        for j in range(3):
+            Fp[3 * i + j] = g[j] + (1.0 if i == j else 0.0)
+    Lam, rho = O.gnd_field(n, H, MAT, _qfield(N), Fp)
+    assert np.abs(Lam).max() < 1e-12 and rho.max() < 1e-12 / MAT["b"]
+
+
+def test_nye_single_slip_sinusoid():
+    """Eq. nye1 with the regularisation of Sec. 3.1: F_p = I + g(x) s(x)n,
+    g = g0 sin(k.x) gives Lambda_ij = s_i (grad g x n)_j / (1 + ell_Fp^2 k^2),
+    and the min-norm densities reproduce it with ||rho|| <= |grad g|/b."""
+    n = (16, 8, 8)
+    N = int(np.prod(n))
+    s, nn = O.fcc_systems()
+    kvec = 2 * np.pi * np.array([2 / (n[0] * H), 1 / (n[1] * H), 0.0])
+    x = (np.arange(n[0])) * H
+    y = (np.arange(n[1])) * H
+    z = (np.arange(n[2])) * H
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    phase = (kvec[0] * X + kvec[1] * Y).reshape(-1)
+    g0 = 1e-4
+    g = g0 * np.sin(phase)
+    Fp = np.zeros((9, N))
+    P0 = np.outer(s[0], nn[0]).reshape(9)
+    for c in range(9):
+        Fp[c] = P0[c] * g + (1.0 if c in (0, 4, 8) else 0.0)
+    Lam, rho = O.gnd_field(n, H, MAT, _qfield(N), Fp)
+    reg = 1.0 / (1.0 + MAT["ell_Fp"] ** 2 * (kvec @ kvec))
+    dg = g0 * np.cos(phase)[None, :] * kvec[:, None]  # grad g, 3 x N
+    cr = np.cross(dg.T, nn[0]).T  # (grad g x n)
+    want = np.einsum("i,jv->ijv", s[0], cr).reshape(9, N) * reg
+    assert np.abs(Lam - want).max() < 1e-9 * np.abs(want).max()
+    A, Ap = O.gnd_basis()
+    assert np.abs(A @ Ap @ A - A).max() < 1e-13
+    assert np.linalg.matrix_rank(A) == 9
+    rvec = Ap @ Lam / MAT["b"]
+    assert np.abs(A @ rvec - Lam / MAT["b"]).max() < 1e-9 * np.abs(Lam / MAT["b"]).max()
+    gradn = np.linalg.norm(dg, axis=0) * reg / MAT["b"]
+    assert np.all(rho <= gradn * (1 + 1e-9) + 1e-6)
+
+
+def test_nye_constant_fp_and_regulariser():
+    """A constant F_p passes the regulariser unchanged and has no curl."""
+    n = (4, 4, 4)
+    N = 64
+    Fp = np.tile((np.eye(3) + 1e-3 * np.arange(9).reshape(3, 3)).reshape(9, 1), (1, N))
+    Lam, rho = O.gnd_field(n, H, MAT, _qfield(N), Fp)
+    assert np.abs(Lam).max() < 1e-14
+
+
+# ------------------------------------------------------ P1 / P9 / P12
+def _run(n, gid, eul, opts, prog, phi0=None, mask=None, naive=False, mat=MAT):
+    r = O.RVE(n, H, gid, eul, mat, opts, phi0=phi0, elastic_only=mask, naive=naive)
+    stats = []
+    for Fb, dt in prog:
+        s, st = r.run_increment(Fb, dt)
+        assert s == 0, st
+        stats.append(st)
+    return r, stats
+
+
+def test_homogeneous_medium_uniform_strain():
+    """Eqs. momentum and fdef: a single crystal with no defect stays uniform,
+    F = Fbar exactly, with zero Krylov iterations (the residual vanishes)."""
+    n = (4, 4, 4)
+    gid, eul = I.single_crystal(n, (0.3, 0.9, 1.7))
+    prog = I.uniaxial_cycle_program(0.004, 8, 1)[:3]
+    r, stats = _run(n, gid, eul, I.solver_options("parity64"), prog)
+    F = r.field("F")
+    assert np.abs(F - prog[-1][0][:, None]).max() < 1e-15
+    assert all(s["lin_it_total"] == 0 for s in stats)
+
+
+def test_mean_strain_and_damage_bounds_polycrystal():
+    """Eq. fdef: the fluctuation has zero mean, <F> = Fbar; Algorithm 1:
+    phi_t <= phi <= 1 through the history, with damage switched on early by a
+    small G_crit."""
+    n = (6, 6, 6)
+    gid, eul = I.voronoi(n, 3, 11)
+    mat = dict(MAT, tau_c0=250.0, G_crit=1e-9, xi_store=1.0)
+    prog = I.uniaxial_cycle_program(0.006, 24, 1)[:5]
+    r = O.RVE(n, H, gid, eul, mat, I.solver_options("paper"))
+    prev = np.zeros(int(np.prod(n)))
+    for Fb, dt in prog:
+        s, st = r.run_increment(Fb, dt)
+        assert s == 0
+        F = r.field("F")
+        assert np.abs(F.mean(axis=1) - Fb).max() < 1e-14
+        phi = r.field("phi_t")
+        assert np.all(phi >= prev) and np.all(phi <= 1.0)
+        prev = phi
+    assert prev.max() > 0  # damage actually evolved
+
+
+def test_naive_dft_vs_fft_full_solve():
+    """A 4^3 polycrystal solved with the naive DFT and with the FFT agrees to
+    round-off through plastic increments (transform independence)."""
+    n = (4, 4, 4)
+    gid, eul = I.voronoi(n, 3, 5)
+    prog = I.uniaxial_cycle_program(0.008, 16, 1)[:5]
+    opts = I.solver_options("parity64")
+    a, _ = _run(n, gid, eul, opts, prog, naive=False)
+    b, _ = _run(n, gid, eul, opts, prog, naive=True)
+    for f in ("F", "Fp", "rho_ssd", "Wp"):
+        x, y = a.field(f), b.field(f)
+        assert np.abs(x - y).max() <= 1e-12 * max(np.abs(x).max(), 1e-30), f
+    assert a.field("gamma").max() > 0  # plasticity happened
+
+
+@pytest.mark.slow
+def test_precrack_mirror_symmetry():
+    """Sec. 4.1 geometry: a [100] single crystal with a centred pre-crack is
+    mirror-symmetric about the plane x = 7.5 h (16^3 grid with the crack on
+    x = 6..9): F_xx, F_yy, F_zz, F_yz are even and F_xy, F_xz odd."""
+    cfg = I.build_config("sx16", n_override=(16, 8, 4))
+    prog = cfg["program"][:3]
+    r, _ = _run(cfg["n"], cfg["grain_ids"], cfg["euler"], I.solver_options("parity64"), prog,
+                phi0=cfg["phi0"], mask=cfg["elastic_only"])
+    n = cfg["n"]
+    F = r.field("F").reshape(3, 3, n[2], n[1], n[0])
+    Fm = F[..., ::-1]
+    sign = np.array([[1, -1, -1], [-1, 1, 1], [-1, 1, 1]])
+    for i in range(3):
+        for j in range(3):
+            assert np.abs(F[i, j] - sign[i, j] * Fm[i, j]).max() < 1e-12
+    assert np.abs(F[0, 1]).max() > 1e-6  # the crack does perturb the field
