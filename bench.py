@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark: voxel-increments/s of the staggered RVE load increment
+(crystal plasticity + FFT Newton-Krylov equilibrium + FFT phase field) on
+the 64^3 / 50-grain periodic Voronoi polycrystal (R = -1 uniaxial-strain
+cycle at 0.6 %, 40 increments per cycle), mixed FP32/FP64 path vs the plain
+FP64 path.
+
+A step is one load increment (GND, constitutive updates, residuals, GMRES,
+F update, phase field, clamp, commit).  N GPUs run N independent replicas
+(weak scaling, no data-path collective).  Prints one JSON line on rank 0.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (each
+step one increment of the same workload).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2304_01125_gb300 import inputs as I  # noqa: E402
+
+METRIC = "voxel-increments/s (CP+FFT equilibrium+phase-field), mixed vs FP64 on GPU at <=1e-4"
+CONFIG_NAME = "poly64"
+L2_NOTE = "working set > L2 (about 0.4 GB mixed per RVE) and a 256 MB L2 flush before every step"
+
+
+def args_():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=6)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", default=CONFIG_NAME)
+    p.add_argument("--tol", default="paper", choices=["paper", "parity32", "parity64"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--verbose", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# algorithmic bytes per voxel for each kernel family (esz = bulk element size)
+def algo_bytes_per_voxel(family, esz):
+    half = 0.5 * 2 * esz  # one half-spectrum complex component per voxel ~ esz bytes
+    table = {
+        # read grad z (9), K (81), phi (1); write tau (9)
+        "tangent_apply": (9 + 81 + 1 + 9) * esz,
+        # read H, Hpi (18 bulk), committed history (32 FP64); write P (9), K (81) and
+        # (history pass) trial history (32 FP64), Hpi_tr (9), drive, We
+        "constitutive": (18 + 9 + 81 + 1) * esz + 8 * 2,
+        # read v (3 complex), write G (9 complex) [+ optional v copy]
+        "precond_grad": (3 + 9) * half,
+        "contract": (9 + 3) * half,
+    }
+    return table.get(family)
+
+
+def run_ours(a):
+    import torch
+
+    from paper_2304_01125_gb300 import fatiguefft as FF
+
+    ws, rank, local = dist()
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2304_01125_gb300 import build as B
+    B.build()
+    cfg = I.build_config(a.config)
+    n, N = cfg["n"], int(np.prod(cfg["n"]))
+    prog = cfg["program"]
+    assert a.warmup + a.steps <= len(prog)
+    mat = I.material("baseline")
+    opts = I.solver_options(a.tol)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            import torch.distributed as tdist
+            tdist.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        import torch.distributed as tdist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    fields = {}
+    for prec in ("fp64", "mixed"):
+        r = FF.RVE(n, I.VOXEL_MM, cfg["grain_ids"], cfg["euler"], mat, opts, prec=prec,
+                   stream=stream)
+        for k in range(a.warmup - 1):
+            r.run_increment(*prog[k])
+        # last warm-up step profiled per kernel family: the dominant kernel of ours
+        r.profile(FF.KERNEL_FAMILIES)
+        r.run_increment(*prog[a.warmup - 1])
+        breakdown = r.profile_read(reset=True)
+        ours = {k: v for k, v in breakdown.items() if not k.startswith("cufft")}
+        dom = max(ours, key=lambda k: ours[k][0])
+        r.profile([dom])
+        barrier()
+        clk = Clocks(local)
+        clk.start()
+        l0 = r.kernel_launches
+        times, stats = [], []
+        t_wall = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(a.warmup, a.warmup + a.steps):
+                flush.fill_(float(k))
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s, st = r.run_increment(*prog[k])
+                e1.record(stream)
+                stats.append(st)
+                times.append((e0, e1))
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+        clocks = clk.stop()
+        launches = r.kernel_launches - l0
+        ms = [e0.elapsed_time(e1) for e0, e1 in times]
+        dom_prof = r.profile_read(reset=True).get(dom, (0.0, 0))
+        r.profile([])
+        tot = max_over_ranks(sum(ms))
+        results[prec] = dict(ms=ms, total_ms=tot, wall_s=t_wall, launches=launches,
+                             stats=stats, breakdown=breakdown, dominant=dom,
+                             dom_ms=dom_prof[0], dom_count=dom_prof[1], clocks=clocks,
+                             device_bytes=r.device_bytes)
+        fields[prec] = {f: r.field(f) for f in ("P", "phi", "F")}
+        r.close()
+
+    # mixed vs FP64 after the same increments (stress, damage, strain fluctuation)
+    def relerr(f, sub=None):
+        x, y = fields["mixed"][f], fields["fp64"][f]
+        if sub is not None:
+            x, y = x - sub, y - sub
+        ny = float(np.linalg.norm(y))
+        return float(np.linalg.norm(x - y) / ny) if ny > 0 else float(np.abs(x).max())
+
+    eye = np.eye(3).reshape(9, 1)
+    errs = {"stress_P": relerr("P"), "damage_phi": relerr("phi"),
+            "strain_F_minus_I": relerr("F", eye)}
+
+    # end to end through the public API with host buffers: per step the
+    # increment's inputs (Fbar, dt) from pinned host memory and the damage
+    # field read back to pinned host memory
+    r = FF.RVE(n, I.VOXEL_MM, cfg["grain_ids"], cfg["euler"], mat, opts, prec="mixed",
+               stream=stream)
+    for k in range(a.warmup):
+        r.run_increment(*prog[k])
+    host_in = torch.empty((a.steps, 10), dtype=torch.float64).pin_memory()
+    for i, k in enumerate(range(a.warmup, a.warmup + a.steps)):
+        host_in[i, :9] = torch.from_numpy(prog[k][0])
+        host_in[i, 9] = prog[k][1]
+    host_out = torch.empty(N, dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(a.steps):
+        row = host_in[i].numpy()
+        r.run_increment(row[:9], float(row[9]))
+        FF.load().fields_out(r._h, FF.FIELDS["phi"][0], host_out.data_ptr(), host_out.nbytes, 0)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    r.close()
+
+    if rank != 0:
+        return None
+    mx = results["mixed"]
+    f64 = results["fp64"]
+    value = ws * N * a.steps / (mx["total_ms"] / 1e3)
+    value64 = ws * N * a.steps / (f64["total_ms"] / 1e3)
+    hbm, peak_kind = peaks()
+    dom = mx["dominant"]
+    bpv = algo_bytes_per_voxel(dom, 4)
+    roof = None
+    if bpv and mx["dom_count"]:
+        avg_s = mx["dom_ms"] / mx["dom_count"] / 1e3
+        achieved = bpv * N / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": None, "kernel": dom,
+                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": int(bpv * N),
+                "avg_launch_us": round(avg_s * 1e6, 2), "launches": mx["dom_count"]}
+    line = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "voxel-increments/s",
+        "n_gpus": ws,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": round(mx["total_ms"] / a.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic (seeded periodic Voronoi, uniform SO(3) orientations)",
+        "config": {"workload": f"{a.config}: 64^3 voxels, 50 grains, R=-1 uniaxial strain "
+                               f"0.6%, 40 increments/cycle, increments {a.warmup + 1}-"
+                               f"{a.warmup + a.steps}",
+                   "tolerances": a.tol, "l2": L2_NOTE, "parallelism": f"replicas x{ws}"},
+        "fp64": {"value": round(value64, 1), "ms_per_step": round(f64["total_ms"] / a.steps, 3),
+                 "dominant_kernel": f64["dominant"]},
+        "mixed_speedup_vs_fp64": round(value / value64, 3),
+        "mixed_vs_fp64_rel_l2": errs,
+        "e2e": {"value": round(ws * N * a.steps / e2e_s, 1), "unit": "voxel-increments/s",
+                "h2d_bytes_per_step": 80, "d2h_bytes_per_step": 8 * N},
+        "gpu_launches": int(mx["launches"]),
+        "roofline": roof,
+        "clocks": mx["clocks"],
+        "iterations": {p: {"newton": sum(s["newton_it"] for s in results[p]["stats"]),
+                           "gmres": sum(s["lin_it_total"] for s in results[p]["stats"]),
+                           "staggered": sum(s["stag_it"] for s in results[p]["stats"]),
+                           "phase_field": sum(s["pf_it_total"] for s in results[p]["stats"])}
+                       for p in results},
+        "kernel_ms_warmup_step": {p: {k: round(v[0], 3) for k, v in results[p]["breakdown"].items()}
+                                  for p in results},
+    }
+    if ws == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, mat, opts, a)
+    return line
+
+
+def cpu_baseline(cfg, mat, opts, a, increments=1):
+    """The FP64 oracle as it stands, on the host cores: the first timed
+    increment of the same workload (after the same warm-up increments run
+    on the oracle, untimed)."""
+    import oracle as O
+    import oracle.build as OB
+
+    OB.build()
+    threads = os.cpu_count() or 1
+    r = O.RVE(cfg["n"], I.VOXEL_MM, cfg["grain_ids"], cfg["euler"], mat, opts, threads=threads)
+    prog = cfg["program"]
+    for k in range(a.warmup):
+        r.run_increment(*prog[k])
+    N = int(np.prod(cfg["n"]))
+    t0 = time.perf_counter()
+    for k in range(a.warmup, a.warmup + increments):
+        r.run_increment(*prog[k])
+    dt = time.perf_counter() - t0
+    return {"value": round(N * increments / dt, 1), "unit": "voxel-increments/s",
+            "cores": threads, "kind": "oracle",
+            "sample": f"{increments} increment(s) of the same 64^3 workload "
+                      f"(increment {a.warmup + 1}), {dt:.1f} s"}
+
+
+def run_reference(a):
+    ws, rank, local = dist()
+    if rank != 0:
+        return None
+    import oracle as O
+    import oracle.build as OB
+
+    OB.build()
+    cfg = I.build_config(a.config)
+    N = int(np.prod(cfg["n"]))
+    mat = I.material("baseline")
+    opts = I.solver_options(a.tol)
+    threads = os.cpu_count() or 1
+    r = O.RVE(cfg["n"], I.VOXEL_MM, cfg["grain_ids"], cfg["euler"], mat, opts, threads=threads)
+    prog = cfg["program"]
+    for k in range(a.warmup):
+        r.run_increment(*prog[k])
+    t0 = time.perf_counter()
+    for k in range(a.warmup, a.warmup + a.steps):
+        r.run_increment(*prog[k])
+    dt = time.perf_counter() - t0
+    value = N * a.steps / dt
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 1),
+        "unit": "voxel-increments/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": round(dt / a.steps * 1e3, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded periodic Voronoi, uniform SO(3) orientations)",
+        "config": {"workload": f"{a.config}: 64^3 voxels, 50 grains, increments "
+                               f"{a.warmup + 1}-{a.warmup + a.steps}", "tolerances": a.tol},
+        "cpu_baseline": {"value": round(value, 1), "unit": "voxel-increments/s",
+                         "cores": threads, "kind": "oracle",
+                         "sample": f"{a.steps} full increments of the workload"},
+        "e2e": {"value": round(value, 1), "unit": "voxel-increments/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    a = args_()
+    line = run_reference(a) if a.impl == "reference" else run_ours(a)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * fatiguefft -- GPU solver for the FFT crystal-plasticity phase-field fatigue
+ * model of Lucarini, Dunne & Martinez-Paneda ("An FFT-based crystal plasticity
+ * phase-field model for micromechanical fatigue cracking based on the stored
+ * energy density").  One periodic voxel RVE (representative volume element)
+ * per handle, solved on one GPU by the staggered load increment of
+ * Algorithm 1:
+ *   (a) per-voxel crystal plasticity (Sec. 2.1; history of Sec. 2.3),
+ *   (b) Newton-Krylov momentum balance in Fourier space with the Green
+ *       preconditioner (Eqs. momentum, fdef, newton, precf, avstiff),
+ *   (c) phase-field damage solved in Fourier space (Eqs. strpf, phase,
+ *       precph) with the irreversibility clamp of Algorithm 1.
+ *
+ * Conventions for every call:
+ *  - Units MPa, mm, s (energies per volume in MPa, G_crit in N/mm).
+ *  - Grid n[0] x n[1] x n[2], x fastest: voxel v = x + n0*(y + n1*z).
+ *  - Voxel fields are component-major double arrays: f[c*N + v]; 3x3
+ *    tensors row-major (c = 3*i + j), sample frame.
+ *  - Orientation per grain: Bunge Euler (phi1, Phi, phi2) in radians,
+ *    passive z-x-z; lattice-to-sample rotation Q = (Rz(phi1) Rx(Phi) Rz(phi2)).
+ *  - The library owns all device memory of a handle (allocated in
+ *    init_rve, released in rve_destroy).  Inputs are copied during the call;
+ *    the caller keeps ownership of its buffers.
+ *  - All device work runs on the stream given in fft_options.cuda_stream
+ *    (0 = legacy default stream).  Calls that return statistics synchronise
+ *    that stream.
+ *  - Errors: every call returns an fft_status; nothing aborts.  The text of
+ *    the last error of a handle is returned by fft_last_error.  On a failed
+ *    increment nothing is committed; the handle still accepts fields_out,
+ *    apply_increment (restarting from the committed state) and rve_destroy.
+ *  - One handle must not be used from two threads at the same time.
+ */
+#ifndef FATIGUEFFT_H
+#define FATIGUEFFT_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fft_rve_s* fft_rve_t;
+
+typedef enum {
+    FFT_OK = 0,
+    FFT_ERR_ARG = -1,            /* invalid argument or size */
+    FFT_ERR_OOM = -2,            /* device allocation failed */
+    FFT_ERR_CUDA = -3,           /* CUDA runtime error */
+    FFT_ERR_CUFFT = -4,          /* cuFFT error */
+    FFT_ERR_NOT_CONVERGED = -5,  /* an iteration cap was hit (stats say which) */
+    FFT_ERR_NONFINITE = -6,      /* NaN/Inf detected in a residual or norm */
+    FFT_ERR_STATE = -7           /* calls made in the wrong order */
+} fft_status;
+
+typedef enum { FFT_PREC_FP64 = 0, FFT_PREC_MIXED = 1 } fft_precision;
+
+/* Grid: voxel counts and voxel edge length h (mm); L_i = n_i h. */
+typedef struct {
+    int n[3];
+    double h;
+} fft_grid;
+
+/* Material: Table 1 of the paper plus the constants it uses without a value
+ * (dV activation volume, mu Taylor shear modulus, xi_store stored-energy
+ * fraction, rho_ssd0 initial SSD density), G_crit, ell, ell_Fp (Sec. 4) and
+ * the residual stiffness k_res of Eq. deg. */
+typedef struct {
+    double C11, C12, C44, tau_c0, b, nu_D, k_B, T, dF, rho_m, lambda_h, dV, mu, xi_store,
+        rho_ssd0, G_crit, ell, ell_Fp, k_res;
+} fft_material;
+
+/* Solver controls.  Tolerances (Sec. 3.1-3.2): tol_stag on the Algorithm 1
+ * ratios, tol_newton on ||grad du||inf / ||F - F_t||inf, tol_lin relative
+ * GMRES residual, tol_pf relative phase-field CG residual, tol_local the
+ * local slip-law residual (MPa).  max_* are iteration caps; restart is the
+ * GMRES restart length (<= 64).  prec selects FP64 or the mixed path (FP32
+ * fields, transforms and constitutive update; FP64 reductions, dot products,
+ * norms and compensated history sums). */
+typedef struct {
+    double tol_stag, tol_newton, tol_lin, tol_pf, tol_local;
+    int max_stag, max_newton, max_lin, max_pf, max_local, restart;
+    fft_precision prec;
+    void* cuda_stream; /* cudaStream_t */
+} fft_options;
+
+/* Per-increment statistics (accumulated since apply_increment). */
+typedef struct {
+    int stag_it, newton_it, lin_it_total, pf_it_total, local_fail;
+    int converged, skipped_equilibrium;
+    double res_F, res_phi; /* last Algorithm 1 ratios */
+    double Pbar[9];        /* volume average of g(phi) P at the current iterate */
+    long cracked;          /* voxels with phi >= 0.9 */
+} fft_stats;
+
+/* Field identifiers for fields_out / fields_in (component count). */
+enum {
+    FFT_FIELD_F = 0,        /* 9  current deformation gradient F */
+    FFT_FIELD_P = 1,        /* 9  degraded first Piola-Kirchhoff stress g(phi) P */
+    FFT_FIELD_PHI = 2,      /* 1  current phase field */
+    FFT_FIELD_FP = 3,       /* 9  committed plastic deformation gradient F_p */
+    FFT_FIELD_RHO_SSD = 4,  /* 1  committed SSD density, 1/mm^2 */
+    FFT_FIELD_RHO_GND = 5,  /* 1  GND density from the committed F_p */
+    FFT_FIELD_WP = 6,       /* 1  committed plastic work, MPa */
+    FFT_FIELD_GS = 7,       /* 1  committed stored energy density G_s, N/mm */
+    FFT_FIELD_HMAX = 8,     /* 1  committed max over time of W_e+ */
+    FFT_FIELD_WCRIT = 9,    /* 1  committed W_crit (0 = not yet reached) */
+    FFT_FIELD_DRIVE = 10,   /* 1  crack driving state function S (Eq. zeta) */
+    FFT_FIELD_GAMMA = 11,   /* 12 committed accumulated slip per system */
+    FFT_FIELD_FT = 12,      /* 9  committed F */
+    FFT_FIELD_PHI_T = 13,   /* 1  committed phase field */
+    FFT_FIELD_WE = 14,      /* 1  W_e+ at the last constitutive evaluation */
+    FFT_FIELD_K = 15,       /* 81 undegraded consistent tangent dP/dF, K[9*(3i+j)+3k+l] */
+    FFT_FIELD_PU = 16       /* 9  undegraded P at the last constitutive evaluation */
+};
+
+/* Create a handle.  grain_ids: n0*n1*n2 int32 in [0, n_grains), host.
+ * euler: 3*n_grains doubles, host.  phi0: optional initial (committed) phase
+ * field, N doubles, host (NULL = 0).  elastic_only: optional N bytes, nonzero
+ * = no slip in that voxel (the paper's soft pre-crack region), host.
+ * Initial state: F = F_p = I, rho_ssd = rho_ssd0, all other history 0. */
+fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_ids,
+                    int n_grains, const double* euler, const fft_material* mat,
+                    const fft_options* opt, const double* phi0, const uint8_t* elastic_only);
+
+/* Start a load increment (Algorithm 1 data): commits the previous increment
+ * if it converged, sets F_0 = F_t + (Fbar_target - Fbar_t) uniformly,
+ * phi^0 = phi_t, the step dt (s), and computes rho_GND from the committed
+ * F_p (Nye tensor, Eq. nyeindexfourier, with the F_p regularisation). */
+fft_status apply_increment(fft_rve_t r, const double Fbar_target[9], double dt);
+
+/* One "solve Eq. momentum" line of Algorithm 1: Newton-Krylov at the current
+ * phase field phi_{i-1}.  Skipped (F_i = F_{i-1}) when phi has not changed
+ * since the previous solve of this increment.  Accumulates into st. */
+fft_status solve_equilibrium(fft_rve_t r, fft_stats* st);
+
+/* The "solve Eq. phase" and clamp lines of Algorithm 1 at F_i: evaluates the
+ * constitutive update and driving force at F_i, solves the phase field,
+ * clamps phi >= phi_t and evaluates the two convergence ratios
+ * (st->converged).  Accumulates into st. */
+fft_status update_damage(fft_rve_t r, fft_stats* st);
+
+/* Accept the current (converged) iterate as the state at t + dt. */
+fft_status commit_increment(fft_rve_t r);
+
+/* apply_increment + repeated solve_equilibrium/update_damage until the
+ * Algorithm 1 ratios are below tol_stag, then commit.  Resets st. */
+fft_status run_increment(fft_rve_t r, const double Fbar_target[9], double dt, fft_stats* st);
+
+/* Copy a field (double, component-major, sample frame) to dst: a host
+ * pointer (dst_is_device = 0) or a device pointer on the handle's GPU
+ * (dst_is_device = 1).  bytes must be at least ncomp*N*8. */
+fft_status fields_out(fft_rve_t r, int field, void* dst, size_t bytes, int dst_is_device);
+
+/* Overwrite a state field from a host double array (F, FT, FP, PHI, PHI_T,
+ * RHO_SSD, WP, GS, HMAX, WCRIT, GAMMA, DRIVE).  For testing and restarts;
+ * history sums restart with a zero compensation term. */
+fft_status fields_in(fft_rve_t r, int field, const double* src, size_t bytes);
+
+/* Stage entry points (same kernels as the increment uses), for checking one
+ * stage at a time.  eval_constitutive: constitutive update at the current F
+ * with the committed history; with_history = 1 also evaluates W_e+, the
+ * driving force and the trial history.  eval_gnd: rho_GND from the committed
+ * F_p.  solve_phase_field: the phase-field solve and clamp with the driving
+ * force of the last eval_constitutive(with_history = 1). */
+fft_status eval_constitutive(fft_rve_t r, double dt, int with_history, int* local_fail);
+fft_status eval_gnd(fft_rve_t r);
+fft_status solve_phase_field(fft_rve_t r, int* iters);
+
+/* Opt-in kernel timing.  mask selects kernel families by bit (0 constitutive,
+ * 1 tangent apply, 2 preconditioner + gradient, 3 divergence, 4 GMRES dot
+ * products, 5 Gram-Schmidt update, 6 GMRES solution update, 7 averaged
+ * tangent, 8 residual, 9 F update, 10 phase field, 11 GND, 12 cuFFT
+ * 9-field transforms, 13 cuFFT scalar transforms, 14 reductions, 15 other);
+ * each selected launch is bracketed by CUDA events on the handle's stream.
+ * 0 switches timing off.  rve_profile_read returns the accumulated device
+ * milliseconds and launch counts per family (16 entries each, caller-owned
+ * arrays), synchronising the stream first; reset = 1 clears them. */
+fft_status rve_profile(fft_rve_t r, unsigned mask);
+fft_status rve_profile_read(fft_rve_t r, double* ms, long long* counts, int reset);
+
+/* Size in bytes of the device memory the handle holds. */
+size_t rve_device_bytes(fft_rve_t r);
+void rve_destroy(fft_rve_t r);
+const char* fft_last_error(fft_rve_t r);
+/* Kernel launches issued by this handle since creation (for accounting). */
+long long rve_kernel_launches(fft_rve_t r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

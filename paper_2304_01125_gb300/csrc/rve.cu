@@ -1,0 +1,1085 @@
+// Host driver and C ABI of the fatiguefft library: the load increment of
+// Algorithm 1 (staggered alternating minimisation), the Newton-Krylov
+// momentum solve (Eqs. momentum, fdef, newton with the Green preconditioner
+// of Eqs. precf, avstiff) and the phase-field solve (Eqs. phase, precph),
+// all on one CUDA stream.  Only convergence decisions cross to the host.
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "fatiguefft.h"
+#include "launch.h"
+#include "spec.h"
+
+using namespace fatfft;
+
+namespace {
+enum { ST_NEW = 0, ST_APPLIED = 1, ST_EQUIL = 2, ST_DAMAGE = 3, ST_COMMITTED = 4 };
+constexpr int kMaxRestart = 64;
+constexpr int kRedSlots = 256;
+}  // namespace
+
+struct fft_rve_s {
+    int prec = 0;
+    size_t esz = 8;  // bytes of the bulk real type
+    SGrid g{};
+    double h = 0;
+    int ngr = 0;
+    fft_material mat{};
+    fft_options opt{};
+    CPParams cpp{};
+    cudaStream_t st = 0;
+    cufftHandle r2c9 = 0, c2r9 = 0, r2c1 = 0, c2r1 = 0;
+    bool plans = false;
+    // device state (bulk type unless noted)
+    void *H = nullptr, *Ht = nullptr, *Hprev = nullptr, *Hpi_t = nullptr, *Hpi_tr = nullptr;
+    void *P = nullptr, *K = nullptr, *rho_gnd = nullptr, *phi = nullptr, *phi_t = nullptr;
+    void *drive = nullptr, *We = nullptr;
+    double *hist_c = nullptr, *hist_tr = nullptr;
+    int32_t* grain = nullptr;
+    uint8_t* elastic = nullptr;
+    double *Qg = nullptr, *G81 = nullptr, *Kbar = nullptr;
+    // work buffers
+    void *rb9 = nullptr, *cb9 = nullptr;                      // real 9N, complex 9Nh
+    void *V = nullptr, *x = nullptr, *b = nullptr, *w = nullptr;  // GMRES (complex)
+    void *pfx = nullptr, *pfr = nullptr, *pfz = nullptr, *pfp = nullptr, *pft = nullptr,
+         *pfq = nullptr;
+    double *part = nullptr, *red = nullptr, *dy = nullptr;
+    double *hred = nullptr, *hy = nullptr;  // pinned host
+    int* dfail = nullptr;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    long long launches = 0;
+    // opt-in kernel timing per family (CUDA events on the handle's stream)
+    unsigned prof_mask = 0;
+    struct ProfEv {
+        cudaEvent_t a, b;
+        int fam;
+    };
+    std::vector<ProfEv> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[16] = {0};
+    long long prof_cnt[16] = {0};
+    // Algorithm 1 bookkeeping
+    double Fbar_t[9], Fbar[9], dt = 0;
+    int state = ST_NEW, stag_it = 0;
+    bool phi_changed = true, skipped = false, converged = false, cp_valid = false;
+    std::string err;
+};
+
+#define FAIL(r, code, ...)                                          \
+    do {                                                            \
+        char _b[512];                                               \
+        std::snprintf(_b, sizeof(_b), __VA_ARGS__);                 \
+        (r)->err = _b;                                              \
+        return code;                                                \
+    } while (0)
+#define CK(r, x)                                                                           \
+    do {                                                                                   \
+        cudaError_t _e = (x);                                                              \
+        if (_e != cudaSuccess) FAIL(r, FFT_ERR_CUDA, "%s: %s", #x, cudaGetErrorString(_e)); \
+    } while (0)
+#define CKF(r, x)                                                                 \
+    do {                                                                          \
+        cufftResult _e = (x);                                                     \
+        if (_e != CUFFT_SUCCESS) FAIL(r, FFT_ERR_CUFFT, "%s: cufft error %d", #x, (int)_e); \
+    } while (0)
+#define TRY(x)                        \
+    do {                              \
+        fft_status _s = (x);          \
+        if (_s != FFT_OK) return _s;  \
+    } while (0)
+
+// kernel families for the opt-in timing
+enum {
+    KF_CP = 0, KF_TANGENT = 1, KF_PRECOND = 2, KF_CONTRACT = 3, KF_MDOT = 4, KF_GSUPD = 5,
+    KF_XUPD = 6, KF_KBAR = 7, KF_RESID = 8, KF_FUPD = 9, KF_PF = 10, KF_GND = 11, KF_FFT9 = 12,
+    KF_FFT1 = 13, KF_FIN = 14, KF_OTHER = 15
+};
+static cudaEvent_t prof_begin(fft_rve_s* r, int fam) {
+    if (!(r->prof_mask >> fam & 1u)) return nullptr;
+    cudaEvent_t e;
+    if (r->prof_pool.empty()) {
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    } else {
+        e = r->prof_pool.back();
+        r->prof_pool.pop_back();
+    }
+    cudaEventRecord(e, r->st);
+    return e;
+}
+static void prof_end(fft_rve_s* r, int fam, cudaEvent_t a) {
+    if (!a) return;
+    cudaEvent_t b;
+    if (r->prof_pool.empty()) {
+        if (cudaEventCreate(&b) != cudaSuccess) return;
+    } else {
+        b = r->prof_pool.back();
+        r->prof_pool.pop_back();
+    }
+    cudaEventRecord(b, r->st);
+    r->prof_pending.push_back({a, b, fam});
+}
+// after a stream synchronisation: fold the recorded pairs into the totals
+static void prof_collect(fft_rve_s* r) {
+    for (auto& p : r->prof_pending) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            r->prof_ms[p.fam] += ms;
+            r->prof_cnt[p.fam] += 1;
+        }
+        r->prof_pool.push_back(p.a);
+        r->prof_pool.push_back(p.b);
+    }
+    r->prof_pending.clear();
+}
+
+static fft_status dalloc(fft_rve_s* r, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        FAIL(r, FFT_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    r->allocs.push_back(*p);
+    r->bytes += bytes;
+    return FFT_OK;
+}
+
+// ---------------------------------------------------------------- cuFFT
+template <typename R> struct FFT;
+template <> struct FFT<float> {
+    static constexpr cufftType R2C = CUFFT_R2C, C2R = CUFFT_C2R;
+    static cufftResult fwd(cufftHandle p, void* i, void* o) {
+        return cufftExecR2C(p, (cufftReal*)i, (cufftComplex*)o);
+    }
+    static cufftResult inv(cufftHandle p, void* i, void* o) {
+        return cufftExecC2R(p, (cufftComplex*)i, (cufftReal*)o);
+    }
+};
+template <> struct FFT<double> {
+    static constexpr cufftType R2C = CUFFT_D2Z, C2R = CUFFT_Z2D;
+    static cufftResult fwd(cufftHandle p, void* i, void* o) {
+        return cufftExecD2Z(p, (cufftDoubleReal*)i, (cufftDoubleComplex*)o);
+    }
+    static cufftResult inv(cufftHandle p, void* i, void* o) {
+        return cufftExecZ2D(p, (cufftDoubleComplex*)i, (cufftDoubleReal*)o);
+    }
+};
+
+// ------------------------------------------------------- host-side tables
+// Lattice-to-sample rotation from Bunge angles: Q = Rz(phi1) Rx(Phi) Rz(phi2).
+static void bunge_Q(const double* e, double* Q) {
+    auto rz = [](double a, double* m) {
+        const double c = std::cos(a), s = std::sin(a);
+        const double t[9] = {c, -s, 0, s, c, 0, 0, 0, 1};
+        std::memcpy(m, t, sizeof(t));
+    };
+    double A[9], B[9], C[9], T[9];
+    rz(e[0], A);
+    const double c = std::cos(e[1]), s = std::sin(e[1]);
+    const double X[9] = {1, 0, 0, 0, c, -s, 0, s, c};
+    std::memcpy(B, X, sizeof(X));
+    rz(e[2], C);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            T[3 * i + j] = 0;
+            for (int k = 0; k < 3; ++k) T[3 * i + j] += A[3 * i + k] * B[3 * k + j];
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            Q[3 * i + j] = 0;
+            for (int k = 0; k < 3; ++k) Q[3 * i + j] += T[3 * i + k] * C[3 * k + j];
+        }
+}
+
+// (A A^T)^-1 for the GND dyad basis of Eq. nye1 (12 edge b(x)t, t = n x b;
+// the distinct screw b(x)b), assembled from the slip table.
+static void gnd_metric(double* G) {
+    const int pl[4][3] = {{1, 1, 1}, {-1, 1, 1}, {1, -1, 1}, {1, 1, -1}};
+    const int dr[12][3] = {{0, 1, -1}, {1, 0, -1}, {1, -1, 0}, {0, 1, -1}, {1, 0, 1}, {1, 1, 0},
+                           {0, 1, 1},  {1, 0, -1}, {1, 1, 0},  {0, 1, 1},  {1, 0, 1}, {1, -1, 0}};
+    std::vector<std::vector<double>> cols;
+    std::vector<std::vector<int>> screws;
+    for (int a = 0; a < 12; ++a) {
+        double b[3], n[3], t[3];
+        for (int i = 0; i < 3; ++i) {
+            b[i] = dr[a][i] / std::sqrt(2.0);
+            n[i] = pl[a / 3][i] / std::sqrt(3.0);
+        }
+        t[0] = n[1] * b[2] - n[2] * b[1];
+        t[1] = n[2] * b[0] - n[0] * b[2];
+        t[2] = n[0] * b[1] - n[1] * b[0];
+        std::vector<double> c(9);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) c[3 * i + j] = b[i] * t[j];
+        cols.push_back(c);
+        // screw directions, distinct up to sign
+        std::vector<int> d = {dr[a][0], dr[a][1], dr[a][2]};
+        std::vector<int> m = {-d[0], -d[1], -d[2]};
+        bool seen = false;
+        for (auto& q : screws) seen = seen || q == d || q == m;
+        if (!seen) screws.push_back(d);
+    }
+    for (auto& d : screws) {
+        std::vector<double> c(9);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) c[3 * i + j] = d[i] * d[j] / 2.0;
+        cols.push_back(c);
+    }
+    double M[81], I[81];
+    for (int r = 0; r < 9; ++r)
+        for (int c = 0; c < 9; ++c) {
+            double s = 0;
+            for (auto& col : cols) s += col[r] * col[c];
+            M[9 * r + c] = s;
+            I[9 * r + c] = r == c ? 1.0 : 0.0;
+        }
+    // Gauss-Jordan inverse with partial pivoting
+    for (int c = 0; c < 9; ++c) {
+        int p = c;
+        for (int r = c + 1; r < 9; ++r)
+            if (std::fabs(M[9 * r + c]) > std::fabs(M[9 * p + c])) p = r;
+        for (int k = 0; k < 9; ++k) {
+            std::swap(M[9 * c + k], M[9 * p + k]);
+            std::swap(I[9 * c + k], I[9 * p + k]);
+        }
+        const double d = M[9 * c + c];
+        for (int k = 0; k < 9; ++k) {
+            M[9 * c + k] /= d;
+            I[9 * c + k] /= d;
+        }
+        for (int r = 0; r < 9; ++r) {
+            if (r == c) continue;
+            const double f = M[9 * r + c];
+            for (int k = 0; k < 9; ++k) {
+                M[9 * r + k] -= f * M[9 * c + k];
+                I[9 * r + k] -= f * I[9 * c + k];
+            }
+        }
+    }
+    std::memcpy(G, I, sizeof(I));
+}
+
+// ------------------------------------------------------- stage helpers
+template <typename R>
+struct Impl {
+    typedef typename Tr<R>::Cx Cx;
+
+    static fft_status fetch(fft_rve_s* r, int n) {
+        CK(r, cudaMemcpyAsync(r->hred, r->red, n * sizeof(double), cudaMemcpyDeviceToHost, r->st));
+        CK(r, cudaStreamSynchronize(r->st));
+        prof_collect(r);
+        for (int i = 0; i < n; ++i)
+            if (!std::isfinite(r->hred[i]))
+                FAIL(r, FFT_ERR_NONFINITE, "non-finite reduction value (slot %d)", i);
+        return FFT_OK;
+    }
+    static fft_status fwd9(fft_rve_s* r) {
+        cudaEvent_t e = prof_begin(r, KF_FFT9);
+        CKF(r, FFT<R>::fwd(r->r2c9, r->rb9, r->cb9));
+        prof_end(r, KF_FFT9, e);
+        return FFT_OK;
+    }
+    static fft_status inv9(fft_rve_s* r) {
+        cudaEvent_t e = prof_begin(r, KF_FFT9);
+        CKF(r, FFT<R>::inv(r->c2r9, r->cb9, r->rb9));
+        prof_end(r, KF_FFT9, e);
+        return FFT_OK;
+    }
+    static fft_status fwd1(fft_rve_s* r, void* in) {
+        cudaEvent_t e = prof_begin(r, KF_FFT1);
+        CKF(r, FFT<R>::fwd(r->r2c1, in, r->cb9));
+        prof_end(r, KF_FFT1, e);
+        return FFT_OK;
+    }
+    static fft_status inv1(fft_rve_s* r, void* out) {
+        cudaEvent_t e = prof_begin(r, KF_FFT1);
+        CKF(r, FFT<R>::inv(r->c2r1, r->cb9, out));
+        prof_end(r, KF_FFT1, e);
+        return FFT_OK;
+    }
+
+    // rho_GND from the committed F_p (Eq. nyeindexfourier + regularisation)
+    static fft_status gnd(fft_rve_s* r) {
+        const size_t N = r->g.N;
+        fp_sample<R>(r->Hpi_t, r->grain, r->Qg, r->rb9, N, r->st);
+        TRY(fwd9(r));
+        nye<R>(r->cb9, r->g, r->mat.ell_Fp * r->mat.ell_Fp, r->st);
+        TRY(inv9(r));
+        gnd_rho<R>(r->rb9, r->grain, r->Qg, r->G81, 1.0 / r->mat.b, r->rho_gnd, N, r->st);
+        r->launches += 3;
+        CK(r, cudaGetLastError());
+        return FFT_OK;
+    }
+
+    static fft_status cp(fft_rve_s* r, bool hist, int* fails) {
+        CPFields f;
+        f.H = r->H;
+        f.Hpi = r->Hpi_t;
+        f.rho_gnd = r->rho_gnd;
+        f.grain = r->grain;
+        f.elastic = r->elastic;
+        f.Qg = r->Qg;
+        f.hist_c = r->hist_c;
+        f.hist_tr = r->hist_tr;
+        f.P = r->P;
+        f.K = r->K;
+        f.Hpi_tr = r->Hpi_tr;
+        f.drive = r->drive;
+        f.We = r->We;
+        f.fail_count = r->dfail;
+        f.N = r->g.N;
+        CPParams p = r->cpp;
+        p.dt = r->dt;
+        CK(r, cudaMemsetAsync(r->dfail, 0, sizeof(int), r->st));
+        cudaEvent_t e = prof_begin(r, KF_CP);
+        launch_constitutive<R>(f, p, hist, r->st);
+        prof_end(r, KF_CP, e);
+        r->launches += 1;
+        CK(r, cudaGetLastError());
+        int nf = 0;
+        CK(r, cudaMemcpyAsync(r->hy, r->dfail, sizeof(int), cudaMemcpyDeviceToHost, r->st));
+        CK(r, cudaStreamSynchronize(r->st));
+        prof_collect(r);
+        std::memcpy(&nf, r->hy, sizeof(int));
+        if (fails) *fails = nf;
+        r->cp_valid = true;
+        return FFT_OK;
+    }
+
+    // w = A u with A u = -F{g K : F^-1{u (x) i xi}} . i xi; use_pre applies
+    // the Green preconditioner to u first (scaled by scale, optionally
+    // stored to vout).
+    static fft_status apply_op(fft_rve_s* r, const void* u, double scale, void* vout, int use_pre,
+                               void* w) {
+        cudaEvent_t e = prof_begin(r, KF_PRECOND);
+        precond_grad<R>(u, scale, vout, r->Kbar, r->g, r->cb9, use_pre, r->st);
+        prof_end(r, KF_PRECOND, e);
+        TRY(inv9(r));
+        e = prof_begin(r, KF_TANGENT);
+        tangent_apply<R>(r->rb9, r->K, r->phi, r->mat.k_res, r->g.N, r->st);
+        prof_end(r, KF_TANGENT, e);
+        TRY(fwd9(r));
+        e = prof_begin(r, KF_CONTRACT);
+        contract<R>(r->cb9, r->g, w, r->st);
+        prof_end(r, KF_CONTRACT, e);
+        r->launches += 3;
+        return FFT_OK;
+    }
+
+    // Restarted GMRES, right-preconditioned by the Green operator, classical
+    // Gram-Schmidt with one re-orthogonalisation; Hermitian-weighted FP64 dot
+    // products; Hessenberg least squares on the host.
+    static fft_status gmres(fft_rve_s* r, double bn, double pn, int* its) {
+        const size_t Nh = r->g.Nh, n3 = 3 * Nh;
+        const double eta = sizeof(R) == 8 ? 1e-12 : 2e-7;
+        const double target = std::max(r->opt.tol_lin * bn, eta * pn);
+        CK(r, cudaMemsetAsync(r->x, 0, n3 * sizeof(Cx), r->st));
+        *its = 0;
+        if (bn <= target) return FFT_OK;
+        const int m = std::max(1, std::min(r->opt.restart, kMaxRestart));
+        const size_t vs = n3;  // stride between Krylov vectors (elements)
+        Cx* V = (Cx*)r->V;
+        std::vector<double> Hm((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+        bool first = true, ok = false;
+        int lin = 0;
+        while (lin < r->opt.max_lin && !ok) {
+            double beta;
+            if (first) {
+                beta = bn;
+                axpby<R>(V, r->b, nullptr, 1.0 / beta, 0.0, n3, r->st);
+            } else {
+                TRY(apply_op(r, r->x, 1.0, nullptr, 0, r->w));
+                axpby<R>(r->w, r->b, r->w, 1.0, -1.0, n3, r->st);
+                mdot<R>(r->w, nullptr, 0, 0, 1, r->g, r->part, r->st);
+                finalize_sum(r->part, 1, 1.0, r->red, r->st);
+                r->launches += 3;
+                TRY(fetch(r, 1));
+                beta = std::sqrt(r->hred[0]);
+                if (beta <= target) {
+                    ok = true;
+                    break;
+                }
+                axpby<R>(V, r->w, nullptr, 1.0 / beta, 0.0, n3, r->st);
+            }
+            r->launches += 1;
+            first = false;
+            std::fill(Hm.begin(), Hm.end(), 0.0);
+            std::fill(gv.begin(), gv.end(), 0.0);
+            gv[0] = beta;
+            double hprev = 0;
+            int k = 0;
+            for (; k < m && lin < r->opt.max_lin; ++k) {
+                ++lin;
+                if (k == 0)
+                    TRY(apply_op(r, V, 1.0, nullptr, 1, r->w));
+                else
+                    TRY(apply_op(r, r->w, 1.0 / hprev, V + (size_t)k * vs, 1, r->w));
+                // h = V^T w ; w -= V h ; h2 = V^T w ; w -= V h2 ; ||w||
+                cudaEvent_t e = prof_begin(r, KF_MDOT);
+                mdot<R>(r->w, V, vs, k + 1, 0, r->g, r->part, r->st);
+                finalize_sum(r->part, k + 1, 1.0, r->red, r->st);
+                prof_end(r, KF_MDOT, e);
+                e = prof_begin(r, KF_GSUPD);
+                gs_update<R>(r->w, V, vs, k + 1, r->red, n3, r->st);
+                prof_end(r, KF_GSUPD, e);
+                e = prof_begin(r, KF_MDOT);
+                mdot<R>(r->w, V, vs, k + 1, 0, r->g, r->part, r->st);
+                finalize_sum(r->part, k + 1, 1.0, r->red + 64, r->st);
+                prof_end(r, KF_MDOT, e);
+                e = prof_begin(r, KF_GSUPD);
+                gs_update<R>(r->w, V, vs, k + 1, r->red + 64, n3, r->st);
+                prof_end(r, KF_GSUPD, e);
+                e = prof_begin(r, KF_MDOT);
+                mdot<R>(r->w, nullptr, 0, 0, 1, r->g, r->part, r->st);
+                finalize_sum(r->part, 1, 1.0, r->red + 128, r->st);
+                prof_end(r, KF_MDOT, e);
+                r->launches += 8;
+                TRY(fetch(r, 129));
+                for (int i = 0; i <= k; ++i) Hm[i * m + k] = r->hred[i] + r->hred[64 + i];
+                const double hn = std::sqrt(std::max(r->hred[128], 0.0));
+                Hm[(k + 1) * m + k] = hn;
+                for (int i = 0; i < k; ++i) {
+                    const double t = cs[i] * Hm[i * m + k] + sn[i] * Hm[(i + 1) * m + k];
+                    Hm[(i + 1) * m + k] = -sn[i] * Hm[i * m + k] + cs[i] * Hm[(i + 1) * m + k];
+                    Hm[i * m + k] = t;
+                }
+                const double den = std::hypot(Hm[k * m + k], Hm[(k + 1) * m + k]);
+                cs[k] = den > 0 ? Hm[k * m + k] / den : 1.0;
+                sn[k] = den > 0 ? Hm[(k + 1) * m + k] / den : 0.0;
+                Hm[k * m + k] = den;
+                Hm[(k + 1) * m + k] = 0.0;
+                gv[k + 1] = -sn[k] * gv[k];
+                gv[k] = cs[k] * gv[k];
+                hprev = hn;
+                if (std::fabs(gv[k + 1]) <= target || hn == 0.0) {
+                    ok = true;
+                    ++k;
+                    break;
+                }
+            }
+            for (int i = k - 1; i >= 0; --i) {
+                double s = gv[i];
+                for (int j = i + 1; j < k; ++j) s -= Hm[i * m + j] * y[j];
+                y[i] = s / Hm[i * m + i];
+            }
+            std::memcpy(r->hy, y.data(), k * sizeof(double));
+            CK(r, cudaMemcpyAsync(r->dy, r->hy, k * sizeof(double), cudaMemcpyHostToDevice, r->st));
+            cudaEvent_t e = prof_begin(r, KF_XUPD);
+            xupdate<R>(r->x, V, vs, k, r->dy, r->Kbar, r->g, r->st);
+            prof_end(r, KF_XUPD, e);
+            r->launches += 1;
+            CK(r, cudaStreamSynchronize(r->st));  // hy is reused by the next fetch
+            prof_collect(r);
+        }
+        *its = lin;
+        CK(r, cudaGetLastError());
+        if (!ok) FAIL(r, FFT_ERR_NOT_CONVERGED, "GMRES reached max_lin = %d", r->opt.max_lin);
+        return FFT_OK;
+    }
+
+    static fft_status solve_equilibrium(fft_rve_s* r, fft_stats* st) {
+        if (r->state != ST_APPLIED && r->state != ST_DAMAGE)
+            FAIL(r, FFT_ERR_STATE, "solve_equilibrium before apply_increment");
+        const size_t N = r->g.N;
+        CK(r, cudaMemcpyAsync(r->Hprev, r->H, 9 * N * sizeof(R), cudaMemcpyDeviceToDevice, r->st));
+        r->skipped = false;
+        r->state = ST_EQUIL;
+        if (r->stag_it >= 1 && !r->phi_changed) {
+            r->skipped = true;
+            if (st) st->skipped_equilibrium = 1;
+            return FFT_OK;
+        }
+        for (int it = 0; it < r->opt.max_newton; ++it) {
+            if (!r->cp_valid) {
+                int nf = 0;
+                TRY(cp(r, false, &nf));
+                if (st) st->local_fail += nf;
+            }
+            if (st) st->newton_it += 1;
+            kbar<R>(r->K, r->phi, r->mat.k_res, N, r->part, r->st);
+            finalize_sum(r->part, 81, 1.0 / (double)N, r->Kbar, r->st);
+            degrade<R>(r->P, r->phi, r->mat.k_res, r->rb9, N, r->st);
+            TRY(fwd9(r));
+            residual<R>(r->cb9, r->g, r->b, r->part, r->st);
+            finalize_sum(r->part, 2, 1.0, r->red, r->st);
+            r->launches += 5;
+            TRY(fetch(r, 2));
+            const double bn = std::sqrt(r->hred[0]), pn = std::sqrt(r->hred[1]);
+            int lin = 0;
+            const fft_status s = gmres(r, bn, pn, &lin);
+            if (st) st->lin_it_total += lin;
+            if (s != FFT_OK) return s;
+            precond_grad<R>(r->x, 1.0, nullptr, r->Kbar, r->g, r->cb9, 0, r->st);
+            TRY(inv9(r));
+            fupdate<R>(r->H, r->rb9, r->Ht, N, r->part, r->st);
+            finalize_max(r->part, 2, r->red, r->st);
+            r->launches += 3;
+            TRY(fetch(r, 2));
+            r->cp_valid = false;
+            const double gmax = r->hred[0], dFt = std::max(r->hred[1], 1e-30);
+            if (gmax / dFt < r->opt.tol_newton) return FFT_OK;
+        }
+        FAIL(r, FFT_ERR_NOT_CONVERGED, "Newton reached max_newton = %d", r->opt.max_newton);
+    }
+
+    // PCG on (1 + 2S) phi - ell^2 lap phi = 2S with M_phi, x0 = current phi;
+    // A p through the recurrence t = M^-1 p = r + beta t (one transform pair
+    // per iteration).  Result in pfx (unclamped).
+    static fft_status pcg_phase(fft_rve_s* r, int* iters) {
+        const size_t N = r->g.N;
+        const double l2 = r->mat.ell * r->mat.ell;
+        *iters = 0;
+        CK(r, cudaMemcpyAsync(r->pfx, r->phi, N * sizeof(R), cudaMemcpyDeviceToDevice, r->st));
+        TRY(fwd1(r, r->pfx));
+        pf_spec<R>(r->cb9, r->g, l2, 0, r->st);
+        TRY(inv1(r, r->pfq));
+        pf_init<R>(r->pfx, r->pfq, r->drive, r->pfr, N, r->part, r->st);
+        finalize_sum(r->part, 2, 1.0, r->red, r->st);
+        r->launches += 3;
+        TRY(fetch(r, 2));
+        const double bn = std::sqrt(r->hred[1]);
+        if (std::sqrt(r->hred[0]) <= r->opt.tol_pf * bn) return FFT_OK;
+        auto precond = [&]() -> fft_status {
+            TRY(fwd1(r, r->pfr));
+            pf_spec<R>(r->cb9, r->g, l2, 1, r->st);
+            TRY(inv1(r, r->pfz));
+            rdot<R>(r->pfr, r->pfz, N, r->part, r->st);
+            finalize_sum(r->part, 1, 1.0, r->red, r->st);
+            r->launches += 3;
+            return fetch(r, 1);
+        };
+        TRY(precond());
+        double rz = r->hred[0];
+        CK(r, cudaMemcpyAsync(r->pfp, r->pfz, N * sizeof(R), cudaMemcpyDeviceToDevice, r->st));
+        CK(r, cudaMemcpyAsync(r->pft, r->pfr, N * sizeof(R), cudaMemcpyDeviceToDevice, r->st));
+        for (int it = 1; it <= r->opt.max_pf; ++it) {
+            *iters = it;
+            pf_q<R>(r->pft, r->pfp, r->drive, r->pfq, N, r->part, r->st);
+            finalize_sum(r->part, 1, 1.0, r->red, r->st);
+            TRY(fetch(r, 1));
+            const double alpha = rz / r->hred[0];
+            pf_xr<R>(r->pfx, r->pfr, r->pfp, r->pfq, alpha, N, r->part, r->st);
+            finalize_sum(r->part, 1, 1.0, r->red, r->st);
+            r->launches += 4;
+            TRY(fetch(r, 1));
+            if (std::sqrt(r->hred[0]) <= r->opt.tol_pf * bn) return FFT_OK;
+            TRY(precond());
+            const double beta = r->hred[0] / rz;
+            rz = r->hred[0];
+            pf_pt<R>(r->pfp, r->pft, r->pfz, r->pfr, beta, N, r->st);
+            r->launches += 1;
+        }
+        FAIL(r, FFT_ERR_NOT_CONVERGED, "phase-field CG reached max_pf = %d", r->opt.max_pf);
+    }
+
+    // phase-field solve (or phi = phi_t when S = 0 everywhere) and clamp;
+    // out: max|phi_new - phi_old|, max|phi_new - phi_t|, changed, cracked.
+    static fft_status phase_field(fft_rve_s* r, int* iters, double* out4) {
+        const size_t N = r->g.N;
+        maxval<R>(r->drive, N, r->part, r->st);
+        finalize_max(r->part, 1, r->red, r->st);
+        r->launches += 2;
+        TRY(fetch(r, 1));
+        *iters = 0;
+        if (r->hred[0] == 0.0) {
+            CK(r, cudaMemcpyAsync(r->pfx, r->phi_t, N * sizeof(R), cudaMemcpyDeviceToDevice, r->st));
+        } else {
+            TRY(pcg_phase(r, iters));
+        }
+        pf_clamp<R>(r->pfx, r->phi_t, r->phi, N, r->part, r->st);
+        finalize_max(r->part, 2, r->red, r->st);
+        finalize_sum(r->part + 2 * kRedBlocks, 2, 1.0, r->red + 2, r->st);
+        r->launches += 3;
+        TRY(fetch(r, 4));
+        for (int i = 0; i < 4; ++i) out4[i] = r->hred[i];
+        return FFT_OK;
+    }
+
+    static fft_status update_damage(fft_rve_s* r, fft_stats* st) {
+        if (r->state != ST_EQUIL) FAIL(r, FFT_ERR_STATE, "update_damage before solve_equilibrium");
+        const size_t N = r->g.N;
+        r->stag_it += 1;
+        r->state = ST_DAMAGE;
+        if (st) st->stag_it = r->stag_it;
+        if (r->skipped) {
+            r->converged = true;
+            if (st) {
+                st->res_F = st->res_phi = 0;
+                st->converged = 1;
+            }
+            return FFT_OK;
+        }
+        int nf = 0;
+        TRY(cp(r, true, &nf));
+        if (st) st->local_fail += nf;
+        int pf_it = 0;
+        double o4[4];
+        TRY(phase_field(r, &pf_it, o4));
+        if (st) st->pf_it_total += pf_it;
+        maxdiff<R>(r->H, r->Hprev, 9 * N, r->part, r->st);
+        maxdiff<R>(r->H, r->Ht, 9 * N, r->part + kRedBlocks, r->st);
+        finalize_max(r->part, 2, r->red, r->st);
+        pbar<R>(r->P, r->phi, r->mat.k_res, N, r->part + 2 * kRedBlocks, r->st);
+        finalize_sum(r->part + 2 * kRedBlocks, 9, 1.0 / (double)N, r->red + 2, r->st);
+        r->launches += 5;
+        TRY(fetch(r, 11));
+        const double dF = r->hred[0], dFt = r->hred[1];
+        const double dphi = o4[0], dphit = o4[1];
+        r->phi_changed = o4[2] > 0;
+        const double tol = r->opt.tol_stag;
+        r->converged = dF <= tol * std::max(dFt, 1e-12) && dphi <= tol * std::max(dphit, 1e-12);
+        if (st) {
+            st->res_F = dF / std::max(dFt, 1e-12);
+            st->res_phi = dphi / std::max(dphit, 1e-12);
+            st->converged = r->converged;
+            for (int c = 0; c < 9; ++c) st->Pbar[c] = r->hred[2 + c];
+            st->cracked = (long)o4[3];
+        }
+        return FFT_OK;
+    }
+
+    static fft_status apply_increment(fft_rve_s* r, const double* Fbar, double dt) {
+        if (r->state == ST_DAMAGE && r->converged) TRY(commit(r));
+        double d[9];
+        for (int c = 0; c < 9; ++c) {
+            d[c] = Fbar[c] - r->Fbar_t[c];
+            r->Fbar[c] = Fbar[c];
+        }
+        const size_t N = r->g.N;
+        add_uniform<R>(r->H, r->Ht, d, N, r->st);
+        r->launches += 1;
+        CK(r, cudaMemcpyAsync(r->phi, r->phi_t, N * sizeof(R), cudaMemcpyDeviceToDevice, r->st));
+        r->dt = dt;
+        TRY(gnd(r));
+        r->stag_it = 0;
+        r->phi_changed = true;
+        r->converged = false;
+        r->cp_valid = false;
+        r->state = ST_APPLIED;
+        return FFT_OK;
+    }
+
+    static fft_status commit(fft_rve_s* r) {
+        if (r->state != ST_DAMAGE || !r->converged)
+            FAIL(r, FFT_ERR_STATE, "commit without a converged increment");
+        const size_t N = r->g.N;
+        std::swap(r->hist_c, r->hist_tr);
+        std::swap(r->Hpi_t, r->Hpi_tr);
+        CK(r, cudaMemcpyAsync(r->Ht, r->H, 9 * N * sizeof(R), cudaMemcpyDeviceToDevice, r->st));
+        CK(r, cudaMemcpyAsync(r->phi_t, r->phi, N * sizeof(R), cudaMemcpyDeviceToDevice, r->st));
+        std::memcpy(r->Fbar_t, r->Fbar, sizeof(r->Fbar));
+        r->state = ST_COMMITTED;
+        r->cp_valid = false;
+        return FFT_OK;
+    }
+
+    static fft_status run_increment(fft_rve_s* r, const double* Fbar, double dt, fft_stats* st) {
+        TRY(apply_increment(r, Fbar, dt));
+        for (int i = 0; i < r->opt.max_stag; ++i) {
+            TRY(solve_equilibrium(r, st));
+            TRY(update_damage(r, st));
+            if (r->converged) return commit(r);
+        }
+        FAIL(r, FFT_ERR_NOT_CONVERGED, "staggered loop reached max_stag = %d", r->opt.max_stag);
+    }
+
+    static fft_status fields_out(fft_rve_s* r, int field, double* d) {
+        const size_t N = r->g.N;
+        cudaStream_t s = r->st;
+        switch (field) {
+            case FFT_FIELD_F: to_double<R>(r->H, d, 9 * N, N, 1, s); break;
+            case FFT_FIELD_FT: to_double<R>(r->Ht, d, 9 * N, N, 1, s); break;
+            case FFT_FIELD_P:
+                degrade<R>(r->P, r->phi, r->mat.k_res, r->rb9, N, s);
+                to_double<R>(r->rb9, d, 9 * N, N, 0, s);
+                break;
+            case FFT_FIELD_PU: to_double<R>(r->P, d, 9 * N, N, 0, s); break;
+            case FFT_FIELD_K: to_double<R>(r->K, d, 81 * N, N, 0, s); break;
+            case FFT_FIELD_PHI: to_double<R>(r->phi, d, N, N, 0, s); break;
+            case FFT_FIELD_PHI_T: to_double<R>(r->phi_t, d, N, N, 0, s); break;
+            case FFT_FIELD_DRIVE: to_double<R>(r->drive, d, N, N, 0, s); break;
+            case FFT_FIELD_WE: to_double<R>(r->We, d, N, N, 0, s); break;
+            case FFT_FIELD_RHO_GND: to_double<R>(r->rho_gnd, d, N, N, 0, s); break;
+            case FFT_FIELD_FP:
+                fp_sample<R>(r->Hpi_t, r->grain, r->Qg, r->rb9, N, s);
+                to_double<R>(r->rb9, d, 9 * N, N, 1, s);
+                break;
+            case FFT_FIELD_RHO_SSD: hist_sum(r->hist_c, HIST_RHO, 1, 1, d, N, s); break;
+            case FFT_FIELD_WP: hist_sum(r->hist_c, HIST_WP, 1, 1, d, N, s); break;
+            case FFT_FIELD_GS: hist_sum(r->hist_c, HIST_GS, 1, 1, d, N, s); break;
+            case FFT_FIELD_HMAX: hist_sum(r->hist_c, HIST_HMAX, 0, 1, d, N, s); break;
+            case FFT_FIELD_WCRIT: hist_sum(r->hist_c, HIST_WCRIT, 0, 1, d, N, s); break;
+            case FFT_FIELD_GAMMA: hist_sum(r->hist_c, HIST_GAMMA, 1, 12, d, N, s); break;
+            default: FAIL(r, FFT_ERR_ARG, "unknown field %d", field);
+        }
+        r->launches += 1;
+        CK(r, cudaGetLastError());
+        return FFT_OK;
+    }
+
+    static fft_status fields_in(fft_rve_s* r, int field, const double* d) {
+        const size_t N = r->g.N;
+        cudaStream_t s = r->st;
+        switch (field) {
+            case FFT_FIELD_F: from_double<R>(d, r->H, 9 * N, N, 1, s); break;
+            case FFT_FIELD_FT: from_double<R>(d, r->Ht, 9 * N, N, 1, s); break;
+            case FFT_FIELD_PHI: from_double<R>(d, r->phi, N, N, 0, s); break;
+            case FFT_FIELD_PHI_T: from_double<R>(d, r->phi_t, N, N, 0, s); break;
+            case FFT_FIELD_FP: fp_in<R>(d, r->grain, r->Qg, r->Hpi_t, N, s); break;
+            case FFT_FIELD_RHO_SSD: hist_set(r->hist_c, HIST_RHO, 1, 1, d, N, s); break;
+            case FFT_FIELD_WP: hist_set(r->hist_c, HIST_WP, 1, 1, d, N, s); break;
+            case FFT_FIELD_GS: hist_set(r->hist_c, HIST_GS, 1, 1, d, N, s); break;
+            case FFT_FIELD_HMAX: hist_set(r->hist_c, HIST_HMAX, 0, 1, d, N, s); break;
+            case FFT_FIELD_WCRIT: hist_set(r->hist_c, HIST_WCRIT, 0, 1, d, N, s); break;
+            case FFT_FIELD_GAMMA: hist_set(r->hist_c, HIST_GAMMA, 1, 12, d, N, s); break;
+            case FFT_FIELD_DRIVE: from_double<R>(d, r->drive, N, N, 0, s); break;
+            default: FAIL(r, FFT_ERR_ARG, "field %d cannot be set", field);
+        }
+        r->launches += 1;
+        r->cp_valid = false;
+        CK(r, cudaGetLastError());
+        return FFT_OK;
+    }
+
+    static fft_status init_state(fft_rve_s* r, const double* phi0) {
+        const size_t N = r->g.N;
+        cudaStream_t s = r->st;
+        for (void* p : {r->H, r->Ht, r->Hprev, r->Hpi_t, r->Hpi_tr})
+            CK(r, cudaMemsetAsync(p, 0, 9 * N * sizeof(R), s));
+        for (void* p : {r->P, r->rb9}) CK(r, cudaMemsetAsync(p, 0, 9 * N * sizeof(R), s));
+        CK(r, cudaMemsetAsync(r->K, 0, 81 * N * sizeof(R), s));
+        for (void* p : {r->rho_gnd, r->phi, r->phi_t, r->drive, r->We})
+            CK(r, cudaMemsetAsync(p, 0, N * sizeof(R), s));
+        CK(r, cudaMemsetAsync(r->hist_c, 0, HIST_SLOTS * N * sizeof(double), s));
+        CK(r, cudaMemsetAsync(r->hist_tr, 0, HIST_SLOTS * N * sizeof(double), s));
+        std::vector<double> rho(N, r->mat.rho_ssd0);
+        double* tmp = nullptr;
+        CK(r, cudaMalloc(&tmp, N * sizeof(double)));
+        cudaMemcpyAsync(tmp, rho.data(), N * sizeof(double), cudaMemcpyHostToDevice, s);
+        hist_set(r->hist_c, HIST_RHO, 1, 1, tmp, N, s);
+        hist_set(r->hist_tr, HIST_RHO, 1, 1, tmp, N, s);
+        if (phi0) {
+            cudaMemcpyAsync(tmp, phi0, N * sizeof(double), cudaMemcpyHostToDevice, s);
+            from_double<R>(tmp, r->phi_t, N, N, 0, s);
+            from_double<R>(tmp, r->phi, N, N, 0, s);
+        }
+        cudaStreamSynchronize(s);
+        cudaFree(tmp);
+        CK(r, cudaGetLastError());
+        return FFT_OK;
+    }
+};
+
+// ------------------------------------------------------------------ C ABI
+#define DISPATCH(r, call) ((r)->prec == FFT_PREC_FP64 ? Impl<double>::call : Impl<float>::call)
+
+static void release(fft_rve_s* r) {
+    for (auto& p : r->prof_pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : r->prof_pool) cudaEventDestroy(e);
+    if (r->plans) {
+        cufftDestroy(r->r2c9);
+        cufftDestroy(r->c2r9);
+        cufftDestroy(r->r2c1);
+        cufftDestroy(r->c2r1);
+    }
+    for (void* p : r->allocs) cudaFree(p);
+    if (r->hred) cudaFreeHost(r->hred);
+    if (r->hy) cudaFreeHost(r->hy);
+}
+
+extern "C" {
+
+fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_ids, int n_grains,
+                    const double* euler, const fft_material* mat, const fft_options* opt,
+                    const double* phi0, const uint8_t* elastic_only) {
+    if (!out || !grid || !grain_ids || !euler || !mat || !opt || n_grains <= 0)
+        return FFT_ERR_ARG;
+    *out = nullptr;
+    for (int d = 0; d < 3; ++d)
+        if (grid->n[d] < 1) return FFT_ERR_ARG;
+    if (!(grid->h > 0) || (opt->prec != FFT_PREC_FP64 && opt->prec != FFT_PREC_MIXED))
+        return FFT_ERR_ARG;
+    fft_rve_s* r = new fft_rve_s();
+    r->prec = opt->prec;
+    r->esz = opt->prec == FFT_PREC_FP64 ? 8 : 4;
+    r->mat = *mat;
+    r->opt = *opt;
+    r->h = grid->h;
+    r->ngr = n_grains;
+    r->st = (cudaStream_t)opt->cuda_stream;
+    SGrid& g = r->g;
+    g.n0 = grid->n[0];
+    g.n1 = grid->n[1];
+    g.n2 = grid->n[2];
+    g.n0h = g.n0 / 2 + 1;
+    g.N = (size_t)g.n0 * g.n1 * g.n2;
+    g.Nh = (size_t)g.n0h * g.n1 * g.n2;
+    g.tpl0 = 2 * M_PI / (g.n0 * grid->h);
+    g.tpl1 = 2 * M_PI / (g.n1 * grid->h);
+    g.tpl2 = 2 * M_PI / (g.n2 * grid->h);
+    const size_t N = g.N, Nh = g.Nh;
+    for (size_t v = 0; v < N; ++v)
+        if (grain_ids[v] < 0 || grain_ids[v] >= n_grains) {
+            delete r;
+            return FFT_ERR_ARG;
+        }
+    // constitutive constants (MPa, mm, s); tau*dV in N mm = 1e-3 J
+    const double kT = mat->k_B * mat->T;
+    r->cpp.C11 = mat->C11;
+    r->cpp.C12 = mat->C12;
+    r->cpp.C44 = mat->C44;
+    r->cpp.tau_c0 = mat->tau_c0;
+    r->cpp.mu_b = mat->mu * mat->b;
+    r->cpp.g0 = mat->rho_m * mat->b * mat->b * mat->nu_D * std::exp(-mat->dF / kT);
+    r->cpp.sT = kT / (mat->dV * 1e-3);
+    r->cpp.lambda_h = mat->lambda_h;
+    r->cpp.xi_store = mat->xi_store;
+    r->cpp.G_crit = mat->G_crit;
+    r->cpp.inv_b = 1.0 / mat->b;
+    r->cpp.tol_local = opt->tol_local;
+    r->cpp.max_local = opt->max_local;
+    const double I9[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    std::memcpy(r->Fbar_t, I9, sizeof(I9));
+    std::memcpy(r->Fbar, I9, sizeof(I9));
+    const size_t es = r->esz, cs = 2 * r->esz;
+    const int m = std::max(1, std::min(opt->restart, kMaxRestart));
+    fft_status s = FFT_OK;
+#define AL(ptr, bytes)                                    \
+    do {                                                  \
+        s = dalloc(r, (void**)&(ptr), (bytes));           \
+        if (s != FFT_OK) {                                \
+            release(r);                                   \
+            delete r;                                     \
+            return s;                                     \
+        }                                                 \
+    } while (0)
+    AL(r->H, 9 * N * es);
+    AL(r->Ht, 9 * N * es);
+    AL(r->Hprev, 9 * N * es);
+    AL(r->Hpi_t, 9 * N * es);
+    AL(r->Hpi_tr, 9 * N * es);
+    AL(r->P, 9 * N * es);
+    AL(r->K, 81 * N * es);
+    AL(r->rho_gnd, N * es);
+    AL(r->phi, N * es);
+    AL(r->phi_t, N * es);
+    AL(r->drive, N * es);
+    AL(r->We, N * es);
+    AL(r->hist_c, HIST_SLOTS * N * sizeof(double));
+    AL(r->hist_tr, HIST_SLOTS * N * sizeof(double));
+    AL(r->grain, N * sizeof(int32_t));
+    AL(r->Qg, 9 * (size_t)n_grains * sizeof(double));
+    AL(r->G81, 81 * sizeof(double));
+    AL(r->Kbar, 81 * sizeof(double));
+    AL(r->rb9, 9 * N * es);
+    AL(r->cb9, 9 * Nh * cs);
+    AL(r->V, (size_t)(m + 1) * 3 * Nh * cs);
+    AL(r->x, 3 * Nh * cs);
+    AL(r->b, 3 * Nh * cs);
+    AL(r->w, 3 * Nh * cs);
+    AL(r->pfx, N * es);
+    AL(r->pfr, N * es);
+    AL(r->pfz, N * es);
+    AL(r->pfp, N * es);
+    AL(r->pft, N * es);
+    AL(r->pfq, N * es);
+    AL(r->part, (size_t)kRedSlots * kRedBlocks * sizeof(double));
+    AL(r->red, kRedSlots * sizeof(double));
+    AL(r->dy, kMaxRestart * sizeof(double));
+    AL(r->dfail, sizeof(int));
+    if (elastic_only) AL(r->elastic, N);
+#undef AL
+    if (cudaMallocHost((void**)&r->hred, kRedSlots * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&r->hy, kMaxRestart * sizeof(double)) != cudaSuccess) {
+        release(r);
+        delete r;
+        return FFT_ERR_OOM;
+    }
+    std::vector<double> Q(9 * (size_t)n_grains);
+    for (int gi = 0; gi < n_grains; ++gi) bunge_Q(euler + 3 * gi, Q.data() + 9 * gi);
+    double G81[81];
+    gnd_metric(G81);
+    cudaMemcpyAsync(r->grain, grain_ids, N * sizeof(int32_t), cudaMemcpyHostToDevice, r->st);
+    cudaMemcpyAsync(r->Qg, Q.data(), Q.size() * sizeof(double), cudaMemcpyHostToDevice, r->st);
+    cudaMemcpyAsync(r->G81, G81, sizeof(G81), cudaMemcpyHostToDevice, r->st);
+    if (elastic_only)
+        cudaMemcpyAsync(r->elastic, elastic_only, N, cudaMemcpyHostToDevice, r->st);
+    upload_slip_table(r->st);
+    // cuFFT plans: dims slowest-first (n2, n1, n0); 9-field batches use the
+    // contiguous component-major layout.
+    int dims[3] = {g.n2, g.n1, g.n0};
+    const cufftType tf = r->prec == FFT_PREC_FP64 ? CUFFT_D2Z : CUFFT_R2C;
+    const cufftType ti = r->prec == FFT_PREC_FP64 ? CUFFT_Z2D : CUFFT_C2R;
+    if (cufftPlanMany(&r->r2c9, 3, dims, nullptr, 1, (int)N, nullptr, 1, (int)Nh, tf, 9) !=
+            CUFFT_SUCCESS ||
+        cufftPlanMany(&r->c2r9, 3, dims, nullptr, 1, (int)Nh, nullptr, 1, (int)N, ti, 9) !=
+            CUFFT_SUCCESS ||
+        cufftPlanMany(&r->r2c1, 3, dims, nullptr, 1, (int)N, nullptr, 1, (int)Nh, tf, 1) !=
+            CUFFT_SUCCESS ||
+        cufftPlanMany(&r->c2r1, 3, dims, nullptr, 1, (int)Nh, nullptr, 1, (int)N, ti, 1) !=
+            CUFFT_SUCCESS) {
+        release(r);
+        delete r;
+        return FFT_ERR_CUFFT;
+    }
+    r->plans = true;
+    cufftSetStream(r->r2c9, r->st);
+    cufftSetStream(r->c2r9, r->st);
+    cufftSetStream(r->r2c1, r->st);
+    cufftSetStream(r->c2r1, r->st);
+    s = DISPATCH(r, init_state(r, phi0));
+    if (s == FFT_OK && cudaStreamSynchronize(r->st) != cudaSuccess) s = FFT_ERR_CUDA;
+    if (s != FFT_OK) {
+        release(r);
+        delete r;
+        return s;
+    }
+    *out = r;
+    return FFT_OK;
+}
+
+fft_status apply_increment(fft_rve_t r, const double Fbar_target[9], double dt) {
+    if (!r || !Fbar_target || !(dt >= 0)) return FFT_ERR_ARG;
+    return DISPATCH(r, apply_increment(r, Fbar_target, dt));
+}
+
+fft_status solve_equilibrium(fft_rve_t r, fft_stats* st) {
+    if (!r) return FFT_ERR_ARG;
+    return DISPATCH(r, solve_equilibrium(r, st));
+}
+
+fft_status update_damage(fft_rve_t r, fft_stats* st) {
+    if (!r) return FFT_ERR_ARG;
+    return DISPATCH(r, update_damage(r, st));
+}
+
+fft_status commit_increment(fft_rve_t r) {
+    if (!r) return FFT_ERR_ARG;
+    fft_status s = DISPATCH(r, commit(r));
+    if (s == FFT_OK && cudaStreamSynchronize(r->st) != cudaSuccess) return FFT_ERR_CUDA;
+    return s;
+}
+
+fft_status run_increment(fft_rve_t r, const double Fbar_target[9], double dt, fft_stats* st) {
+    if (!r || !Fbar_target || !(dt >= 0)) return FFT_ERR_ARG;
+    if (st) std::memset(st, 0, sizeof(*st));
+    fft_status s = DISPATCH(r, run_increment(r, Fbar_target, dt, st));
+    if (s == FFT_OK && cudaStreamSynchronize(r->st) != cudaSuccess) return FFT_ERR_CUDA;
+    return s;
+}
+
+fft_status fields_out(fft_rve_t r, int field, void* dst, size_t bytes, int dst_is_device) {
+    if (!r || !dst) return FFT_ERR_ARG;
+    int nc = 1;
+    if (field == FFT_FIELD_F || field == FFT_FIELD_FT || field == FFT_FIELD_P ||
+        field == FFT_FIELD_PU || field == FFT_FIELD_FP)
+        nc = 9;
+    else if (field == FFT_FIELD_GAMMA)
+        nc = 12;
+    else if (field == FFT_FIELD_K)
+        nc = 81;
+    const size_t need = (size_t)nc * r->g.N * sizeof(double);
+    if (bytes < need) FAIL(r, FFT_ERR_ARG, "fields_out: %zu bytes < %zu", bytes, need);
+    double* d = (double*)dst;
+    double* tmp = nullptr;
+    if (!dst_is_device) {
+        if (cudaMalloc(&tmp, need) != cudaSuccess) FAIL(r, FFT_ERR_OOM, "fields_out staging");
+        d = tmp;
+    }
+    fft_status s = DISPATCH(r, fields_out(r, field, d));
+    if (s == FFT_OK && !dst_is_device)
+        if (cudaMemcpyAsync(dst, tmp, need, cudaMemcpyDeviceToHost, r->st) != cudaSuccess)
+            s = FFT_ERR_CUDA;
+    if (cudaStreamSynchronize(r->st) != cudaSuccess && s == FFT_OK) s = FFT_ERR_CUDA;
+    if (tmp) cudaFree(tmp);
+    return s;
+}
+
+fft_status fields_in(fft_rve_t r, int field, const double* src, size_t bytes) {
+    if (!r || !src) return FFT_ERR_ARG;
+    int nc = 1;
+    if (field == FFT_FIELD_F || field == FFT_FIELD_FT || field == FFT_FIELD_FP)
+        nc = 9;
+    else if (field == FFT_FIELD_GAMMA)
+        nc = 12;
+    const size_t need = (size_t)nc * r->g.N * sizeof(double);
+    if (bytes < need) FAIL(r, FFT_ERR_ARG, "fields_in: %zu bytes < %zu", bytes, need);
+    double* tmp = nullptr;
+    if (cudaMalloc(&tmp, need) != cudaSuccess) FAIL(r, FFT_ERR_OOM, "fields_in staging");
+    fft_status s = FFT_OK;
+    if (cudaMemcpyAsync(tmp, src, need, cudaMemcpyHostToDevice, r->st) != cudaSuccess)
+        s = FFT_ERR_CUDA;
+    if (s == FFT_OK) s = DISPATCH(r, fields_in(r, field, tmp));
+    if (cudaStreamSynchronize(r->st) != cudaSuccess && s == FFT_OK) s = FFT_ERR_CUDA;
+    cudaFree(tmp);
+    return s;
+}
+
+fft_status eval_constitutive(fft_rve_t r, double dt, int with_history, int* local_fail) {
+    if (!r || !(dt >= 0)) return FFT_ERR_ARG;
+    r->dt = dt;
+    return DISPATCH(r, cp(r, with_history != 0, local_fail));
+}
+
+fft_status eval_gnd(fft_rve_t r) {
+    if (!r) return FFT_ERR_ARG;
+    fft_status s = DISPATCH(r, gnd(r));
+    if (s == FFT_OK && cudaStreamSynchronize(r->st) != cudaSuccess) return FFT_ERR_CUDA;
+    return s;
+}
+
+fft_status solve_phase_field(fft_rve_t r, int* iters) {
+    if (!r) return FFT_ERR_ARG;
+    double o4[4];
+    int it = 0;
+    fft_status s = DISPATCH(r, phase_field(r, &it, o4));
+    if (iters) *iters = it;
+    return s;
+}
+
+size_t rve_device_bytes(fft_rve_t r) { return r ? r->bytes : 0; }
+
+fft_status rve_profile(fft_rve_t r, unsigned mask) {
+    if (!r) return FFT_ERR_ARG;
+    r->prof_mask = mask & 0xffffu;
+    return FFT_OK;
+}
+
+fft_status rve_profile_read(fft_rve_t r, double* ms, long long* counts, int reset) {
+    if (!r || !ms || !counts) return FFT_ERR_ARG;
+    if (cudaStreamSynchronize(r->st) != cudaSuccess) return FFT_ERR_CUDA;
+    prof_collect(r);
+    for (int i = 0; i < 16; ++i) {
+        ms[i] = r->prof_ms[i];
+        counts[i] = r->prof_cnt[i];
+        if (reset) {
+            r->prof_ms[i] = 0;
+            r->prof_cnt[i] = 0;
+        }
+    }
+    return FFT_OK;
+}
+
+long long rve_kernel_launches(fft_rve_t r) { return r ? r->launches : 0; }
+
+void rve_destroy(fft_rve_t r) {
+    if (!r) return;
+    cudaStreamSynchronize(r->st);
+    release(r);
+    delete r;
+}
+
+const char* fft_last_error(fft_rve_t r) { return r ? r->err.c_str() : "null handle"; }
+
+}  // extern "C"

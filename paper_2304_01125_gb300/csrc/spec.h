@@ -1,0 +1,54 @@
+// Launchers of the Fourier-space, vector and reduction kernels
+// (kernels_spec.cu), instantiated for float and double bulk types.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace fatfft {
+
+// Grid and half-spectrum geometry; tpl_i = 2 pi / L_i.
+struct SGrid {
+    int n0, n1, n2, n0h;
+    size_t N, Nh;
+    double tpl0, tpl1, tpl2;
+};
+struct Mat9 {
+    double a[9];
+};
+
+void finalize_sum(const double* part, int nvals, double scale, double* out, cudaStream_t s);
+void finalize_max(const double* part, int nvals, double* out, cudaStream_t s);
+
+template <typename R> void add_uniform(void* H, const void* Ht, const double* d, size_t N, cudaStream_t s);
+template <typename R> void fp_sample(const void* Hpi, const int32_t* grain, const double* Qg, void* out, size_t N, cudaStream_t s);
+template <typename R> void nye(void* F, const SGrid& g, double l2, cudaStream_t s);
+template <typename R> void gnd_rho(const void* Lam, const int32_t* grain, const double* Qg, const double* G81, double inv_b, void* rho, size_t N, cudaStream_t s);
+template <typename R> void kbar(const void* K, const void* phi, double kres, size_t N, double* part, cudaStream_t s);
+template <typename R> void degrade(const void* P, const void* phi, double kres, void* out, size_t N, cudaStream_t s);
+template <typename R> void residual(const void* Ph, const SGrid& g, void* b, double* part, cudaStream_t s);
+template <typename R> void precond_grad(const void* vin, double scale, void* vout, const double* Kbar, const SGrid& g, void* G, int use_pre, cudaStream_t s);
+template <typename R> void tangent_apply(void* G, const void* K, const void* phi, double kres, size_t N, cudaStream_t s);
+template <typename R> void contract(const void* T, const SGrid& g, void* w, cudaStream_t s);
+template <typename R> void mdot(const void* w, const void* V, size_t vstride, int nv, int with_norm, const SGrid& g, double* part, cudaStream_t s);
+template <typename R> void gs_update(void* w, const void* V, size_t vstride, int nv, const double* h, size_t n3, cudaStream_t s);
+template <typename R> void xupdate(void* x, const void* V, size_t vstride, int k, const double* y, const double* Kbar, const SGrid& g, cudaStream_t s);
+template <typename R> void axpby(void* out, const void* a, const void* b, double alpha, double beta, size_t n, cudaStream_t s);
+template <typename R> void fupdate(void* H, const void* G, const void* Ht, size_t N, double* part, cudaStream_t s);
+template <typename R> void maxdiff(const void* a, const void* b, size_t n, double* part, cudaStream_t s);
+template <typename R> void maxval(const void* a, size_t n, double* part, cudaStream_t s);
+template <typename R> void pbar(const void* P, const void* phi, double kres, size_t N, double* part, cudaStream_t s);
+template <typename R> void pf_spec(void* f, const SGrid& g, double l2, int mode, cudaStream_t s);
+template <typename R> void pf_init(const void* x, const void* lapx, const void* S, void* r, size_t N, double* part, cudaStream_t s);
+template <typename R> void rdot(const void* a, const void* b, size_t N, double* part, cudaStream_t s);
+template <typename R> void pf_q(const void* t, const void* p, const void* S, void* q, size_t N, double* part, cudaStream_t s);
+template <typename R> void pf_xr(void* x, void* r, const void* p, const void* q, double alpha, size_t N, double* part, cudaStream_t s);
+template <typename R> void pf_pt(void* p, void* t, const void* z, const void* r, double beta, size_t N, cudaStream_t s);
+template <typename R> void pf_clamp(const void* x, const void* phi_t, void* phi, size_t N, double* part, cudaStream_t s);
+template <typename R> void to_double(const void* src, double* dst, size_t n, size_t N, int add_eye, cudaStream_t s);
+template <typename R> void from_double(const double* src, void* dst, size_t n, size_t N, int sub_eye, cudaStream_t s);
+template <typename R> void fp_in(const double* Fp, const int32_t* grain, const double* Qg, void* Hpi, size_t N, cudaStream_t s);
+void hist_sum(const double* hist, int slot, int comp, int count, double* dst, size_t N, cudaStream_t s);
+void hist_set(double* hist, int slot, int comp, int count, const double* src, size_t N, cudaStream_t s);
+
+}  // namespace fatfft

@@ -1,0 +1,266 @@
+"""ctypes binding of ``libfatiguefft.so`` (declared in ``include/fatiguefft.h``).
+
+Argument marshalling only: every stage of the solve runs in the library's
+CUDA kernels.  Importing works without a GPU; creating a handle needs the
+built library and a CUDA device and raises otherwise (there is no CPU path).
+PyTorch, when given, supplies the CUDA stream and device buffers.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfatiguefft.so")
+
+FFT_OK, FFT_ERR_ARG, FFT_ERR_OOM, FFT_ERR_CUDA = 0, -1, -2, -3
+FFT_ERR_CUFFT, FFT_ERR_NOT_CONVERGED, FFT_ERR_NONFINITE, FFT_ERR_STATE = -4, -5, -6, -7
+FFT_PREC_FP64, FFT_PREC_MIXED = 0, 1
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_CUFFT",
+          -5: "ERR_NOT_CONVERGED", -6: "ERR_NONFINITE", -7: "ERR_STATE"}
+
+# field name -> (id, components)
+FIELDS = {"F": (0, 9), "P": (1, 9), "phi": (2, 1), "Fp": (3, 9), "rho_ssd": (4, 1),
+          "rho_gnd": (5, 1), "Wp": (6, 1), "Gs": (7, 1), "Hmax": (8, 1), "Wcrit": (9, 1),
+          "drive": (10, 1), "gamma": (11, 12), "Ft": (12, 9), "phi_t": (13, 1), "We": (14, 1),
+          "K": (15, 81), "Pu": (16, 9)}
+SYMBOLS = ["init_rve", "apply_increment", "solve_equilibrium", "update_damage",
+           "commit_increment", "run_increment", "fields_out", "fields_in", "eval_constitutive",
+           "eval_gnd", "solve_phase_field", "rve_device_bytes", "rve_destroy", "fft_last_error",
+           "rve_kernel_launches", "rve_profile", "rve_profile_read"]
+KERNEL_FAMILIES = ["constitutive", "tangent_apply", "precond_grad", "contract", "gmres_dot",
+                   "gs_update", "gmres_xupdate", "kbar", "residual", "f_update", "phase_field",
+                   "gnd", "cufft_9field", "cufft_scalar", "reductions", "other"]
+
+
+class Grid(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("h", C.c_double)]
+
+
+class Material(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "C11", "C12", "C44", "tau_c0", "b", "nu_D", "k_B", "T", "dF", "rho_m", "lambda_h",
+        "dV", "mu", "xi_store", "rho_ssd0", "G_crit", "ell", "ell_Fp", "k_res")]
+
+
+class Options(C.Structure):
+    _fields_ = [("tol_stag", C.c_double), ("tol_newton", C.c_double), ("tol_lin", C.c_double),
+                ("tol_pf", C.c_double), ("tol_local", C.c_double),
+                ("max_stag", C.c_int), ("max_newton", C.c_int), ("max_lin", C.c_int),
+                ("max_pf", C.c_int), ("max_local", C.c_int), ("restart", C.c_int),
+                ("prec", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("stag_it", C.c_int), ("newton_it", C.c_int), ("lin_it_total", C.c_int),
+                ("pf_it_total", C.c_int), ("local_fail", C.c_int), ("converged", C.c_int),
+                ("skipped_equilibrium", C.c_int), ("res_F", C.c_double),
+                ("res_phi", C.c_double), ("Pbar", C.c_double * 9), ("cracked", C.c_long)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["Pbar"] = list(self.Pbar)
+        return d
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2304_01125_gb300.build")
+    L = C.CDLL(path)
+    vp, dp = C.c_void_p, C.POINTER(C.c_double)
+    L.init_rve.argtypes = [C.POINTER(vp), C.POINTER(Grid), C.c_void_p, C.c_int, C.c_void_p,
+                           C.POINTER(Material), C.POINTER(Options), C.c_void_p, C.c_void_p]
+    L.apply_increment.argtypes = [vp, dp, C.c_double]
+    L.solve_equilibrium.argtypes = [vp, C.POINTER(Stats)]
+    L.update_damage.argtypes = [vp, C.POINTER(Stats)]
+    L.commit_increment.argtypes = [vp]
+    L.run_increment.argtypes = [vp, dp, C.c_double, C.POINTER(Stats)]
+    L.fields_out.argtypes = [vp, C.c_int, C.c_void_p, C.c_size_t, C.c_int]
+    L.fields_in.argtypes = [vp, C.c_int, C.c_void_p, C.c_size_t]
+    L.eval_constitutive.argtypes = [vp, C.c_double, C.c_int, C.POINTER(C.c_int)]
+    L.eval_gnd.argtypes = [vp]
+    L.solve_phase_field.argtypes = [vp, C.POINTER(C.c_int)]
+    L.rve_device_bytes.argtypes = [vp]
+    L.rve_device_bytes.restype = C.c_size_t
+    L.rve_kernel_launches.argtypes = [vp]
+    L.rve_kernel_launches.restype = C.c_longlong
+    L.rve_profile.argtypes = [vp, C.c_uint]
+    L.rve_profile.restype = C.c_int
+    L.rve_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]
+    L.rve_profile_read.restype = C.c_int
+    L.rve_destroy.argtypes = [vp]
+    L.rve_destroy.restype = None
+    L.fft_last_error.argtypes = [vp]
+    L.fft_last_error.restype = C.c_char_p
+    for t in ("init_rve", "apply_increment", "solve_equilibrium", "update_damage",
+              "commit_increment", "run_increment", "fields_out", "fields_in",
+              "eval_constitutive", "eval_gnd", "solve_phase_field"):
+        getattr(L, t).restype = C.c_int
+    _lib = L
+    return L
+
+
+class FFTError(RuntimeError):
+    def __init__(self, call, status, msg):
+        super().__init__(f"{call}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _material(params):
+    m = Material()
+    for k, _ in Material._fields_:
+        setattr(m, k, float(params[k]))
+    return m
+
+
+def _options(opts, prec, stream):
+    o = Options()
+    for k in ("tol_stag", "tol_newton", "tol_lin", "tol_pf", "tol_local"):
+        setattr(o, k, float(opts[k]))
+    for k in ("max_stag", "max_newton", "max_lin", "max_pf", "max_local", "restart"):
+        setattr(o, k, int(opts[k]))
+    o.prec = FFT_PREC_FP64 if prec in ("fp64", FFT_PREC_FP64) else FFT_PREC_MIXED
+    o.cuda_stream = stream or None
+    return o
+
+
+class RVE:
+    """One RVE handle of the library.  ``prec``: "fp64" or "mixed".
+    ``stream``: a ``torch.cuda.Stream`` or raw ``cudaStream_t`` (int)."""
+
+    def __init__(self, n, h, grain_ids, euler, params, opts, prec="fp64", phi0=None,
+                 elastic_only=None, stream=None):
+        L = load()
+        self.n = tuple(int(x) for x in n)
+        self.N = int(np.prod(self.n))
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self._stream = stream
+        g = Grid()
+        g.n[:] = self.n
+        g.h = float(h)
+        gid = np.ascontiguousarray(grain_ids, dtype=np.int32).reshape(-1)
+        eul = np.ascontiguousarray(euler, dtype=np.float64).reshape(-1)
+        assert gid.size == self.N
+        p0 = None if phi0 is None else np.ascontiguousarray(phi0, dtype=np.float64).reshape(-1)
+        eo = None if elastic_only is None else np.ascontiguousarray(elastic_only,
+                                                                    dtype=np.uint8).reshape(-1)
+        self._m = _material(params)
+        self._o = _options(opts, prec, stream)
+        h_ = C.c_void_p()
+        s = L.init_rve(C.byref(h_), C.byref(g), gid.ctypes.data, int(eul.size // 3),
+                       eul.ctypes.data, C.byref(self._m), C.byref(self._o),
+                       None if p0 is None else p0.ctypes.data,
+                       None if eo is None else eo.ctypes.data)
+        if s != FFT_OK:
+            raise FFTError("init_rve", s, "")
+        self._h = h_
+
+    # -- helpers
+    def _check(self, call, s):
+        if s != FFT_OK:
+            raise FFTError(call, s, load().fft_last_error(self._h).decode())
+        return s
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- the C calls
+    def apply_increment(self, Fbar, dt):
+        F = np.ascontiguousarray(Fbar, dtype=np.float64).reshape(9)
+        return self._check("apply_increment", load().apply_increment(
+            self._h, F.ctypes.data_as(C.POINTER(C.c_double)), float(dt)))
+
+    def solve_equilibrium(self, st=None, check=True):
+        st = st or Stats()
+        s = load().solve_equilibrium(self._h, C.byref(st))
+        if check:
+            self._check("solve_equilibrium", s)
+        return s, st
+
+    def update_damage(self, st=None, check=True):
+        st = st or Stats()
+        s = load().update_damage(self._h, C.byref(st))
+        if check:
+            self._check("update_damage", s)
+        return s, st
+
+    def commit_increment(self):
+        return self._check("commit_increment", load().commit_increment(self._h))
+
+    def run_increment(self, Fbar, dt, check=True):
+        F = np.ascontiguousarray(Fbar, dtype=np.float64).reshape(9)
+        st = Stats()
+        s = load().run_increment(self._h, F.ctypes.data_as(C.POINTER(C.c_double)), float(dt),
+                                 C.byref(st))
+        if check:
+            self._check("run_increment", s)
+        return s, st.as_dict()
+
+    def field(self, name):
+        fid, nc = FIELDS[name]
+        out = np.empty(nc * self.N, dtype=np.float64)
+        self._check("fields_out", load().fields_out(self._h, fid, out.ctypes.data, out.nbytes, 0))
+        return out.reshape(nc, self.N) if nc > 1 else out
+
+    def field_to_device(self, name, dst_ptr, nbytes):
+        fid, _ = FIELDS[name]
+        return self._check("fields_out", load().fields_out(self._h, fid, int(dst_ptr),
+                                                           int(nbytes), 1))
+
+    def set_field(self, name, values):
+        fid, nc = FIELDS[name]
+        a = np.ascontiguousarray(values, dtype=np.float64).reshape(-1)
+        assert a.size == nc * self.N
+        return self._check("fields_in", load().fields_in(self._h, fid, a.ctypes.data, a.nbytes))
+
+    def eval_constitutive(self, dt, with_history=False):
+        nf = C.c_int(0)
+        self._check("eval_constitutive", load().eval_constitutive(self._h, float(dt),
+                                                                  int(with_history),
+                                                                  C.byref(nf)))
+        return nf.value
+
+    def eval_gnd(self):
+        return self._check("eval_gnd", load().eval_gnd(self._h))
+
+    def solve_phase_field(self):
+        it = C.c_int(0)
+        self._check("solve_phase_field", load().solve_phase_field(self._h, C.byref(it)))
+        return it.value
+
+    def profile(self, families):
+        """Time the given kernel families (names from KERNEL_FAMILIES)."""
+        mask = 0
+        for f in families:
+            mask |= 1 << KERNEL_FAMILIES.index(f)
+        return self._check("rve_profile", load().rve_profile(self._h, mask))
+
+    def profile_read(self, reset=True):
+        ms = (C.c_double * 16)()
+        cnt = (C.c_longlong * 16)()
+        self._check("rve_profile_read", load().rve_profile_read(self._h, ms, cnt, int(reset)))
+        return {f: (ms[i], cnt[i]) for i, f in enumerate(KERNEL_FAMILIES) if cnt[i]}
+
+    @property
+    def device_bytes(self):
+        return load().rve_device_bytes(self._h)
+
+    @property
+    def kernel_launches(self):
+        return load().rve_kernel_launches(self._h)

@@ -1,0 +1,57 @@
+"""The C ABI library builds, loads and exports every call include/fatiguefft.h
+declares; argument checks that need no GPU return FFT_ERR_ARG.  No compute
+call runs here (there may be no GPU)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from paper_2304_01125_gb300 import build as B
+from paper_2304_01125_gb300 import fatiguefft as FF
+from paper_2304_01125_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fatiguefft.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b([A-Za-z_]\w*)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "return", "sizeof")))
+
+
+def test_library_builds_and_exports_every_declared_call():
+    path = B.build()
+    L = C.CDLL(path)
+    decl = _declared()
+    assert len(decl) >= 15
+    for name in decl:
+        assert hasattr(L, name), name
+    assert set(FF.SYMBOLS) <= set(decl)
+
+
+def test_init_rejects_bad_arguments_without_touching_the_gpu():
+    L = FF.load(B.build())
+    g = FF.Grid()
+    g.n[:] = (0, 4, 4)
+    g.h = I.VOXEL_MM
+    m = FF._material(I.material("baseline"))
+    o = FF._options(I.solver_options("paper"), "fp64", None)
+    gid = np.zeros(16, dtype=np.int32)
+    eul = np.zeros(3)
+    h = C.c_void_p()
+    assert L.init_rve(C.byref(h), C.byref(g), gid.ctypes.data, 1, eul.ctypes.data, C.byref(m),
+                      C.byref(o), None, None) == FF.FFT_ERR_ARG
+    g.n[:] = (4, 2, 2)
+    g.h = -1.0
+    assert L.init_rve(C.byref(h), C.byref(g), gid.ctypes.data, 1, eul.ctypes.data, C.byref(m),
+                      C.byref(o), None, None) == FF.FFT_ERR_ARG
+    g.h = I.VOXEL_MM
+    bad = np.full(16, 3, dtype=np.int32)  # grain id out of range
+    assert L.init_rve(C.byref(h), C.byref(g), bad.ctypes.data, 1, eul.ctypes.data, C.byref(m),
+                      C.byref(o), None, None) == FF.FFT_ERR_ARG
+    assert L.init_rve(None, C.byref(g), gid.ctypes.data, 1, eul.ctypes.data, C.byref(m),
+                      C.byref(o), None, None) == FF.FFT_ERR_ARG
+    assert L.apply_increment(None, None, 1.0) == FF.FFT_ERR_ARG
+    assert L.rve_device_bytes(None) == 0

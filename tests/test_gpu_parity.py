@@ -1,0 +1,276 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU
+oracle on the same seeded inputs.
+
+Tolerances (relative L2 over each field unless noted):
+  * FP64 path: 1e-9 for increments run at the tight "parity64" preset
+    (Newton/staggered 1e-9, Krylov 1e-10); stage kernels tighter.
+  * mixed path (FP32 bulk, FP64 reductions): 1e-4 per field, the stress and
+    damage bound the method is held to.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2304_01125_gb300 import build as B
+from paper_2304_01125_gb300 import fatiguefft as FF
+from paper_2304_01125_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+H = I.VOXEL_MM
+MAT = I.material("baseline")
+PREC = ["fp64", "mixed"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    B.build()
+    FF.load()
+
+
+def rel(a, b, floor=1e-300):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), floor))
+
+
+def opts_for(prec, **kw):
+    return I.solver_options("parity64" if prec == "fp64" else "parity32", **kw)
+
+
+def q_per_voxel(gid, eul):
+    Qg = np.stack([O.euler_to_Q(e).reshape(9) for e in eul])
+    return Qg[gid]
+
+
+def random_state(n, seed, grains=3, amp_f=3e-3, amp_p=1e-3):
+    rng = np.random.default_rng(seed)
+    N = int(np.prod(n))
+    gid, eul = I.voronoi(n, grains, seed)
+    F = np.eye(3).reshape(9, 1) + amp_f * rng.standard_normal((9, N))
+    Fp = np.eye(3).reshape(9, 1) + amp_p * rng.standard_normal((9, N))
+    rho = MAT["rho_ssd0"] * (1 + rng.random(N))
+    return gid, eul, F, Fp, rho
+
+
+# ------------------------------------------------------------- K-CP kernel
+@pytest.mark.parametrize("prec", PREC)
+def test_constitutive_kernel_matches_oracle(prec):
+    n = (6, 5, 4)
+    gid, eul, F, Fp, rho = random_state(n, 7)
+    r = FF.RVE(n, H, gid, eul, MAT, opts_for(prec), prec=prec)
+    r.set_field("F", F)
+    r.set_field("Fp", Fp)
+    r.set_field("rho_ssd", rho)
+    r.eval_gnd()
+    rg = r.field("rho_gnd")
+    dt = 1.0
+    nf = r.eval_constitutive(dt, with_history=True)
+    assert nf == 0
+    P, K, We = r.field("Pu"), r.field("K"), r.field("We")
+    Qv = q_per_voxel(gid, eul)
+    Po, Ko, Weo, active = [], [], [], 0
+    for v in range(gid.size):
+        Q = Qv[v].reshape(3, 3)
+        FpL = Q.T @ Fp[:, v].reshape(3, 3) @ Q
+        o = O.cp_point(MAT, Q, F[:, v], FpL, rho[v], rg[v], dt, tol_local=1e-11)
+        assert o["fail"] == 0
+        active += int(np.any(o["dgamma"] != 0))
+        Po.append(o["P"].reshape(9))
+        Ko.append(o["K"].reshape(81))
+        Weo.append(o["We_plus"])
+    Po, Ko, Weo = np.array(Po).T, np.array(Ko).T, np.array(Weo)
+    assert active > gid.size // 4  # the states are plastic
+    tp, tk = (1e-11, 1e-8) if prec == "fp64" else (2e-6, 2e-3)
+    assert rel(P, Po) < tp
+    assert rel(K, Ko) < tk
+    assert rel(We, Weo) < (1e-10 if prec == "fp64" else 1e-5)
+
+
+# -------------------------------------------------------------- GND stage
+@pytest.mark.parametrize("prec", PREC)
+def test_gnd_stage_matches_oracle(prec):
+    n = (8, 6, 5)
+    N = int(np.prod(n))
+    rng = np.random.default_rng(3)
+    gid, eul = I.voronoi(n, 4, 3)
+    x = np.stack(np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]),
+                             indexing="ij"), 0).reshape(3, N)[::-1] * H
+    Fp = np.tile(np.eye(3).reshape(9, 1), (1, N)).astype(float)
+    for c in range(9):
+        for _ in range(3):
+            k = 2 * np.pi * rng.integers(-2, 3, size=3) / (np.array(n) * H)
+            Fp[c] += 1e-3 * rng.standard_normal() * np.sin(k @ x + rng.random() * 6)
+    r = FF.RVE(n, H, gid, eul, MAT, opts_for(prec), prec=prec)
+    r.set_field("Fp", Fp)
+    r.eval_gnd()
+    rho = r.field("rho_gnd")
+    _, rho_o = O.gnd_field(n, H, MAT, q_per_voxel(gid, eul), Fp)
+    assert rho_o.max() > 0
+    assert rel(rho, rho_o) < (1e-10 if prec == "fp64" else 1e-4)
+
+
+# ---------------------------------------------------------- phase field
+@pytest.mark.parametrize("prec", PREC)
+def test_phase_field_stage_matches_oracle(prec):
+    n = (10, 8, 6)
+    N = int(np.prod(n))
+    rng = np.random.default_rng(5)
+    S = np.maximum(0.0, rng.standard_normal(N)) * 0.3
+    phit = np.where(rng.random(N) > 0.9, 0.95, 0.0)
+    gid, eul = I.single_crystal(n)
+    r = FF.RVE(n, H, gid, eul, MAT, opts_for(prec), prec=prec, phi0=phit)
+    r.set_field("drive", S)
+    r.set_field("phi", phit)
+    it = r.solve_phase_field()
+    phi = r.field("phi")
+    phi_o, it_o, st = O.phase_field(n, H, MAT["ell"], S, phit, phit, tol=1e-13)
+    assert st == 0 and it > 0
+    assert np.all(phi >= phit)
+    assert rel(phi, phi_o) < (1e-9 if prec == "fp64" else 1e-5)
+
+
+# -------------------------------------------------------- full increments
+FIELDS_CMP = ["F", "P", "phi", "Fp", "rho_ssd", "Wp", "Gs", "gamma", "Wcrit"]
+
+
+def _compare(gpu, orc, prec, tag):
+    out = {}
+    for f in FIELDS_CMP:
+        a, b = gpu.field(f), orc.field(f)
+        if f in ("F", "Fp"):
+            eye = np.eye(3).reshape(9, 1)
+            a, b = a - eye, b - eye
+        if f == "rho_ssd":
+            a, b = a - MAT["rho_ssd0"], b - MAT["rho_ssd0"]
+        out[f] = rel(a, b, floor=1e-30) if np.abs(b).max() > 0 else float(np.abs(a).max())
+    tol = 1e-9 if prec == "fp64" else 1e-4
+    bad = {k: v for k, v in out.items() if not v < tol}
+    assert not bad, (tag, bad, out)
+    return out
+
+
+def _run_pair(n, gid, eul, prog, prec, mat=MAT, phi0=None, mask=None, opts=None):
+    opts = opts or opts_for(prec)
+    g = FF.RVE(n, H, gid, eul, mat, opts, prec=prec, phi0=phi0, elastic_only=mask)
+    o = O.RVE(n, H, gid, eul, mat, I.solver_options("parity64"), phi0=phi0, elastic_only=mask)
+    hist = []
+    for k, (Fb, dt) in enumerate(prog):
+        sg, stg = g.run_increment(Fb, dt)
+        so, sto = o.run_increment(Fb, dt)
+        assert so == 0 and sg == 0
+        hist.append((_compare(g, o, prec, k), stg, sto))
+    return g, o, hist
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_increments_single_crystal_precrack(prec):
+    """sx16 geometry on a 16x8x4 grid: [100] crystal with the pre-crack plane."""
+    cfg = I.build_config("sx16", n_override=(16, 8, 4))
+    _run_pair(cfg["n"], cfg["grain_ids"], cfg["euler"], cfg["program"][:4], prec,
+              phi0=cfg["phi0"], mask=cfg["elastic_only"])
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_increments_polycrystal_plasticity_and_damage(prec):
+    """Plastic polycrystal with damage switched on early (small G_crit):
+    plasticity, W_crit events and phase-field growth are all exercised."""
+    n = (6, 6, 6)
+    gid, eul = I.voronoi(n, 3, 11)
+    mat = dict(MAT, tau_c0=250.0, G_crit=1e-9, xi_store=1.0)
+    prog = I.uniaxial_cycle_program(0.006, 24, 1)[:5 if prec == "fp64" else 4]
+    g, o, hist = _run_pair(n, gid, eul, prog, prec, mat=mat)
+    assert o.field("gamma").max() > 0
+    if prec == "fp64":
+        assert o.field("phi_t").max() > 0.05
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_ragged_odd_grid(prec):
+    """Odd and non-power-of-two extents (Nyquist rows absent on odd axes)."""
+    n = (5, 7, 3)
+    gid, eul = I.voronoi(n, 3, 2)
+    mat = dict(MAT, tau_c0=250.0)
+    prog = I.uniaxial_cycle_program(0.006, 24, 1)[:4]
+    _run_pair(n, gid, eul, prog, prec, mat=mat)
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_homogeneous_medium_stays_uniform(prec):
+    n = (8, 6, 4)
+    gid, eul = I.single_crystal(n, (0.3, 0.9, 1.7))
+    r = FF.RVE(n, H, gid, eul, MAT, opts_for(prec), prec=prec)
+    prog = I.uniaxial_cycle_program(0.004, 8, 1)[:3]
+    for Fb, dt in prog:
+        s, st = r.run_increment(Fb, dt)
+        assert st["lin_it_total"] == 0
+    F = r.field("F")
+    assert np.abs(F - prog[-1][0][:, None]).max() < (1e-14 if prec == "fp64" else 1e-7)
+
+
+def test_precrack_mirror_symmetry_gpu():
+    cfg = I.build_config("sx16", n_override=(16, 8, 4))
+    r = FF.RVE(cfg["n"], H, cfg["grain_ids"], cfg["euler"], MAT, opts_for("fp64"),
+               prec="fp64", phi0=cfg["phi0"], elastic_only=cfg["elastic_only"])
+    for Fb, dt in cfg["program"][:3]:
+        r.run_increment(Fb, dt)
+    n = cfg["n"]
+    F = r.field("F").reshape(3, 3, n[2], n[1], n[0])
+    sign = np.array([[1, -1, -1], [-1, 1, 1], [-1, 1, 1]])
+    for i in range(3):
+        for j in range(3):
+            assert np.abs(F[i, j] - sign[i, j] * F[i, j][..., ::-1]).max() < 1e-12
+    assert np.abs(F[0, 1]).max() > 1e-6
+
+
+# ----------------------------------------------------------- failure paths
+def test_call_order_errors():
+    n = (4, 4, 4)
+    gid, eul = I.single_crystal(n)
+    r = FF.RVE(n, H, gid, eul, MAT, opts_for("fp64"), prec="fp64")
+    s, _ = r.solve_equilibrium(check=False)
+    assert s == FF.FFT_ERR_STATE
+    s, _ = r.update_damage(check=False)
+    assert s == FF.FFT_ERR_STATE
+    with pytest.raises(FF.FFTError):
+        r.commit_increment()
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_iteration_cap_is_reported(prec):
+    n = (6, 6, 6)
+    gid, eul = I.voronoi(n, 3, 11)
+    r = FF.RVE(n, H, gid, eul, MAT, opts_for(prec, max_lin=1, tol_lin=1e-14), prec=prec)
+    Fb, dt = I.uniaxial_cycle_program(0.004, 8, 1)[0]
+    s, st = r.run_increment(Fb, dt, check=False)
+    assert s == FF.FFT_ERR_NOT_CONVERGED
+    assert r.field("F").shape == (9, 216)  # the handle still answers
+
+
+# ------------------------------------------------- full size, sampled
+@pytest.mark.parametrize("prec", PREC)
+def test_full_size_poly64_sampled(prec):
+    """The timed workload (64^3, 50 grains) in the benchmark's launch
+    configuration: two increments, then the constitutive update at 64
+    sampled voxels against the oracle, and the invariants <F> = Fbar and
+    phi_t <= phi <= 1 over the whole grid."""
+    cfg = I.build_config("poly64")
+    n, gid, eul = cfg["n"], cfg["grain_ids"], cfg["euler"]
+    r = FF.RVE(n, H, gid, eul, MAT, I.solver_options("paper"), prec=prec)
+    for Fb, dt in cfg["program"][:2]:
+        s, st = r.run_increment(Fb, dt)
+    F = r.field("F")
+    assert np.abs(F.mean(axis=1) - Fb).max() < (1e-13 if prec == "fp64" else 1e-7)
+    phi, phit = r.field("phi"), r.field("phi_t")
+    assert np.all(phi >= phit) and np.all(phi <= 1)
+    r.eval_gnd()
+    r.eval_constitutive(dt, with_history=False)
+    P, Fp, rho, rg = r.field("Pu"), r.field("Fp"), r.field("rho_ssd"), r.field("rho_gnd")
+    Qv = q_per_voxel(gid, eul)
+    rng = np.random.default_rng(0)
+    errs = []
+    for v in rng.choice(gid.size, 64, replace=False):
+        Q = Qv[v].reshape(3, 3)
+        FpL = Q.T @ Fp[:, v].reshape(3, 3) @ Q
+        o = O.cp_point(MAT, Q, F[:, v], FpL, rho[v], rg[v], dt, tangent=False)
+        errs.append(np.abs(P[:, v] - o["P"].reshape(9)).max() / np.abs(o["P"]).max())
+    assert max(errs) < (1e-10 if prec == "fp64" else 1e-5)
