@@ -20,9 +20,9 @@
 //    dyads, divided by b;
 //  - Algorithm 1 ratios guarded: converged when ||F_i - F_{i-1}|| <=
 //    tol * max(||F_i - F_t||, 1e-12) (same for phi);
-//  - the Krylov solve stops at max(tol_lin ||b||, 1e-12 ||F{g P}||): below
-//    1e-12 of the stress spectrum the residual is round-off (a residual
-//    already that small gets no correction);
+//  - the Krylov solve stops at max(tol_lin ||b||, 1e-12 s_b) with s_b the
+//    norm of the terms F{g P}_ij xi_j summed into b: below that the residual
+//    is round-off (a residual already that small gets no correction);
 //  - an equilibrium solve whose phase field has not changed since the last
 //    solve is skipped (same problem, same answer), and the increment is then
 //    converged;
@@ -586,10 +586,14 @@ int orc_solve_equilibrium(orc_rve* r, orc_stats* st) {
             xs[i].assign(N, 0.0);
         }
         const double bn = std::sqrt(dot(bv, bv));
-        // a residual at round-off of the stress spectrum needs no correction
+        // round-off scale of b: ||F{gP}_ij xi_j|| before the sum over j
         double pn = 0;
-        for (int c = 0; c < 9; ++c)
-            for (size_t v = 0; v < N; ++v) pn += std::norm(Ph[c][v]);
+        for (size_t v = 0; v < N; ++v) {
+            double xi[3], xid[3];
+            kvec(f, v, xi, xid);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) pn += std::norm(Ph[3 * i + j][v]) * xid[j] * xid[j];
+        }
         pn = std::sqrt(pn);
         const double target = std::max(r->o.tol_lin * bn, 1e-12 * pn);
         int lin_it = 0;

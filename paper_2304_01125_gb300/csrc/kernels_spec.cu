@@ -245,7 +245,8 @@ void degrade(const void* P, const void* phi, double kres, void* out, size_t N, c
 }
 
 // b_i = sum_j F{gP}_ij i xi_j (Eq. momentum / newton right-hand side, sign
-// flipped); partials of ||b||^2 and ||F{gP}||^2 (Hermitian-weighted).
+// flipped); partials of ||b||^2 and of the round-off scale of b,
+// sum_ij |F{gP}_ij xi_j|^2 (Hermitian-weighted).
 template <typename R>
 __global__ void k_residual(const typename Tr<R>::Cx* Ph, SGrid g, typename Tr<R>::Cx* b,
                            double* part) {
@@ -264,7 +265,8 @@ __global__ void k_residual(const typename Tr<R>::Cx* Ph, SGrid g, typename Tr<R>
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 const Cx p = Ph[(3 * i + j) * Nh + e];
-                np += (double)w * ((double)p.x * p.x + (double)p.y * p.y);
+                np += (double)w * ((double)p.x * p.x + (double)p.y * p.y) * (double)xd[j] *
+                      (double)xd[j];
                 const Cx t = cmul_i(p, xd[j]);
                 s.x += t.x;
                 s.y += t.y;
@@ -282,6 +284,50 @@ template <typename R>
 void residual(const void* Ph, const SGrid& g, void* b, double* part, cudaStream_t s) {
     k_residual<R><<<kRedBlocks, kThreads, 0, s>>>((const typename Tr<R>::Cx*)Ph, g,
                                                   (typename Tr<R>::Cx*)b, part);
+}
+
+// Projection onto real fields: on the kx = 0 plane (and kx = n0/2 for even
+// n0) the entries at (ky, kz) and (-ky, -kz) are set to the mean of one and
+// the conjugate of the other; self-conjugate entries lose their imaginary
+// part.  The inverse real transform ignores the anti-Hermitian part, so
+// without this the forward transform's round-off there is a residual the
+// Krylov solver cannot reduce.
+template <typename R>
+__global__ void k_hermitize(typename Tr<R>::Cx* v, int ncomp, SGrid g) {
+    typedef typename Tr<R>::Cx Cx;
+    const int planes = (g.n0 % 2 == 0 && g.n0 > 1) ? 2 : 1;
+    const size_t per = (size_t)g.n1 * g.n2;
+    GRID_STRIDE(t, per * planes * ncomp) {
+        const size_t q = t % per;
+        const int pl = (int)((t / per) % planes);
+        const int c = (int)(t / (per * planes));
+        const int kx = pl == 0 ? 0 : g.n0 / 2;
+        const int ky = (int)(q % g.n1), kz = (int)(q / g.n1);
+        const int py = (g.n1 - ky) % g.n1, pz = (g.n2 - kz) % g.n2;
+        const size_t qp = (size_t)py + (size_t)g.n1 * pz;
+        if (qp < q) continue;  // the partner with the smaller index does the pair
+        Cx* base = v + (size_t)c * g.Nh;
+        const size_t e = (size_t)kx + (size_t)g.n0h * q;
+        const size_t ep = (size_t)kx + (size_t)g.n0h * qp;
+        const Cx a = base[e], b = base[ep];
+        if (qp == q) {
+            Cx r = a;
+            r.y = 0;
+            base[e] = r;
+        } else {
+            Cx m;
+            m.x = R(0.5) * (a.x + b.x);
+            m.y = R(0.5) * (a.y - b.y);
+            base[e] = m;
+            m.y = -m.y;
+            base[ep] = m;
+        }
+    }
+}
+template <typename R>
+void hermitize(void* v, int ncomp, const SGrid& g, cudaStream_t s) {
+    const size_t n = (size_t)g.n1 * g.n2 * ((g.n0 % 2 == 0 && g.n0 > 1) ? 2 : 1) * ncomp;
+    k_hermitize<R><<<grid_for(n), kThreads, 0, s>>>((typename Tr<R>::Cx*)v, ncomp, g);
 }
 
 // -------------------------------------------------------------------- GMRES
@@ -896,6 +942,7 @@ void fp_in(const double* Fp, const int32_t* grain, const double* Qg, void* Hpi, 
     template void tangent_apply<R>(void*, const void*, const void*, double, size_t,             \
                                    cudaStream_t);                                               \
     template void contract<R>(const void*, const SGrid&, void*, cudaStream_t);                  \
+    template void hermitize<R>(void*, int, const SGrid&, cudaStream_t);                         \
     template void mdot<R>(const void*, const void*, size_t, int, int, const SGrid&, double*,    \
                           cudaStream_t);                                                        \
     template void gs_update<R>(void*, const void*, size_t, int, const double*, size_t,          \

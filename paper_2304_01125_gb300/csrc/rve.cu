@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -70,6 +71,7 @@ struct fft_rve_s {
     double Fbar_t[9], Fbar[9], dt = 0;
     int state = ST_NEW, stag_it = 0;
     bool phi_changed = true, skipped = false, converged = false, cp_valid = false;
+    bool verbose = false;  // FATIGUEFFT_VERBOSE: solver traces on stderr
     std::string err;
 };
 
@@ -369,8 +371,9 @@ struct Impl {
         TRY(fwd9(r));
         e = prof_begin(r, KF_CONTRACT);
         contract<R>(r->cb9, r->g, w, r->st);
+        hermitize<R>(w, 3, r->g, r->st);
         prof_end(r, KF_CONTRACT, e);
-        r->launches += 3;
+        r->launches += 4;
         return FFT_OK;
     }
 
@@ -379,7 +382,8 @@ struct Impl {
     // products; Hessenberg least squares on the host.
     static fft_status gmres(fft_rve_s* r, double bn, double pn, int* its) {
         const size_t Nh = r->g.Nh, n3 = 3 * Nh;
-        const double eta = sizeof(R) == 8 ? 1e-12 : 2e-7;
+        // round-off floor relative to the scale of the terms summed into b
+        const double eta = sizeof(R) == 8 ? 1e-12 : 5e-7;
         const double target = std::max(r->opt.tol_lin * bn, eta * pn);
         CK(r, cudaMemsetAsync(r->x, 0, n3 * sizeof(Cx), r->st));
         *its = 0;
@@ -459,6 +463,9 @@ struct Impl {
                 gv[k + 1] = -sn[k] * gv[k];
                 gv[k] = cs[k] * gv[k];
                 hprev = hn;
+                if (r->verbose)
+                    std::fprintf(stderr, "  gmres it %d |r|/|b| %.3e (|b| %.3e, h %.3e)\n", lin,
+                                 std::fabs(gv[k + 1]) / bn, bn, hn);
                 if (std::fabs(gv[k + 1]) <= target || hn == 0.0) {
                     ok = true;
                     ++k;
@@ -509,8 +516,11 @@ struct Impl {
             degrade<R>(r->P, r->phi, r->mat.k_res, r->rb9, N, r->st);
             TRY(fwd9(r));
             residual<R>(r->cb9, r->g, r->b, r->part, r->st);
-            finalize_sum(r->part, 2, 1.0, r->red, r->st);
-            r->launches += 5;
+            finalize_sum(r->part + kRedBlocks, 1, 1.0, r->red + 1, r->st);
+            hermitize<R>(r->b, 3, r->g, r->st);
+            mdot<R>(r->b, nullptr, 0, 0, 1, r->g, r->part, r->st);
+            finalize_sum(r->part, 1, 1.0, r->red, r->st);
+            r->launches += 8;
             TRY(fetch(r, 2));
             const double bn = std::sqrt(r->hred[0]), pn = std::sqrt(r->hred[1]);
             int lin = 0;
@@ -525,6 +535,9 @@ struct Impl {
             TRY(fetch(r, 2));
             r->cp_valid = false;
             const double gmax = r->hred[0], dFt = std::max(r->hred[1], 1e-30);
+            if (r->verbose)
+                std::fprintf(stderr, "newton %d |b| %.3e |Phat| %.3e lin %d gmax %.3e ratio %.3e\n",
+                             it, bn, pn, lin, gmax, gmax / dFt);
             if (gmax / dFt < r->opt.tol_newton) return FFT_OK;
         }
         FAIL(r, FFT_ERR_NOT_CONVERGED, "Newton reached max_newton = %d", r->opt.max_newton);
@@ -813,6 +826,7 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
     fft_rve_s* r = new fft_rve_s();
     r->prec = opt->prec;
     r->esz = opt->prec == FFT_PREC_FP64 ? 8 : 4;
+    r->verbose = std::getenv("FATIGUEFFT_VERBOSE") != nullptr;
     r->mat = *mat;
     r->opt = *opt;
     r->h = grid->h;

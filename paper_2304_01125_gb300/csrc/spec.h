@@ -29,6 +29,7 @@ template <typename R> void degrade(const void* P, const void* phi, double kres, 
 template <typename R> void residual(const void* Ph, const SGrid& g, void* b, double* part, cudaStream_t s);
 template <typename R> void precond_grad(const void* vin, double scale, void* vout, const double* Kbar, const SGrid& g, void* G, int use_pre, cudaStream_t s);
 template <typename R> void tangent_apply(void* G, const void* K, const void* phi, double kres, size_t N, cudaStream_t s);
+template <typename R> void hermitize(void* v, int ncomp, const SGrid& g, cudaStream_t s);
 template <typename R> void contract(const void* T, const SGrid& g, void* w, cudaStream_t s);
 template <typename R> void mdot(const void* w, const void* V, size_t vstride, int nv, int with_norm, const SGrid& g, double* part, cudaStream_t s);
 template <typename R> void gs_update(void* w, const void* V, size_t vstride, int nv, const double* h, size_t n3, cudaStream_t s);

@@ -80,7 +80,8 @@ def test_constitutive_kernel_matches_oracle(prec):
         Weo.append(o["We_plus"])
     Po, Ko, Weo = np.array(Po).T, np.array(Ko).T, np.array(Weo)
     assert active > gid.size // 4  # the states are plastic
-    tp, tk = (1e-11, 1e-8) if prec == "fp64" else (2e-6, 2e-3)
+    # FP32: stress from F32 arithmetic on O(1e3) MPa components, ~1e-6 relative
+    tp, tk = (1e-11, 1e-8) if prec == "fp64" else (1e-5, 2e-3)
     assert rel(P, Po) < tp
     assert rel(K, Ko) < tk
     assert rel(We, Weo) < (1e-10 if prec == "fp64" else 1e-5)
@@ -125,24 +126,30 @@ def test_phase_field_stage_matches_oracle(prec):
     phi = r.field("phi")
     phi_o, it_o, st = O.phase_field(n, H, MAT["ell"], S, phit, phit, tol=1e-13)
     assert st == 0 and it > 0
-    assert np.all(phi >= phit)
+    phit_r = phit.astype(np.float32) if prec == "mixed" else phit  # the library's phi_t
+    assert np.all(phi >= phit_r)
     assert rel(phi, phi_o) < (1e-9 if prec == "fp64" else 1e-5)
 
 
 # -------------------------------------------------------- full increments
 FIELDS_CMP = ["F", "P", "phi", "Fp", "rho_ssd", "Wp", "Gs", "gamma", "Wcrit"]
+# per-entry scales below which a difference is round-off, not a result
+# (F - I ~ strain, P in MPa, rho - rho0 in 1/mm^2, Wp/Wcrit in MPa, Gs in N/mm)
+FLOOR = {"F": 1e-4, "P": 1.0, "phi": 1e-4, "Fp": 1e-7, "rho_ssd": 1e2, "Wp": 1e-6,
+         "Gs": 1e-10, "gamma": 1e-7, "Wcrit": 1e-6}
 
 
 def _compare(gpu, orc, prec, tag):
+    """Relative L2 error per field, relative to max(||oracle||, floor)."""
     out = {}
+    eye = np.eye(3).reshape(9, 1)
     for f in FIELDS_CMP:
         a, b = gpu.field(f), orc.field(f)
         if f in ("F", "Fp"):
-            eye = np.eye(3).reshape(9, 1)
             a, b = a - eye, b - eye
         if f == "rho_ssd":
             a, b = a - MAT["rho_ssd0"], b - MAT["rho_ssd0"]
-        out[f] = rel(a, b, floor=1e-30) if np.abs(b).max() > 0 else float(np.abs(a).max())
+        out[f] = rel(a, b, floor=FLOOR[f] * np.sqrt(b.size))
     tol = 1e-9 if prec == "fp64" else 1e-4
     bad = {k: v for k, v in out.items() if not v < tol}
     assert not bad, (tag, bad, out)
