@@ -178,6 +178,28 @@ fft_status solve_phase_field(fft_rve_t r, int* iters);
 fft_status rve_profile(fft_rve_t r, unsigned mask);
 fft_status rve_profile_read(fft_rve_t r, double* ms, long long* counts, int reset);
 
+/* Allocation-free reduction, for callers that may not call cudaMalloc (a
+ * host framework that owns all device memory, a pre-sized pool, or code
+ * that must not allocate or synchronise once a run has started).  The
+ * paper has no counterpart: this is a standalone copy of the library's
+ * degraded volume average, out[c] = (1/N) sum_v ((1 - phi_v)^2 + k_res)
+ * X[c*N + v] for c < ncomp, the reduction behind the averaged tangent and
+ * the reported mean stress.
+ *   X: device, ncomp*N doubles, component-major; phi: device, N doubles;
+ *   out: device, ncomp doubles (written); cuda_stream: cudaStream_t (0 =
+ *   legacy default stream).  The call only enqueues work on that stream.
+ * It allocates nothing: the per-block partial sums go to one fixed array of
+ * device memory inside the library (kept by every GPU that loads it until
+ * the process exits), sized for ncomp <= 81; a larger ncomp, N = 0 or a null
+ * pointer returns FFT_ERR_ARG without launching anything.  The first call on
+ * each device (with that device current) looks up the array's device
+ * address, so make that first call before any stream capture.  All calls on
+ * a device share the array: calls whose work overlaps on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.  Each
+ * call overwrites every partial it later reads, so no clearing is needed. */
+fft_status degraded_average_noalloc(const double* X, int ncomp, const double* phi, size_t N,
+                                    double k_res, double* out, void* cuda_stream);
+
 /* Size in bytes of the device memory the handle holds. */
 size_t rve_device_bytes(fft_rve_t r);
 void rve_destroy(fft_rve_t r);

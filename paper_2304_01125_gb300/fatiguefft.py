@@ -27,7 +27,8 @@ FIELDS = {"F": (0, 9), "P": (1, 9), "phi": (2, 1), "Fp": (3, 9), "rho_ssd": (4, 
 SYMBOLS = ["init_rve", "apply_increment", "solve_equilibrium", "update_damage",
            "commit_increment", "run_increment", "fields_out", "fields_in", "eval_constitutive",
            "eval_gnd", "solve_phase_field", "rve_device_bytes", "rve_destroy", "fft_last_error",
-           "rve_kernel_launches", "rve_profile", "rve_profile_read"]
+           "rve_kernel_launches", "rve_profile", "rve_profile_read",
+           "degraded_average_noalloc"]
 KERNEL_FAMILIES = ["constitutive", "tangent_apply", "precond_grad", "contract", "gmres_dot",
                    "gs_update", "gmres_xupdate", "kbar", "residual", "f_update", "phase_field",
                    "gnd", "cufft_9field", "cufft_scalar", "reductions", "other"]
@@ -95,6 +96,9 @@ def load(path=LIB_PATH):
     L.rve_profile.restype = C.c_int
     L.rve_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]
     L.rve_profile_read.restype = C.c_int
+    L.degraded_average_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t,
+                                           C.c_double, C.c_void_p, C.c_void_p]
+    L.degraded_average_noalloc.restype = C.c_int
     L.rve_destroy.argtypes = [vp]
     L.rve_destroy.restype = None
     L.fft_last_error.argtypes = [vp]
@@ -105,6 +109,13 @@ def load(path=LIB_PATH):
         getattr(L, t).restype = C.c_int
     _lib = L
     return L
+
+
+def degraded_average_noalloc(X_ptr, ncomp, phi_ptr, N, k_res, out_ptr, stream=0):
+    """(1/N) sum_v g(phi_v) X[c][v] into out (device pointers), allocating
+    nothing; see include/fatiguefft.h.  Returns the status code."""
+    return load().degraded_average_noalloc(int(X_ptr), int(ncomp), int(phi_ptr), int(N),
+                                           float(k_res), int(out_ptr), int(stream) or None)
 
 
 class FFTError(RuntimeError):
