@@ -37,7 +37,7 @@ L2_NOTE = "working set > L2 (about 0.4 GB mixed per RVE) and a 256 MB L2 flush b
 def args_():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=6)
+    p.add_argument("--steps", type=int, default=80)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", default=CONFIG_NAME)
@@ -71,7 +71,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -110,22 +110,6 @@ def dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
-
-
-# algorithmic bytes per voxel for each kernel family (esz = bulk element size)
-def algo_bytes_per_voxel(family, esz):
-    half = 0.5 * 2 * esz  # one half-spectrum complex component per voxel ~ esz bytes
-    table = {
-        # read grad z (9), K (81), phi (1); write tau (9)
-        "tangent_apply": (9 + 81 + 1 + 9) * esz,
-        # read H, Hpi (18 bulk), committed history (32 FP64); write P (9), K (81) and
-        # (history pass) trial history (32 FP64), Hpi_tr (9), drive, We
-        "constitutive": (18 + 9 + 81 + 1) * esz + 8 * 2,
-        # read v (3 complex), write G (9 complex) [+ optional v copy]
-        "precond_grad": (3 + 9) * half,
-        "contract": (9 + 3) * half,
-    }
-    return table.get(family)
 
 
 def run_ours(a):
@@ -184,6 +168,7 @@ def run_ours(a):
         l0 = r.kernel_launches
         times, stats = [], []
         t_wall = time.perf_counter()
+        torch.cuda.nvtx.range_push(f"timed_{prec}")
         with torch.cuda.stream(stream):
             for k in range(a.warmup, a.warmup + a.steps):
                 flush.fill_(float(k))
@@ -195,16 +180,18 @@ def run_ours(a):
                 stats.append(st)
                 times.append((e0, e1))
         barrier()
+        torch.cuda.nvtx.range_pop()
         t_wall = time.perf_counter() - t_wall
         clocks = clk.stop()
         launches = r.kernel_launches - l0
         ms = [e0.elapsed_time(e1) for e0, e1 in times]
-        dom_prof = r.profile_read(reset=True).get(dom, (0.0, 0))
+        dom_prof = r.profile_read(reset=True).get(dom, (0.0, 0, 0.0))
         r.profile([])
         tot = max_over_ranks(sum(ms))
         results[prec] = dict(ms=ms, total_ms=tot, wall_s=t_wall, launches=launches,
                              stats=stats, breakdown=breakdown, dominant=dom,
-                             dom_ms=dom_prof[0], dom_count=dom_prof[1], clocks=clocks,
+                             dom_ms=dom_prof[0], dom_count=dom_prof[1], dom_bytes=dom_prof[2],
+                             clocks=clocks,
                              device_bytes=r.device_bytes)
         fields[prec] = {f: r.field(f) for f in ("P", "phi", "F")}
         r.close()
@@ -251,14 +238,14 @@ def run_ours(a):
     value64 = ws * N * a.steps / (f64["total_ms"] / 1e3)
     hbm, peak_kind = peaks()
     dom = mx["dominant"]
-    bpv = algo_bytes_per_voxel(dom, 4)
     roof = None
-    if bpv and mx["dom_count"]:
+    if mx["dom_count"] and mx["dom_ms"] > 0:
         avg_s = mx["dom_ms"] / mx["dom_count"] / 1e3
-        achieved = bpv * N / avg_s / 1e9
+        bytes_per_launch = mx["dom_bytes"] / mx["dom_count"]
+        achieved = bytes_per_launch / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": None, "kernel": dom,
-                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": int(bpv * N),
+                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": int(bytes_per_launch),
                 "avg_launch_us": round(avg_s * 1e6, 2), "launches": mx["dom_count"]}
     line = {
         "metric": METRIC,
@@ -293,6 +280,9 @@ def run_ours(a):
                        for p in results},
         "kernel_ms_warmup_step": {p: {k: round(v[0], 3) for k, v in results[p]["breakdown"].items()}
                                   for p in results},
+        "kernel_gbs_warmup_step": {p: {k: round(v[2] / v[0] / 1e6, 1)
+                                       for k, v in results[p]["breakdown"].items() if v[2] > 0}
+                                   for p in results},
     }
     if ws == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, mat, opts, a)

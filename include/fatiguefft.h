@@ -173,10 +173,13 @@ fft_status solve_phase_field(fft_rve_t r, int* iters);
  * 9-field transforms, 13 cuFFT scalar transforms, 14 reductions, 15 other);
  * each selected launch is bracketed by CUDA events on the handle's stream.
  * 0 switches timing off.  rve_profile_read returns the accumulated device
- * milliseconds and launch counts per family (16 entries each, caller-owned
- * arrays), synchronising the stream first; reset = 1 clears them. */
+ * milliseconds, launch counts and algorithmic bytes (the minimum HBM traffic
+ * of the timed launches; bytes may be NULL) per family (16 entries each,
+ * caller-owned arrays), synchronising the stream first; reset = 1 clears
+ * them. */
 fft_status rve_profile(fft_rve_t r, unsigned mask);
-fft_status rve_profile_read(fft_rve_t r, double* ms, long long* counts, int reset);
+fft_status rve_profile_read(fft_rve_t r, double* ms, long long* counts, double* bytes,
+                            int reset);
 
 /* Allocation-free reduction, for callers that may not call cudaMalloc (a
  * host framework that owns all device memory, a pre-sized pool, or code

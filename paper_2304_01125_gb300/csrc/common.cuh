@@ -19,9 +19,13 @@ template <> struct Tr<float> {
 
 // ---- launch geometry ----
 constexpr int kThreads = 256;
-// Reduction kernels run a fixed grid (a multiple of the 152 SMs) so that
+// Reduction kernels run a fixed grid (two blocks per SM of the 152) so that
 // their partial sums are combined in a fixed order (deterministic results).
-constexpr int kRedBlocks = 608;
+constexpr int kRedBlocks = 304;
+// Largest Krylov basis (GMRES restart length) the fused kernels support.
+constexpr int kMaxKrylov = 32;
+// Partial-sum slots per reduction (values x blocks) in the scratch buffer.
+constexpr int kRedSlots = 256;
 
 inline int grid_for(size_t n, int threads = kThreads) {
     size_t b = (n + threads - 1) / threads;
@@ -83,6 +87,84 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
     if (threadIdx.x == 0)
         for (int i = 0; i < NT / 32; ++i) s = fmax(s, sh[i]);
     return s;
+}
+
+// ---- grid-wide multi-value reductions finished by the last block ----
+// Every block reduces its per-thread accumulators to one partial per value
+// (part[v * gridDim.x + blockIdx.x]; a 2-D grid gives each row of blocks its
+// own value, written through part + blockIdx.y * gridDim.x); the last block
+// of the whole grid to finish (atomic ticket)
+// combines the partials in block order and writes out[v] -- sums scaled by
+// `scale`, values whose bit is set in `maxmask` as maxima.  The combination
+// order is fixed, so results do not depend on which block finishes last.
+struct Red {
+    double* part;       // [values][gridDim.x] partials
+    unsigned* counter;  // zero between reductions
+    double* out;        // [values] results
+};
+
+template <int NV, int NT>
+__device__ __forceinline__ void block_partials(const double (&acc)[NV], int nv, unsigned maxmask,
+                                               double* part) {
+    __shared__ double sh[NT / 32][NV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        if (v < nv) {
+            double x = acc[v];
+            const bool mx = (maxmask >> v) & 1u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double y = __shfl_down_sync(0xffffffffu, x, o);
+                x = mx ? fmax(x, y) : x + y;
+            }
+            if (lane == 0) sh[wid][v] = x;
+        }
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < nv; v += NT) {
+        const bool mx = (maxmask >> v) & 1u;
+        double s = 0.0;
+        for (int w = 0; w < NT / 32; ++w) s = mx ? fmax(s, sh[w][v]) : s + sh[w][v];
+        part[(size_t)v * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void grid_finish(const Red& r, int nv, unsigned maxmask, double scale) {
+    __shared__ unsigned s_last;
+    __threadfence();
+    __syncthreads();
+    const unsigned total = gridDim.x * gridDim.y;  // 2-D grids: one value per row of blocks
+    if (threadIdx.x == 0) s_last = atomicAdd(r.counter, 1u) == total - 1 ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31;
+    const int nb = gridDim.x;
+    // one warp per value; four independent loads in flight per lane
+    for (int v = threadIdx.x >> 5; v < nv; v += NT / 32) {
+        const bool mx = (maxmask >> v) & 1u;
+        const double* p = r.part + (size_t)v * nb;
+        double s = 0.0;
+        int i = lane;
+        for (; i + 96 < nb; i += 128) {
+            const double a = __ldcg(p + i), b = __ldcg(p + i + 32), c = __ldcg(p + i + 64),
+                         d = __ldcg(p + i + 96);
+            s = mx ? fmax(s, fmax(fmax(a, b), fmax(c, d))) : s + ((a + b) + (c + d));
+        }
+        for (; i < nb; i += 32) {
+            const double a = __ldcg(p + i);
+            s = mx ? fmax(s, a) : s + a;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_down_sync(0xffffffffu, s, o);
+            s = mx ? fmax(s, y) : s + y;
+        }
+        if (lane == 0) r.out[v] = mx ? s : s * scale;
+    }
+    if (threadIdx.x == 0) *r.counter = 0u;
 }
 
 // Neumaier compensated addition: (s, c) += x.

@@ -13,19 +13,25 @@
 // multipliers i xi_i are zero on the Nyquist frequency of an even axis; the
 // Laplacian keeps -|xi|^2 there.
 //
-// Every reduction kernel runs exactly kRedBlocks blocks and writes one partial
-// per block and value; k_finalize_* combine them in a fixed order.
+// Every reduction kernel runs kRedBlocks blocks; each block writes one FP64
+// partial per value and the last block to finish combines them in a fixed
+// order (deterministic results, no separate finalisation launch).
 #include "common.cuh"
 #include "spec.h"
 
 namespace fatfft {
 
+// Frequency, derivative frequency and Hermitian weight of half-spectrum
+// entry e (32-bit index arithmetic: every grid here has Nh < 2^31).
 template <typename R>
-__device__ __forceinline__ void hs_freq(const SGrid& g, size_t e, R* xi, R* xid, R& w) {
-    const int kx = (int)(e % g.n0h);
-    const size_t rest = e / g.n0h;
-    const int ky = (int)(rest % g.n1);
-    const int kz = (int)(rest / g.n1);
+__device__ __forceinline__ void hs_freq(const SGrid& g, size_t e64, R* xi, R* xid, R& w) {
+    const unsigned e = (unsigned)e64;
+    const unsigned n0h = (unsigned)g.n0h, n1 = (unsigned)g.n1;
+    const unsigned rest = e / n0h;
+    const int kx = (int)(e - rest * n0h);
+    const unsigned kz_ = rest / n1;
+    const int ky = (int)(rest - kz_ * n1);
+    const int kz = (int)kz_;
     const int sy = ky < (g.n1 + 1) / 2 ? ky : ky - g.n1;
     const int sz = kz < (g.n2 + 1) / 2 ? kz : kz - g.n2;
     xi[0] = (R)(g.tpl0 * kx);
@@ -50,28 +56,6 @@ __device__ __forceinline__ Cx cmul_i(Cx a, decltype(a.x) s) {  // a * (i s)
 
 #define GRID_STRIDE(i, n) \
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
-
-// ---------------------------------------------------------------- finalize
-__global__ void k_finalize_sum(const double* part, int nb, double scale, double* out) {
-    __shared__ double sh[32];
-    double a = 0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) a += part[(size_t)blockIdx.x * nb + i];
-    const double s = block_sum<kThreads>(a, sh);
-    if (threadIdx.x == 0) out[blockIdx.x] = s * scale;
-}
-__global__ void k_finalize_max(const double* part, int nb, double* out) {
-    __shared__ double sh[32];
-    double a = 0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) a = fmax(a, part[(size_t)blockIdx.x * nb + i]);
-    const double s = block_max<kThreads>(a, sh);
-    if (threadIdx.x == 0) out[blockIdx.x] = s;
-}
-void finalize_sum(const double* part, int nvals, double scale, double* out, cudaStream_t s) {
-    k_finalize_sum<<<nvals, kThreads, 0, s>>>(part, kRedBlocks, scale, out);
-}
-void finalize_max(const double* part, int nvals, double* out, cudaStream_t s) {
-    k_finalize_max<<<nvals, kThreads, 0, s>>>(part, kRedBlocks, out);
-}
 
 // ------------------------------------------------------------- elementwise
 template <typename R>
@@ -209,23 +193,30 @@ void gnd_rho(const void* Lam, const int32_t* grain, const double* Qg, const doub
 }
 
 // -------------------------------------------------------- averaged tangent
-// Kbar = <g(phi) K> (Eq. avstiff), partial sums per component (grid.y = 81).
+// Kbar = <g(phi) K> (Eq. avstiff).  Each thread accumulates all 81 entries
+// over its voxels (bulk precision, a few voxels per thread), blocks combine
+// in FP64, the last block writes Kbar.
 template <typename R>
-__global__ void k_kbar(const R* K, const R* phi, R kres, size_t N, double* part) {
-    __shared__ double sh[32];
-    const int c = blockIdx.y;
-    double a = 0;
+__global__ void __launch_bounds__(kThreads) k_kbar(const R* K, const R* phi, R kres, size_t N,
+                                                   Red red) {
+    R acc[81];
+#pragma unroll
+    for (int c = 0; c < 81; ++c) acc[c] = 0;
     GRID_STRIDE(v, N) {
         const R om = R(1) - phi[v];
-        a += (double)((om * om + kres) * K[(size_t)c * N + v]);
+        const R g = om * om + kres;
+#pragma unroll
+        for (int c = 0; c < 81; ++c) acc[c] += g * K[(size_t)c * N + v];
     }
-    const double s = block_sum<kThreads>(a, sh);
-    if (threadIdx.x == 0) part[(size_t)c * gridDim.x + blockIdx.x] = s;
+    double accd[81];
+#pragma unroll
+    for (int c = 0; c < 81; ++c) accd[c] = (double)acc[c];
+    block_partials<81, kThreads>(accd, 81, 0u, red.part);
+    grid_finish<kThreads>(red, 81, 0u, 1.0 / (double)N);
 }
 template <typename R>
-void kbar(const void* K, const void* phi, double kres, size_t N, double* part, cudaStream_t s) {
-    k_kbar<R><<<dim3(kRedBlocks, 81), kThreads, 0, s>>>((const R*)K, (const R*)phi, (R)kres, N,
-                                                        part);
+void kbar(const void* K, const void* phi, double kres, size_t N, const Red& red, cudaStream_t s) {
+    k_kbar<R><<<kRedBlocks, kThreads, 0, s>>>((const R*)K, (const R*)phi, (R)kres, N, red);
 }
 
 // ------------------------------------------------------------------ residual
@@ -244,90 +235,99 @@ void degrade(const void* P, const void* phi, double kres, void* out, size_t N, c
                                                   N);
 }
 
-// b_i = sum_j F{gP}_ij i xi_j (Eq. momentum / newton right-hand side, sign
-// flipped); partials of ||b||^2 and of the round-off scale of b,
-// sum_ij |F{gP}_ij xi_j|^2 (Hermitian-weighted).
+// Partner of a half-spectrum entry on the kx = 0 plane (or kx = n0/2 for an
+// even n0): the entry holding the conjugate frequency (-ky, -kz).  Returns
+// false for entries off those planes.
+__device__ __forceinline__ bool hs_partner(const SGrid& g, size_t e64, size_t& p) {
+    const unsigned e = (unsigned)e64;
+    const unsigned n0h = (unsigned)g.n0h, n1 = (unsigned)g.n1;
+    const unsigned rest = e / n0h;
+    const int kx = (int)(e - rest * n0h);
+    if (!(kx == 0 || ((g.n0 % 2 == 0) && kx == g.n0 / 2))) return false;
+    const unsigned kz_ = rest / n1;
+    const int ky = (int)(rest - kz_ * n1), kz = (int)kz_;
+    const int py = (g.n1 - ky) % g.n1, pz = (g.n2 - kz) % g.n2;
+    p = (size_t)kx + (size_t)g.n0h * ((size_t)py + (size_t)g.n1 * pz);
+    return true;
+}
+
+// sign * sum_j T_ij(e) i xi_j(e), i = 0..2
 template <typename R>
-__global__ void k_residual(const typename Tr<R>::Cx* Ph, SGrid g, typename Tr<R>::Cx* b,
-                           double* part) {
+__device__ __forceinline__ void div3(const typename Tr<R>::Cx* T, size_t Nh, size_t e,
+                                     const R* xd, R sign, typename Tr<R>::Cx* out) {
     typedef typename Tr<R>::Cx Cx;
-    __shared__ double sh[32];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        Cx s;
+        s.x = 0;
+        s.y = 0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const Cx t = cmul_i(T[(3 * i + j) * Nh + e], xd[j]);
+            s.x += t.x;
+            s.y += t.y;
+        }
+        out[i].x = sign * s.x;
+        out[i].y = sign * s.y;
+    }
+}
+
+// div3 projected onto real fields: on the kx = 0 and Nyquist planes the
+// value is the mean of the entry and the conjugate of its partner's value,
+// so the pair is exactly conjugate (the inverse real transform ignores the
+// anti-Hermitian part; left in, its forward-transform round-off is a
+// residual no Krylov step can reduce).
+template <typename R>
+__device__ __forceinline__ void div3_real(const typename Tr<R>::Cx* T, const SGrid& g, size_t e,
+                                          const R* xd, R sign, typename Tr<R>::Cx* out) {
+    typedef typename Tr<R>::Cx Cx;
+    div3<R>(T, g.Nh, e, xd, sign, out);
+    size_t p;
+    if (hs_partner(g, e, p)) {
+        R xi2[3], xd2[3], w2;
+        hs_freq<R>(g, p, xi2, xd2, w2);
+        Cx q[3];
+        div3<R>(T, g.Nh, p, xd2, sign, q);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            out[i].x = R(0.5) * (out[i].x + q[i].x);
+            out[i].y = R(0.5) * (out[i].y - q[i].y);
+        }
+    }
+}
+
+// b_i = sum_j F{gP}_ij i xi_j (Eq. momentum / newton right-hand side, sign
+// flipped), projected onto real fields.  out[0] = ||b||^2, out[1] = the
+// round-off scale of b, sum_ij |F{gP}_ij xi_j|^2 (Hermitian-weighted).
+template <typename R>
+__global__ void k_residual(const typename Tr<R>::Cx* Ph, SGrid g, typename Tr<R>::Cx* b, Red red) {
+    typedef typename Tr<R>::Cx Cx;
     const size_t Nh = g.Nh;
-    double nb = 0, np = 0;
+    double acc[2] = {0.0, 0.0};
     GRID_STRIDE(e, Nh) {
         R xi[3], xd[3], w;
         hs_freq<R>(g, e, xi, xd, w);
+        Cx s[3];
+        div3_real<R>(Ph, g, e, xd, R(1), s);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            Cx s;
-            s.x = 0;
-            s.y = 0;
+            b[i * Nh + e] = s[i];
+            acc[0] += (double)w * ((double)s[i].x * s[i].x + (double)s[i].y * s[i].y);
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
-                const Cx p = Ph[(3 * i + j) * Nh + e];
-                np += (double)w * ((double)p.x * p.x + (double)p.y * p.y) * (double)xd[j] *
-                      (double)xd[j];
-                const Cx t = cmul_i(p, xd[j]);
-                s.x += t.x;
-                s.y += t.y;
+                const Cx q = Ph[(3 * i + j) * Nh + e];
+                acc[1] += (double)w * ((double)q.x * q.x + (double)q.y * q.y) * (double)xd[j] *
+                          (double)xd[j];
             }
-            b[i * Nh + e] = s;
-            nb += (double)w * ((double)s.x * s.x + (double)s.y * s.y);
         }
     }
-    double r = block_sum<kThreads>(nb, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = r;
-    r = block_sum<kThreads>(np, sh);
-    if (threadIdx.x == 0) part[kRedBlocks + blockIdx.x] = r;
+    block_partials<2, kThreads>(acc, 2, 0u, red.part);
+    grid_finish<kThreads>(red, 2, 0u, 1.0);
 }
 template <typename R>
-void residual(const void* Ph, const SGrid& g, void* b, double* part, cudaStream_t s) {
+void residual(const void* Ph, const SGrid& g, void* b, const Red& red, cudaStream_t s) {
     k_residual<R><<<kRedBlocks, kThreads, 0, s>>>((const typename Tr<R>::Cx*)Ph, g,
-                                                  (typename Tr<R>::Cx*)b, part);
-}
-
-// Projection onto real fields: on the kx = 0 plane (and kx = n0/2 for even
-// n0) the entries at (ky, kz) and (-ky, -kz) are set to the mean of one and
-// the conjugate of the other; self-conjugate entries lose their imaginary
-// part.  The inverse real transform ignores the anti-Hermitian part, so
-// without this the forward transform's round-off there is a residual the
-// Krylov solver cannot reduce.
-template <typename R>
-__global__ void k_hermitize(typename Tr<R>::Cx* v, int ncomp, SGrid g) {
-    typedef typename Tr<R>::Cx Cx;
-    const int planes = (g.n0 % 2 == 0 && g.n0 > 1) ? 2 : 1;
-    const size_t per = (size_t)g.n1 * g.n2;
-    GRID_STRIDE(t, per * planes * ncomp) {
-        const size_t q = t % per;
-        const int pl = (int)((t / per) % planes);
-        const int c = (int)(t / (per * planes));
-        const int kx = pl == 0 ? 0 : g.n0 / 2;
-        const int ky = (int)(q % g.n1), kz = (int)(q / g.n1);
-        const int py = (g.n1 - ky) % g.n1, pz = (g.n2 - kz) % g.n2;
-        const size_t qp = (size_t)py + (size_t)g.n1 * pz;
-        if (qp < q) continue;  // the partner with the smaller index does the pair
-        Cx* base = v + (size_t)c * g.Nh;
-        const size_t e = (size_t)kx + (size_t)g.n0h * q;
-        const size_t ep = (size_t)kx + (size_t)g.n0h * qp;
-        const Cx a = base[e], b = base[ep];
-        if (qp == q) {
-            Cx r = a;
-            r.y = 0;
-            base[e] = r;
-        } else {
-            Cx m;
-            m.x = R(0.5) * (a.x + b.x);
-            m.y = R(0.5) * (a.y - b.y);
-            base[e] = m;
-            m.y = -m.y;
-            base[ep] = m;
-        }
-    }
-}
-template <typename R>
-void hermitize(void* v, int ncomp, const SGrid& g, cudaStream_t s) {
-    const size_t n = (size_t)g.n1 * g.n2 * ((g.n0 % 2 == 0 && g.n0 > 1) ? 2 : 1) * ncomp;
-    k_hermitize<R><<<grid_for(n), kThreads, 0, s>>>((typename Tr<R>::Cx*)v, ncomp, g);
+                                                  (typename Tr<R>::Cx*)b, red);
 }
 
 // -------------------------------------------------------------------- GMRES
@@ -335,9 +335,10 @@ void hermitize(void* v, int ncomp, const SGrid& g, cudaStream_t s) {
 // preconditioner M = [xi . Kbar . xi]^-1 (Eq. precf) when use_pre, else z =
 // v; G_ij = z_i i xi_j, the 9-component spectrum of grad z.
 template <typename R>
-__global__ void k_precond_grad(const typename Tr<R>::Cx* vin, R scale,
-                               typename Tr<R>::Cx* vout, const double* Kbar, SGrid g,
-                               typename Tr<R>::Cx* G, int use_pre) {
+__device__ __forceinline__ void precond_grad_body(const typename Tr<R>::Cx* vin, R scale,
+                                                  typename Tr<R>::Cx* vout, const double* Kbar,
+                                                  const SGrid& g, typename Tr<R>::Cx* G,
+                                                  int use_pre) {
     typedef typename Tr<R>::Cx Cx;
     __shared__ R Ks[81];
     for (int k = threadIdx.x; k < 81; k += blockDim.x) Ks[k] = (R)Kbar[k];
@@ -404,6 +405,12 @@ __global__ void k_precond_grad(const typename Tr<R>::Cx* vin, R scale,
     }
 }
 template <typename R>
+__global__ void __launch_bounds__(kThreads, 3) k_precond_grad(const typename Tr<R>::Cx* vin, R scale,
+                               typename Tr<R>::Cx* vout, const double* Kbar, SGrid g,
+                               typename Tr<R>::Cx* G, int use_pre) {
+    precond_grad_body<R>(vin, scale, vout, Kbar, g, G, use_pre);
+}
+template <typename R>
 void precond_grad(const void* vin, double scale, void* vout, const double* Kbar, const SGrid& g,
                   void* G, int use_pre, cudaStream_t s) {
     typedef typename Tr<R>::Cx Cx;
@@ -412,32 +419,233 @@ void precond_grad(const void* vin, double scale, void* vout, const double* Kbar,
 }
 
 // tau = g(phi) K : grad z in place (grad z arrives scaled by N from the
-// unnormalised inverse transform).
+// unnormalised inverse transform).  For even N each thread owns a pair of
+// neighbouring voxels and moves them with one 2-wide load per component
+// (every component offset c*N + v is then even, so the loads are aligned);
+// odd N takes the one-voxel loop.
+template <typename R> struct V2;
+template <> struct V2<float> { typedef float2 T; };
+template <> struct V2<double> { typedef double2 T; };
 template <typename R>
-__global__ void k_tangent_apply(R* G, const R* K, const R* phi, R kres, R invN, size_t N) {
-    GRID_STRIDE(v, N) {
-        R gz[9];
+__global__ void __launch_bounds__(kThreads) k_tangent_apply(R* G, const R* K, const R* phi, R kres,
+                                                            R invN, size_t N) {
+    typedef typename V2<R>::T T2;
+    if (N & 1) {
+        GRID_STRIDE(v, N) {
+            R gz[9];
 #pragma unroll
-        for (int b = 0; b < 9; ++b) gz[b] = G[b * N + v];
-        const R om = R(1) - phi[v];
-        const R sc = (om * om + kres) * invN;
+            for (int b = 0; b < 9; ++b) gz[b] = G[b * N + v];
+            const R om = R(1) - phi[v];
+            const R sc = (om * om + kres) * invN;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                R t = 0;
+#pragma unroll
+                for (int b = 0; b < 9; ++b) t += K[(size_t)(9 * a + b) * N + v] * gz[b];
+                G[a * N + v] = sc * t;
+            }
+        }
+        return;
+    }
+    const size_t Np = N / 2;
+    GRID_STRIDE(q, Np) {
+        const size_t v = 2 * q;
+        T2 gz[9];
+#pragma unroll
+        for (int b = 0; b < 9; ++b) gz[b] = *reinterpret_cast<const T2*>(G + b * N + v);
+        const T2 ph = *reinterpret_cast<const T2*>(phi + v);
+        const R o0 = R(1) - ph.x, o1 = R(1) - ph.y;
+        const R s0 = (o0 * o0 + kres) * invN, s1 = (o1 * o1 + kres) * invN;
+        T2 out[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            R t = 0;
+            R t0 = 0, t1 = 0;
 #pragma unroll
-            for (int b = 0; b < 9; ++b) t += K[(size_t)(9 * a + b) * N + v] * gz[b];
-            G[a * N + v] = sc * t;
+            for (int b = 0; b < 9; ++b) {
+                const T2 k = *reinterpret_cast<const T2*>(K + (size_t)(9 * a + b) * N + v);
+                t0 += k.x * gz[b].x;
+                t1 += k.y * gz[b].y;
+            }
+            out[a].x = s0 * t0;
+            out[a].y = s1 * t1;
         }
+#pragma unroll
+        for (int a = 0; a < 9; ++a) *reinterpret_cast<T2*>(G + a * N + v) = out[a];
     }
 }
 template <typename R>
 void tangent_apply(void* G, const void* K, const void* phi, double kres, size_t N,
                    cudaStream_t s) {
-    k_tangent_apply<R><<<grid_for(N), kThreads, 0, s>>>((R*)G, (const R*)K, (const R*)phi,
-                                                        (R)kres, (R)(1.0 / (double)N), N);
+    k_tangent_apply<R><<<grid_for((N & 1) ? N : N / 2), kThreads, 0, s>>>(
+        (R*)G, (const R*)K, (const R*)phi, (R)kres, (R)(1.0 / (double)N), N);
 }
 
-// w_i = -sum_j i xi_j T_ij (divergence, sign giving the positive operator)
+// w_i = -sum_j i xi_j T_ij (the divergence, with the sign that makes the
+// operator positive), projected onto real fields and stored; in the same
+// pass ||w||^2 -> out[0] and the Gram-Schmidt coefficients <V_i, w> ->
+// out[1 + i] (i < nv).
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_contract_dots(const typename Tr<R>::Cx* T, SGrid g,
+                                                            typename Tr<R>::Cx* w,
+                                                            const typename Tr<R>::Cx* V,
+                                                            size_t vstride, int nv, Red red,
+                                                            const GmState* gst) {
+    typedef typename Tr<R>::Cx Cx;
+    const size_t Nh = g.Nh;
+    if (gst) nv = gst->k + 1;
+    R acc[kMaxKrylov + 1];  // per-thread partials over its few entries
+#pragma unroll
+    for (int i = 0; i <= kMaxKrylov; ++i) acc[i] = R(0);
+    GRID_STRIDE(e, Nh) {
+        R xi[3], xd[3], wt;
+        hs_freq<R>(g, e, xi, xd, wt);
+        Cx a[3];
+        div3_real<R>(T, g, e, xd, R(-1), a);
+        R nn = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            w[c * Nh + e] = a[c];
+            nn += a[c].x * a[c].x + a[c].y * a[c].y;
+        }
+        acc[0] += wt * nn;
+#pragma unroll
+        for (int i = 0; i < kMaxKrylov; ++i) {
+            if (i < nv) {
+                const Cx* Vi = V + (size_t)i * vstride;
+                R d = 0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const Cx q = Vi[c * Nh + e];
+                    d += q.x * a[c].x + q.y * a[c].y;
+                }
+                acc[1 + i] += wt * d;
+            }
+        }
+    }
+    double accd[kMaxKrylov + 1];
+#pragma unroll
+    for (int i = 0; i <= kMaxKrylov; ++i) accd[i] = (double)acc[i];
+    block_partials<kMaxKrylov + 1, kThreads>(accd, nv + 1, 0u, red.part);
+    grid_finish<kThreads>(red, nv + 1, 0u, 1.0);
+}
+template <typename R>
+void contract_dots(const void* T, const SGrid& g, void* w, const void* V, size_t vstride, int nv,
+                   const Red& red, cudaStream_t s, const GmState* st) {
+    typedef typename Tr<R>::Cx Cx;
+    k_contract_dots<R><<<kRedBlocks, kThreads, 0, s>>>((const Cx*)T, g, (Cx*)w, (const Cx*)V,
+                                                       vstride, nv, red, st);
+}
+
+// w -= sum_{i < nv} h_i V_i with h = hin[1 + i] (device memory, the layout
+// contract_dots writes); out[0] = ||w_new||^2 and, with dots, out[1 + i] =
+// <V_i, w_new> for a second Gram-Schmidt pass.
+template <typename R>
+__device__ __forceinline__ void gs_update_body(typename Tr<R>::Cx* w,
+                                               const typename Tr<R>::Cx* V, size_t vstride,
+                                               int nv, const double* hin, int dots,
+                                               const SGrid& g, const Red& red) {
+    typedef typename Tr<R>::Cx Cx;
+    const size_t Nh = g.Nh;
+    __shared__ R hs[kMaxKrylov];
+    for (int i = threadIdx.x; i < kMaxKrylov; i += blockDim.x)
+        hs[i] = (i < nv && hin) ? (R)hin[1 + i] : R(0);
+    __syncthreads();
+    R acc[kMaxKrylov + 1];  // per-thread partials over its few entries
+#pragma unroll
+    for (int i = 0; i <= kMaxKrylov; ++i) acc[i] = R(0);
+    GRID_STRIDE(e, Nh) {
+        R xi[3], xd[3], wt;
+        hs_freq<R>(g, e, xi, xd, wt);
+        Cx a[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a[c] = w[c * Nh + e];
+        if (hin) {
+#pragma unroll
+            for (int i = 0; i < kMaxKrylov; ++i) {
+                if (i < nv) {
+                    const Cx* Vi = V + (size_t)i * vstride;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const Cx q = Vi[c * Nh + e];
+                        a[c].x -= hs[i] * q.x;
+                        a[c].y -= hs[i] * q.y;
+                    }
+                }
+            }
+        }
+        R nn = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (hin) w[c * Nh + e] = a[c];
+            nn += a[c].x * a[c].x + a[c].y * a[c].y;
+        }
+        acc[0] += wt * nn;
+        if (dots) {
+#pragma unroll
+            for (int i = 0; i < kMaxKrylov; ++i) {
+                if (i < nv) {
+                    const Cx* Vi = V + (size_t)i * vstride;
+                    R d = 0;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const Cx q = Vi[c * Nh + e];
+                        d += q.x * a[c].x + q.y * a[c].y;
+                    }
+                    acc[1 + i] += wt * d;
+                }
+            }
+        }
+    }
+    const int nvals = dots ? nv + 1 : 1;
+    double accd[kMaxKrylov + 1];
+#pragma unroll
+    for (int i = 0; i <= kMaxKrylov; ++i) accd[i] = (double)acc[i];
+    block_partials<kMaxKrylov + 1, kThreads>(accd, nvals, 0u, red.part);
+    grid_finish<kThreads>(red, nvals, 0u, 1.0);
+}
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_gs_update(typename Tr<R>::Cx* w,
+                                                        const typename Tr<R>::Cx* V,
+                                                        size_t vstride, int nv, const double* hin,
+                                                        int dots, SGrid g, Red red,
+                                                        const GmState* gst) {
+    if (gst) nv = gst->k + 1;
+    gs_update_body<R>(w, V, vstride, nv, hin, dots, g, red);
+}
+template <typename R>
+void gs_update(void* w, const void* V, size_t vstride, int nv, const double* h, int dots,
+               const SGrid& g, const Red& red, cudaStream_t s, const GmState* st) {
+    typedef typename Tr<R>::Cx Cx;
+    k_gs_update<R><<<kRedBlocks, kThreads, 0, s>>>((Cx*)w, (const Cx*)V, vstride, nv, h, dots, g,
+                                                   red, st);
+}
+
+// ---------------------------------------------- tiled Krylov vector kernels
+// The Krylov vectors are 3 Nh complex entries laid out as one flat array
+// (component-major); the Hermitian weight of flat entry f depends on its kx
+// = (f mod Nh) mod n0h.  Each block owns tiles of kTileItems * kThreads
+// consecutive entries; a thread keeps its kTileItems entries of w in
+// registers and streams each Krylov vector's tile with independent
+// coalesced loads (the loop is a tall-skinny V^T w / w - V h).
+constexpr int kUpdItems = 2;  // entries per thread in the w - V h update
+
+__device__ __forceinline__ float hs_weight(const SGrid& g, unsigned f) {
+    const unsigned Nh = (unsigned)g.Nh, n0h = (unsigned)g.n0h;
+    const unsigned e = f % Nh;
+    const unsigned kx = e % n0h;
+    const bool nyx = (g.n0 % 2 == 0) && (int)kx == g.n0 / 2;
+    return (kx == 0 || nyx) ? 1.0f : 2.0f;
+}
+
+inline int tile_blocks(size_t n3, int items) {
+    const size_t tile = (size_t)items * kThreads;
+    size_t t = (n3 + tile - 1) / tile;
+    if (t > (size_t)(8 * 152)) t = 8 * 152;
+    return (int)(t < 1 ? 1 : t);
+}
+
+// w_i = -sum_j i xi_j T_ij projected onto real fields (the GMRES operator's
+// last step), stored.
 template <typename R>
 __global__ void k_contract(const typename Tr<R>::Cx* T, SGrid g, typename Tr<R>::Cx* w) {
     typedef typename Tr<R>::Cx Cx;
@@ -445,19 +653,10 @@ __global__ void k_contract(const typename Tr<R>::Cx* T, SGrid g, typename Tr<R>:
     GRID_STRIDE(e, Nh) {
         R xi[3], xd[3], wt;
         hs_freq<R>(g, e, xi, xd, wt);
+        Cx a[3];
+        div3_real<R>(T, g, e, xd, R(-1), a);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            Cx s;
-            s.x = 0;
-            s.y = 0;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const Cx t = cmul_i(T[(3 * i + j) * Nh + e], xd[j]);
-                s.x -= t.x;
-                s.y -= t.y;
-            }
-            w[i * Nh + e] = s;
-        }
+        for (int c = 0; c < 3; ++c) w[c * Nh + e] = a[c];
     }
 }
 template <typename R>
@@ -466,59 +665,219 @@ void contract(const void* T, const SGrid& g, void* w, cudaStream_t s) {
     k_contract<R><<<grid_for(g.Nh), kThreads, 0, s>>>((const Cx*)T, g, (Cx*)w);
 }
 
-// Partial Hermitian-weighted dots <V_y, w> for y < nv, and <w, w> for y = nv.
+// out[0] = ||w||^2, out[1 + i] = <V_i, w> (i < nv); skipped entirely when
+// need_flag is set and st->reorth is zero (the
+// optional second Gram-Schmidt pass).  2-D grid: blockIdx.x walks tiles of
+// kThreads * kDotItems entries, blockIdx.y selects the value (0: the norm,
+// 1 + i: vector i); w is re-read from L2 by each row.
+constexpr int kDotItems = 4;
 template <typename R>
-__global__ void k_mdot(const typename Tr<R>::Cx* w, const typename Tr<R>::Cx* V, size_t vstride,
-                       int nv, SGrid g, double* part) {
+__global__ void __launch_bounds__(kThreads) k_vdots(const typename Tr<R>::Cx* w,
+                                                    const typename Tr<R>::Cx* V, size_t vstride,
+                                                    int nv, SGrid g, Red red, const GmState* st,
+                                                    int need_flag) {
     typedef typename Tr<R>::Cx Cx;
-    __shared__ double sh[32];
-    const size_t Nh = g.Nh;
+    if (need_flag && !st->reorth) return;
     const int y = blockIdx.y;
-    const Cx* a = y < nv ? V + (size_t)y * vstride : w;
-    double acc = 0;
+    const Cx* a = y == 0 ? w : V + (size_t)(y - 1) * vstride;
+    const unsigned n3 = (unsigned)(3 * g.Nh);
+    const unsigned step = gridDim.x * kThreads * kDotItems;
+    R acc = 0;
+    for (unsigned base = blockIdx.x * kThreads * kDotItems; base < n3; base += step) {
+        Cx p[kDotItems], q[kDotItems];
+#pragma unroll
+        for (int t = 0; t < kDotItems; ++t) {
+            const unsigned f = base + t * kThreads + threadIdx.x;
+            if (f < n3) {
+                p[t] = a[f];
+                q[t] = w[f];
+            } else {
+                p[t].x = p[t].y = q[t].x = q[t].y = 0;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kDotItems; ++t) {
+            const unsigned f = base + t * kThreads + threadIdx.x;
+            if (f < n3) acc += (R)hs_weight(g, f) * (p[t].x * q[t].x + p[t].y * q[t].y);
+        }
+    }
+    double d[1] = {(double)acc};
+    block_partials<1, kThreads>(d, 1, 0u, red.part + (size_t)y * gridDim.x);
+    grid_finish<kThreads>(red, nv + 1, 0u, 1.0);
+}
+
+// w -= sum_{i < nv} h_i V_i with h_i = hin[1 + i]; out[0] = ||w||^2.  With
+// need_flag, skipped when st->reorth is zero.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_vupdate(typename Tr<R>::Cx* w,
+                                                      const typename Tr<R>::Cx* V, size_t vstride,
+                                                      int nv, const double* hin, SGrid g, Red red,
+                                                      const GmState* st, int need_flag) {
+    typedef typename Tr<R>::Cx Cx;
+    if (need_flag && !st->reorth) return;
+    __shared__ R hs[kMaxKrylov];
+    for (int i = threadIdx.x; i < kMaxKrylov; i += blockDim.x) hs[i] = i < nv ? (R)hin[1 + i] : R(0);
+    __syncthreads();
+    const unsigned n3 = (unsigned)(3 * g.Nh);
+    double acc[1] = {0.0};
+    constexpr int kTileItems = kUpdItems;
+    constexpr int kTile = kUpdItems * kThreads;
+    for (unsigned base = blockIdx.x * kTile; base < n3; base += gridDim.x * kTile) {
+        Cx wv[kTileItems];
+#pragma unroll
+        for (int t = 0; t < kTileItems; ++t) {
+            const unsigned f = base + t * kThreads + threadIdx.x;
+            if (f < n3)
+                wv[t] = w[f];
+            else
+                wv[t].x = wv[t].y = 0;
+        }
+#pragma unroll
+        for (int i = 0; i < kMaxKrylov; ++i) {
+            if (i < nv) {
+                const Cx* Vi = V + (size_t)i * vstride;
+                const R h = hs[i];
+#pragma unroll
+                for (int t = 0; t < kTileItems; ++t) {
+                    const unsigned f = base + t * kThreads + threadIdx.x;
+                    if (f < n3) {
+                        const Cx q = Vi[f];
+                        wv[t].x -= h * q.x;
+                        wv[t].y -= h * q.y;
+                    }
+                }
+            }
+        }
+        R nn = 0;
+#pragma unroll
+        for (int t = 0; t < kTileItems; ++t) {
+            const unsigned f = base + t * kThreads + threadIdx.x;
+            if (f < n3) {
+                w[f] = wv[t];
+                nn += (R)hs_weight(g, f) * (wv[t].x * wv[t].x + wv[t].y * wv[t].y);
+            }
+        }
+        acc[0] += (double)nn;
+    }
+    block_partials<1, kThreads>(acc, 1, 0u, red.part);
+    grid_finish<kThreads>(red, 1, 0u, 1.0);
+}
+
+template <typename R>
+void vdots(const void* w, const void* V, size_t vstride, int nv, const SGrid& g, const Red& red,
+           cudaStream_t s, const GmState* st, int need_flag) {
+    typedef typename Tr<R>::Cx Cx;
+    const int rows = nv + 1;
+    int bx = tile_blocks(3 * g.Nh, kDotItems);
+    if ((size_t)bx * rows > (size_t)kRedSlots * kRedBlocks / 2) bx = kRedSlots * kRedBlocks / 2 / rows;
+    k_vdots<R><<<dim3(bx, rows), kThreads, 0, s>>>((const Cx*)w, (const Cx*)V, vstride, nv, g,
+                                                   red, st, need_flag);
+}
+template <typename R>
+void vupdate(void* w, const void* V, size_t vstride, int nv, const double* hin, const SGrid& g,
+             const Red& red, cudaStream_t s, const GmState* st, int need_flag) {
+    typedef typename Tr<R>::Cx Cx;
+    k_vupdate<R><<<tile_blocks(3 * g.Nh, kUpdItems), kThreads, 0, s>>>(
+        (Cx*)w, (const Cx*)V, vstride, nv, hin, g, red, st, need_flag);
+}
+// Look-ahead GMRES step 1: operands from GmState (see GmArgs), then the
+// Green preconditioner and the gradient spectrum, as precond_grad.
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 3) k_gm_precond_grad(GmArgs a, const double* Kbar, SGrid g,
+                                  typename Tr<R>::Cx* G) {
+    typedef typename Tr<R>::Cx Cx;
+    const int k = a.st->k;
+    const Cx* vin = (const Cx*)(k == 0 ? a.V : a.w);
+    const R scale = k == 0 ? R(1) : (R)(1.0 / a.st->hprev);
+    Cx* vout = k == 0 ? nullptr : (Cx*)a.V + (size_t)k * a.vstride;
+    precond_grad_body<R>(vin, scale, vout, Kbar, g, G, 1);
+}
+template <typename R>
+void gm_precond_grad(const GmArgs& a, const double* Kbar, const SGrid& g, void* G,
+                     cudaStream_t s) {
+    k_gm_precond_grad<R><<<grid_for(g.Nh), kThreads, 0, s>>>(a, Kbar, g,
+                                                             (typename Tr<R>::Cx*)G);
+}
+
+// Second Gram-Schmidt pass, taken on the device when the update shrank the
+// norm below 1/sqrt(2) of its value (red[0]: before, red[64]: after): the
+// dots of the updated w go to red_dots, then w is updated again and its norm
+// replaces red[64] (via red_norm).  Otherwise nothing happens.
+template <typename R>
+__global__ void k_gm_reorth_flag(const double* red, GmState* st) {
+    st->reorth = red[64] < 0.5 * red[0] ? 1 : 0;
+}
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_gm_reorth_dots(const typename Tr<R>::Cx* w,
+                                                             const typename Tr<R>::Cx* V,
+                                                             size_t vstride, const GmState* st,
+                                                             SGrid g, Red red) {
+    typedef typename Tr<R>::Cx Cx;
+    if (!st->reorth) return;
+    const int nv = st->k + 1;
+    const size_t Nh = g.Nh;
+    double acc[kMaxKrylov + 1];
+#pragma unroll
+    for (int i = 0; i <= kMaxKrylov; ++i) acc[i] = 0.0;
     GRID_STRIDE(e, Nh) {
         R xi[3], xd[3], wt;
         hs_freq<R>(g, e, xi, xd, wt);
-        R s = 0;
+        Cx a[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const Cx p = a[i * Nh + e], q = w[i * Nh + e];
-            s += p.x * q.x + p.y * q.y;
+        for (int c = 0; c < 3; ++c) a[c] = w[c * Nh + e];
+#pragma unroll
+        for (int i = 0; i < kMaxKrylov; ++i) {
+            if (i < nv) {
+                const Cx* Vi = V + (size_t)i * vstride;
+                R d = 0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const Cx q = Vi[c * Nh + e];
+                    d += q.x * a[c].x + q.y * a[c].y;
+                }
+                acc[1 + i] += (double)wt * (double)d;
+            }
         }
-        acc += (double)wt * (double)s;
     }
-    const double r = block_sum<kThreads>(acc, sh);
-    if (threadIdx.x == 0) part[(size_t)y * gridDim.x + blockIdx.x] = r;
+    block_partials<kMaxKrylov + 1, kThreads>(acc, nv + 1, 0u, red.part);
+    grid_finish<kThreads>(red, nv + 1, 0u, 1.0);
 }
 template <typename R>
-void mdot(const void* w, const void* V, size_t vstride, int nv, int with_norm, const SGrid& g,
-          double* part, cudaStream_t s) {
+__global__ void __launch_bounds__(kThreads) k_gm_reorth_update(typename Tr<R>::Cx* w,
+                                                               const typename Tr<R>::Cx* V,
+                                                               size_t vstride, const double* hin,
+                                                               const GmState* st, SGrid g,
+                                                               Red red) {
+    if (!st->reorth) return;
+    gs_update_body<R>(w, V, vstride, st->k + 1, hin, 0, g, red);
+}
+template <typename R>
+void gm_reorth_flag(const double* red, GmState* st, cudaStream_t s) {
+    k_gm_reorth_flag<R><<<1, 1, 0, s>>>(red, st);
+}
+template <typename R>
+void gm_reorth(void* w, const void* V, size_t vstride, const double* red, GmState* st,
+               const SGrid& g, const Red& red_dots, const Red& red_norm, cudaStream_t s) {
     typedef typename Tr<R>::Cx Cx;
-    k_mdot<R><<<dim3(kRedBlocks, nv + (with_norm ? 1 : 0)), kThreads, 0, s>>>(
-        (const Cx*)w, (const Cx*)V, vstride, nv, g, part);
+    k_gm_reorth_flag<R><<<1, 1, 0, s>>>(red, st);
+    k_gm_reorth_dots<R><<<kRedBlocks, kThreads, 0, s>>>((const Cx*)w, (const Cx*)V, vstride, st, g,
+                                                        red_dots);
+    k_gm_reorth_update<R><<<kRedBlocks, kThreads, 0, s>>>((Cx*)w, (const Cx*)V, vstride,
+                                                          red_dots.out, st, g, red_norm);
 }
 
-// w -= sum_i h_i V_i
-template <typename R>
-__global__ void k_gs_update(typename Tr<R>::Cx* w, const typename Tr<R>::Cx* V, size_t vstride,
-                            int nv, const double* h, size_t n3) {
-    typedef typename Tr<R>::Cx Cx;
-    GRID_STRIDE(e, n3) {
-        Cx a = w[e];
-        for (int i = 0; i < nv; ++i) {
-            const R hi = (R)h[i];
-            const Cx v = V[(size_t)i * vstride + e];
-            a.x -= hi * v.x;
-            a.y -= hi * v.y;
-        }
-        w[e] = a;
-    }
+__global__ void k_gm_reset(GmState* st) {
+    st->k = 0;
+    st->reorth = 0;
+    st->hprev = 1.0;
 }
-template <typename R>
-void gs_update(void* w, const void* V, size_t vstride, int nv, const double* h, size_t n3,
-               cudaStream_t s) {
-    typedef typename Tr<R>::Cx Cx;
-    k_gs_update<R><<<grid_for(n3), kThreads, 0, s>>>((Cx*)w, (const Cx*)V, vstride, nv, h, n3);
+__global__ void k_gm_advance(GmState* st, const double* norm2) {
+    st->hprev = sqrt(fmax(norm2[0], 0.0));
+    st->k += 1;
+}
+void gm_reset(GmState* st, cudaStream_t s) { k_gm_reset<<<1, 1, 0, s>>>(st); }
+void gm_advance(GmState* st, const double* norm2, cudaStream_t s) {
+    k_gm_advance<<<1, 1, 0, s>>>(st, norm2);
 }
 
 // x += M (sum_i y_i V_i)  (right-preconditioned GMRES update)
@@ -613,77 +972,94 @@ void axpby(void* out, const void* a, const void* b, double alpha, double beta, s
                                                 (R)beta, n);
 }
 
-// ----------------------------------------------------------- Newton update
-// H += grad(du) (arriving scaled by N); partial maxima of |grad du| and
-// |H - Ht| (the test of Sec. 3.1).
+// ||v||^2 (Hermitian-weighted) of a 3-component half-spectrum vector.
 template <typename R>
-__global__ void k_fupdate(R* H, const R* G, R invN, const R* Ht, size_t N, double* part) {
-    __shared__ double sh[32];
-    double m0 = 0, m1 = 0;
+__global__ void k_norm2(const typename Tr<R>::Cx* v, SGrid g, Red red) {
+    typedef typename Tr<R>::Cx Cx;
+    double acc[1] = {0.0};
+    GRID_STRIDE(e, g.Nh) {
+        R xi[3], xd[3], wt;
+        hs_freq<R>(g, e, xi, xd, wt);
+        R nn = 0;  // ||v||^2 -> out[0]
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const Cx q = v[c * g.Nh + e];
+            nn += q.x * q.x + q.y * q.y;
+        }
+        acc[0] += (double)wt * (double)nn;
+    }
+    block_partials<1, kThreads>(acc, 1, 0u, red.part);
+    grid_finish<kThreads>(red, 1, 0u, 1.0);
+}
+template <typename R>
+void norm2(const void* v, const SGrid& g, const Red& red, cudaStream_t s) {
+    k_norm2<R><<<kRedBlocks, kThreads, 0, s>>>((const typename Tr<R>::Cx*)v, g, red);
+}
+
+// ----------------------------------------------------------- Newton update
+// H += grad(du) (arriving scaled by N); out[0] = max |grad du|,
+// out[1] = max |H - Ht| (the Newton test of Sec. 3.1).
+template <typename R>
+__global__ void k_fupdate(R* H, const R* G, R invN, const R* Ht, size_t N, Red red) {
+    double acc[2] = {0.0, 0.0};
     GRID_STRIDE(v, N) {
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
             const R d = G[c * N + v] * invN;
             const R h = H[c * N + v] + d;
             H[c * N + v] = h;
-            m0 = fmax(m0, (double)fabs(d));
-            m1 = fmax(m1, (double)fabs(h - Ht[c * N + v]));
+            acc[0] = fmax(acc[0], (double)fabs(d));
+            acc[1] = fmax(acc[1], (double)fabs(h - Ht[c * N + v]));
         }
     }
-    double r = block_max<kThreads>(m0, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = r;
-    r = block_max<kThreads>(m1, sh);
-    if (threadIdx.x == 0) part[kRedBlocks + blockIdx.x] = r;
+    block_partials<2, kThreads>(acc, 2, 3u, red.part);
+    grid_finish<kThreads>(red, 2, 3u, 1.0);
 }
 template <typename R>
-void fupdate(void* H, const void* G, const void* Ht, size_t N, double* part, cudaStream_t s) {
+void fupdate(void* H, const void* G, const void* Ht, size_t N, const Red& red, cudaStream_t s) {
     k_fupdate<R><<<kRedBlocks, kThreads, 0, s>>>((R*)H, (const R*)G, (R)(1.0 / (double)N),
-                                                 (const R*)Ht, N, part);
+                                                 (const R*)Ht, N, red);
 }
 
+// Algorithm 1 ratios and the mean degraded stress in one pass:
+// out[0] = max |H - Hprev|, out[1] = max |H - Ht|, out[2 + c] = <g(phi) P_c>.
 template <typename R>
-__global__ void k_maxdiff(const R* a, const R* b, size_t n, double* part) {
-    __shared__ double sh[32];
-    double m = 0;
-    GRID_STRIDE(i, n) m = fmax(m, (double)fabs(a[i] - b[i]));
-    const double r = block_max<kThreads>(m, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = r;
-}
-template <typename R>
-void maxdiff(const void* a, const void* b, size_t n, double* part, cudaStream_t s) {
-    k_maxdiff<R><<<kRedBlocks, kThreads, 0, s>>>((const R*)a, (const R*)b, n, part);
-}
-
-template <typename R>
-__global__ void k_maxval(const R* a, size_t n, double* part) {
-    __shared__ double sh[32];
-    double m = 0;
-    GRID_STRIDE(i, n) m = fmax(m, (double)a[i]);
-    const double r = block_max<kThreads>(m, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = r;
-}
-template <typename R>
-void maxval(const void* a, size_t n, double* part, cudaStream_t s) {
-    k_maxval<R><<<kRedBlocks, kThreads, 0, s>>>((const R*)a, n, part);
-}
-
-// <g(phi) P_c> partial sums (grid.y = 9)
-template <typename R>
-__global__ void k_pbar(const R* P, const R* phi, R kres, size_t N, double* part) {
-    __shared__ double sh[32];
-    const int c = blockIdx.y;
-    double a = 0;
+__global__ void k_stag_stats(const R* H, const R* Hprev, const R* Ht, const R* P, const R* phi,
+                             R kres, size_t N, Red red) {
+    double acc[11];
+#pragma unroll
+    for (int i = 0; i < 11; ++i) acc[i] = 0.0;
     GRID_STRIDE(v, N) {
         const R om = R(1) - phi[v];
-        a += (double)((om * om + kres) * P[(size_t)c * N + v]);
+        const R g = om * om + kres;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            const R h = H[c * N + v];
+            acc[0] = fmax(acc[0], (double)fabs(h - Hprev[c * N + v]));
+            acc[1] = fmax(acc[1], (double)fabs(h - Ht[c * N + v]));
+            acc[2 + c] += (double)(g * P[c * N + v]);
+        }
     }
-    const double s = block_sum<kThreads>(a, sh);
-    if (threadIdx.x == 0) part[(size_t)c * gridDim.x + blockIdx.x] = s;
+    block_partials<11, kThreads>(acc, 11, 3u, red.part);
+    grid_finish<kThreads>(red, 11, 3u, 1.0 / (double)N);
 }
 template <typename R>
-void pbar(const void* P, const void* phi, double kres, size_t N, double* part, cudaStream_t s) {
-    k_pbar<R><<<dim3(kRedBlocks, 9), kThreads, 0, s>>>((const R*)P, (const R*)phi, (R)kres, N,
-                                                       part);
+void stag_stats(const void* H, const void* Hprev, const void* Ht, const void* P, const void* phi,
+                double kres, size_t N, const Red& red, cudaStream_t s) {
+    k_stag_stats<R><<<kRedBlocks, kThreads, 0, s>>>((const R*)H, (const R*)Hprev, (const R*)Ht,
+                                                    (const R*)P, (const R*)phi, (R)kres, N, red);
+}
+
+template <typename R>
+__global__ void k_maxval(const R* a, size_t n, Red red) {
+    double acc[1] = {0.0};
+    GRID_STRIDE(i, n) acc[0] = fmax(acc[0], (double)a[i]);
+    block_partials<1, kThreads>(acc, 1, 1u, red.part);
+    grid_finish<kThreads>(red, 1, 1u, 1.0);
+}
+template <typename R>
+void maxval(const void* a, size_t n, const Red& red, cudaStream_t s) {
+    k_maxval<R><<<kRedBlocks, kThreads, 0, s>>>((const R*)a, n, red);
 }
 
 // ------------------------------------------------------------- phase field
@@ -709,82 +1085,76 @@ void pf_spec(void* f, const SGrid& g, double l2, int mode, cudaStream_t s) {
                                                      (R)(1.0 / (double)g.N), mode);
 }
 
-// r = 2S - (1 + 2S) x - lapx; partials ||r||^2 and ||2S||^2
+// r = 2S - (1 + 2S) x - lapx; out[0] = ||r||^2, out[1] = ||2S||^2
 template <typename R>
-__global__ void k_pf_init(const R* x, const R* lapx, const R* S, R* r, size_t N, double* part) {
-    __shared__ double sh[32];
-    double a = 0, b = 0;
+__global__ void k_pf_init(const R* x, const R* lapx, const R* S, R* r, size_t N, Red red) {
+    double acc[2] = {0.0, 0.0};
     GRID_STRIDE(v, N) {
         const R s2 = R(2) * S[v];
         const R rv = s2 - (R(1) + s2) * x[v] - lapx[v];
         r[v] = rv;
-        a += (double)rv * rv;
-        b += (double)s2 * s2;
+        acc[0] += (double)rv * rv;
+        acc[1] += (double)s2 * s2;
     }
-    double q = block_sum<kThreads>(a, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = q;
-    q = block_sum<kThreads>(b, sh);
-    if (threadIdx.x == 0) part[kRedBlocks + blockIdx.x] = q;
+    block_partials<2, kThreads>(acc, 2, 0u, red.part);
+    grid_finish<kThreads>(red, 2, 0u, 1.0);
 }
 template <typename R>
-void pf_init(const void* x, const void* lapx, const void* S, void* r, size_t N, double* part,
+void pf_init(const void* x, const void* lapx, const void* S, void* r, size_t N, const Red& red,
              cudaStream_t s) {
-    k_pf_init<R><<<kRedBlocks, kThreads, 0, s>>>((const R*)x, (const R*)lapx, (const R*)S,
-                                                 (R*)r, N, part);
+    k_pf_init<R><<<kRedBlocks, kThreads, 0, s>>>((const R*)x, (const R*)lapx, (const R*)S, (R*)r,
+                                                 N, red);
 }
 
 template <typename R>
-__global__ void k_rdot(const R* a, const R* b, size_t N, double* part) {
-    __shared__ double sh[32];
-    double acc = 0;
-    GRID_STRIDE(v, N) acc += (double)a[v] * (double)b[v];
-    const double q = block_sum<kThreads>(acc, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = q;
+__global__ void k_rdot(const R* a, const R* b, size_t N, Red red) {
+    double acc[1] = {0.0};
+    GRID_STRIDE(v, N) acc[0] += (double)a[v] * (double)b[v];
+    block_partials<1, kThreads>(acc, 1, 0u, red.part);
+    grid_finish<kThreads>(red, 1, 0u, 1.0);
 }
 template <typename R>
-void rdot(const void* a, const void* b, size_t N, double* part, cudaStream_t s) {
-    k_rdot<R><<<kRedBlocks, kThreads, 0, s>>>((const R*)a, (const R*)b, N, part);
+void rdot(const void* a, const void* b, size_t N, const Red& red, cudaStream_t s) {
+    k_rdot<R><<<kRedBlocks, kThreads, 0, s>>>((const R*)a, (const R*)b, N, red);
 }
 
-// q = t + 2 S p  (A p through the recurrence t = M^-1 p);  partial <p, q>
+// q = t + 2 S p  (A p through the recurrence t = M^-1 p);  out[0] = <p, q>
 template <typename R>
-__global__ void k_pf_q(const R* t, const R* p, const R* S, R* q, size_t N, double* part) {
-    __shared__ double sh[32];
-    double acc = 0;
+__global__ void k_pf_q(const R* t, const R* p, const R* S, R* q, size_t N, Red red) {
+    double acc[1] = {0.0};
     GRID_STRIDE(v, N) {
         const R qv = t[v] + R(2) * S[v] * p[v];
         q[v] = qv;
-        acc += (double)p[v] * qv;
+        acc[0] += (double)p[v] * qv;
     }
-    const double r = block_sum<kThreads>(acc, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = r;
+    block_partials<1, kThreads>(acc, 1, 0u, red.part);
+    grid_finish<kThreads>(red, 1, 0u, 1.0);
 }
 template <typename R>
-void pf_q(const void* t, const void* p, const void* S, void* q, size_t N, double* part,
+void pf_q(const void* t, const void* p, const void* S, void* q, size_t N, const Red& red,
           cudaStream_t s) {
     k_pf_q<R><<<kRedBlocks, kThreads, 0, s>>>((const R*)t, (const R*)p, (const R*)S, (R*)q, N,
-                                              part);
+                                              red);
 }
 
-// x += alpha p; r -= alpha q; partial ||r||^2
+// x += alpha p; r -= alpha q; out[0] = ||r||^2
 template <typename R>
-__global__ void k_pf_xr(R* x, R* r, const R* p, const R* q, R alpha, size_t N, double* part) {
-    __shared__ double sh[32];
-    double acc = 0;
+__global__ void k_pf_xr(R* x, R* r, const R* p, const R* q, R alpha, size_t N, Red red) {
+    double acc[1] = {0.0};
     GRID_STRIDE(v, N) {
         x[v] += alpha * p[v];
         const R rv = r[v] - alpha * q[v];
         r[v] = rv;
-        acc += (double)rv * rv;
+        acc[0] += (double)rv * rv;
     }
-    const double q2 = block_sum<kThreads>(acc, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = q2;
+    block_partials<1, kThreads>(acc, 1, 0u, red.part);
+    grid_finish<kThreads>(red, 1, 0u, 1.0);
 }
 template <typename R>
-void pf_xr(void* x, void* r, const void* p, const void* q, double alpha, size_t N, double* part,
+void pf_xr(void* x, void* r, const void* p, const void* q, double alpha, size_t N, const Red& red,
            cudaStream_t s) {
     k_pf_xr<R><<<kRedBlocks, kThreads, 0, s>>>((R*)x, (R*)r, (const R*)p, (const R*)q, (R)alpha,
-                                               N, part);
+                                               N, red);
 }
 
 // p = z + beta p; t = r + beta t
@@ -802,36 +1172,29 @@ void pf_pt(void* p, void* t, const void* z, const void* r, double beta, size_t N
                                                 N);
 }
 
-// phi_new = max(x, phi_t) (irreversibility, Algorithm 1); partial maxima of
-// |phi_new - phi_old|, |phi_new - phi_t|, and counts of changed and cracked
-// (phi >= 0.9) voxels.
+// phi_new = max(x, phi_t) (irreversibility, Algorithm 1); out: max
+// |phi_new - phi_old|, max |phi_new - phi_t|, count of changed and of
+// cracked (phi >= 0.9) voxels.
 template <typename R>
-__global__ void k_pf_clamp(const R* x, const R* phi_t, R* phi, size_t N, double* part) {
-    __shared__ double sh[32];
-    double m0 = 0, m1 = 0, c0 = 0, c1 = 0;
+__global__ void k_pf_clamp(const R* x, const R* phi_t, R* phi, size_t N, Red red) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
     GRID_STRIDE(v, N) {
         const R pt = phi_t[v];
         const R pn = fmax(x[v], pt);
         const R po = phi[v];
         phi[v] = pn;
-        m0 = fmax(m0, (double)fabs(pn - po));
-        m1 = fmax(m1, (double)fabs(pn - pt));
-        c0 += pn != po ? 1.0 : 0.0;
-        c1 += pn >= R(0.9) ? 1.0 : 0.0;
+        acc[0] = fmax(acc[0], (double)fabs(pn - po));
+        acc[1] = fmax(acc[1], (double)fabs(pn - pt));
+        acc[2] += pn != po ? 1.0 : 0.0;
+        acc[3] += pn >= R(0.9) ? 1.0 : 0.0;
     }
-    double r = block_max<kThreads>(m0, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = r;
-    r = block_max<kThreads>(m1, sh);
-    if (threadIdx.x == 0) part[kRedBlocks + blockIdx.x] = r;
-    r = block_sum<kThreads>(c0, sh);
-    if (threadIdx.x == 0) part[2 * kRedBlocks + blockIdx.x] = r;
-    r = block_sum<kThreads>(c1, sh);
-    if (threadIdx.x == 0) part[3 * kRedBlocks + blockIdx.x] = r;
+    block_partials<4, kThreads>(acc, 4, 3u, red.part);
+    grid_finish<kThreads>(red, 4, 3u, 1.0);
 }
 template <typename R>
-void pf_clamp(const void* x, const void* phi_t, void* phi, size_t N, double* part,
+void pf_clamp(const void* x, const void* phi_t, void* phi, size_t N, const Red& red,
               cudaStream_t s) {
-    k_pf_clamp<R><<<kRedBlocks, kThreads, 0, s>>>((const R*)x, (const R*)phi_t, (R*)phi, N, part);
+    k_pf_clamp<R><<<kRedBlocks, kThreads, 0, s>>>((const R*)x, (const R*)phi_t, (R*)phi, N, red);
 }
 
 // ----------------------------------------------------------- conversions
@@ -934,38 +1297,48 @@ void fp_in(const double* Fp, const int32_t* grain, const double* Qg, void* Hpi, 
     template void nye<R>(void*, const SGrid&, double, cudaStream_t);                            \
     template void gnd_rho<R>(const void*, const int32_t*, const double*, const double*, double, \
                              void*, size_t, cudaStream_t);                                      \
-    template void kbar<R>(const void*, const void*, double, size_t, double*, cudaStream_t);     \
+    template void kbar<R>(const void*, const void*, double, size_t, const Red&, cudaStream_t);  \
     template void degrade<R>(const void*, const void*, double, void*, size_t, cudaStream_t);    \
-    template void residual<R>(const void*, const SGrid&, void*, double*, cudaStream_t);         \
+    template void residual<R>(const void*, const SGrid&, void*, const Red&, cudaStream_t);      \
     template void precond_grad<R>(const void*, double, void*, const double*, const SGrid&,      \
                                   void*, int, cudaStream_t);                                    \
     template void tangent_apply<R>(void*, const void*, const void*, double, size_t,             \
                                    cudaStream_t);                                               \
+    template void contract_dots<R>(const void*, const SGrid&, void*, const void*, size_t, int,  \
+                                   const Red&, cudaStream_t, const GmState*);                   \
+    template void gs_update<R>(void*, const void*, size_t, int, const double*, int,             \
+                               const SGrid&, const Red&, cudaStream_t, const GmState*);         \
+    template void gm_precond_grad<R>(const GmArgs&, const double*, const SGrid&, void*,         \
+                                     cudaStream_t);                                             \
+    template void gm_reorth<R>(void*, const void*, size_t, const double*, GmState*,             \
+                               const SGrid&, const Red&, const Red&, cudaStream_t);             \
+    template void gm_reorth_flag<R>(const double*, GmState*, cudaStream_t);                     \
     template void contract<R>(const void*, const SGrid&, void*, cudaStream_t);                  \
-    template void hermitize<R>(void*, int, const SGrid&, cudaStream_t);                         \
-    template void mdot<R>(const void*, const void*, size_t, int, int, const SGrid&, double*,    \
-                          cudaStream_t);                                                        \
-    template void gs_update<R>(void*, const void*, size_t, int, const double*, size_t,          \
-                               cudaStream_t);                                                   \
+    template void vdots<R>(const void*, const void*, size_t, int, const SGrid&, const Red&,     \
+                           cudaStream_t, const GmState*, int);                                  \
+    template void vupdate<R>(void*, const void*, size_t, int, const double*, const SGrid&,      \
+                             const Red&, cudaStream_t, const GmState*, int);                    \
+    template void norm2<R>(const void*, const SGrid&, const Red&, cudaStream_t);                \
     template void xupdate<R>(void*, const void*, size_t, int, const double*, const double*,     \
                              const SGrid&, cudaStream_t);                                       \
     template void axpby<R>(void*, const void*, const void*, double, double, size_t,             \
                            cudaStream_t);                                                       \
-    template void fupdate<R>(void*, const void*, const void*, size_t, double*, cudaStream_t);   \
-    template void maxdiff<R>(const void*, const void*, size_t, double*, cudaStream_t);          \
-    template void maxval<R>(const void*, size_t, double*, cudaStream_t);                        \
-    template void pbar<R>(const void*, const void*, double, size_t, double*, cudaStream_t);     \
+    template void fupdate<R>(void*, const void*, const void*, size_t, const Red&, cudaStream_t);\
+    template void stag_stats<R>(const void*, const void*, const void*, const void*,             \
+                                const void*, double, size_t, const Red&, cudaStream_t);         \
+    template void maxval<R>(const void*, size_t, const Red&, cudaStream_t);                     \
     template void pf_spec<R>(void*, const SGrid&, double, int, cudaStream_t);                   \
-    template void pf_init<R>(const void*, const void*, const void*, void*, size_t, double*,     \
+    template void pf_init<R>(const void*, const void*, const void*, void*, size_t, const Red&,  \
                              cudaStream_t);                                                     \
-    template void rdot<R>(const void*, const void*, size_t, double*, cudaStream_t);             \
-    template void pf_q<R>(const void*, const void*, const void*, void*, size_t, double*,        \
+    template void rdot<R>(const void*, const void*, size_t, const Red&, cudaStream_t);          \
+    template void pf_q<R>(const void*, const void*, const void*, void*, size_t, const Red&,     \
                           cudaStream_t);                                                        \
-    template void pf_xr<R>(void*, void*, const void*, const void*, double, size_t, double*,     \
+    template void pf_xr<R>(void*, void*, const void*, const void*, double, size_t, const Red&,  \
                            cudaStream_t);                                                       \
     template void pf_pt<R>(void*, void*, const void*, const void*, double, size_t,              \
                            cudaStream_t);                                                       \
-    template void pf_clamp<R>(const void*, const void*, void*, size_t, double*, cudaStream_t);  \
+    template void pf_clamp<R>(const void*, const void*, void*, size_t, const Red&,              \
+                              cudaStream_t);                                                    \
     template void to_double<R>(const void*, double*, size_t, size_t, int, cudaStream_t);        \
     template void from_double<R>(const double*, void*, size_t, size_t, int, cudaStream_t);      \
     template void fp_in<R>(const double*, const int32_t*, const double*, void*, size_t,         \

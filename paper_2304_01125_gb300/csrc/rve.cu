@@ -23,7 +23,7 @@ using namespace fatfft;
 namespace {
 enum { ST_NEW = 0, ST_APPLIED = 1, ST_EQUIL = 2, ST_DAMAGE = 3, ST_COMMITTED = 4 };
 constexpr int kMaxRestart = 64;
-constexpr int kRedSlots = 256;
+constexpr int kSlot = 160;  // doubles per look-ahead slot: red[0..130) + GmState
 }  // namespace
 
 struct fft_rve_s {
@@ -51,9 +51,15 @@ struct fft_rve_s {
     void *V = nullptr, *x = nullptr, *b = nullptr, *w = nullptr;  // GMRES (complex)
     void *pfx = nullptr, *pfr = nullptr, *pfz = nullptr, *pfp = nullptr, *pft = nullptr,
          *pfq = nullptr;
-    double *part = nullptr, *red = nullptr, *dy = nullptr;
+    double *part = nullptr, *red = nullptr, *dy = nullptr, *dzero = nullptr;
+    unsigned* counter = nullptr;  // ticket of the last-block reductions
     double *hred = nullptr, *hy = nullptr;  // pinned host
+    double* hslot = nullptr;                // pinned look-ahead slots, 2 x kSlot doubles
+    GmState* gst = nullptr;                 // device Arnoldi position
+    cudaEvent_t slot_ev[2] = {nullptr, nullptr};
     int* dfail = nullptr;
+    double* stage = nullptr;  // device staging for host fields_out / fields_in
+    size_t stage_bytes = 0;
     std::vector<void*> allocs;
     size_t bytes = 0;
     long long launches = 0;
@@ -62,10 +68,12 @@ struct fft_rve_s {
     struct ProfEv {
         cudaEvent_t a, b;
         int fam;
+        double bytes;
     };
     std::vector<ProfEv> prof_pending;
     std::vector<cudaEvent_t> prof_pool;
     double prof_ms[16] = {0};
+    double prof_bytes[16] = {0};
     long long prof_cnt[16] = {0};
     // Algorithm 1 bookkeeping
     double Fbar_t[9], Fbar[9], dt = 0;
@@ -98,6 +106,8 @@ struct fft_rve_s {
         if (_s != FFT_OK) return _s;  \
     } while (0)
 
+static Red red_at(fft_rve_s* r, double* out) { return Red{r->part, r->counter, out}; }
+
 // kernel families for the opt-in timing
 enum {
     KF_CP = 0, KF_TANGENT = 1, KF_PRECOND = 2, KF_CONTRACT = 3, KF_MDOT = 4, KF_GSUPD = 5,
@@ -116,7 +126,8 @@ static cudaEvent_t prof_begin(fft_rve_s* r, int fam) {
     cudaEventRecord(e, r->st);
     return e;
 }
-static void prof_end(fft_rve_s* r, int fam, cudaEvent_t a) {
+// bytes: the algorithmic HBM traffic of the bracketed launch(es)
+static void prof_end(fft_rve_s* r, int fam, cudaEvent_t a, double bytes = 0.0) {
     if (!a) return;
     cudaEvent_t b;
     if (r->prof_pool.empty()) {
@@ -126,7 +137,7 @@ static void prof_end(fft_rve_s* r, int fam, cudaEvent_t a) {
         r->prof_pool.pop_back();
     }
     cudaEventRecord(b, r->st);
-    r->prof_pending.push_back({a, b, fam});
+    r->prof_pending.push_back({a, b, fam, bytes});
 }
 // after a stream synchronisation: fold the recorded pairs into the totals
 static void prof_collect(fft_rve_s* r) {
@@ -134,12 +145,35 @@ static void prof_collect(fft_rve_s* r) {
         float ms = 0;
         if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
             r->prof_ms[p.fam] += ms;
+            r->prof_bytes[p.fam] += p.bytes;
             r->prof_cnt[p.fam] += 1;
         }
         r->prof_pool.push_back(p.a);
         r->prof_pool.push_back(p.b);
     }
     r->prof_pending.clear();
+}
+
+// fold in the recorded pairs whose end event has completed (no waiting)
+static void prof_collect_if_done(fft_rve_s* r) {
+    if (r->prof_pending.empty()) return;
+    std::vector<fft_rve_s::ProfEv> keep;
+    for (auto& p : r->prof_pending) {
+        if (cudaEventQuery(p.b) != cudaSuccess) {
+            keep.push_back(p);
+            continue;
+        }
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            r->prof_ms[p.fam] += ms;
+            r->prof_bytes[p.fam] += p.bytes;
+            r->prof_cnt[p.fam] += 1;
+        }
+        r->prof_pool.push_back(p.a);
+        r->prof_pool.push_back(p.b);
+    }
+    r->prof_pending.swap(keep);
+    cudaGetLastError();  // cudaEventQuery's cudaErrorNotReady is not an error here
 }
 
 static fft_status dalloc(fft_rve_s* r, void** p, size_t bytes) {
@@ -343,7 +377,12 @@ struct Impl {
         CK(r, cudaMemsetAsync(r->dfail, 0, sizeof(int), r->st));
         cudaEvent_t e = prof_begin(r, KF_CP);
         launch_constitutive<R>(f, p, hist, r->st);
-        prof_end(r, KF_CP, e);
+        // H, Hpi, rho_gnd, grain, rho history in; P, K out; with history also
+        // the 32-slot FP64 history in and out, Hpi_tr, drive, W_e+ out
+        const double N = (double)r->g.N, es = (double)sizeof(R);
+        prof_end(r, KF_CP, e,
+                 N * (es * (9 + 9 + 1 + 9 + 81) + 4 + 16 +
+                      (hist ? 2.0 * HIST_SLOTS * 8 + es * 11 : 0.0)));
         r->launches += 1;
         CK(r, cudaGetLastError());
         int nf = 0;
@@ -356,39 +395,85 @@ struct Impl {
         return FFT_OK;
     }
 
-    // w = A u with A u = -F{g K : F^-1{u (x) i xi}} . i xi; use_pre applies
-    // the Green preconditioner to u first (scaled by scale, optionally
-    // stored to vout).
+    // w = A u with A u = -F{g K : F^-1{u (x) i xi}} . i xi, projected onto
+    // real fields; use_pre applies the Green preconditioner to u first
+    // (u scaled by scale, optionally stored to vout).
     static fft_status apply_op(fft_rve_s* r, const void* u, double scale, void* vout, int use_pre,
-                               void* w) {
+                               void* w, int nv) {
+        const double N = (double)r->g.N, Nh = (double)r->g.Nh, es = (double)sizeof(R);
         cudaEvent_t e = prof_begin(r, KF_PRECOND);
         precond_grad<R>(u, scale, vout, r->Kbar, r->g, r->cb9, use_pre, r->st);
-        prof_end(r, KF_PRECOND, e);
+        prof_end(r, KF_PRECOND, e, Nh * 2 * es * (3 + 9 + (vout ? 3 : 0)));
         TRY(inv9(r));
         e = prof_begin(r, KF_TANGENT);
         tangent_apply<R>(r->rb9, r->K, r->phi, r->mat.k_res, r->g.N, r->st);
-        prof_end(r, KF_TANGENT, e);
+        prof_end(r, KF_TANGENT, e, N * es * (9 + 81 + 1 + 9));
         TRY(fwd9(r));
         e = prof_begin(r, KF_CONTRACT);
         contract<R>(r->cb9, r->g, w, r->st);
-        hermitize<R>(w, 3, r->g, r->st);
-        prof_end(r, KF_CONTRACT, e);
-        r->launches += 4;
+        prof_end(r, KF_CONTRACT, e, Nh * 2 * es * (9 + 3));
+        r->launches += 3;
+        (void)nv;
         return FFT_OK;
     }
 
-    // Restarted GMRES, right-preconditioned by the Green operator, classical
-    // Gram-Schmidt with one re-orthogonalisation; Hermitian-weighted FP64 dot
-    // products; Hessenberg least squares on the host.
+    // One Arnoldi step with operands from the device state (look-ahead GMRES):
+    // w = A M v_k projected onto real fields, red[0] = ||w||^2 and
+    // red[1 + i] = <V_i, w>; first Gram-Schmidt update (red[64] = new
+    // ||w||^2); optional second pass (red[97 + i], red[64] replaced); the
+    // results are copied to slot j % 2 and the state advanced.
+    static fft_status enqueue_step(fft_rve_s* r, int j) {
+        const double N = (double)r->g.N, Nh = (double)r->g.Nh, es = (double)sizeof(R);
+        const size_t vs = 3 * r->g.Nh;
+        GmArgs ga{r->gst, r->V, r->w, vs};
+        cudaEvent_t e = prof_begin(r, KF_PRECOND);
+        gm_precond_grad<R>(ga, r->Kbar, r->g, r->cb9, r->st);
+        prof_end(r, KF_PRECOND, e, Nh * 2 * es * (3 + 9 + (j ? 3 : 0)));
+        TRY(inv9(r));
+        e = prof_begin(r, KF_TANGENT);
+        tangent_apply<R>(r->rb9, r->K, r->phi, r->mat.k_res, r->g.N, r->st);
+        prof_end(r, KF_TANGENT, e, N * es * (9 + 81 + 1 + 9));
+        TRY(fwd9(r));
+        e = prof_begin(r, KF_CONTRACT);
+        contract<R>(r->cb9, r->g, r->w, r->st);
+        prof_end(r, KF_CONTRACT, e, Nh * 2 * es * (9 + 3));
+        // red[0] = ||w||^2, red[1 + i] = <V_i, w>; w -= V h, red[64] = ||w||^2
+        e = prof_begin(r, KF_MDOT);
+        vdots<R>(r->w, r->V, vs, j + 1, r->g, red_at(r, r->red), r->st, r->gst, 0);
+        prof_end(r, KF_MDOT, e, Nh * 2 * es * 3 * (j + 2));
+        e = prof_begin(r, KF_GSUPD);
+        vupdate<R>(r->w, r->V, vs, j + 1, r->red, r->g, red_at(r, r->red + 64), r->st, r->gst, 0);
+        prof_end(r, KF_GSUPD, e, Nh * 2 * es * 3 * (j + 3));
+        // second pass only when the norm dropped below 1/sqrt(2) (decided on the device)
+        gm_reorth_flag<R>(r->red, r->gst, r->st);
+        vdots<R>(r->w, r->V, vs, j + 1, r->g, red_at(r, r->red + 96), r->st, r->gst, 1);
+        vupdate<R>(r->w, r->V, vs, j + 1, r->red + 96, r->g, red_at(r, r->red + 64), r->st, r->gst,
+                   1);
+        double* slot = r->hslot + (size_t)(j % 2) * kSlot;
+        CK(r, cudaMemcpyAsync(slot, r->red, 130 * sizeof(double), cudaMemcpyDeviceToHost, r->st));
+        CK(r, cudaMemcpyAsync(slot + 130, r->gst, sizeof(GmState), cudaMemcpyDeviceToHost, r->st));
+        gm_advance(r->gst, r->red + 64, r->st);
+        CK(r, cudaEventRecord(r->slot_ev[j % 2], r->st));
+        r->launches += 9;
+        return FFT_OK;
+    }
+
+    // Restarted GMRES, right-preconditioned by the Green operator; classical
+    // Gram-Schmidt with a second pass when the norm drops below 1/sqrt(2) of
+    // its value (the DGKS test, decided on the device); Hermitian-weighted
+    // FP64 dot products; Hessenberg least squares on the host one step behind
+    // the GPU (step j runs while column j - 1 is processed, so the device
+    // never waits for the host; the step after convergence is discarded).
     static fft_status gmres(fft_rve_s* r, double bn, double pn, int* its) {
         const size_t Nh = r->g.Nh, n3 = 3 * Nh;
+        const double es = (double)sizeof(R);
         // round-off floor relative to the scale of the terms summed into b
         const double eta = sizeof(R) == 8 ? 1e-12 : 5e-7;
         const double target = std::max(r->opt.tol_lin * bn, eta * pn);
         CK(r, cudaMemsetAsync(r->x, 0, n3 * sizeof(Cx), r->st));
         *its = 0;
         if (bn <= target) return FFT_OK;
-        const int m = std::max(1, std::min(r->opt.restart, kMaxRestart));
+        const int m = std::max(1, std::min(r->opt.restart, kMaxKrylov - 1));
         const size_t vs = n3;  // stride between Krylov vectors (elements)
         Cx* V = (Cx*)r->V;
         std::vector<double> Hm((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
@@ -400,11 +485,10 @@ struct Impl {
                 beta = bn;
                 axpby<R>(V, r->b, nullptr, 1.0 / beta, 0.0, n3, r->st);
             } else {
-                TRY(apply_op(r, r->x, 1.0, nullptr, 0, r->w));
+                TRY(apply_op(r, r->x, 1.0, nullptr, 0, r->w, 0));
                 axpby<R>(r->w, r->b, r->w, 1.0, -1.0, n3, r->st);
-                mdot<R>(r->w, nullptr, 0, 0, 1, r->g, r->part, r->st);
-                finalize_sum(r->part, 1, 1.0, r->red, r->st);
-                r->launches += 3;
+                norm2<R>(r->w, r->g, red_at(r, r->red), r->st);
+                r->launches += 2;
                 TRY(fetch(r, 1));
                 beta = std::sqrt(r->hred[0]);
                 if (beta <= target) {
@@ -413,42 +497,32 @@ struct Impl {
                 }
                 axpby<R>(V, r->w, nullptr, 1.0 / beta, 0.0, n3, r->st);
             }
-            r->launches += 1;
+            gm_reset(r->gst, r->st);
+            r->launches += 2;
             first = false;
             std::fill(Hm.begin(), Hm.end(), 0.0);
             std::fill(gv.begin(), gv.end(), 0.0);
             gv[0] = beta;
-            double hprev = 0;
-            int k = 0;
-            for (; k < m && lin < r->opt.max_lin; ++k) {
-                ++lin;
-                if (k == 0)
-                    TRY(apply_op(r, V, 1.0, nullptr, 1, r->w));
-                else
-                    TRY(apply_op(r, r->w, 1.0 / hprev, V + (size_t)k * vs, 1, r->w));
-                // h = V^T w ; w -= V h ; h2 = V^T w ; w -= V h2 ; ||w||
-                cudaEvent_t e = prof_begin(r, KF_MDOT);
-                mdot<R>(r->w, V, vs, k + 1, 0, r->g, r->part, r->st);
-                finalize_sum(r->part, k + 1, 1.0, r->red, r->st);
-                prof_end(r, KF_MDOT, e);
-                e = prof_begin(r, KF_GSUPD);
-                gs_update<R>(r->w, V, vs, k + 1, r->red, n3, r->st);
-                prof_end(r, KF_GSUPD, e);
-                e = prof_begin(r, KF_MDOT);
-                mdot<R>(r->w, V, vs, k + 1, 0, r->g, r->part, r->st);
-                finalize_sum(r->part, k + 1, 1.0, r->red + 64, r->st);
-                prof_end(r, KF_MDOT, e);
-                e = prof_begin(r, KF_GSUPD);
-                gs_update<R>(r->w, V, vs, k + 1, r->red + 64, n3, r->st);
-                prof_end(r, KF_GSUPD, e);
-                e = prof_begin(r, KF_MDOT);
-                mdot<R>(r->w, nullptr, 0, 0, 1, r->g, r->part, r->st);
-                finalize_sum(r->part, 1, 1.0, r->red + 128, r->st);
-                prof_end(r, KF_MDOT, e);
-                r->launches += 8;
-                TRY(fetch(r, 129));
-                for (int i = 0; i <= k; ++i) Hm[i * m + k] = r->hred[i] + r->hred[64 + i];
-                const double hn = std::sqrt(std::max(r->hred[128], 0.0));
+            int kcols = 0;
+            for (int j = 0;; ++j) {
+                const bool enq = j < m && lin + j < r->opt.max_lin;
+                if (enq) TRY(enqueue_step(r, j));
+                if (j == 0) {
+                    if (!enq) break;
+                    continue;
+                }
+                // column k = j - 1
+                const int k = j - 1;
+                CK(r, cudaEventSynchronize(r->slot_ev[k % 2]));
+                prof_collect_if_done(r);
+                const double* slot = r->hslot + (size_t)(k % 2) * kSlot;
+                GmState gs;
+                std::memcpy(&gs, slot + 130, sizeof(GmState));
+                for (int i = 0; i <= k; ++i)
+                    Hm[i * m + k] = slot[1 + i] + (gs.reorth ? slot[97 + i] : 0.0);
+                const double hn = std::sqrt(std::max(slot[64], 0.0));
+                if (!std::isfinite(hn) || !std::isfinite(slot[0]))
+                    FAIL(r, FFT_ERR_NONFINITE, "non-finite Krylov vector (step %d)", lin + 1);
                 Hm[(k + 1) * m + k] = hn;
                 for (int i = 0; i < k; ++i) {
                     const double t = cs[i] * Hm[i * m + k] + sn[i] * Hm[(i + 1) * m + k];
@@ -462,26 +536,30 @@ struct Impl {
                 Hm[(k + 1) * m + k] = 0.0;
                 gv[k + 1] = -sn[k] * gv[k];
                 gv[k] = cs[k] * gv[k];
-                hprev = hn;
+                ++lin;
+                kcols = k + 1;
                 if (r->verbose)
-                    std::fprintf(stderr, "  gmres it %d |r|/|b| %.3e (|b| %.3e, h %.3e)\n", lin,
-                                 std::fabs(gv[k + 1]) / bn, bn, hn);
+                    std::fprintf(stderr, "  gmres it %d |r|/|b| %.3e (|b| %.3e, h %.3e%s)\n", lin,
+                                 std::fabs(gv[k + 1]) / bn, bn, hn, gs.reorth ? ", reorth" : "");
                 if (std::fabs(gv[k + 1]) <= target || hn == 0.0) {
                     ok = true;
-                    ++k;
                     break;
                 }
+                if (!enq) break;
             }
+            const int k = kcols;
             for (int i = k - 1; i >= 0; --i) {
                 double s = gv[i];
                 for (int j = i + 1; j < k; ++j) s -= Hm[i * m + j] * y[j];
                 y[i] = s / Hm[i * m + i];
             }
+            CK(r, cudaStreamSynchronize(r->st));  // the discarded look-ahead step, hy reuse
+            prof_collect(r);
             std::memcpy(r->hy, y.data(), k * sizeof(double));
             CK(r, cudaMemcpyAsync(r->dy, r->hy, k * sizeof(double), cudaMemcpyHostToDevice, r->st));
             cudaEvent_t e = prof_begin(r, KF_XUPD);
             xupdate<R>(r->x, V, vs, k, r->dy, r->Kbar, r->g, r->st);
-            prof_end(r, KF_XUPD, e);
+            prof_end(r, KF_XUPD, e, (double)Nh * 2 * es * 3 * (k + 2));
             r->launches += 1;
             CK(r, cudaStreamSynchronize(r->st));  // hy is reused by the next fetch
             prof_collect(r);
@@ -511,27 +589,31 @@ struct Impl {
                 if (st) st->local_fail += nf;
             }
             if (st) st->newton_it += 1;
-            kbar<R>(r->K, r->phi, r->mat.k_res, N, r->part, r->st);
-            finalize_sum(r->part, 81, 1.0 / (double)N, r->Kbar, r->st);
+            cudaEvent_t e = prof_begin(r, KF_KBAR);
+            kbar<R>(r->K, r->phi, r->mat.k_res, N, red_at(r, r->Kbar), r->st);
+            prof_end(r, KF_KBAR, e, (double)N * sizeof(R) * 82);
+            e = prof_begin(r, KF_RESID);
             degrade<R>(r->P, r->phi, r->mat.k_res, r->rb9, N, r->st);
+            prof_end(r, KF_RESID, e, (double)N * sizeof(R) * 19);
             TRY(fwd9(r));
-            residual<R>(r->cb9, r->g, r->b, r->part, r->st);
-            finalize_sum(r->part + kRedBlocks, 1, 1.0, r->red + 1, r->st);
-            hermitize<R>(r->b, 3, r->g, r->st);
-            mdot<R>(r->b, nullptr, 0, 0, 1, r->g, r->part, r->st);
-            finalize_sum(r->part, 1, 1.0, r->red, r->st);
-            r->launches += 8;
+            e = prof_begin(r, KF_RESID);
+            residual<R>(r->cb9, r->g, r->b, red_at(r, r->red), r->st);
+            prof_end(r, KF_RESID, e, (double)r->g.Nh * 2 * sizeof(R) * 12);
+            r->launches += 3;
             TRY(fetch(r, 2));
             const double bn = std::sqrt(r->hred[0]), pn = std::sqrt(r->hred[1]);
             int lin = 0;
             const fft_status s = gmres(r, bn, pn, &lin);
             if (st) st->lin_it_total += lin;
             if (s != FFT_OK) return s;
+            e = prof_begin(r, KF_PRECOND);
             precond_grad<R>(r->x, 1.0, nullptr, r->Kbar, r->g, r->cb9, 0, r->st);
+            prof_end(r, KF_PRECOND, e, (double)r->g.Nh * 2 * sizeof(R) * 12);
             TRY(inv9(r));
-            fupdate<R>(r->H, r->rb9, r->Ht, N, r->part, r->st);
-            finalize_max(r->part, 2, r->red, r->st);
-            r->launches += 3;
+            e = prof_begin(r, KF_FUPD);
+            fupdate<R>(r->H, r->rb9, r->Ht, N, red_at(r, r->red), r->st);
+            prof_end(r, KF_FUPD, e, (double)N * sizeof(R) * 36);
+            r->launches += 2;
             TRY(fetch(r, 2));
             r->cp_valid = false;
             const double gmax = r->hred[0], dFt = std::max(r->hred[1], 1e-30);
@@ -554,9 +636,8 @@ struct Impl {
         TRY(fwd1(r, r->pfx));
         pf_spec<R>(r->cb9, r->g, l2, 0, r->st);
         TRY(inv1(r, r->pfq));
-        pf_init<R>(r->pfx, r->pfq, r->drive, r->pfr, N, r->part, r->st);
-        finalize_sum(r->part, 2, 1.0, r->red, r->st);
-        r->launches += 3;
+        pf_init<R>(r->pfx, r->pfq, r->drive, r->pfr, N, red_at(r, r->red), r->st);
+        r->launches += 2;
         TRY(fetch(r, 2));
         const double bn = std::sqrt(r->hred[1]);
         if (std::sqrt(r->hred[0]) <= r->opt.tol_pf * bn) return FFT_OK;
@@ -564,9 +645,8 @@ struct Impl {
             TRY(fwd1(r, r->pfr));
             pf_spec<R>(r->cb9, r->g, l2, 1, r->st);
             TRY(inv1(r, r->pfz));
-            rdot<R>(r->pfr, r->pfz, N, r->part, r->st);
-            finalize_sum(r->part, 1, 1.0, r->red, r->st);
-            r->launches += 3;
+            rdot<R>(r->pfr, r->pfz, N, red_at(r, r->red), r->st);
+            r->launches += 2;
             return fetch(r, 1);
         };
         TRY(precond());
@@ -575,13 +655,11 @@ struct Impl {
         CK(r, cudaMemcpyAsync(r->pft, r->pfr, N * sizeof(R), cudaMemcpyDeviceToDevice, r->st));
         for (int it = 1; it <= r->opt.max_pf; ++it) {
             *iters = it;
-            pf_q<R>(r->pft, r->pfp, r->drive, r->pfq, N, r->part, r->st);
-            finalize_sum(r->part, 1, 1.0, r->red, r->st);
+            pf_q<R>(r->pft, r->pfp, r->drive, r->pfq, N, red_at(r, r->red), r->st);
             TRY(fetch(r, 1));
             const double alpha = rz / r->hred[0];
-            pf_xr<R>(r->pfx, r->pfr, r->pfp, r->pfq, alpha, N, r->part, r->st);
-            finalize_sum(r->part, 1, 1.0, r->red, r->st);
-            r->launches += 4;
+            pf_xr<R>(r->pfx, r->pfr, r->pfp, r->pfq, alpha, N, red_at(r, r->red), r->st);
+            r->launches += 2;
             TRY(fetch(r, 1));
             if (std::sqrt(r->hred[0]) <= r->opt.tol_pf * bn) return FFT_OK;
             TRY(precond());
@@ -597,9 +675,8 @@ struct Impl {
     // out: max|phi_new - phi_old|, max|phi_new - phi_t|, changed, cracked.
     static fft_status phase_field(fft_rve_s* r, int* iters, double* out4) {
         const size_t N = r->g.N;
-        maxval<R>(r->drive, N, r->part, r->st);
-        finalize_max(r->part, 1, r->red, r->st);
-        r->launches += 2;
+        maxval<R>(r->drive, N, red_at(r, r->red), r->st);
+        r->launches += 1;
         TRY(fetch(r, 1));
         *iters = 0;
         if (r->hred[0] == 0.0) {
@@ -607,10 +684,8 @@ struct Impl {
         } else {
             TRY(pcg_phase(r, iters));
         }
-        pf_clamp<R>(r->pfx, r->phi_t, r->phi, N, r->part, r->st);
-        finalize_max(r->part, 2, r->red, r->st);
-        finalize_sum(r->part + 2 * kRedBlocks, 2, 1.0, r->red + 2, r->st);
-        r->launches += 3;
+        pf_clamp<R>(r->pfx, r->phi_t, r->phi, N, red_at(r, r->red), r->st);
+        r->launches += 1;
         TRY(fetch(r, 4));
         for (int i = 0; i < 4; ++i) out4[i] = r->hred[i];
         return FFT_OK;
@@ -637,12 +712,9 @@ struct Impl {
         double o4[4];
         TRY(phase_field(r, &pf_it, o4));
         if (st) st->pf_it_total += pf_it;
-        maxdiff<R>(r->H, r->Hprev, 9 * N, r->part, r->st);
-        maxdiff<R>(r->H, r->Ht, 9 * N, r->part + kRedBlocks, r->st);
-        finalize_max(r->part, 2, r->red, r->st);
-        pbar<R>(r->P, r->phi, r->mat.k_res, N, r->part + 2 * kRedBlocks, r->st);
-        finalize_sum(r->part + 2 * kRedBlocks, 9, 1.0 / (double)N, r->red + 2, r->st);
-        r->launches += 5;
+        stag_stats<R>(r->H, r->Hprev, r->Ht, r->P, r->phi, r->mat.k_res, N, red_at(r, r->red),
+                      r->st);
+        r->launches += 1;
         TRY(fetch(r, 11));
         const double dF = r->hred[0], dFt = r->hred[1];
         const double dphi = o4[0], dphit = o4[1];
@@ -807,8 +879,32 @@ static void release(fft_rve_s* r) {
         cufftDestroy(r->c2r1);
     }
     for (void* p : r->allocs) cudaFree(p);
+    if (r->stage) cudaFree(r->stage);
     if (r->hred) cudaFreeHost(r->hred);
     if (r->hy) cudaFreeHost(r->hy);
+    if (r->hslot) cudaFreeHost(r->hslot);
+    for (auto e : r->slot_ev)
+        if (e) cudaEventDestroy(e);
+}
+
+// Staging buffer for host-side field copies, grown on demand (field copies
+// are not on the increment's path).
+static fft_status ensure_stage(fft_rve_s* r, size_t bytes) {
+    if (r->stage_bytes >= bytes) return FFT_OK;
+    if (r->stage) {
+        cudaStreamSynchronize(r->st);
+        cudaFree(r->stage);
+        r->bytes -= r->stage_bytes;
+        r->stage = nullptr;
+        r->stage_bytes = 0;
+    }
+    if (cudaMalloc((void**)&r->stage, bytes) != cudaSuccess) {
+        r->stage = nullptr;
+        FAIL(r, FFT_ERR_OOM, "field staging buffer (%zu bytes)", bytes);
+    }
+    r->stage_bytes = bytes;
+    r->bytes += bytes;
+    return FFT_OK;
 }
 
 extern "C" {
@@ -867,7 +963,7 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
     std::memcpy(r->Fbar_t, I9, sizeof(I9));
     std::memcpy(r->Fbar, I9, sizeof(I9));
     const size_t es = r->esz, cs = 2 * r->esz;
-    const int m = std::max(1, std::min(opt->restart, kMaxRestart));
+    const int m = std::max(1, std::min(opt->restart, kMaxKrylov - 1));
     fft_status s = FFT_OK;
 #define AL(ptr, bytes)                                    \
     do {                                                  \
@@ -911,11 +1007,17 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
     AL(r->part, (size_t)kRedSlots * kRedBlocks * sizeof(double));
     AL(r->red, kRedSlots * sizeof(double));
     AL(r->dy, kMaxRestart * sizeof(double));
+    AL(r->dzero, kMaxRestart * sizeof(double));
+    AL(r->counter, sizeof(unsigned));
+    AL(r->gst, sizeof(GmState));
     AL(r->dfail, sizeof(int));
     if (elastic_only) AL(r->elastic, N);
 #undef AL
     if (cudaMallocHost((void**)&r->hred, kRedSlots * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost((void**)&r->hy, kMaxRestart * sizeof(double)) != cudaSuccess) {
+        cudaMallocHost((void**)&r->hy, kMaxRestart * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&r->hslot, 2 * kSlot * sizeof(double)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r->slot_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r->slot_ev[1], cudaEventDisableTiming) != cudaSuccess) {
         release(r);
         delete r;
         return FFT_ERR_OOM;
@@ -929,6 +1031,8 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
     cudaMemcpyAsync(r->G81, G81, sizeof(G81), cudaMemcpyHostToDevice, r->st);
     if (elastic_only)
         cudaMemcpyAsync(r->elastic, elastic_only, N, cudaMemcpyHostToDevice, r->st);
+    cudaMemsetAsync(r->dzero, 0, kMaxRestart * sizeof(double), r->st);
+    cudaMemsetAsync(r->counter, 0, sizeof(unsigned), r->st);
     upload_slip_table(r->st);
     // cuFFT plans: dims slowest-first (n2, n1, n0); 9-field batches use the
     // contiguous component-major layout.
@@ -1006,17 +1110,16 @@ fft_status fields_out(fft_rve_t r, int field, void* dst, size_t bytes, int dst_i
     const size_t need = (size_t)nc * r->g.N * sizeof(double);
     if (bytes < need) FAIL(r, FFT_ERR_ARG, "fields_out: %zu bytes < %zu", bytes, need);
     double* d = (double*)dst;
-    double* tmp = nullptr;
     if (!dst_is_device) {
-        if (cudaMalloc(&tmp, need) != cudaSuccess) FAIL(r, FFT_ERR_OOM, "fields_out staging");
-        d = tmp;
+        fft_status a = ensure_stage(r, need);
+        if (a != FFT_OK) return a;
+        d = r->stage;
     }
     fft_status s = DISPATCH(r, fields_out(r, field, d));
     if (s == FFT_OK && !dst_is_device)
-        if (cudaMemcpyAsync(dst, tmp, need, cudaMemcpyDeviceToHost, r->st) != cudaSuccess)
+        if (cudaMemcpyAsync(dst, d, need, cudaMemcpyDeviceToHost, r->st) != cudaSuccess)
             s = FFT_ERR_CUDA;
     if (cudaStreamSynchronize(r->st) != cudaSuccess && s == FFT_OK) s = FFT_ERR_CUDA;
-    if (tmp) cudaFree(tmp);
     return s;
 }
 
@@ -1029,14 +1132,12 @@ fft_status fields_in(fft_rve_t r, int field, const double* src, size_t bytes) {
         nc = 12;
     const size_t need = (size_t)nc * r->g.N * sizeof(double);
     if (bytes < need) FAIL(r, FFT_ERR_ARG, "fields_in: %zu bytes < %zu", bytes, need);
-    double* tmp = nullptr;
-    if (cudaMalloc(&tmp, need) != cudaSuccess) FAIL(r, FFT_ERR_OOM, "fields_in staging");
-    fft_status s = FFT_OK;
-    if (cudaMemcpyAsync(tmp, src, need, cudaMemcpyHostToDevice, r->st) != cudaSuccess)
+    fft_status s = ensure_stage(r, need);
+    if (s != FFT_OK) return s;
+    if (cudaMemcpyAsync(r->stage, src, need, cudaMemcpyHostToDevice, r->st) != cudaSuccess)
         s = FFT_ERR_CUDA;
-    if (s == FFT_OK) s = DISPATCH(r, fields_in(r, field, tmp));
+    if (s == FFT_OK) s = DISPATCH(r, fields_in(r, field, r->stage));
     if (cudaStreamSynchronize(r->st) != cudaSuccess && s == FFT_OK) s = FFT_ERR_CUDA;
-    cudaFree(tmp);
     return s;
 }
 
@@ -1070,16 +1171,19 @@ fft_status rve_profile(fft_rve_t r, unsigned mask) {
     return FFT_OK;
 }
 
-fft_status rve_profile_read(fft_rve_t r, double* ms, long long* counts, int reset) {
+fft_status rve_profile_read(fft_rve_t r, double* ms, long long* counts, double* bytes,
+                            int reset) {
     if (!r || !ms || !counts) return FFT_ERR_ARG;
     if (cudaStreamSynchronize(r->st) != cudaSuccess) return FFT_ERR_CUDA;
     prof_collect(r);
     for (int i = 0; i < 16; ++i) {
         ms[i] = r->prof_ms[i];
         counts[i] = r->prof_cnt[i];
+        if (bytes) bytes[i] = r->prof_bytes[i];
         if (reset) {
             r->prof_ms[i] = 0;
             r->prof_cnt[i] = 0;
+            r->prof_bytes[i] = 0;
         }
     }
     return FFT_OK;

@@ -94,7 +94,8 @@ def load(path=LIB_PATH):
     L.rve_kernel_launches.restype = C.c_longlong
     L.rve_profile.argtypes = [vp, C.c_uint]
     L.rve_profile.restype = C.c_int
-    L.rve_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]
+    L.rve_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                   C.POINTER(C.c_double), C.c_int]
     L.rve_profile_read.restype = C.c_int
     L.degraded_average_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t,
                                            C.c_double, C.c_void_p, C.c_void_p]
@@ -265,8 +266,10 @@ class RVE:
     def profile_read(self, reset=True):
         ms = (C.c_double * 16)()
         cnt = (C.c_longlong * 16)()
-        self._check("rve_profile_read", load().rve_profile_read(self._h, ms, cnt, int(reset)))
-        return {f: (ms[i], cnt[i]) for i, f in enumerate(KERNEL_FAMILIES) if cnt[i]}
+        by = (C.c_double * 16)()
+        self._check("rve_profile_read", load().rve_profile_read(self._h, ms, cnt, by,
+                                                                int(reset)))
+        return {f: (ms[i], cnt[i], by[i]) for i, f in enumerate(KERNEL_FAMILIES) if cnt[i]}
 
     @property
     def device_bytes(self):
