@@ -54,7 +54,9 @@ typedef enum {
 
 typedef enum { FFT_PREC_FP64 = 0, FFT_PREC_MIXED = 1 } fft_precision;
 
-/* Grid: voxel counts and voxel edge length h (mm); L_i = n_i h. */
+/* Grid: voxel counts and voxel edge length h (mm); L_i = n_i h.  Each n_i in
+ * [1, 4096] and 9 (n0/2 + 1) n1 n2 < 2^31 (32-bit spectral indexing; 512^3
+ * fits), else FFT_ERR_ARG. */
 typedef struct {
     int n[3];
     double h;

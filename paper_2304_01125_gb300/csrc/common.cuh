@@ -103,68 +103,86 @@ struct Red {
     double* out;        // [values] results
 };
 
-template <int NV, int NT>
-__device__ __forceinline__ void block_partials(const double (&acc)[NV], int nv, unsigned maxmask,
+// Per-block partial sums (or maxima, bit v of maxmask) of nv <= NV values:
+// warp shuffles and the combine over warps run in the accumulator type T
+// (the bulk type: FP64 arithmetic is a narrow pipe on this GPU), and one
+// FP64 partial per value is stored at part[v * gridDim.x + blockIdx.x].
+template <int NV, int NT, typename T>
+__device__ __forceinline__ void block_partials(const T (&acc)[NV], int nv, unsigned maxmask,
                                                double* part) {
-    __shared__ double sh[NT / 32][NV];
+    __shared__ T sh[NT / 32][NV];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         if (v < nv) {
-            double x = acc[v];
-            const bool mx = (maxmask >> v) & 1u;
+            T x = acc[v];
+            const bool mx = v < 32 && ((maxmask >> v) & 1u);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const double y = __shfl_down_sync(0xffffffffu, x, o);
-                x = mx ? fmax(x, y) : x + y;
+                const T y = __shfl_down_sync(0xffffffffu, x, o);
+                x = mx ? (x > y ? x : y) : x + y;
             }
             if (lane == 0) sh[wid][v] = x;
         }
     }
     __syncthreads();
     for (int v = threadIdx.x; v < nv; v += NT) {
-        const bool mx = (maxmask >> v) & 1u;
-        double s = 0.0;
-        for (int w = 0; w < NT / 32; ++w) s = mx ? fmax(s, sh[w][v]) : s + sh[w][v];
-        part[(size_t)v * gridDim.x + blockIdx.x] = s;
+        const bool mx = v < 32 && ((maxmask >> v) & 1u);
+        T s = 0;
+        for (int w = 0; w < NT / 32; ++w) s = mx ? (s > sh[w][v] ? s : sh[w][v]) : s + sh[w][v];
+        part[(size_t)v * gridDim.x + blockIdx.x] = (double)s;
+        __threadfence();  // publish the partial before the block takes its ticket
     }
 }
 
-template <int NT>
-__device__ __forceinline__ void grid_finish(const Red& r, int nv, unsigned maxmask, double scale) {
+// Returns true in the block that combined the partials (block-uniform).
+// NVMAX bounds nv at compile time: warp w of the last block combines values
+// w, w + NT/32, ..., issuing the loads of all its values before reducing
+// (one L2 round trip per 32 partials instead of one per value).
+template <int NT, int NVMAX>
+__device__ __forceinline__ bool grid_finish(const Red& r, int nv, unsigned maxmask, double scale) {
+    constexpr int NW = NT / 32;
+    constexpr int VPW = (NVMAX + NW - 1) / NW;
     __shared__ unsigned s_last;
-    __threadfence();
-    __syncthreads();
+    __syncthreads();  // the writers' partials are fenced (block_partials)
     const unsigned total = gridDim.x * gridDim.y;  // 2-D grids: one value per row of blocks
     if (threadIdx.x == 0) s_last = atomicAdd(r.counter, 1u) == total - 1 ? 1u : 0u;
     __syncthreads();
-    if (!s_last) return;
+    if (!s_last) return false;
     __threadfence();
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nb = gridDim.x;
-    // one warp per value; four independent loads in flight per lane
-    for (int v = threadIdx.x >> 5; v < nv; v += NT / 32) {
-        const bool mx = (maxmask >> v) & 1u;
-        const double* p = r.part + (size_t)v * nb;
-        double s = 0.0;
-        int i = lane;
-        for (; i + 96 < nb; i += 128) {
-            const double a = __ldcg(p + i), b = __ldcg(p + i + 32), c = __ldcg(p + i + 64),
-                         d = __ldcg(p + i + 96);
-            s = mx ? fmax(s, fmax(fmax(a, b), fmax(c, d))) : s + ((a + b) + (c + d));
-        }
-        for (; i < nb; i += 32) {
-            const double a = __ldcg(p + i);
-            s = mx ? fmax(s, a) : s + a;
+    double s[VPW];
+#pragma unroll
+    for (int j = 0; j < VPW; ++j) s[j] = 0.0;
+#pragma unroll 8
+    for (int i = lane; i < nb; i += 32) {
+        double x[VPW];
+#pragma unroll
+        for (int j = 0; j < VPW; ++j) {
+            const int v = w + j * NW;
+            x[j] = v < nv ? __ldcg(r.part + (size_t)v * nb + i) : 0.0;
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double y = __shfl_down_sync(0xffffffffu, s, o);
-            s = mx ? fmax(s, y) : s + y;
+        for (int j = 0; j < VPW; ++j) {
+            const int v = w + j * NW;
+            s[j] = ((maxmask >> (v & 31)) & 1u) && v < 32 ? fmax(s[j], x[j]) : s[j] + x[j];
         }
-        if (lane == 0) r.out[v] = mx ? s : s * scale;
+    }
+#pragma unroll
+    for (int j = 0; j < VPW; ++j) {
+        const int v = w + j * NW;
+        const bool mx = v < 32 && ((maxmask >> v) & 1u);
+        double t = s[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_down_sync(0xffffffffu, t, o);
+            t = mx ? fmax(t, y) : t + y;
+        }
+        if (lane == 0 && v < nv) r.out[v] = mx ? t : t * scale;
     }
     if (threadIdx.x == 0) *r.counter = 0u;
+    return true;
 }
 
 // Neumaier compensated addition: (s, c) += x.

@@ -27,9 +27,9 @@ template <typename R>
 __device__ __forceinline__ void hs_freq(const SGrid& g, size_t e64, R* xi, R* xid, R& w) {
     const unsigned e = (unsigned)e64;
     const unsigned n0h = (unsigned)g.n0h, n1 = (unsigned)g.n1;
-    const unsigned rest = e / n0h;
+    const unsigned rest = fdiv(e, g.fd_n0h);
     const int kx = (int)(e - rest * n0h);
-    const unsigned kz_ = rest / n1;
+    const unsigned kz_ = fdiv(rest, g.fd_n1);
     const int ky = (int)(rest - kz_ * n1);
     const int kz = (int)kz_;
     const int sy = ky < (g.n1 + 1) / 2 ? ky : ky - g.n1;
@@ -193,30 +193,29 @@ void gnd_rho(const void* Lam, const int32_t* grain, const double* Qg, const doub
 }
 
 // -------------------------------------------------------- averaged tangent
-// Kbar = <g(phi) K> (Eq. avstiff).  Each thread accumulates all 81 entries
-// over its voxels (bulk precision, a few voxels per thread), blocks combine
-// in FP64, the last block writes Kbar.
+// Kbar = <g(phi) K> (Eq. avstiff).  2-D grid: block row y sums entries
+// 9y .. 9y + 8 (a few voxels per thread in the bulk type, FP64 across
+// threads and blocks); the last block of the grid writes all 81 means.
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_kbar(const R* K, const R* phi, R kres, size_t N,
                                                    Red red) {
-    R acc[81];
+    const int y = blockIdx.y;
+    const R* Ky = K + (size_t)9 * y * N;
+    R acc[9];
 #pragma unroll
-    for (int c = 0; c < 81; ++c) acc[c] = 0;
+    for (int c = 0; c < 9; ++c) acc[c] = 0;
     GRID_STRIDE(v, N) {
         const R om = R(1) - phi[v];
-        const R g = om * om + kres;
+        const R gv = om * om + kres;
 #pragma unroll
-        for (int c = 0; c < 81; ++c) acc[c] += g * K[(size_t)c * N + v];
+        for (int c = 0; c < 9; ++c) acc[c] += gv * Ky[(size_t)c * N + v];
     }
-    double accd[81];
-#pragma unroll
-    for (int c = 0; c < 81; ++c) accd[c] = (double)acc[c];
-    block_partials<81, kThreads>(accd, 81, 0u, red.part);
-    grid_finish<kThreads>(red, 81, 0u, 1.0 / (double)N);
+    block_partials<9, kThreads>(acc, 9, 0u, red.part + (size_t)9 * y * gridDim.x);
+    grid_finish<kThreads, 81>(red, 81, 0u, 1.0 / (double)N);
 }
 template <typename R>
 void kbar(const void* K, const void* phi, double kres, size_t N, const Red& red, cudaStream_t s) {
-    k_kbar<R><<<kRedBlocks, kThreads, 0, s>>>((const R*)K, (const R*)phi, (R)kres, N, red);
+    k_kbar<R><<<dim3(2 * 152, 9), kThreads, 0, s>>>((const R*)K, (const R*)phi, (R)kres, N, red);
 }
 
 // ------------------------------------------------------------------ residual
@@ -241,57 +240,58 @@ void degrade(const void* P, const void* phi, double kres, void* out, size_t N, c
 __device__ __forceinline__ bool hs_partner(const SGrid& g, size_t e64, size_t& p) {
     const unsigned e = (unsigned)e64;
     const unsigned n0h = (unsigned)g.n0h, n1 = (unsigned)g.n1;
-    const unsigned rest = e / n0h;
+    const unsigned rest = fdiv(e, g.fd_n0h);
     const int kx = (int)(e - rest * n0h);
     if (!(kx == 0 || ((g.n0 % 2 == 0) && kx == g.n0 / 2))) return false;
-    const unsigned kz_ = rest / n1;
+    const unsigned kz_ = fdiv(rest, g.fd_n1);
     const int ky = (int)(rest - kz_ * n1), kz = (int)kz_;
     const int py = (g.n1 - ky) % g.n1, pz = (g.n2 - kz) % g.n2;
     p = (size_t)kx + (size_t)g.n0h * ((size_t)py + (size_t)g.n1 * pz);
     return true;
 }
 
-// sign * sum_j T_ij(e) i xi_j(e), i = 0..2
-template <typename R>
-__device__ __forceinline__ void div3(const typename Tr<R>::Cx* T, size_t Nh, size_t e,
-                                     const R* xd, R sign, typename Tr<R>::Cx* out) {
-    typedef typename Tr<R>::Cx Cx;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        Cx s;
-        s.x = 0;
-        s.y = 0;
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const Cx t = cmul_i(T[(3 * i + j) * Nh + e], xd[j]);
-            s.x += t.x;
-            s.y += t.y;
-        }
-        out[i].x = sign * s.x;
-        out[i].y = sign * s.y;
-    }
-}
-
-// div3 projected onto real fields: on the kx = 0 and Nyquist planes the
+// sign * sum_j T_ij(e) i xi_j(e), i = 0..2, projected onto real fields: on the kx = 0 and Nyquist planes the
 // value is the mean of the entry and the conjugate of its partner's value,
 // so the pair is exactly conjugate (the inverse real transform ignores the
 // anti-Hermitian part; left in, its forward-transform round-off is a
-// residual no Krylov step can reduce).
+// residual no Krylov step can reduce).  The partner (kx, -ky, -kz) has the
+// derivative frequencies (xd0, -xd1, -xd2) (exact: the Nyquist rows, where
+// k and -k coincide, have zero multipliers).  Its entries are loaded with
+// the entry's own (off the planes p = e, a cache hit), so no lane waits for
+// a second round of loads.
 template <typename R>
 __device__ __forceinline__ void div3_real(const typename Tr<R>::Cx* T, const SGrid& g, size_t e,
                                           const R* xd, R sign, typename Tr<R>::Cx* out) {
     typedef typename Tr<R>::Cx Cx;
-    div3<R>(T, g.Nh, e, xd, sign, out);
     size_t p;
-    if (hs_partner(g, e, p)) {
-        R xi2[3], xd2[3], w2;
-        hs_freq<R>(g, p, xi2, xd2, w2);
-        Cx q[3];
-        div3<R>(T, g.Nh, p, xd2, sign, q);
+    const bool hp = hs_partner(g, e, p);
+    if (!hp) p = e;
+    const size_t Nh = g.Nh;
+    Cx te[9], tp[9];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            out[i].x = R(0.5) * (out[i].x + q[i].x);
-            out[i].y = R(0.5) * (out[i].y - q[i].y);
+    for (int q = 0; q < 9; ++q) {
+        te[q] = T[q * Nh + e];
+        tp[q] = T[q * Nh + p];
+    }
+    const R xp[3] = {xd[0], -xd[1], -xd[2]};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        Cx s, r;
+        s.x = s.y = r.x = r.y = 0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const Cx t = cmul_i(te[3 * i + j], xd[j]);
+            s.x += t.x;
+            s.y += t.y;
+            const Cx u = cmul_i(tp[3 * i + j], xp[j]);
+            r.x += u.x;
+            r.y += u.y;
+        }
+        out[i].x = sign * s.x;
+        out[i].y = sign * s.y;
+        if (hp) {
+            out[i].x = R(0.5) * (out[i].x + sign * r.x);
+            out[i].y = R(0.5) * (out[i].y - sign * r.y);
         }
     }
 }
@@ -303,7 +303,7 @@ template <typename R>
 __global__ void k_residual(const typename Tr<R>::Cx* Ph, SGrid g, typename Tr<R>::Cx* b, Red red) {
     typedef typename Tr<R>::Cx Cx;
     const size_t Nh = g.Nh;
-    double acc[2] = {0.0, 0.0};
+    R acc[2] = {R(0), R(0)};
     GRID_STRIDE(e, Nh) {
         R xi[3], xd[3], w;
         hs_freq<R>(g, e, xi, xd, w);
@@ -312,17 +312,16 @@ __global__ void k_residual(const typename Tr<R>::Cx* Ph, SGrid g, typename Tr<R>
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             b[i * Nh + e] = s[i];
-            acc[0] += (double)w * ((double)s[i].x * s[i].x + (double)s[i].y * s[i].y);
+            acc[0] += w * (s[i].x * s[i].x + s[i].y * s[i].y);
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 const Cx q = Ph[(3 * i + j) * Nh + e];
-                acc[1] += (double)w * ((double)q.x * q.x + (double)q.y * q.y) * (double)xd[j] *
-                          (double)xd[j];
+                acc[1] += w * (q.x * q.x + q.y * q.y) * xd[j] * xd[j];
             }
         }
     }
     block_partials<2, kThreads>(acc, 2, 0u, red.part);
-    grid_finish<kThreads>(red, 2, 0u, 1.0);
+    grid_finish<kThreads, 2>(red, 2, 0u, 1.0);
 }
 template <typename R>
 void residual(const void* Ph, const SGrid& g, void* b, const Red& red, cudaStream_t s) {
@@ -331,14 +330,57 @@ void residual(const void* Ph, const SGrid& g, void* b, const Red& red, cudaStrea
 }
 
 // -------------------------------------------------------------------- GMRES
-// v = scale * vin (optionally stored to vout); z = M(xi) v with the Green
-// preconditioner M = [xi . Kbar . xi]^-1 (Eq. precf) when use_pre, else z =
-// v; G_ij = z_i i xi_j, the 9-component spectrum of grad z.
+// z = M(xi) v with the Green preconditioner M = [xi . Kbar . xi]^-1 of
+// Eq. precf (Kbar in shared memory); z = 0 where every derivative frequency
+// vanishes (the mean and the Nyquist corners, held at zero).
 template <typename R>
-__device__ __forceinline__ void precond_grad_body(const typename Tr<R>::Cx* vin, R scale,
-                                                  typename Tr<R>::Cx* vout, const double* Kbar,
-                                                  const SGrid& g, typename Tr<R>::Cx* G,
-                                                  int use_pre) {
+__device__ __forceinline__ void green_apply(const R* Ks, const R* xd,
+                                            const typename Tr<R>::Cx* v,
+                                            typename Tr<R>::Cx* z) {
+    if (xd[0] == R(0) && xd[1] == R(0) && xd[2] == R(0)) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) z[i].x = z[i].y = 0;
+        return;
+    }
+    R A[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            R s = 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int l = 0; l < 3; ++l) s += xd[j] * Ks[9 * (3 * i + j) + 3 * k + l] * xd[l];
+            A[3 * i + k] = s;
+        }
+    const R det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                  A[2] * (A[3] * A[7] - A[4] * A[6]);
+    const R id = R(1) / det;
+    R Mi[9];
+    Mi[0] = (A[4] * A[8] - A[5] * A[7]) * id;
+    Mi[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+    Mi[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    Mi[3] = (A[5] * A[6] - A[3] * A[8]) * id;
+    Mi[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+    Mi[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    Mi[6] = (A[3] * A[7] - A[4] * A[6]) * id;
+    Mi[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+    Mi[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        z[i].x = Mi[3 * i] * v[0].x + Mi[3 * i + 1] * v[1].x + Mi[3 * i + 2] * v[2].x;
+        z[i].y = Mi[3 * i] * v[0].y + Mi[3 * i + 1] * v[1].y + Mi[3 * i + 2] * v[2].y;
+    }
+}
+
+// v = scale * vin (optionally stored to vout); z = M(xi) v when use_pre,
+// else z = v; G_ij = z_i i xi_j, the 9-component spectrum of grad z.
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 3) k_precond_grad(const typename Tr<R>::Cx* vin,
+                                                              R scale, typename Tr<R>::Cx* vout,
+                                                              const double* Kbar, SGrid g,
+                                                              typename Tr<R>::Cx* G, int use_pre) {
     typedef typename Tr<R>::Cx Cx;
     __shared__ R Ks[81];
     for (int k = threadIdx.x; k < 81; k += blockDim.x) Ks[k] = (R)Kbar[k];
@@ -356,44 +398,7 @@ __device__ __forceinline__ void precond_grad_body(const typename Tr<R>::Cx* vin,
             if (vout) vout[i * Nh + e] = v[i];
         }
         if (use_pre) {
-            const bool zero = xd[0] == R(0) && xd[1] == R(0) && xd[2] == R(0);
-            if (zero) {
-#pragma unroll
-                for (int i = 0; i < 3; ++i) z[i].x = z[i].y = 0;
-            } else {
-                R A[9];
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        R s = 0;
-#pragma unroll
-                        for (int j = 0; j < 3; ++j)
-#pragma unroll
-                            for (int l = 0; l < 3; ++l)
-                                s += xd[j] * Ks[9 * (3 * i + j) + 3 * k + l] * xd[l];
-                        A[3 * i + k] = s;
-                    }
-                const R det = A[0] * (A[4] * A[8] - A[5] * A[7]) -
-                              A[1] * (A[3] * A[8] - A[5] * A[6]) +
-                              A[2] * (A[3] * A[7] - A[4] * A[6]);
-                const R id = R(1) / det;
-                R Mi[9];
-                Mi[0] = (A[4] * A[8] - A[5] * A[7]) * id;
-                Mi[1] = (A[2] * A[7] - A[1] * A[8]) * id;
-                Mi[2] = (A[1] * A[5] - A[2] * A[4]) * id;
-                Mi[3] = (A[5] * A[6] - A[3] * A[8]) * id;
-                Mi[4] = (A[0] * A[8] - A[2] * A[6]) * id;
-                Mi[5] = (A[2] * A[3] - A[0] * A[5]) * id;
-                Mi[6] = (A[3] * A[7] - A[4] * A[6]) * id;
-                Mi[7] = (A[1] * A[6] - A[0] * A[7]) * id;
-                Mi[8] = (A[0] * A[4] - A[1] * A[3]) * id;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    z[i].x = Mi[3 * i] * v[0].x + Mi[3 * i + 1] * v[1].x + Mi[3 * i + 2] * v[2].x;
-                    z[i].y = Mi[3 * i] * v[0].y + Mi[3 * i + 1] * v[1].y + Mi[3 * i + 2] * v[2].y;
-                }
-            }
+            green_apply<R>(Ks, xd, v, z);
         } else {
 #pragma unroll
             for (int i = 0; i < 3; ++i) z[i] = v[i];
@@ -403,12 +408,6 @@ __device__ __forceinline__ void precond_grad_body(const typename Tr<R>::Cx* vin,
 #pragma unroll
             for (int j = 0; j < 3; ++j) G[(3 * i + j) * Nh + e] = cmul_i(z[i], xd[j]);
     }
-}
-template <typename R>
-__global__ void __launch_bounds__(kThreads, 3) k_precond_grad(const typename Tr<R>::Cx* vin, R scale,
-                               typename Tr<R>::Cx* vout, const double* Kbar, SGrid g,
-                               typename Tr<R>::Cx* G, int use_pre) {
-    precond_grad_body<R>(vin, scale, vout, Kbar, g, G, use_pre);
 }
 template <typename R>
 void precond_grad(const void* vin, double scale, void* vout, const double* Kbar, const SGrid& g,
@@ -480,159 +479,29 @@ void tangent_apply(void* G, const void* K, const void* phi, double kres, size_t 
         (R*)G, (const R*)K, (const R*)phi, (R)kres, (R)(1.0 / (double)N), N);
 }
 
-// w_i = -sum_j i xi_j T_ij (the divergence, with the sign that makes the
-// operator positive), projected onto real fields and stored; in the same
-// pass ||w||^2 -> out[0] and the Gram-Schmidt coefficients <V_i, w> ->
-// out[1 + i] (i < nv).
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_contract_dots(const typename Tr<R>::Cx* T, SGrid g,
-                                                            typename Tr<R>::Cx* w,
-                                                            const typename Tr<R>::Cx* V,
-                                                            size_t vstride, int nv, Red red,
-                                                            const GmState* gst) {
-    typedef typename Tr<R>::Cx Cx;
-    const size_t Nh = g.Nh;
-    if (gst) nv = gst->k + 1;
-    R acc[kMaxKrylov + 1];  // per-thread partials over its few entries
-#pragma unroll
-    for (int i = 0; i <= kMaxKrylov; ++i) acc[i] = R(0);
-    GRID_STRIDE(e, Nh) {
-        R xi[3], xd[3], wt;
-        hs_freq<R>(g, e, xi, xd, wt);
-        Cx a[3];
-        div3_real<R>(T, g, e, xd, R(-1), a);
-        R nn = 0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            w[c * Nh + e] = a[c];
-            nn += a[c].x * a[c].x + a[c].y * a[c].y;
-        }
-        acc[0] += wt * nn;
-#pragma unroll
-        for (int i = 0; i < kMaxKrylov; ++i) {
-            if (i < nv) {
-                const Cx* Vi = V + (size_t)i * vstride;
-                R d = 0;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const Cx q = Vi[c * Nh + e];
-                    d += q.x * a[c].x + q.y * a[c].y;
-                }
-                acc[1 + i] += wt * d;
-            }
-        }
-    }
-    double accd[kMaxKrylov + 1];
-#pragma unroll
-    for (int i = 0; i <= kMaxKrylov; ++i) accd[i] = (double)acc[i];
-    block_partials<kMaxKrylov + 1, kThreads>(accd, nv + 1, 0u, red.part);
-    grid_finish<kThreads>(red, nv + 1, 0u, 1.0);
-}
-template <typename R>
-void contract_dots(const void* T, const SGrid& g, void* w, const void* V, size_t vstride, int nv,
-                   const Red& red, cudaStream_t s, const GmState* st) {
-    typedef typename Tr<R>::Cx Cx;
-    k_contract_dots<R><<<kRedBlocks, kThreads, 0, s>>>((const Cx*)T, g, (Cx*)w, (const Cx*)V,
-                                                       vstride, nv, red, st);
-}
-
-// w -= sum_{i < nv} h_i V_i with h = hin[1 + i] (device memory, the layout
-// contract_dots writes); out[0] = ||w_new||^2 and, with dots, out[1 + i] =
-// <V_i, w_new> for a second Gram-Schmidt pass.
-template <typename R>
-__device__ __forceinline__ void gs_update_body(typename Tr<R>::Cx* w,
-                                               const typename Tr<R>::Cx* V, size_t vstride,
-                                               int nv, const double* hin, int dots,
-                                               const SGrid& g, const Red& red) {
-    typedef typename Tr<R>::Cx Cx;
-    const size_t Nh = g.Nh;
-    __shared__ R hs[kMaxKrylov];
-    for (int i = threadIdx.x; i < kMaxKrylov; i += blockDim.x)
-        hs[i] = (i < nv && hin) ? (R)hin[1 + i] : R(0);
-    __syncthreads();
-    R acc[kMaxKrylov + 1];  // per-thread partials over its few entries
-#pragma unroll
-    for (int i = 0; i <= kMaxKrylov; ++i) acc[i] = R(0);
-    GRID_STRIDE(e, Nh) {
-        R xi[3], xd[3], wt;
-        hs_freq<R>(g, e, xi, xd, wt);
-        Cx a[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) a[c] = w[c * Nh + e];
-        if (hin) {
-#pragma unroll
-            for (int i = 0; i < kMaxKrylov; ++i) {
-                if (i < nv) {
-                    const Cx* Vi = V + (size_t)i * vstride;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const Cx q = Vi[c * Nh + e];
-                        a[c].x -= hs[i] * q.x;
-                        a[c].y -= hs[i] * q.y;
-                    }
-                }
-            }
-        }
-        R nn = 0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            if (hin) w[c * Nh + e] = a[c];
-            nn += a[c].x * a[c].x + a[c].y * a[c].y;
-        }
-        acc[0] += wt * nn;
-        if (dots) {
-#pragma unroll
-            for (int i = 0; i < kMaxKrylov; ++i) {
-                if (i < nv) {
-                    const Cx* Vi = V + (size_t)i * vstride;
-                    R d = 0;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const Cx q = Vi[c * Nh + e];
-                        d += q.x * a[c].x + q.y * a[c].y;
-                    }
-                    acc[1 + i] += wt * d;
-                }
-            }
-        }
-    }
-    const int nvals = dots ? nv + 1 : 1;
-    double accd[kMaxKrylov + 1];
-#pragma unroll
-    for (int i = 0; i <= kMaxKrylov; ++i) accd[i] = (double)acc[i];
-    block_partials<kMaxKrylov + 1, kThreads>(accd, nvals, 0u, red.part);
-    grid_finish<kThreads>(red, nvals, 0u, 1.0);
-}
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_gs_update(typename Tr<R>::Cx* w,
-                                                        const typename Tr<R>::Cx* V,
-                                                        size_t vstride, int nv, const double* hin,
-                                                        int dots, SGrid g, Red red,
-                                                        const GmState* gst) {
-    if (gst) nv = gst->k + 1;
-    gs_update_body<R>(w, V, vstride, nv, hin, dots, g, red);
-}
-template <typename R>
-void gs_update(void* w, const void* V, size_t vstride, int nv, const double* h, int dots,
-               const SGrid& g, const Red& red, cudaStream_t s, const GmState* st) {
-    typedef typename Tr<R>::Cx Cx;
-    k_gs_update<R><<<kRedBlocks, kThreads, 0, s>>>((Cx*)w, (const Cx*)V, vstride, nv, h, dots, g,
-                                                   red, st);
-}
-
-// ---------------------------------------------- tiled Krylov vector kernels
-// The Krylov vectors are 3 Nh complex entries laid out as one flat array
-// (component-major); the Hermitian weight of flat entry f depends on its kx
-// = (f mod Nh) mod n0h.  Each block owns tiles of kTileItems * kThreads
-// consecutive entries; a thread keeps its kTileItems entries of w in
-// registers and streams each Krylov vector's tile with independent
-// coalesced loads (the loop is a tall-skinny V^T w / w - V h).
-constexpr int kUpdItems = 2;  // entries per thread in the w - V h update
+// ------------------------------------------------------ Arnoldi step kernels
+// Arnoldi with classical Gram-Schmidt and delayed reorthogonalisation
+// (DCGS2): the operator is applied to the candidate c_k, which has been
+// projected once against the final basis Q_k = [q_0 .. q_{k-1}] but neither
+// reorthogonalised nor normalised.  One pass over Q_k then gives both the
+// reorthogonalisation coefficients a = Q_k^T c_k and the projections
+// b = Q_k^T z of z = A M c_k; a second pass writes the final
+// q_k = (c_k - Q_k a) / nu and the next candidate c_{k+1}.  Because
+// A M Q_k = Q_{k+1} Hbar (the Arnoldi relation of the final columns),
+//   A M q_k = (z - Q_{k+1} Hbar a) / nu,
+// so the column k coefficients follow from a, b, alpha = c_k.c_k,
+// beta = c_k.z and Hbar alone.  Per GMRES step: C2R, tangent apply, R2C,
+// contraction, k_dcgs_dots, k_dcgs_update.
+//
+// The Krylov vectors are 3 Nh complex entries in one flat, component-major
+// array; the Hermitian weight of flat entry f depends on kx = (f mod Nh) mod
+// n0h.  Hessenberg columns live on the device in FP64: Hd (final columns)
+// and Hp (provisional columns), column i at offset i * kHcol.
 
 __device__ __forceinline__ float hs_weight(const SGrid& g, unsigned f) {
     const unsigned Nh = (unsigned)g.Nh, n0h = (unsigned)g.n0h;
-    const unsigned e = f % Nh;
-    const unsigned kx = e % n0h;
+    const unsigned e = f - Nh * fdiv(f, g.fd_Nh);
+    const unsigned kx = e - n0h * fdiv(e, g.fd_n0h);
     const bool nyx = (g.n0 % 2 == 0) && (int)kx == g.n0 / 2;
     return (kx == 0 || nyx) ? 1.0f : 2.0f;
 }
@@ -644,8 +513,8 @@ inline int tile_blocks(size_t n3, int items) {
     return (int)(t < 1 ? 1 : t);
 }
 
-// w_i = -sum_j i xi_j T_ij projected onto real fields (the GMRES operator's
-// last step), stored.
+// w = -div(T) = -sum_j i xi_j T_ij (the sign that makes the operator
+// positive), projected onto real fields.
 template <typename R>
 __global__ void k_contract(const typename Tr<R>::Cx* T, SGrid g, typename Tr<R>::Cx* w) {
     typedef typename Tr<R>::Cx Cx;
@@ -665,219 +534,250 @@ void contract(const void* T, const SGrid& g, void* w, cudaStream_t s) {
     k_contract<R><<<grid_for(g.Nh), kThreads, 0, s>>>((const Cx*)T, g, (Cx*)w);
 }
 
-// out[0] = ||w||^2, out[1 + i] = <V_i, w> (i < nv); skipped entirely when
-// need_flag is set and st->reorth is zero (the
-// optional second Gram-Schmidt pass).  2-D grid: blockIdx.x walks tiles of
-// kThreads * kDotItems entries, blockIdx.y selects the value (0: the norm,
-// 1 + i: vector i); w is re-read from L2 by each row.
-constexpr int kDotItems = 4;
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_vdots(const typename Tr<R>::Cx* w,
-                                                    const typename Tr<R>::Cx* V, size_t vstride,
-                                                    int nv, SGrid g, Red red, const GmState* st,
-                                                    int need_flag) {
-    typedef typename Tr<R>::Cx Cx;
-    if (need_flag && !st->reorth) return;
-    const int y = blockIdx.y;
-    const Cx* a = y == 0 ? w : V + (size_t)(y - 1) * vstride;
-    const unsigned n3 = (unsigned)(3 * g.Nh);
-    const unsigned step = gridDim.x * kThreads * kDotItems;
-    R acc = 0;
-    for (unsigned base = blockIdx.x * kThreads * kDotItems; base < n3; base += step) {
-        Cx p[kDotItems], q[kDotItems];
+// Coefficients of DCGS2 step k from the dots d (layout of k_dcgs_dots) and
+// the Hessenberg columns (one warp, FP64):
+//   nu = sqrt(alpha - |a|^2)          (|c_k - Q_k a|; 0 on breakdown)
+//   column k-1, final:  Hp[k-1] + a (rows < k), nu (row k)
+//   t = Hbar a over the final columns 0 .. k-1 (rows 0 .. k)
+//   h_l = (b_l - t_l) / nu (l < k),  h_k = ((beta - a.b) / nu - t_k) / nu
+//   dd_l = t_l / nu + h_l,  e_l = dd_l - a_l dd_k / nu
+// Stores the final column k-1 to Hd, the provisional column k (h) to Hp,
+// both to slot (rows at 0 and kSlotProv, nu at kSlotNu) for the host, and
+// coef = [a (kMaxKrylov), e (kMaxKrylov), 1/nu, dd_k/nu] for k_dcgs_update.
+// Hs: the final columns 0 .. k-2 and the provisional column k-1, staged in
+// shared memory (column i at i * kHcol).
+__device__ void dcgs_coefficients(int k, const double* d, const double* Hs, double* Hd, double* Hp,
+                                  double* slot, double* coef) {
+    const int l = threadIdx.x & 31;
+    const double alpha = d[0], beta = d[1];
+    const double al = l < k ? d[3 + 2 * l] : 0.0;
+    const double bl = l < k ? d[4 + 2 * l] : 0.0;
+    double aa = al * al, ab = al * bl;
 #pragma unroll
-        for (int t = 0; t < kDotItems; ++t) {
-            const unsigned f = base + t * kThreads + threadIdx.x;
-            if (f < n3) {
-                p[t] = a[f];
-                q[t] = w[f];
-            } else {
-                p[t].x = p[t].y = q[t].x = q[t].y = 0;
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < kDotItems; ++t) {
-            const unsigned f = base + t * kThreads + threadIdx.x;
-            if (f < n3) acc += (R)hs_weight(g, f) * (p[t].x * q[t].x + p[t].y * q[t].y);
-        }
+    for (int o = 16; o > 0; o >>= 1) {
+        aa += __shfl_xor_sync(0xffffffffu, aa, o);
+        ab += __shfl_xor_sync(0xffffffffu, ab, o);
     }
-    double d[1] = {(double)acc};
-    block_partials<1, kThreads>(d, 1, 0u, red.part + (size_t)y * gridDim.x);
-    grid_finish<kThreads>(red, nv + 1, 0u, 1.0);
+    const double nu2 = alpha - aa;
+    const bool brk = !(nu2 > 1e-28 * alpha) || !(alpha > 0.0);
+    const double nu = brk ? 0.0 : sqrt(nu2);
+    const double inu = brk ? 0.0 : 1.0 / nu;
+    // final column k-1 (row l in lane l); the other columns' row l prefetched
+    double fin = 0.0;
+    if (k >= 1 && l <= k) fin = l < k ? Hs[(k - 1) * kHcol + l] + al : nu;
+    double t = 0.0;
+    for (int i = 0; i < k; ++i) {  // uniform trip count: the shuffle needs all lanes
+        const double ai = __shfl_sync(0xffffffffu, al, i);
+        if (l <= i + 1 && l <= k) t += (i == k - 1 ? fin : Hs[i * kHcol + l]) * ai;
+    }
+    double h = 0.0;
+    if (l < k) h = (bl - t) * inu;
+    if (l == k) h = ((beta - ab) * inu - t) * inu;
+    const double dd = t * inu + h;
+    const double ddk = __shfl_sync(0xffffffffu, dd, k < 32 ? k : 31);
+    if (l < k) {
+        coef[l] = al;
+        coef[kMaxKrylov + l] = dd - al * ddk * inu;
+    }
+    if (l == 0) {
+        coef[2 * kMaxKrylov] = inu;
+        coef[2 * kMaxKrylov + 1] = ddk * inu;
+        slot[kSlotNu] = nu;
+    }
+    if (k >= 1 && l <= k) {
+        Hd[(size_t)(k - 1) * kHcol + l] = fin;
+        slot[l] = fin;
+    }
+    if (l <= k) {
+        Hp[(size_t)k * kHcol + l] = h;
+        slot[kSlotProv + l] = h;
+    }
 }
 
-// w -= sum_{i < nv} h_i V_i with h_i = hin[1 + i]; out[0] = ||w||^2.  With
-// need_flag, skipped when st->reorth is zero.
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_vupdate(typename Tr<R>::Cx* w,
-                                                      const typename Tr<R>::Cx* V, size_t vstride,
-                                                      int nv, const double* hin, SGrid g, Red red,
-                                                      const GmState* st, int need_flag) {
+// Dots of step k: out[0] = alpha = c.c, out[1] = beta = c.z, out[2] = z.z,
+// out[3 + 2i] = a_i = q_i.c, out[4 + 2i] = b_i = q_i.z (i < k <= NQ).  Each
+// thread streams its entries once (U entries per trip, all loads issued
+// before use) and keeps the 3 + 2k sums in registers; blocks combine in FP64
+// and the last block forms the step's coefficients (dcgs_coefficients).
+template <typename R, int NQ>
+__global__ void __launch_bounds__(kThreads, 2) k_dcgs_dots(const typename Tr<R>::Cx* c,
+                                                           const typename Tr<R>::Cx* z,
+                                                           const typename Tr<R>::Cx* V,
+                                                           size_t vstride, int k, SGrid g,
+                                                           Red red, double* Hd, double* Hp,
+                                                           double* slot, double* coef) {
     typedef typename Tr<R>::Cx Cx;
-    if (need_flag && !st->reorth) return;
-    __shared__ R hs[kMaxKrylov];
-    for (int i = threadIdx.x; i < kMaxKrylov; i += blockDim.x) hs[i] = i < nv ? (R)hin[1 + i] : R(0);
-    __syncthreads();
+    constexpr int U = NQ <= 4 ? 4 : (NQ <= 8 ? 2 : 1);
+    constexpr int G = NQ < 8 ? NQ : 8;
+    R acc[3 + 2 * NQ];
+#pragma unroll
+    for (int v = 0; v < 3 + 2 * NQ; ++v) acc[v] = 0;
     const unsigned n3 = (unsigned)(3 * g.Nh);
-    double acc[1] = {0.0};
-    constexpr int kTileItems = kUpdItems;
-    constexpr int kTile = kUpdItems * kThreads;
-    for (unsigned base = blockIdx.x * kTile; base < n3; base += gridDim.x * kTile) {
-        Cx wv[kTileItems];
+    const unsigned stride = gridDim.x * kThreads;
+    for (unsigned f0 = blockIdx.x * kThreads + threadIdx.x; f0 < n3; f0 += U * stride) {
+        Cx cv[U], zv[U];
+        R wt[U];
 #pragma unroll
-        for (int t = 0; t < kTileItems; ++t) {
-            const unsigned f = base + t * kThreads + threadIdx.x;
-            if (f < n3)
-                wv[t] = w[f];
-            else
-                wv[t].x = wv[t].y = 0;
+        for (int u = 0; u < U; ++u) {
+            const unsigned f = f0 + u * stride;
+            if (f < n3) {
+                cv[u] = c[f];
+                zv[u] = z[f];
+                wt[u] = (R)hs_weight(g, f);
+            } else {
+                cv[u].x = cv[u].y = zv[u].x = zv[u].y = 0;
+                wt[u] = 0;
+            }
         }
+        // basis vectors in groups of up to 8 loads in flight (bounded registers)
 #pragma unroll
-        for (int i = 0; i < kMaxKrylov; ++i) {
-            if (i < nv) {
-                const Cx* Vi = V + (size_t)i * vstride;
-                const R h = hs[i];
+        for (int i0 = 0; i0 < NQ; i0 += 8) {
+            Cx q[U][G > 0 ? G : 1];
 #pragma unroll
-                for (int t = 0; t < kTileItems; ++t) {
-                    const unsigned f = base + t * kThreads + threadIdx.x;
-                    if (f < n3) {
-                        const Cx q = Vi[f];
-                        wv[t].x -= h * q.x;
-                        wv[t].y -= h * q.y;
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    const unsigned f = f0 + u * stride;
+                    if (i0 + t < k && f < n3) {
+                        q[u][t] = V[(size_t)(i0 + t) * vstride + f];
+                    } else {
+                        q[u][t].x = q[u][t].y = 0;
                     }
                 }
-            }
-        }
-        R nn = 0;
 #pragma unroll
-        for (int t = 0; t < kTileItems; ++t) {
-            const unsigned f = base + t * kThreads + threadIdx.x;
-            if (f < n3) {
-                w[f] = wv[t];
-                nn += (R)hs_weight(g, f) * (wv[t].x * wv[t].x + wv[t].y * wv[t].y);
-            }
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    acc[3 + 2 * (i0 + t)] += wt[u] * (q[u][t].x * cv[u].x + q[u][t].y * cv[u].y);
+                    acc[4 + 2 * (i0 + t)] += wt[u] * (q[u][t].x * zv[u].x + q[u][t].y * zv[u].y);
+                }
         }
-        acc[0] += (double)nn;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            acc[0] += wt[u] * (cv[u].x * cv[u].x + cv[u].y * cv[u].y);
+            acc[1] += wt[u] * (cv[u].x * zv[u].x + cv[u].y * zv[u].y);
+            acc[2] += wt[u] * (zv[u].x * zv[u].x + zv[u].y * zv[u].y);
+        }
     }
-    block_partials<1, kThreads>(acc, 1, 0u, red.part);
-    grid_finish<kThreads>(red, 1, 0u, 1.0);
+    block_partials<3 + 2 * NQ, kThreads>(acc, 3 + 2 * k, 0u, red.part);
+    if (grid_finish<kThreads, 3 + 2 * NQ>(red, 3 + 2 * k, 0u, 1.0)) {
+        // the last block: stage the Hessenberg columns the step needs, then
+        // warp 0 forms the coefficients (the dots were written by this block)
+        __shared__ double s_H[NQ > 0 ? NQ * kHcol : 1];
+        if (NQ > 0) {
+            const int nH = (k - 1) * kHcol;
+            for (int q = threadIdx.x; q < k * kHcol; q += blockDim.x)
+                s_H[q] = q < nH ? __ldcg(Hd + q) : __ldcg(Hp + q);  // column k-1: provisional
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) dcgs_coefficients(k, red.out, s_H, Hd, Hp, slot, coef);
+    }
+}
+template <typename R>
+void dcgs_dots(const void* c, const void* z, const void* V, size_t vstride, int k,
+               const SGrid& g, const Red& red, double* Hd, double* Hp, double* slot,
+               double* coef, cudaStream_t s) {
+    typedef typename Tr<R>::Cx Cx;
+    const size_t n3 = 3 * g.Nh;
+    size_t nb = (n3 + kThreads - 1) / kThreads;
+    if (nb > 2 * 152) nb = 2 * 152;  // one wave of two blocks per SM
+    const dim3 gr((unsigned)nb);
+    const Cx *cc = (const Cx*)c, *zz = (const Cx*)z, *VV = (const Cx*)V;
+#define DOTS(NQ)                                                                               \
+    k_dcgs_dots<R, NQ><<<gr, kThreads, 0, s>>>(cc, zz, VV, vstride, k, g, red, Hd, Hp, slot, \
+                                               coef)
+    if (k <= 0)
+        DOTS(0);
+    else if (k <= 4)
+        DOTS(4);
+    else if (k <= 8)
+        DOTS(8);
+    else if (k <= 16)
+        DOTS(16);
+    else
+        DOTS(kMaxKrylov);
+#undef DOTS
 }
 
+// Update of step k with the coefficients from k_dcgs_dots (coef):
+//   q_k = (c_k - Q_k a) / nu                     -> slot k (in place)
+//   c_{k+1} = z / nu - Q_k e - c_k dd_k / nu     -> slot k + 1
+//   G = (M c_{k+1}) (x) i xi                     -> the next step's gradient
+// and out[0] = |c_{k+1}|^2.
 template <typename R>
-void vdots(const void* w, const void* V, size_t vstride, int nv, const SGrid& g, const Red& red,
-           cudaStream_t s, const GmState* st, int need_flag) {
+__global__ void __launch_bounds__(kThreads, 2) k_dcgs_update(typename Tr<R>::Cx* V,
+                                                             size_t vstride, int k,
+                                                             const typename Tr<R>::Cx* z,
+                                                             const double* coef,
+                                                             const double* Kbar, SGrid g,
+                                                             typename Tr<R>::Cx* G, Red red) {
     typedef typename Tr<R>::Cx Cx;
-    const int rows = nv + 1;
-    int bx = tile_blocks(3 * g.Nh, kDotItems);
-    if ((size_t)bx * rows > (size_t)kRedSlots * kRedBlocks / 2) bx = kRedSlots * kRedBlocks / 2 / rows;
-    k_vdots<R><<<dim3(bx, rows), kThreads, 0, s>>>((const Cx*)w, (const Cx*)V, vstride, nv, g,
-                                                   red, st, need_flag);
-}
-template <typename R>
-void vupdate(void* w, const void* V, size_t vstride, int nv, const double* hin, const SGrid& g,
-             const Red& red, cudaStream_t s, const GmState* st, int need_flag) {
-    typedef typename Tr<R>::Cx Cx;
-    k_vupdate<R><<<tile_blocks(3 * g.Nh, kUpdItems), kThreads, 0, s>>>(
-        (Cx*)w, (const Cx*)V, vstride, nv, hin, g, red, st, need_flag);
-}
-// Look-ahead GMRES step 1: operands from GmState (see GmArgs), then the
-// Green preconditioner and the gradient spectrum, as precond_grad.
-template <typename R>
-__global__ void __launch_bounds__(kThreads, 3) k_gm_precond_grad(GmArgs a, const double* Kbar, SGrid g,
-                                  typename Tr<R>::Cx* G) {
-    typedef typename Tr<R>::Cx Cx;
-    const int k = a.st->k;
-    const Cx* vin = (const Cx*)(k == 0 ? a.V : a.w);
-    const R scale = k == 0 ? R(1) : (R)(1.0 / a.st->hprev);
-    Cx* vout = k == 0 ? nullptr : (Cx*)a.V + (size_t)k * a.vstride;
-    precond_grad_body<R>(vin, scale, vout, Kbar, g, G, 1);
-}
-template <typename R>
-void gm_precond_grad(const GmArgs& a, const double* Kbar, const SGrid& g, void* G,
-                     cudaStream_t s) {
-    k_gm_precond_grad<R><<<grid_for(g.Nh), kThreads, 0, s>>>(a, Kbar, g,
-                                                             (typename Tr<R>::Cx*)G);
-}
-
-// Second Gram-Schmidt pass, taken on the device when the update shrank the
-// norm below 1/sqrt(2) of its value (red[0]: before, red[64]: after): the
-// dots of the updated w go to red_dots, then w is updated again and its norm
-// replaces red[64] (via red_norm).  Otherwise nothing happens.
-template <typename R>
-__global__ void k_gm_reorth_flag(const double* red, GmState* st) {
-    st->reorth = red[64] < 0.5 * red[0] ? 1 : 0;
-}
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_gm_reorth_dots(const typename Tr<R>::Cx* w,
-                                                             const typename Tr<R>::Cx* V,
-                                                             size_t vstride, const GmState* st,
-                                                             SGrid g, Red red) {
-    typedef typename Tr<R>::Cx Cx;
-    if (!st->reorth) return;
-    const int nv = st->k + 1;
+    __shared__ R s_a[kMaxKrylov], s_e[kMaxKrylov];
+    __shared__ R Ks[81];
+    for (int q = threadIdx.x; q < 81; q += blockDim.x) Ks[q] = (R)Kbar[q];
+    for (int q = threadIdx.x; q < k; q += blockDim.x) {
+        s_a[q] = (R)coef[q];
+        s_e[q] = (R)coef[kMaxKrylov + q];
+    }
+    const R inu = (R)coef[2 * kMaxKrylov], cc = (R)coef[2 * kMaxKrylov + 1];
+    __syncthreads();
     const size_t Nh = g.Nh;
-    double acc[kMaxKrylov + 1];
-#pragma unroll
-    for (int i = 0; i <= kMaxKrylov; ++i) acc[i] = 0.0;
+    Cx* ck = V + (size_t)k * vstride;
+    Cx* cn = V + (size_t)(k + 1) * vstride;
+    R acc[1] = {};
     GRID_STRIDE(e, Nh) {
         R xi[3], xd[3], wt;
         hs_freq<R>(g, e, xi, xd, wt);
-        Cx a[3];
+        Cx sa[3], se[3], cv[3], zv[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) a[c] = w[c * Nh + e];
+        for (int c = 0; c < 3; ++c) {
+            sa[c].x = sa[c].y = se[c].x = se[c].y = 0;
+            cv[c] = ck[c * Nh + e];
+            zv[c] = z[c * Nh + e];
+        }
+#pragma unroll 4
+        for (int i = 0; i < k; ++i) {
+            const Cx* qi = V + (size_t)i * vstride;
+            const R ai = s_a[i], ei = s_e[i];
 #pragma unroll
-        for (int i = 0; i < kMaxKrylov; ++i) {
-            if (i < nv) {
-                const Cx* Vi = V + (size_t)i * vstride;
-                R d = 0;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const Cx q = Vi[c * Nh + e];
-                    d += q.x * a[c].x + q.y * a[c].y;
-                }
-                acc[1 + i] += (double)wt * (double)d;
+            for (int c = 0; c < 3; ++c) {
+                const Cx q = qi[c * Nh + e];
+                sa[c].x += ai * q.x;
+                sa[c].y += ai * q.y;
+                se[c].x += ei * q.x;
+                se[c].y += ei * q.y;
             }
         }
+        Cx nx[3];
+        R nn = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Cx qk;
+            qk.x = (cv[c].x - sa[c].x) * inu;
+            qk.y = (cv[c].y - sa[c].y) * inu;
+            ck[c * Nh + e] = qk;
+            nx[c].x = zv[c].x * inu - se[c].x - cv[c].x * cc;
+            nx[c].y = zv[c].y * inu - se[c].y - cv[c].y * cc;
+            cn[c * Nh + e] = nx[c];
+            nn += nx[c].x * nx[c].x + nx[c].y * nx[c].y;
+        }
+        acc[0] += wt * nn;
+        Cx zz[3];
+        green_apply<R>(Ks, xd, nx, zz);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) G[(3 * i + j) * Nh + e] = cmul_i(zz[i], xd[j]);
     }
-    block_partials<kMaxKrylov + 1, kThreads>(acc, nv + 1, 0u, red.part);
-    grid_finish<kThreads>(red, nv + 1, 0u, 1.0);
+    block_partials<1, kThreads>(acc, 1, 0u, red.part);
+    grid_finish<kThreads, 1>(red, 1, 0u, 1.0);
 }
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_gm_reorth_update(typename Tr<R>::Cx* w,
-                                                               const typename Tr<R>::Cx* V,
-                                                               size_t vstride, const double* hin,
-                                                               const GmState* st, SGrid g,
-                                                               Red red) {
-    if (!st->reorth) return;
-    gs_update_body<R>(w, V, vstride, st->k + 1, hin, 0, g, red);
-}
-template <typename R>
-void gm_reorth_flag(const double* red, GmState* st, cudaStream_t s) {
-    k_gm_reorth_flag<R><<<1, 1, 0, s>>>(red, st);
-}
-template <typename R>
-void gm_reorth(void* w, const void* V, size_t vstride, const double* red, GmState* st,
-               const SGrid& g, const Red& red_dots, const Red& red_norm, cudaStream_t s) {
+void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* coef,
+                 const double* Kbar, const SGrid& g, void* G, const Red& red, cudaStream_t s) {
     typedef typename Tr<R>::Cx Cx;
-    k_gm_reorth_flag<R><<<1, 1, 0, s>>>(red, st);
-    k_gm_reorth_dots<R><<<kRedBlocks, kThreads, 0, s>>>((const Cx*)w, (const Cx*)V, vstride, st, g,
-                                                        red_dots);
-    k_gm_reorth_update<R><<<kRedBlocks, kThreads, 0, s>>>((Cx*)w, (const Cx*)V, vstride,
-                                                          red_dots.out, st, g, red_norm);
-}
-
-__global__ void k_gm_reset(GmState* st) {
-    st->k = 0;
-    st->reorth = 0;
-    st->hprev = 1.0;
-}
-__global__ void k_gm_advance(GmState* st, const double* norm2) {
-    st->hprev = sqrt(fmax(norm2[0], 0.0));
-    st->k += 1;
-}
-void gm_reset(GmState* st, cudaStream_t s) { k_gm_reset<<<1, 1, 0, s>>>(st); }
-void gm_advance(GmState* st, const double* norm2, cudaStream_t s) {
-    k_gm_advance<<<1, 1, 0, s>>>(st, norm2);
+    k_dcgs_update<R><<<grid_for(g.Nh), kThreads, 0, s>>>((Cx*)V, vstride, k, (const Cx*)z, coef,
+                                                         Kbar, g, (Cx*)G, red);
 }
 
 // x += M (sum_i y_i V_i)  (right-preconditioned GMRES update)
@@ -892,8 +792,7 @@ __global__ void k_xupdate(typename Tr<R>::Cx* x, const typename Tr<R>::Cx* V, si
     GRID_STRIDE(e, Nh) {
         R xi[3], xd[3], wt;
         hs_freq<R>(g, e, xi, xd, wt);
-        if (xd[0] == R(0) && xd[1] == R(0) && xd[2] == R(0)) continue;
-        Cx c[3];
+        Cx c[3], z[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) c[i].x = c[i].y = 0;
         for (int q = 0; q < k; ++q) {
@@ -905,36 +804,12 @@ __global__ void k_xupdate(typename Tr<R>::Cx* x, const typename Tr<R>::Cx* V, si
                 c[i].y += yq * v.y;
             }
         }
-        R A[9];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int kk = 0; kk < 3; ++kk) {
-                R s = 0;
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-#pragma unroll
-                    for (int l = 0; l < 3; ++l) s += xd[j] * Ks[9 * (3 * i + j) + 3 * kk + l] * xd[l];
-                A[3 * i + kk] = s;
-            }
-        const R det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
-                      A[2] * (A[3] * A[7] - A[4] * A[6]);
-        const R id = R(1) / det;
-        R Mi[9];
-        Mi[0] = (A[4] * A[8] - A[5] * A[7]) * id;
-        Mi[1] = (A[2] * A[7] - A[1] * A[8]) * id;
-        Mi[2] = (A[1] * A[5] - A[2] * A[4]) * id;
-        Mi[3] = (A[5] * A[6] - A[3] * A[8]) * id;
-        Mi[4] = (A[0] * A[8] - A[2] * A[6]) * id;
-        Mi[5] = (A[2] * A[3] - A[0] * A[5]) * id;
-        Mi[6] = (A[3] * A[7] - A[4] * A[6]) * id;
-        Mi[7] = (A[1] * A[6] - A[0] * A[7]) * id;
-        Mi[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+        green_apply<R>(Ks, xd, c, z);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             Cx xv = x[i * Nh + e];
-            xv.x += Mi[3 * i] * c[0].x + Mi[3 * i + 1] * c[1].x + Mi[3 * i + 2] * c[2].x;
-            xv.y += Mi[3 * i] * c[0].y + Mi[3 * i + 1] * c[1].y + Mi[3 * i + 2] * c[2].y;
+            xv.x += z[i].x;
+            xv.y += z[i].y;
             x[i * Nh + e] = xv;
         }
     }
@@ -976,7 +851,7 @@ void axpby(void* out, const void* a, const void* b, double alpha, double beta, s
 template <typename R>
 __global__ void k_norm2(const typename Tr<R>::Cx* v, SGrid g, Red red) {
     typedef typename Tr<R>::Cx Cx;
-    double acc[1] = {0.0};
+    R acc[1] = {};
     GRID_STRIDE(e, g.Nh) {
         R xi[3], xd[3], wt;
         hs_freq<R>(g, e, xi, xd, wt);
@@ -986,10 +861,10 @@ __global__ void k_norm2(const typename Tr<R>::Cx* v, SGrid g, Red red) {
             const Cx q = v[c * g.Nh + e];
             nn += q.x * q.x + q.y * q.y;
         }
-        acc[0] += (double)wt * (double)nn;
+        acc[0] += wt * nn;
     }
     block_partials<1, kThreads>(acc, 1, 0u, red.part);
-    grid_finish<kThreads>(red, 1, 0u, 1.0);
+    grid_finish<kThreads, 1>(red, 1, 0u, 1.0);
 }
 template <typename R>
 void norm2(const void* v, const SGrid& g, const Red& red, cudaStream_t s) {
@@ -1001,19 +876,19 @@ void norm2(const void* v, const SGrid& g, const Red& red, cudaStream_t s) {
 // out[1] = max |H - Ht| (the Newton test of Sec. 3.1).
 template <typename R>
 __global__ void k_fupdate(R* H, const R* G, R invN, const R* Ht, size_t N, Red red) {
-    double acc[2] = {0.0, 0.0};
+    R acc[2] = {};
     GRID_STRIDE(v, N) {
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
             const R d = G[c * N + v] * invN;
             const R h = H[c * N + v] + d;
             H[c * N + v] = h;
-            acc[0] = fmax(acc[0], (double)fabs(d));
-            acc[1] = fmax(acc[1], (double)fabs(h - Ht[c * N + v]));
+            acc[0] = fmax(acc[0], fabs(d));
+            acc[1] = fmax(acc[1], fabs(h - Ht[c * N + v]));
         }
     }
     block_partials<2, kThreads>(acc, 2, 3u, red.part);
-    grid_finish<kThreads>(red, 2, 3u, 1.0);
+    grid_finish<kThreads, 2>(red, 2, 3u, 1.0);
 }
 template <typename R>
 void fupdate(void* H, const void* G, const void* Ht, size_t N, const Red& red, cudaStream_t s) {
@@ -1026,22 +901,20 @@ void fupdate(void* H, const void* G, const void* Ht, size_t N, const Red& red, c
 template <typename R>
 __global__ void k_stag_stats(const R* H, const R* Hprev, const R* Ht, const R* P, const R* phi,
                              R kres, size_t N, Red red) {
-    double acc[11];
-#pragma unroll
-    for (int i = 0; i < 11; ++i) acc[i] = 0.0;
+    R acc[11] = {};
     GRID_STRIDE(v, N) {
         const R om = R(1) - phi[v];
         const R g = om * om + kres;
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
             const R h = H[c * N + v];
-            acc[0] = fmax(acc[0], (double)fabs(h - Hprev[c * N + v]));
-            acc[1] = fmax(acc[1], (double)fabs(h - Ht[c * N + v]));
-            acc[2 + c] += (double)(g * P[c * N + v]);
+            acc[0] = fmax(acc[0], fabs(h - Hprev[c * N + v]));
+            acc[1] = fmax(acc[1], fabs(h - Ht[c * N + v]));
+            acc[2 + c] += g * P[c * N + v];
         }
     }
     block_partials<11, kThreads>(acc, 11, 3u, red.part);
-    grid_finish<kThreads>(red, 11, 3u, 1.0 / (double)N);
+    grid_finish<kThreads, 11>(red, 11, 3u, 1.0 / (double)N);
 }
 template <typename R>
 void stag_stats(const void* H, const void* Hprev, const void* Ht, const void* P, const void* phi,
@@ -1052,10 +925,10 @@ void stag_stats(const void* H, const void* Hprev, const void* Ht, const void* P,
 
 template <typename R>
 __global__ void k_maxval(const R* a, size_t n, Red red) {
-    double acc[1] = {0.0};
-    GRID_STRIDE(i, n) acc[0] = fmax(acc[0], (double)a[i]);
+    R acc[1] = {};
+    GRID_STRIDE(i, n) acc[0] = fmax(acc[0], a[i]);
     block_partials<1, kThreads>(acc, 1, 1u, red.part);
-    grid_finish<kThreads>(red, 1, 1u, 1.0);
+    grid_finish<kThreads, 1>(red, 1, 1u, 1.0);
 }
 template <typename R>
 void maxval(const void* a, size_t n, const Red& red, cudaStream_t s) {
@@ -1088,16 +961,16 @@ void pf_spec(void* f, const SGrid& g, double l2, int mode, cudaStream_t s) {
 // r = 2S - (1 + 2S) x - lapx; out[0] = ||r||^2, out[1] = ||2S||^2
 template <typename R>
 __global__ void k_pf_init(const R* x, const R* lapx, const R* S, R* r, size_t N, Red red) {
-    double acc[2] = {0.0, 0.0};
+    R acc[2] = {};
     GRID_STRIDE(v, N) {
         const R s2 = R(2) * S[v];
         const R rv = s2 - (R(1) + s2) * x[v] - lapx[v];
         r[v] = rv;
-        acc[0] += (double)rv * rv;
-        acc[1] += (double)s2 * s2;
+        acc[0] += rv * rv;
+        acc[1] += s2 * s2;
     }
     block_partials<2, kThreads>(acc, 2, 0u, red.part);
-    grid_finish<kThreads>(red, 2, 0u, 1.0);
+    grid_finish<kThreads, 2>(red, 2, 0u, 1.0);
 }
 template <typename R>
 void pf_init(const void* x, const void* lapx, const void* S, void* r, size_t N, const Red& red,
@@ -1108,10 +981,10 @@ void pf_init(const void* x, const void* lapx, const void* S, void* r, size_t N, 
 
 template <typename R>
 __global__ void k_rdot(const R* a, const R* b, size_t N, Red red) {
-    double acc[1] = {0.0};
-    GRID_STRIDE(v, N) acc[0] += (double)a[v] * (double)b[v];
+    R acc[1] = {};
+    GRID_STRIDE(v, N) acc[0] += a[v] * b[v];
     block_partials<1, kThreads>(acc, 1, 0u, red.part);
-    grid_finish<kThreads>(red, 1, 0u, 1.0);
+    grid_finish<kThreads, 1>(red, 1, 0u, 1.0);
 }
 template <typename R>
 void rdot(const void* a, const void* b, size_t N, const Red& red, cudaStream_t s) {
@@ -1121,14 +994,14 @@ void rdot(const void* a, const void* b, size_t N, const Red& red, cudaStream_t s
 // q = t + 2 S p  (A p through the recurrence t = M^-1 p);  out[0] = <p, q>
 template <typename R>
 __global__ void k_pf_q(const R* t, const R* p, const R* S, R* q, size_t N, Red red) {
-    double acc[1] = {0.0};
+    R acc[1] = {};
     GRID_STRIDE(v, N) {
         const R qv = t[v] + R(2) * S[v] * p[v];
         q[v] = qv;
-        acc[0] += (double)p[v] * qv;
+        acc[0] += p[v] * qv;
     }
     block_partials<1, kThreads>(acc, 1, 0u, red.part);
-    grid_finish<kThreads>(red, 1, 0u, 1.0);
+    grid_finish<kThreads, 1>(red, 1, 0u, 1.0);
 }
 template <typename R>
 void pf_q(const void* t, const void* p, const void* S, void* q, size_t N, const Red& red,
@@ -1140,15 +1013,15 @@ void pf_q(const void* t, const void* p, const void* S, void* q, size_t N, const 
 // x += alpha p; r -= alpha q; out[0] = ||r||^2
 template <typename R>
 __global__ void k_pf_xr(R* x, R* r, const R* p, const R* q, R alpha, size_t N, Red red) {
-    double acc[1] = {0.0};
+    R acc[1] = {};
     GRID_STRIDE(v, N) {
         x[v] += alpha * p[v];
         const R rv = r[v] - alpha * q[v];
         r[v] = rv;
-        acc[0] += (double)rv * rv;
+        acc[0] += rv * rv;
     }
     block_partials<1, kThreads>(acc, 1, 0u, red.part);
-    grid_finish<kThreads>(red, 1, 0u, 1.0);
+    grid_finish<kThreads, 1>(red, 1, 0u, 1.0);
 }
 template <typename R>
 void pf_xr(void* x, void* r, const void* p, const void* q, double alpha, size_t N, const Red& red,
@@ -1177,19 +1050,19 @@ void pf_pt(void* p, void* t, const void* z, const void* r, double beta, size_t N
 // cracked (phi >= 0.9) voxels.
 template <typename R>
 __global__ void k_pf_clamp(const R* x, const R* phi_t, R* phi, size_t N, Red red) {
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    R acc[4] = {};
     GRID_STRIDE(v, N) {
         const R pt = phi_t[v];
         const R pn = fmax(x[v], pt);
         const R po = phi[v];
         phi[v] = pn;
-        acc[0] = fmax(acc[0], (double)fabs(pn - po));
-        acc[1] = fmax(acc[1], (double)fabs(pn - pt));
-        acc[2] += pn != po ? 1.0 : 0.0;
-        acc[3] += pn >= R(0.9) ? 1.0 : 0.0;
+        acc[0] = fmax(acc[0], fabs(pn - po));
+        acc[1] = fmax(acc[1], fabs(pn - pt));
+        acc[2] += pn != po ? R(1) : R(0);
+        acc[3] += pn >= R(0.9) ? R(1) : R(0);
     }
     block_partials<4, kThreads>(acc, 4, 3u, red.part);
-    grid_finish<kThreads>(red, 4, 3u, 1.0);
+    grid_finish<kThreads, 4>(red, 4, 3u, 1.0);
 }
 template <typename R>
 void pf_clamp(const void* x, const void* phi_t, void* phi, size_t N, const Red& red,
@@ -1304,20 +1177,12 @@ void fp_in(const double* Fp, const int32_t* grain, const double* Qg, void* Hpi, 
                                   void*, int, cudaStream_t);                                    \
     template void tangent_apply<R>(void*, const void*, const void*, double, size_t,             \
                                    cudaStream_t);                                               \
-    template void contract_dots<R>(const void*, const SGrid&, void*, const void*, size_t, int,  \
-                                   const Red&, cudaStream_t, const GmState*);                   \
-    template void gs_update<R>(void*, const void*, size_t, int, const double*, int,             \
-                               const SGrid&, const Red&, cudaStream_t, const GmState*);         \
-    template void gm_precond_grad<R>(const GmArgs&, const double*, const SGrid&, void*,         \
-                                     cudaStream_t);                                             \
-    template void gm_reorth<R>(void*, const void*, size_t, const double*, GmState*,             \
-                               const SGrid&, const Red&, const Red&, cudaStream_t);             \
-    template void gm_reorth_flag<R>(const double*, GmState*, cudaStream_t);                     \
     template void contract<R>(const void*, const SGrid&, void*, cudaStream_t);                  \
-    template void vdots<R>(const void*, const void*, size_t, int, const SGrid&, const Red&,     \
-                           cudaStream_t, const GmState*, int);                                  \
-    template void vupdate<R>(void*, const void*, size_t, int, const double*, const SGrid&,      \
-                             const Red&, cudaStream_t, const GmState*, int);                    \
+    template void dcgs_dots<R>(const void*, const void*, const void*, size_t, int,              \
+                               const SGrid&, const Red&, double*, double*, double*, double*,   \
+                               cudaStream_t);                                                   \
+    template void dcgs_update<R>(void*, size_t, int, const void*, const double*,                \
+                                 const double*, const SGrid&, void*, const Red&, cudaStream_t); \
     template void norm2<R>(const void*, const SGrid&, const Red&, cudaStream_t);                \
     template void xupdate<R>(void*, const void*, size_t, int, const double*, const double*,     \
                              const SGrid&, cudaStream_t);                                       \

@@ -23,7 +23,11 @@ using namespace fatfft;
 namespace {
 enum { ST_NEW = 0, ST_APPLIED = 1, ST_EQUIL = 2, ST_DAMAGE = 3, ST_COMMITTED = 4 };
 constexpr int kMaxRestart = 64;
-constexpr int kSlot = 160;  // doubles per look-ahead slot: red[0..130) + GmState
+constexpr int kSlot = 96;    // doubles per look-ahead slot (kSlotLen used)
+constexpr int kDslot = 128;  // device copy of the slot: red + kDslot
+static_assert(kSlotLen <= kSlot, "host slot too small");
+static_assert(kDslot + kSlotLen <= kRedSlots, "device slot outside the reduction buffer");
+static_assert(3 + 2 * (kMaxKrylov - 1) <= kDslot, "Arnoldi dots overlap the device slot");
 }  // namespace
 
 struct fft_rve_s {
@@ -46,6 +50,8 @@ struct fft_rve_s {
     int32_t* grain = nullptr;
     uint8_t* elastic = nullptr;
     double *Qg = nullptr, *G81 = nullptr, *Kbar = nullptr;
+    double* Hd = nullptr;  // Hessenberg columns, final then provisional (kMaxKrylov x kHcol
+                           // each), then the DCGS2 step coefficients
     // work buffers
     void *rb9 = nullptr, *cb9 = nullptr;                      // real 9N, complex 9Nh
     void *V = nullptr, *x = nullptr, *b = nullptr, *w = nullptr;  // GMRES (complex)
@@ -55,8 +61,14 @@ struct fft_rve_s {
     unsigned* counter = nullptr;  // ticket of the last-block reductions
     double *hred = nullptr, *hy = nullptr;  // pinned host
     double* hslot = nullptr;                // pinned look-ahead slots, 2 x kSlot doubles
-    GmState* gst = nullptr;                 // device Arnoldi position
     cudaEvent_t slot_ev[2] = {nullptr, nullptr};
+    // one CUDA graph per Arnoldi column j (the step's pointers and grid
+    // shapes depend on j only), captured on first use; off on the legacy
+    // default stream, while the kernel profiler runs, or with
+    // FATIGUEFFT_GRAPHS=0
+    cudaGraphExec_t step_exec[kMaxKrylov] = {};
+    long long step_launches[kMaxKrylov] = {};
+    bool graphs = true;
     int* dfail = nullptr;
     double* stage = nullptr;  // device staging for host fields_out / fields_in
     size_t stage_bytes = 0;
@@ -69,8 +81,12 @@ struct fft_rve_s {
         cudaEvent_t a, b;
         int fam;
         double bytes;
+        bool owned;  // recorded by a step graph's event nodes; kept by the graph
     };
     std::vector<ProfEv> prof_pending;
+    bool capturing = false;                      // a step graph is being captured
+    std::vector<ProfEv> cap_prof;                // its profiler event pairs
+    std::vector<ProfEv> step_prof[kMaxKrylov];   // per column, replayed with it
     std::vector<cudaEvent_t> prof_pool;
     double prof_ms[16] = {0};
     double prof_bytes[16] = {0};
@@ -114,30 +130,43 @@ enum {
     KF_XUPD = 6, KF_KBAR = 7, KF_RESID = 8, KF_FUPD = 9, KF_PF = 10, KF_GND = 11, KF_FFT9 = 12,
     KF_FFT1 = 13, KF_FIN = 14, KF_OTHER = 15
 };
-static cudaEvent_t prof_begin(fft_rve_s* r, int fam) {
-    if (!(r->prof_mask >> fam & 1u)) return nullptr;
-    cudaEvent_t e;
-    if (r->prof_pool.empty()) {
+// Event for the profiler: from the pool, or (while a step graph is captured)
+// a new one owned by that graph and recorded through an event node.
+static cudaEvent_t prof_event(fft_rve_s* r) {
+    cudaEvent_t e = nullptr;
+    if (r->capturing || r->prof_pool.empty()) {
         if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
     } else {
         e = r->prof_pool.back();
         r->prof_pool.pop_back();
     }
-    cudaEventRecord(e, r->st);
+    const cudaError_t ce = r->capturing
+                               ? cudaEventRecordWithFlags(e, r->st, cudaEventRecordExternal)
+                               : cudaEventRecord(e, r->st);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e);
+        return nullptr;
+    }
     return e;
+}
+static cudaEvent_t prof_begin(fft_rve_s* r, int fam) {
+    if (!(r->prof_mask >> fam & 1u)) return nullptr;
+    return prof_event(r);
 }
 // bytes: the algorithmic HBM traffic of the bracketed launch(es)
 static void prof_end(fft_rve_s* r, int fam, cudaEvent_t a, double bytes = 0.0) {
     if (!a) return;
-    cudaEvent_t b;
-    if (r->prof_pool.empty()) {
-        if (cudaEventCreate(&b) != cudaSuccess) return;
-    } else {
-        b = r->prof_pool.back();
-        r->prof_pool.pop_back();
-    }
-    cudaEventRecord(b, r->st);
-    r->prof_pending.push_back({a, b, fam, bytes});
+    cudaEvent_t b = prof_event(r);
+    if (!b) return;
+    if (r->capturing)
+        r->cap_prof.push_back({a, b, fam, bytes, true});
+    else
+        r->prof_pending.push_back({a, b, fam, bytes, false});
+}
+static void prof_release(fft_rve_s* r, const fft_rve_s::ProfEv& p) {
+    if (p.owned) return;
+    r->prof_pool.push_back(p.a);
+    r->prof_pool.push_back(p.b);
 }
 // after a stream synchronisation: fold the recorded pairs into the totals
 static void prof_collect(fft_rve_s* r) {
@@ -148,8 +177,7 @@ static void prof_collect(fft_rve_s* r) {
             r->prof_bytes[p.fam] += p.bytes;
             r->prof_cnt[p.fam] += 1;
         }
-        r->prof_pool.push_back(p.a);
-        r->prof_pool.push_back(p.b);
+        prof_release(r, p);
     }
     r->prof_pending.clear();
 }
@@ -169,11 +197,28 @@ static void prof_collect_if_done(fft_rve_s* r) {
             r->prof_bytes[p.fam] += p.bytes;
             r->prof_cnt[p.fam] += 1;
         }
-        r->prof_pool.push_back(p.a);
-        r->prof_pool.push_back(p.b);
+        prof_release(r, p);
     }
     r->prof_pending.swap(keep);
     cudaGetLastError();  // cudaEventQuery's cudaErrorNotReady is not an error here
+}
+
+// Destroy the cached step graphs and their timing events (call with the
+// stream idle and the profiler's pending list folded in).
+static void drop_graphs(fft_rve_s* r) {
+    std::vector<fft_rve_s::ProfEv> keep;  // forget replays not yet folded in
+    for (auto& p : r->prof_pending)
+        if (!p.owned) keep.push_back(p);
+    r->prof_pending.swap(keep);
+    for (int j = 0; j < kMaxKrylov; ++j) {
+        if (r->step_exec[j]) cudaGraphExecDestroy(r->step_exec[j]);
+        r->step_exec[j] = nullptr;
+        for (auto& p : r->step_prof[j]) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+        r->step_prof[j].clear();
+    }
 }
 
 static fft_status dalloc(fft_rve_s* r, void** p, size_t bytes) {
@@ -417,18 +462,81 @@ struct Impl {
         return FFT_OK;
     }
 
-    // One Arnoldi step with operands from the device state (look-ahead GMRES):
-    // w = A M v_k projected onto real fields, red[0] = ||w||^2 and
-    // red[1 + i] = <V_i, w>; first Gram-Schmidt update (red[64] = new
-    // ||w||^2); optional second pass (red[97 + i], red[64] replaced); the
-    // results are copied to slot j % 2 and the state advanced.
-    static fft_status enqueue_step(fft_rve_s* r, int j) {
+    // One Arnoldi step j.  Krylov slot j holds the unnormalised vector w^_j
+    // (for j = 0 it is formed here as src * scale, normalised) and cb9 the
+    // spectrum of grad(M w^_j), written by the previous step's update.  The
+    // step forms w = A M V_j with V_j = w^_j / ||w^_j|| (the norm from
+    // red[64], applied in the tangent apply; slot j is normalised by the
+    // contraction), red[0] = ||w||^2, red[1 + i] = <V_i, w>, the Gram-Schmidt
+    // update w^_{j+1} into slot j + 1 with red[64] = ||w^_{j+1}||^2 and the
+    // next gradient spectrum, and the optional second pass (red[95] = 1,
+    // red[97 + i]); red[0, 130) is then copied to host slot j % 2.
+    static fft_status enqueue_step(fft_rve_s* r, int j, const void* src, double scale) {
+        if (j == 0) {
+            const double Nh = (double)r->g.Nh, es = (double)sizeof(R);
+            cudaEvent_t e = prof_begin(r, KF_PRECOND);
+            precond_grad<R>(src, scale, r->V, r->Kbar, r->g, r->cb9, 1, r->st);
+            prof_end(r, KF_PRECOND, e, Nh * 2 * es * (3 + 3 + 9));
+            r->launches += 1;
+        }
+        if (r->graphs && r->st) {
+            if (!r->step_exec[j]) {
+                const long long l0 = r->launches;
+                CK(r, cudaStreamBeginCapture(r->st, cudaStreamCaptureModeThreadLocal));
+                r->capturing = true;
+                r->cap_prof.clear();
+                const fft_status sb = step_body(r, j);
+                r->capturing = false;
+                cudaGraph_t gr = nullptr;
+                const cudaError_t ce = cudaStreamEndCapture(r->st, &gr);
+                r->step_prof[j].swap(r->cap_prof);
+                for (auto& p : r->cap_prof) {
+                    cudaEventDestroy(p.a);
+                    cudaEventDestroy(p.b);
+                }
+                r->cap_prof.clear();
+                cudaError_t ie = ce;
+                if (sb == FFT_OK && ce == cudaSuccess)
+                    ie = cudaGraphInstantiate(&r->step_exec[j], gr, 0);
+                if (gr) cudaGraphDestroy(gr);
+                const long long nl = r->launches - l0;  // this column's own kernels
+                r->launches = l0;
+                if (sb != FFT_OK || ie != cudaSuccess) {
+                    // capture unsupported here: run this handle without graphs
+                    // (a genuine error then surfaces from the direct launch)
+                    cudaGetLastError();
+                    r->step_exec[j] = nullptr;
+                    drop_graphs(r);
+                    r->graphs = false;
+                    if (r->verbose)
+                        std::fprintf(stderr, "  step graph capture failed (%s, %s); graphs off\n",
+                                     cudaGetErrorString(ie), r->err.c_str());
+                    TRY(step_body(r, j));
+                    CK(r, cudaEventRecord(r->slot_ev[j % 2], r->st));
+                    return FFT_OK;
+                }
+                r->step_launches[j] = nl;
+            }
+            CK(r, cudaGraphLaunch(r->step_exec[j], r->st));
+            r->launches += r->step_launches[j];
+            // the graph's timing events; folded in before it is launched again
+            // (every GMRES cycle ends with a stream synchronisation)
+            for (auto& p : r->step_prof[j]) r->prof_pending.push_back(p);
+        } else {
+            TRY(step_body(r, j));
+        }
+        CK(r, cudaEventRecord(r->slot_ev[j % 2], r->st));
+        return FFT_OK;
+    }
+
+    // The body of Arnoldi step j after its first-column set-up (see
+    // enqueue_step); captured into the column's graph when graphs are on.
+    static fft_status step_body(fft_rve_s* r, int k) {
         const double N = (double)r->g.N, Nh = (double)r->g.Nh, es = (double)sizeof(R);
         const size_t vs = 3 * r->g.Nh;
-        GmArgs ga{r->gst, r->V, r->w, vs};
-        cudaEvent_t e = prof_begin(r, KF_PRECOND);
-        gm_precond_grad<R>(ga, r->Kbar, r->g, r->cb9, r->st);
-        prof_end(r, KF_PRECOND, e, Nh * 2 * es * (3 + 9 + (j ? 3 : 0)));
+        Cx* V = (Cx*)r->V;
+        double* dslot = r->red + kDslot;
+        cudaEvent_t e;
         TRY(inv9(r));
         e = prof_begin(r, KF_TANGENT);
         tangent_apply<R>(r->rb9, r->K, r->phi, r->mat.k_res, r->g.N, r->st);
@@ -437,33 +545,67 @@ struct Impl {
         e = prof_begin(r, KF_CONTRACT);
         contract<R>(r->cb9, r->g, r->w, r->st);
         prof_end(r, KF_CONTRACT, e, Nh * 2 * es * (9 + 3));
-        // red[0] = ||w||^2, red[1 + i] = <V_i, w>; w -= V h, red[64] = ||w||^2
+        // one pass over q_0 .. q_{k-1}, c_k and z: alpha, beta, a, b
         e = prof_begin(r, KF_MDOT);
-        vdots<R>(r->w, r->V, vs, j + 1, r->g, red_at(r, r->red), r->st, r->gst, 0);
-        prof_end(r, KF_MDOT, e, Nh * 2 * es * 3 * (j + 2));
+        double* Hp = r->Hd + (size_t)kMaxKrylov * kHcol;
+        double* coef = Hp + (size_t)kMaxKrylov * kHcol;
+        dcgs_dots<R>(V + (size_t)k * vs, r->w, V, vs, k, r->g, red_at(r, r->red), r->Hd, Hp,
+                     dslot, coef, r->st);
+        prof_end(r, KF_MDOT, e, Nh * 2 * es * 3 * (k + 2));
+        // q_k final, c_{k+1} and the next gradient spectrum
         e = prof_begin(r, KF_GSUPD);
-        vupdate<R>(r->w, r->V, vs, j + 1, r->red, r->g, red_at(r, r->red + 64), r->st, r->gst, 0);
-        prof_end(r, KF_GSUPD, e, Nh * 2 * es * 3 * (j + 3));
-        // second pass only when the norm dropped below 1/sqrt(2) (decided on the device)
-        gm_reorth_flag<R>(r->red, r->gst, r->st);
-        vdots<R>(r->w, r->V, vs, j + 1, r->g, red_at(r, r->red + 96), r->st, r->gst, 1);
-        vupdate<R>(r->w, r->V, vs, j + 1, r->red + 96, r->g, red_at(r, r->red + 64), r->st, r->gst,
-                   1);
-        double* slot = r->hslot + (size_t)(j % 2) * kSlot;
-        CK(r, cudaMemcpyAsync(slot, r->red, 130 * sizeof(double), cudaMemcpyDeviceToHost, r->st));
-        CK(r, cudaMemcpyAsync(slot + 130, r->gst, sizeof(GmState), cudaMemcpyDeviceToHost, r->st));
-        gm_advance(r->gst, r->red + 64, r->st);
-        CK(r, cudaEventRecord(r->slot_ev[j % 2], r->st));
-        r->launches += 9;
+        dcgs_update<R>(V, vs, k, r->w, coef, r->Kbar, r->g, r->cb9,
+                       red_at(r, dslot + kSlotNorm), r->st);
+        prof_end(r, KF_GSUPD, e, Nh * 2 * es * 3 * (k + 2 + 2 + 3));
+        double* slot = r->hslot + (size_t)(k % 2) * kSlot;
+        CK(r, cudaMemcpyAsync(slot, dslot, kSlotLen * sizeof(double), cudaMemcpyDeviceToHost,
+                              r->st));
+        r->launches += 4;
         return FFT_OK;
     }
 
-    // Restarted GMRES, right-preconditioned by the Green operator; classical
-    // Gram-Schmidt with a second pass when the norm drops below 1/sqrt(2) of
-    // its value (the DGKS test, decided on the device); Hermitian-weighted
-    // FP64 dot products; Hessenberg least squares on the host one step behind
-    // the GPU (step j runs while column j - 1 is processed, so the device
-    // never waits for the host; the step after convergence is discarded).
+    // Least squares of restarted GMRES over columns 0 .. kc-1 of the host
+    // Hessenberg copy (row stride m): Givens QR from scratch (kc <= 31, so
+    // this is cheap and lets the last column be replaced by its final value),
+    // residual |g_kc| returned; with y, the back substitution.
+    static double hess_lsq(const std::vector<double>& Hm, int m, int kc, double beta, double* y) {
+        std::vector<double> Rm((size_t)(kc + 1) * kc), g(kc + 1, 0.0), cs(kc), sn(kc);
+        for (int i = 0; i <= kc; ++i)
+            for (int c = 0; c < kc; ++c) Rm[(size_t)i * kc + c] = Hm[(size_t)i * m + c];
+        g[0] = beta;
+        for (int c = 0; c < kc; ++c) {
+            for (int i = 0; i < c; ++i) {
+                const double a = Rm[(size_t)i * kc + c], b = Rm[(size_t)(i + 1) * kc + c];
+                Rm[(size_t)i * kc + c] = cs[i] * a + sn[i] * b;
+                Rm[(size_t)(i + 1) * kc + c] = -sn[i] * a + cs[i] * b;
+            }
+            const double a = Rm[(size_t)c * kc + c], b = Rm[(size_t)(c + 1) * kc + c];
+            const double den = std::hypot(a, b);
+            cs[c] = den > 0 ? a / den : 1.0;
+            sn[c] = den > 0 ? b / den : 0.0;
+            Rm[(size_t)c * kc + c] = den;
+            Rm[(size_t)(c + 1) * kc + c] = 0.0;
+            g[c + 1] = -sn[c] * g[c];
+            g[c] = cs[c] * g[c];
+        }
+        if (y)
+            for (int i = kc - 1; i >= 0; --i) {
+                double s = g[i];
+                for (int j = i + 1; j < kc; ++j) s -= Rm[(size_t)i * kc + j] * y[j];
+                y[i] = Rm[(size_t)i * kc + i] != 0.0 ? s / Rm[(size_t)i * kc + i] : 0.0;
+            }
+        return std::fabs(g[kc]);
+    }
+
+    // Restarted GMRES, right-preconditioned by the Green operator, with the
+    // DCGS2 Arnoldi step above (two passes over the basis per step);
+    // Hermitian-weighted FP64 dot products.  The host solves the Hessenberg
+    // least squares one step behind the GPU (step j runs while the results
+    // of step j - 1 are processed, so the device never waits for the host;
+    // the step after convergence is discarded).  After step k the columns
+    // 0 .. k-1 are final and column k is provisional: its reorthogonalisation
+    // correction arrives with step k + 1 and is of the order of the FP
+    // rounding of the first projection.
     static fft_status gmres(fft_rve_s* r, double bn, double pn, int* its) {
         const size_t Nh = r->g.Nh, n3 = 3 * Nh;
         const double es = (double)sizeof(R);
@@ -476,14 +618,14 @@ struct Impl {
         const int m = std::max(1, std::min(r->opt.restart, kMaxKrylov - 1));
         const size_t vs = n3;  // stride between Krylov vectors (elements)
         Cx* V = (Cx*)r->V;
-        std::vector<double> Hm((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+        std::vector<double> Hm((size_t)(m + 1) * m), y(m);
         bool first = true, ok = false;
         int lin = 0;
         while (lin < r->opt.max_lin && !ok) {
             double beta;
+            const void* src = r->b;
             if (first) {
                 beta = bn;
-                axpby<R>(V, r->b, nullptr, 1.0 / beta, 0.0, n3, r->st);
             } else {
                 TRY(apply_op(r, r->x, 1.0, nullptr, 0, r->w, 0));
                 axpby<R>(r->w, r->b, r->w, 1.0, -1.0, n3, r->st);
@@ -495,74 +637,65 @@ struct Impl {
                     ok = true;
                     break;
                 }
-                axpby<R>(V, r->w, nullptr, 1.0 / beta, 0.0, n3, r->st);
+                src = r->w;
             }
-            gm_reset(r->gst, r->st);
-            r->launches += 2;
             first = false;
             std::fill(Hm.begin(), Hm.end(), 0.0);
-            std::fill(gv.begin(), gv.end(), 0.0);
-            gv[0] = beta;
             int kcols = 0;
             for (int j = 0;; ++j) {
                 const bool enq = j < m && lin + j < r->opt.max_lin;
-                if (enq) TRY(enqueue_step(r, j));
+                if (enq) TRY(enqueue_step(r, j, src, 1.0 / beta));
                 if (j == 0) {
                     if (!enq) break;
                     continue;
                 }
-                // column k = j - 1
+                // results of step k = j - 1
                 const int k = j - 1;
                 CK(r, cudaEventSynchronize(r->slot_ev[k % 2]));
                 prof_collect_if_done(r);
                 const double* slot = r->hslot + (size_t)(k % 2) * kSlot;
-                GmState gs;
-                std::memcpy(&gs, slot + 130, sizeof(GmState));
-                for (int i = 0; i <= k; ++i)
-                    Hm[i * m + k] = slot[1 + i] + (gs.reorth ? slot[97 + i] : 0.0);
-                const double hn = std::sqrt(std::max(slot[64], 0.0));
-                if (!std::isfinite(hn) || !std::isfinite(slot[0]))
-                    FAIL(r, FFT_ERR_NONFINITE, "non-finite Krylov vector (step %d)", lin + 1);
-                Hm[(k + 1) * m + k] = hn;
-                for (int i = 0; i < k; ++i) {
-                    const double t = cs[i] * Hm[i * m + k] + sn[i] * Hm[(i + 1) * m + k];
-                    Hm[(i + 1) * m + k] = -sn[i] * Hm[i * m + k] + cs[i] * Hm[(i + 1) * m + k];
-                    Hm[i * m + k] = t;
-                }
-                const double den = std::hypot(Hm[k * m + k], Hm[(k + 1) * m + k]);
-                cs[k] = den > 0 ? Hm[k * m + k] / den : 1.0;
-                sn[k] = den > 0 ? Hm[(k + 1) * m + k] / den : 0.0;
-                Hm[k * m + k] = den;
-                Hm[(k + 1) * m + k] = 0.0;
-                gv[k + 1] = -sn[k] * gv[k];
-                gv[k] = cs[k] * gv[k];
+                for (int i = 0; i < kSlotLen; ++i)
+                    if (!std::isfinite(slot[i]))
+                        FAIL(r, FFT_ERR_NONFINITE, "non-finite Krylov coefficient (step %d)",
+                             lin + 1);
+                if (k >= 1)
+                    for (int l = 0; l <= k; ++l) Hm[(size_t)l * m + k - 1] = slot[l];
+                for (int l = 0; l <= k; ++l) Hm[(size_t)l * m + k] = slot[kSlotProv + l];
+                const double hn = std::sqrt(std::max(slot[kSlotNorm], 0.0));
+                Hm[(size_t)(k + 1) * m + k] = hn;
                 ++lin;
                 kcols = k + 1;
+                if (k >= 1 && slot[kSlotNu] == 0.0) {
+                    // c_k lay in the span of q_0 .. q_{k-1}: column k - 1 is exact
+                    kcols = k;
+                    ok = true;
+                    break;
+                }
+                const double res = hess_lsq(Hm, m, kcols, beta, nullptr);
                 if (r->verbose)
-                    std::fprintf(stderr, "  gmres it %d |r|/|b| %.3e (|b| %.3e, h %.3e%s)\n", lin,
-                                 std::fabs(gv[k + 1]) / bn, bn, hn, gs.reorth ? ", reorth" : "");
-                if (std::fabs(gv[k + 1]) <= target || hn == 0.0) {
+                    std::fprintf(stderr, "  gmres it %d |r|/|b| %.3e (|b| %.3e, h %.3e)\n", lin,
+                                 res / bn, bn, hn);
+                if (res <= target || hn == 0.0) {
                     ok = true;
                     break;
                 }
                 if (!enq) break;
             }
             const int k = kcols;
-            for (int i = k - 1; i >= 0; --i) {
-                double s = gv[i];
-                for (int j = i + 1; j < k; ++j) s -= Hm[i * m + j] * y[j];
-                y[i] = s / Hm[i * m + i];
-            }
+            hess_lsq(Hm, m, k, beta, y.data());
             CK(r, cudaStreamSynchronize(r->st));  // the discarded look-ahead step, hy reuse
             prof_collect(r);
-            std::memcpy(r->hy, y.data(), k * sizeof(double));
-            CK(r, cudaMemcpyAsync(r->dy, r->hy, k * sizeof(double), cudaMemcpyHostToDevice, r->st));
-            cudaEvent_t e = prof_begin(r, KF_XUPD);
-            xupdate<R>(r->x, V, vs, k, r->dy, r->Kbar, r->g, r->st);
-            prof_end(r, KF_XUPD, e, (double)Nh * 2 * es * 3 * (k + 2));
-            r->launches += 1;
-            CK(r, cudaStreamSynchronize(r->st));  // hy is reused by the next fetch
-            prof_collect(r);
+            if (k > 0) {
+                std::memcpy(r->hy, y.data(), k * sizeof(double));
+                CK(r, cudaMemcpyAsync(r->dy, r->hy, k * sizeof(double), cudaMemcpyHostToDevice,
+                                      r->st));
+                cudaEvent_t e = prof_begin(r, KF_XUPD);
+                xupdate<R>(r->x, V, vs, k, r->dy, r->Kbar, r->g, r->st);
+                prof_end(r, KF_XUPD, e, (double)Nh * 2 * es * 3 * (k + 2));
+                r->launches += 1;
+                CK(r, cudaStreamSynchronize(r->st));  // hy is reused by the next fetch
+                prof_collect(r);
+            }
         }
         *its = lin;
         CK(r, cudaGetLastError());
@@ -867,11 +1000,15 @@ struct Impl {
 #define DISPATCH(r, call) ((r)->prec == FFT_PREC_FP64 ? Impl<double>::call : Impl<float>::call)
 
 static void release(fft_rve_s* r) {
-    for (auto& p : r->prof_pending) {
-        cudaEventDestroy(p.a);
-        cudaEventDestroy(p.b);
-    }
+    for (auto& p : r->prof_pending)
+        if (!p.owned) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+    r->prof_pending.clear();
     for (auto e : r->prof_pool) cudaEventDestroy(e);
+    r->prof_pool.clear();
+    drop_graphs(r);
     if (r->plans) {
         cufftDestroy(r->r2c9);
         cufftDestroy(r->c2r9);
@@ -916,13 +1053,22 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
         return FFT_ERR_ARG;
     *out = nullptr;
     for (int d = 0; d < 3; ++d)
-        if (grid->n[d] < 1) return FFT_ERR_ARG;
+        if (grid->n[d] < 1 || grid->n[d] > 4096) return FFT_ERR_ARG;
+    {
+        // spectral kernels index 9 half-spectrum components with 32 bits
+        const uint64_t nh = (uint64_t)(grid->n[0] / 2 + 1) * grid->n[1] * grid->n[2];
+        if (9 * nh >= (1ull << 31)) return FFT_ERR_ARG;
+    }
     if (!(grid->h > 0) || (opt->prec != FFT_PREC_FP64 && opt->prec != FFT_PREC_MIXED))
         return FFT_ERR_ARG;
     fft_rve_s* r = new fft_rve_s();
     r->prec = opt->prec;
     r->esz = opt->prec == FFT_PREC_FP64 ? 8 : 4;
     r->verbose = std::getenv("FATIGUEFFT_VERBOSE") != nullptr;
+    {
+        const char* gv = std::getenv("FATIGUEFFT_GRAPHS");
+        r->graphs = !(gv && gv[0] == '0');
+    }
     r->mat = *mat;
     r->opt = *opt;
     r->h = grid->h;
@@ -938,6 +1084,9 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
     g.tpl0 = 2 * M_PI / (g.n0 * grid->h);
     g.tpl1 = 2 * M_PI / (g.n1 * grid->h);
     g.tpl2 = 2 * M_PI / (g.n2 * grid->h);
+    g.fd_n0h = make_fastdiv((uint32_t)g.n0h);
+    g.fd_n1 = make_fastdiv((uint32_t)g.n1);
+    g.fd_Nh = make_fastdiv((uint32_t)g.Nh);
     const size_t N = g.N, Nh = g.Nh;
     for (size_t v = 0; v < N; ++v)
         if (grain_ids[v] < 0 || grain_ids[v] >= n_grains) {
@@ -1006,10 +1155,10 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
     AL(r->pfq, N * es);
     AL(r->part, (size_t)kRedSlots * kRedBlocks * sizeof(double));
     AL(r->red, kRedSlots * sizeof(double));
+    AL(r->Hd, ((size_t)2 * kMaxKrylov * kHcol + 2 * kMaxKrylov + 2) * sizeof(double));
     AL(r->dy, kMaxRestart * sizeof(double));
     AL(r->dzero, kMaxRestart * sizeof(double));
     AL(r->counter, sizeof(unsigned));
-    AL(r->gst, sizeof(GmState));
     AL(r->dfail, sizeof(int));
     if (elastic_only) AL(r->elastic, N);
 #undef AL
@@ -1167,7 +1316,14 @@ size_t rve_device_bytes(fft_rve_t r) { return r ? r->bytes : 0; }
 
 fft_status rve_profile(fft_rve_t r, unsigned mask) {
     if (!r) return FFT_ERR_ARG;
-    r->prof_mask = mask & 0xffffu;
+    mask &= 0xffffu;
+    if (mask != r->prof_mask) {
+        // the step graphs carry the old mask's timing events: rebuild them
+        if (cudaStreamSynchronize(r->st) != cudaSuccess) return FFT_ERR_CUDA;
+        prof_collect(r);
+        drop_graphs(r);
+    }
+    r->prof_mask = mask;
     return FFT_OK;
 }
 

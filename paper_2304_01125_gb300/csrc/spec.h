@@ -6,36 +6,21 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "fastdiv.h"
 
 namespace fatfft {
 
-// Grid and half-spectrum geometry; tpl_i = 2 pi / L_i.
+// Grid and half-spectrum geometry; tpl_i = 2 pi / L_i; dividers for the
+// index decode of half-spectrum entries.
 struct SGrid {
     int n0, n1, n2, n0h;
     size_t N, Nh;
     double tpl0, tpl1, tpl2;
+    FastDiv fd_n0h, fd_n1, fd_Nh;
 };
 struct Mat9 {
     double a[9];
 };
-// Device-resident Arnoldi position used by the look-ahead GMRES: column
-// index k, norm of the last unnormalised Krylov vector, and whether the
-// current column took a second Gram-Schmidt pass.
-struct GmState {
-    int k;
-    int reorth;
-    double hprev;
-};
-// Where a GMRES step finds its operands when they come from GmState:
-// column 0 reads V (scale 1); column k > 0 reads w scaled by 1/hprev and
-// stores the normalised vector as V_k.
-struct GmArgs {
-    const GmState* st;
-    void* V;
-    void* w;
-    size_t vstride;
-};
-
 // Reductions write FP64 results to red.out (see Red in common.cuh).
 template <typename R> void add_uniform(void* H, const void* Ht, const double* d, size_t N, cudaStream_t s);
 template <typename R> void fp_sample(const void* Hpi, const int32_t* grain, const double* Qg, void* out, size_t N, cudaStream_t s);
@@ -46,20 +31,15 @@ template <typename R> void degrade(const void* P, const void* phi, double kres, 
 template <typename R> void residual(const void* Ph, const SGrid& g, void* b, const Red& red, cudaStream_t s);
 template <typename R> void precond_grad(const void* vin, double scale, void* vout, const double* Kbar, const SGrid& g, void* G, int use_pre, cudaStream_t s);
 template <typename R> void tangent_apply(void* G, const void* K, const void* phi, double kres, size_t N, cudaStream_t s);
-template <typename R> void contract_dots(const void* T, const SGrid& g, void* w, const void* V, size_t vstride, int nv, const Red& red, cudaStream_t s, const GmState* st = nullptr);
-template <typename R> void gs_update(void* w, const void* V, size_t vstride, int nv, const double* h, int dots, const SGrid& g, const Red& red, cudaStream_t s, const GmState* st = nullptr);
-// tiled Krylov vector kernels: out[0] = ||w||^2, out[1 + i] = <V_i, w>; and
-// w -= V h with out[0] = ||w||^2.  With need_flag the kernel runs only when
-// st->reorth is set.
 template <typename R> void contract(const void* T, const SGrid& g, void* w, cudaStream_t s);
-template <typename R> void vdots(const void* w, const void* V, size_t vstride, int nv, const SGrid& g, const Red& red, cudaStream_t s, const GmState* st, int need_flag);
-template <typename R> void vupdate(void* w, const void* V, size_t vstride, int nv, const double* hin, const SGrid& g, const Red& red, cudaStream_t s, const GmState* st, int need_flag);
-template <typename R> void gm_reorth_flag(const double* red, GmState* st, cudaStream_t s);
-// look-ahead GMRES helpers
-template <typename R> void gm_precond_grad(const GmArgs& a, const double* Kbar, const SGrid& g, void* G, cudaStream_t s);
-template <typename R> void gm_reorth(void* w, const void* V, size_t vstride, const double* red, GmState* st, const SGrid& g, const Red& red_dots, const Red& red_norm, cudaStream_t s);
-void gm_reset(GmState* st, cudaStream_t s);
-void gm_advance(GmState* st, const double* norm2, cudaStream_t s);
+// Arnoldi step kernels (DCGS2, see kernels_spec.cu).  Hessenberg columns on
+// the device are kHcol doubles apart; the host slot holds the final column
+// k-1 at 0, the provisional column k at kSlotProv, nu_k at kSlotNu and
+// |c_{k+1}|^2 at kSlotNorm.
+constexpr int kHcol = kMaxKrylov + 1;
+constexpr int kSlotProv = 40, kSlotNorm = 80, kSlotNu = 81, kSlotLen = 82;
+template <typename R> void dcgs_dots(const void* c, const void* z, const void* V, size_t vstride, int k, const SGrid& g, const Red& red, double* Hd, double* Hp, double* slot, double* coef, cudaStream_t s);
+template <typename R> void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* coef, const double* Kbar, const SGrid& g, void* G, const Red& red, cudaStream_t s);
 template <typename R> void norm2(const void* v, const SGrid& g, const Red& red, cudaStream_t s);
 template <typename R> void xupdate(void* x, const void* V, size_t vstride, int k, const double* y, const double* Kbar, const SGrid& g, cudaStream_t s);
 template <typename R> void axpby(void* out, const void* a, const void* b, double alpha, double beta, size_t n, cudaStream_t s);

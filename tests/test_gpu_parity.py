@@ -7,6 +7,8 @@ Tolerances (relative L2 over each field unless noted):
   * mixed path (FP32 bulk, FP64 reductions): 1e-4 per field, the stress and
     damage bound the method is held to.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -25,6 +27,19 @@ PREC = ["fp64", "mixed"]
 def _lib():
     B.build()
     FF.load()
+
+
+_STREAM = []
+
+
+def stream():
+    """A side stream (as the benchmark uses): the library then runs each
+    GMRES column as a captured CUDA graph.  Handles created without a stream
+    run on the legacy default stream with direct launches."""
+    if not _STREAM:
+        import torch
+        _STREAM.append(torch.cuda.Stream())
+    return _STREAM[0]
 
 
 def rel(a, b, floor=1e-300):
@@ -158,7 +173,8 @@ def _compare(gpu, orc, prec, tag):
 
 def _run_pair(n, gid, eul, prog, prec, mat=MAT, phi0=None, mask=None, opts=None):
     opts = opts or opts_for(prec)
-    g = FF.RVE(n, H, gid, eul, mat, opts, prec=prec, phi0=phi0, elastic_only=mask)
+    g = FF.RVE(n, H, gid, eul, mat, opts, prec=prec, phi0=phi0, elastic_only=mask,
+               stream=stream())
     o = O.RVE(n, H, gid, eul, mat, I.solver_options("parity64"), phi0=phi0, elastic_only=mask)
     hist = []
     for k, (Fb, dt) in enumerate(prog):
@@ -229,6 +245,30 @@ def test_precrack_mirror_symmetry_gpu():
     assert np.abs(F[0, 1]).max() > 1e-6
 
 
+@pytest.mark.parametrize("prec", PREC)
+def test_graph_replay_matches_direct_launches(prec, monkeypatch):
+    """The GMRES columns replayed from captured graphs give the same bits
+    as direct launches (same kernels, launch shapes and order; the
+    reductions are deterministic), over increments with plasticity."""
+    n = (6, 6, 6)
+    gid, eul = I.voronoi(n, 3, 11)
+    mat = dict(MAT, tau_c0=250.0)
+    prog = I.uniaxial_cycle_program(0.006, 24, 1)[:4]
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("FATIGUEFFT_GRAPHS", flag)
+        r = FF.RVE(n, H, gid, eul, mat, opts_for(prec), prec=prec, stream=stream())
+        its = 0
+        for Fb, dt in prog:
+            _, st = r.run_increment(Fb, dt)
+            its += st["lin_it_total"]
+        out.append((its, {f: r.field(f) for f in ("F", "P", "Fp", "gamma")}))
+        r.close()
+    assert out[0][0] == out[1][0] > 0
+    for f in out[0][1]:
+        assert np.array_equal(out[0][1][f], out[1][1][f]), f
+
+
 # ----------------------------------------------------------- failure paths
 def test_call_order_errors():
     n = (4, 4, 4)
@@ -262,7 +302,7 @@ def test_full_size_poly64_sampled(prec):
     phi_t <= phi <= 1 over the whole grid."""
     cfg = I.build_config("poly64")
     n, gid, eul = cfg["n"], cfg["grain_ids"], cfg["euler"]
-    r = FF.RVE(n, H, gid, eul, MAT, I.solver_options("paper"), prec=prec)
+    r = FF.RVE(n, H, gid, eul, MAT, I.solver_options("paper"), prec=prec, stream=stream())
     for Fb, dt in cfg["program"][:2]:
         s, st = r.run_increment(Fb, dt)
     F = r.field("F")
