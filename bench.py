@@ -13,6 +13,7 @@ F update, phase field, clamp, commit).  N GPUs run N independent replicas
 step one increment of the same workload).
 """
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -32,6 +33,12 @@ from paper_2304_01125_gb300 import inputs as I  # noqa: E402
 METRIC = "voxel-increments/s (CP+FFT equilibrium+phase-field), mixed vs FP64 on GPU at <=1e-4"
 CONFIG_NAME = "poly64"
 L2_NOTE = "working set > L2 (about 0.4 GB mixed per RVE) and a 256 MB L2 flush before every step"
+# kernel families bound by HBM traffic (the constitutive update is ALU-bound;
+# cuFFT is a library; "other" carries no byte count)
+HBM_FAMILIES = ("tangent_apply", "precond_grad", "contract", "gmres_dot", "gs_update",
+                "gmres_xupdate", "kbar", "residual", "f_update", "phase_field", "gnd",
+                "reductions")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 
 
 def args_():
@@ -44,7 +51,56 @@ def args_():
     p.add_argument("--tol", default="paper", choices=["paper", "parity32", "parity64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--verbose", action="store_true")
+    p.add_argument("--ref-budget-s", type=float, default=150.0,
+                   help="--impl reference: stop timing the oracle after this many seconds")
     return p.parse_args()
+
+
+def source_sha1():
+    """Hash of the CUDA sources: ncu counters recorded for another version
+    of the kernels are not reported."""
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_2304_01125_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()
+
+
+def ncu_traffic(family):
+    """DRAM bytes per launch of the family's kernel from the committed ncu
+    summary, or None when absent or taken on other kernel sources."""
+    try:
+        d = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        return None
+    e = d.get(family)
+    if not e or e.get("source_sha1") != source_sha1():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def probe_dominant(FF, cfg, mat, opts, stream, prec):
+    """Per-family kernel times over plastic increments of the workload
+    (untimed, on a separate handle): the HBM-bound family with the largest
+    total time is the one the timed region measures."""
+    import torch
+    n = cfg["n"]
+    prog = cfg["program"]
+    r = FF.RVE(n, I.VOXEL_MM, cfg["grain_ids"], cfg["euler"], mat, opts, prec=prec,
+               stream=stream)
+    for k in range(8):
+        r.run_increment(*prog[k])
+    r.profile(FF.KERNEL_FAMILIES)
+    torch.cuda.nvtx.range_push(f"probe_{prec}")  # the window of the committed ncu launch list
+    for k in range(8, 14):
+        r.run_increment(*prog[k])
+    bd = r.profile_read(reset=True)
+    torch.cuda.nvtx.range_pop()
+    r.close()
+    hbm = {k: v for k, v in bd.items() if k in HBM_FAMILIES and v[1] > 0 and v[2] > 0}
+    return max(hbm, key=lambda k: hbm[k][0]), bd
 
 
 def peaks():
@@ -151,16 +207,12 @@ def run_ours(a):
     results = {}
     fields = {}
     for prec in ("fp64", "mixed"):
+        dom, breakdown = probe_dominant(FF, cfg, mat, opts, stream, prec)
         r = FF.RVE(n, I.VOXEL_MM, cfg["grain_ids"], cfg["euler"], mat, opts, prec=prec,
                    stream=stream)
-        for k in range(a.warmup - 1):
+        for k in range(a.warmup):
             r.run_increment(*prog[k])
-        # last warm-up step profiled per kernel family: the dominant kernel of ours
-        r.profile(FF.KERNEL_FAMILIES)
-        r.run_increment(*prog[a.warmup - 1])
-        breakdown = r.profile_read(reset=True)
-        ours = {k: v for k, v in breakdown.items() if not k.startswith("cufft")}
-        dom = max(ours, key=lambda k: ours[k][0])
+        # only the dominant family is timed (CUDA events in the same stream)
         r.profile([dom])
         barrier()
         clk = Clocks(local)
@@ -243,10 +295,15 @@ def run_ours(a):
         avg_s = mx["dom_ms"] / mx["dom_count"] / 1e3
         bytes_per_launch = mx["dom_bytes"] / mx["dom_count"]
         achieved = bytes_per_launch / avg_s / 1e9
+        traffic = ncu_traffic(dom)
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": None, "kernel": dom,
-                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": int(bytes_per_launch),
-                "avg_launch_us": round(avg_s * 1e6, 2), "launches": mx["dom_count"]}
+                "frac": round(achieved / hbm, 4),
+                "traffic": int(traffic) if traffic is not None else None,
+                "kernel": dom, "peak_kind": f"{peak_kind} (copy bandwidth, burst)",
+                "algorithmic_bytes_per_launch": int(bytes_per_launch),
+                "avg_launch_us": round(avg_s * 1e6, 2), "launches": mx["dom_count"],
+                "timing": "CUDA events around the kernel inside the timed region; launches "
+                          "replayed from GMRES step graphs are timed on every 8th replay"}
     line = {
         "metric": METRIC,
         "value": round(value, 1),
@@ -278,15 +335,129 @@ def run_ours(a):
                            "staggered": sum(s["stag_it"] for s in results[p]["stats"]),
                            "phase_field": sum(s["pf_it_total"] for s in results[p]["stats"])}
                        for p in results},
-        "kernel_ms_warmup_step": {p: {k: round(v[0], 3) for k, v in results[p]["breakdown"].items()}
-                                  for p in results},
-        "kernel_gbs_warmup_step": {p: {k: round(v[2] / v[0] / 1e6, 1)
-                                       for k, v in results[p]["breakdown"].items() if v[2] > 0}
-                                   for p in results},
+        "kernel_ms_probe_increments_9_14": {
+            p: {k: round(v[0], 3) for k, v in results[p]["breakdown"].items() if v[1]}
+            for p in results},
+        "kernel_gbs_probe_increments_9_14": {
+            p: {k: round(v[2] / v[0] / 1e6, 1)
+                for k, v in results[p]["breakdown"].items() if v[2] > 0 and v[0] > 0}
+            for p in results},
     }
     if ws == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, mat, opts, a)
     return line
+
+
+def run_batch(a):
+    """The batched workload: 32 polycrystals with grids from {32,48,64,96}^3
+    and 20-150 grains, advanced together (batch_run_increment, one stream
+    per RVE), mixed precision.  A step is one load increment of every RVE."""
+    import torch
+
+    from paper_2304_01125_gb300 import build as B
+    from paper_2304_01125_gb300 import fatiguefft as FF
+
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    c = I.CONFIGS["batch32"]
+    cfgs = I.batch_configs(seed=c["seed"], count=c["count"], sizes=c["sizes"],
+                           grains=c["grains"])
+    prog = I.uniaxial_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"])
+    assert a.warmup + a.steps <= len(prog)
+    mat = I.material("baseline")
+    opts = I.solver_options(a.tol)
+    nvox = [int(np.prod(x["n"])) for x in cfgs]
+    Ntot = sum(nvox)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def make():
+        rv = [FF.RVE(x["n"], I.VOXEL_MM, x["grain_ids"], x["euler"], mat, opts, prec="mixed",
+                     stream=torch.cuda.Stream(device=dev)) for x in cfgs]
+        return rv, FF.Batch(rv)
+
+    def step(b, k):
+        return b.run_increment([prog[k][0]] * len(cfgs), [prog[k][1]] * len(cfgs))
+
+    rves, b = make()
+    for k in range(a.warmup):
+        step(b, k)
+    for r in rves:
+        r.profile(["tangent_apply"])
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    l0 = sum(r.kernel_launches for r in rves)
+    ms, its = [], 0
+    for k in range(a.warmup, a.warmup + a.steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, _, st = step(b, k)  # returns once every RVE's stream is idle
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        its += sum(x["lin_it_total"] for x in st)
+    clocks = clk.stop()
+    launches = sum(r.kernel_launches for r in rves) - l0
+    prof = [r.profile_read(reset=True).get("tangent_apply", (0.0, 0, 0.0)) for r in rves]
+    dms, dcnt, dbytes = (sum(p[i] for p in prof) for i in range(3))
+    b.close()
+    for r in rves:
+        r.close()
+    total_s = sum(ms) / 1e3
+    value = Ntot * a.steps / total_s
+    hbm, peak_kind = peaks()
+    roof = None
+    if dcnt and dms > 0:
+        avg_s = dms / dcnt / 1e3
+        bpl = dbytes / dcnt
+        roof = {"bound": "hbm", "achieved": round(bpl / avg_s / 1e9, 1), "peak": hbm,
+                "unit": "GB/s", "frac": round(bpl / avg_s / 1e9 / hbm, 4), "traffic": None,
+                "kernel": "tangent_apply (mean over the batch's grid sizes)",
+                "peak_kind": f"{peak_kind} (copy bandwidth, burst)",
+                "algorithmic_bytes_per_launch": int(bpl), "avg_launch_us": round(avg_s * 1e6, 2),
+                "launches": int(dcnt)}
+    # end to end: fresh handles, inputs from pinned host memory, every RVE's
+    # damage field read back each step
+    rves, b = make()
+    for k in range(a.warmup):
+        step(b, k)
+    host_out = [torch.empty(nv, dtype=torch.float64).pin_memory() for nv in nvox]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(a.warmup, a.warmup + a.steps):
+        step(b, k)
+        for r, h in zip(rves, host_out):
+            FF.load().fields_out(r._h, FF.FIELDS["phi"][0], h.data_ptr(), h.nbytes, 0)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    b.close()
+    for r in rves:
+        r.close()
+    sizes = {}
+    for x in cfgs:
+        sizes[x["n"][0]] = sizes.get(x["n"][0], 0) + 1
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "voxel-increments/s",
+        "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": round(sum(ms) / a.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded periodic Voronoi, uniform SO(3) orientations)",
+        "config": {"workload": f"batch32: {len(cfgs)} RVEs, grids "
+                               + ", ".join(f"{k}^3 x{v}" for k, v in sorted(sizes.items()))
+                               + f" ({Ntot} voxels), 20-150 grains, R=-1 uniaxial strain 0.6%, "
+                               f"30 increments/cycle, increments {a.warmup + 1}-"
+                               f"{a.warmup + a.steps}",
+                   "tolerances": a.tol, "l2": L2_NOTE, "parallelism": "one stream per RVE"},
+        "e2e": {"value": round(Ntot * a.steps / e2e_s, 1), "unit": "voxel-increments/s",
+                "h2d_bytes_per_step": 80 * len(cfgs), "d2h_bytes_per_step": 8 * Ntot},
+        "gpu_launches": int(launches), "roofline": roof, "clocks": clocks,
+        "iterations": {"gmres": its},
+    }
+    return line if rank == 0 else None
 
 
 def cpu_baseline(cfg, mat, opts, a, increments=1):
@@ -331,21 +502,28 @@ def run_reference(a):
     for k in range(a.warmup):
         r.run_increment(*prog[k])
     t0 = time.perf_counter()
+    done = 0
     for k in range(a.warmup, a.warmup + a.steps):
         r.run_increment(*prog[k])
+        done += 1
+        if time.perf_counter() - t0 > a.ref_budget_s:
+            break
     dt = time.perf_counter() - t0
-    value = N * a.steps / dt
+    value = N * done / dt
     return {
         "impl": "reference", "metric": METRIC, "value": round(value, 1),
         "unit": "voxel-increments/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
-        "ms_per_step": round(dt / a.steps * 1e3, 1), "higher_is_better": True,
+        "ms_per_step": round(dt / done * 1e3, 1), "higher_is_better": True,
+        "steps_timed": done,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded periodic Voronoi, uniform SO(3) orientations)",
         "config": {"workload": f"{a.config}: 64^3 voxels, 50 grains, increments "
                                f"{a.warmup + 1}-{a.warmup + a.steps}", "tolerances": a.tol},
         "cpu_baseline": {"value": round(value, 1), "unit": "voxel-increments/s",
                          "cores": threads, "kind": "oracle",
-                         "sample": f"{a.steps} full increments of the workload"},
+                         "sample": f"{done} full increments of the workload (increments "
+                                   f"{a.warmup + 1}-{a.warmup + done}; the run stops timing "
+                                   f"after {a.ref_budget_s:.0f} s), {dt:.1f} s"},
         "e2e": {"value": round(value, 1), "unit": "voxel-increments/s",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -353,7 +531,12 @@ def run_reference(a):
 
 def main():
     a = args_()
-    line = run_reference(a) if a.impl == "reference" else run_ours(a)
+    if a.impl == "reference":
+        line = run_reference(a)
+    elif a.config == "batch32":
+        line = run_batch(a)
+    else:
+        line = run_ours(a)
     if line is not None:
         print(json.dumps(line), flush=True)
 

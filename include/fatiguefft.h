@@ -40,6 +40,7 @@ extern "C" {
 #endif
 
 typedef struct fft_rve_s* fft_rve_t;
+typedef struct fft_batch_s* fft_batch_t;
 
 typedef enum {
     FFT_OK = 0,
@@ -174,6 +175,10 @@ fft_status solve_phase_field(fft_rve_t r, int* iters);
  * tangent, 8 residual, 9 F update, 10 phase field, 11 GND, 12 cuFFT
  * 9-field transforms, 13 cuFFT scalar transforms, 14 reductions, 15 other);
  * each selected launch is bracketed by CUDA events on the handle's stream.
+ * GMRES steps replayed from CUDA graphs (handles with a stream) are timed
+ * on every S-th replay only (S from the environment variable
+ * FATIGUEFFT_PROF_SAMPLE at init_rve, default 8), the others replaying a
+ * graph without event nodes; counts report the timed launches.
  * 0 switches timing off.  rve_profile_read returns the accumulated device
  * milliseconds, launch counts and algorithmic bytes (the minimum HBM traffic
  * of the timed launches; bytes may be NULL) per family (16 entries each,
@@ -209,6 +214,24 @@ fft_status degraded_average_noalloc(const double* X, int ncomp, const double* ph
 size_t rve_device_bytes(fft_rve_t r);
 void rve_destroy(fft_rve_t r);
 const char* fft_last_error(fft_rve_t r);
+
+/* Batched RVEs (many independent problems of uneven size, one GPU; the
+ * paper solves one RVE at a time).  batch_create groups n existing handles,
+ * which must be distinct and each created with its own non-default
+ * cuda_stream (FFT_ERR_ARG otherwise); the caller keeps ownership of the
+ * handles and must not use them from other threads while the batch runs.
+ * n_threads host threads (<= 0: the hardware concurrency; at most n) drive
+ * the handles' increments concurrently, largest grid first.
+ * batch_run_increment = run_increment on every handle: Fbar 9n doubles
+ * (row-major per handle), dt n doubles, stats n entries (may be NULL),
+ * status n ints (may be NULL) receive each handle's own result; returns
+ * FFT_OK or the first failing handle's status (the others still ran).
+ * A failed handle behaves as after its own failed run_increment. */
+fft_status batch_create(fft_batch_t* out, fft_rve_t const* rves, int n, int n_threads);
+fft_status batch_run_increment(fft_batch_t b, const double* Fbar, const double* dt,
+                               fft_stats* stats, int* status);
+int batch_size(fft_batch_t b);
+void batch_destroy(fft_batch_t b);
 /* Kernel launches issued by this handle since creation (for accounting). */
 long long rve_kernel_launches(fft_rve_t r);
 

@@ -40,6 +40,7 @@ struct fft_rve_s {
     fft_options opt{};
     CPParams cpp{};
     cudaStream_t st = 0;
+    int dev = 0;  // the device current at init_rve
     cufftHandle r2c9 = 0, c2r9 = 0, r2c1 = 0, c2r1 = 0;
     bool plans = false;
     // device state (bulk type unless noted)
@@ -69,6 +70,12 @@ struct fft_rve_s {
     cudaGraphExec_t step_exec[kMaxKrylov] = {};
     long long step_launches[kMaxKrylov] = {};
     bool graphs = true;
+    // with the profiler on, a second graph per column carries the timing
+    // event nodes and replaces the plain one on every prof_sample-th replay
+    // (FATIGUEFFT_PROF_SAMPLE, default 8), so timing perturbs few replays
+    cudaGraphExec_t step_exec_prof[kMaxKrylov] = {};
+    int prof_sample = 8;
+    long long prof_tick = 0;
     int* dfail = nullptr;
     double* stage = nullptr;  // device staging for host fields_out / fields_in
     size_t stage_bytes = 0;
@@ -213,6 +220,8 @@ static void drop_graphs(fft_rve_s* r) {
     for (int j = 0; j < kMaxKrylov; ++j) {
         if (r->step_exec[j]) cudaGraphExecDestroy(r->step_exec[j]);
         r->step_exec[j] = nullptr;
+        if (r->step_exec_prof[j]) cudaGraphExecDestroy(r->step_exec_prof[j]);
+        r->step_exec_prof[j] = nullptr;
         for (auto& p : r->step_prof[j]) {
             cudaEventDestroy(p.a);
             cudaEventDestroy(p.b);
@@ -480,24 +489,28 @@ struct Impl {
             r->launches += 1;
         }
         if (r->graphs && r->st) {
-            if (!r->step_exec[j]) {
+            const bool timed = r->prof_mask && (r->prof_tick++ % r->prof_sample) == 0;
+            cudaGraphExec_t& ex = timed ? r->step_exec_prof[j] : r->step_exec[j];
+            if (!ex) {
                 const long long l0 = r->launches;
+                const unsigned mask = r->prof_mask;
+                if (!timed) r->prof_mask = 0;  // the plain graph has no event nodes
                 CK(r, cudaStreamBeginCapture(r->st, cudaStreamCaptureModeThreadLocal));
                 r->capturing = true;
                 r->cap_prof.clear();
                 const fft_status sb = step_body(r, j);
                 r->capturing = false;
+                r->prof_mask = mask;
                 cudaGraph_t gr = nullptr;
                 const cudaError_t ce = cudaStreamEndCapture(r->st, &gr);
-                r->step_prof[j].swap(r->cap_prof);
+                if (timed) r->step_prof[j].swap(r->cap_prof);
                 for (auto& p : r->cap_prof) {
                     cudaEventDestroy(p.a);
                     cudaEventDestroy(p.b);
                 }
                 r->cap_prof.clear();
                 cudaError_t ie = ce;
-                if (sb == FFT_OK && ce == cudaSuccess)
-                    ie = cudaGraphInstantiate(&r->step_exec[j], gr, 0);
+                if (sb == FFT_OK && ce == cudaSuccess) ie = cudaGraphInstantiate(&ex, gr, 0);
                 if (gr) cudaGraphDestroy(gr);
                 const long long nl = r->launches - l0;  // this column's own kernels
                 r->launches = l0;
@@ -505,7 +518,7 @@ struct Impl {
                     // capture unsupported here: run this handle without graphs
                     // (a genuine error then surfaces from the direct launch)
                     cudaGetLastError();
-                    r->step_exec[j] = nullptr;
+                    ex = nullptr;
                     drop_graphs(r);
                     r->graphs = false;
                     if (r->verbose)
@@ -517,11 +530,12 @@ struct Impl {
                 }
                 r->step_launches[j] = nl;
             }
-            CK(r, cudaGraphLaunch(r->step_exec[j], r->st));
+            CK(r, cudaGraphLaunch(ex, r->st));
             r->launches += r->step_launches[j];
             // the graph's timing events; folded in before it is launched again
             // (every GMRES cycle ends with a stream synchronisation)
-            for (auto& p : r->step_prof[j]) r->prof_pending.push_back(p);
+            if (timed)
+                for (auto& p : r->step_prof[j]) r->prof_pending.push_back(p);
         } else {
             TRY(step_body(r, j));
         }
@@ -1068,12 +1082,15 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
     {
         const char* gv = std::getenv("FATIGUEFFT_GRAPHS");
         r->graphs = !(gv && gv[0] == '0');
+        const char* ps = std::getenv("FATIGUEFFT_PROF_SAMPLE");
+        if (ps && std::atoi(ps) >= 1) r->prof_sample = std::atoi(ps);
     }
     r->mat = *mat;
     r->opt = *opt;
     r->h = grid->h;
     r->ngr = n_grains;
     r->st = (cudaStream_t)opt->cuda_stream;
+    cudaGetDevice(&r->dev);
     SGrid& g = r->g;
     g.n0 = grid->n[0];
     g.n1 = grid->n[1];
@@ -1346,6 +1363,15 @@ fft_status rve_profile_read(fft_rve_t r, double* ms, long long* counts, double* 
 }
 
 long long rve_kernel_launches(fft_rve_t r) { return r ? r->launches : 0; }
+
+}  // extern "C"
+
+// Library-internal accessors for the batch driver (batch.cu).
+int fatfft_rve_device(fft_rve_t r) { return r ? r->dev : -1; }
+void* fatfft_rve_stream(fft_rve_t r) { return r ? (void*)r->st : nullptr; }
+size_t fatfft_rve_voxels(fft_rve_t r) { return r ? r->g.N : 0; }
+
+extern "C" {
 
 void rve_destroy(fft_rve_t r) {
     if (!r) return;

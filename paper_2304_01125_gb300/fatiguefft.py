@@ -28,7 +28,8 @@ SYMBOLS = ["init_rve", "apply_increment", "solve_equilibrium", "update_damage",
            "commit_increment", "run_increment", "fields_out", "fields_in", "eval_constitutive",
            "eval_gnd", "solve_phase_field", "rve_device_bytes", "rve_destroy", "fft_last_error",
            "rve_kernel_launches", "rve_profile", "rve_profile_read",
-           "degraded_average_noalloc"]
+           "degraded_average_noalloc", "batch_create", "batch_run_increment", "batch_size",
+           "batch_destroy"]
 KERNEL_FAMILIES = ["constitutive", "tangent_apply", "precond_grad", "contract", "gmres_dot",
                    "gs_update", "gmres_xupdate", "kbar", "residual", "f_update", "phase_field",
                    "gnd", "cufft_9field", "cufft_scalar", "reductions", "other"]
@@ -102,6 +103,14 @@ def load(path=LIB_PATH):
     L.degraded_average_noalloc.restype = C.c_int
     L.rve_destroy.argtypes = [vp]
     L.rve_destroy.restype = None
+    L.batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int, C.c_int]
+    L.batch_create.restype = C.c_int
+    L.batch_run_increment.argtypes = [vp, dp, dp, C.POINTER(Stats), C.POINTER(C.c_int)]
+    L.batch_run_increment.restype = C.c_int
+    L.batch_size.argtypes = [vp]
+    L.batch_size.restype = C.c_int
+    L.batch_destroy.argtypes = [vp]
+    L.batch_destroy.restype = None
     L.fft_last_error.argtypes = [vp]
     L.fft_last_error.restype = C.c_char_p
     for t in ("init_rve", "apply_increment", "solve_equilibrium", "update_damage",
@@ -278,3 +287,47 @@ class RVE:
     @property
     def kernel_launches(self):
         return load().rve_kernel_launches(self._h)
+
+
+class Batch:
+    """Many independent RVE handles advanced together (batch_run_increment):
+    each handle needs its own stream; a native thread pool of ``threads``
+    host threads (None: the hardware concurrency) drives them concurrently.
+    The handles stay owned by the caller."""
+
+    def __init__(self, rves, threads=None):
+        self.rves = list(rves)
+        arr = (C.c_void_p * len(self.rves))(*[r._h for r in self.rves])
+        h = C.c_void_p()
+        s = load().batch_create(C.byref(h), arr, len(self.rves), int(threads or 0))
+        if s != FFT_OK:
+            raise FFTError("batch_create", s, "distinct handles, each with its own stream")
+        self._h = h
+
+    def run_increment(self, Fbars, dts, check=True):
+        """Fbars: (n, 9) absolute macroscopic F per handle; dts: (n,).
+        Returns (status, per-handle statuses, per-handle stats dicts)."""
+        n = len(self.rves)
+        F = np.ascontiguousarray(np.asarray(Fbars, dtype=np.float64).reshape(n, 9))
+        dt = np.ascontiguousarray(np.asarray(dts, dtype=np.float64).reshape(n))
+        stats = (Stats * n)()
+        st = (C.c_int * n)()
+        s = load().batch_run_increment(self._h, F.ctypes.data_as(C.POINTER(C.c_double)),
+                                       dt.ctypes.data_as(C.POINTER(C.c_double)), stats, st)
+        per = list(st)
+        if check and s != FFT_OK:
+            bad = [i for i, x in enumerate(per) if x != FFT_OK]
+            msg = load().fft_last_error(self.rves[bad[0]]._h).decode() if bad else ""
+            raise FFTError("batch_run_increment", s, f"handles {bad}: {msg}")
+        return s, per, [x.as_dict() for x in stats]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

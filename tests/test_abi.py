@@ -60,4 +60,10 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu():
         assert L.init_rve(C.byref(h), C.byref(g), gid.ctypes.data, 1, eul.ctypes.data,
                           C.byref(m), C.byref(o), None, None) == FF.FFT_ERR_ARG
     assert L.apply_increment(None, None, 1.0) == FF.FFT_ERR_ARG
+    b = C.c_void_p()
+    assert L.batch_create(C.byref(b), None, 2, 1) == FF.FFT_ERR_ARG
+    arr = (C.c_void_p * 1)(None)
+    assert L.batch_create(C.byref(b), arr, 1, 1) == FF.FFT_ERR_ARG
+    assert L.batch_create(C.byref(b), arr, 0, 1) == FF.FFT_ERR_ARG
+    assert L.batch_size(None) == 0
     assert L.rve_device_bytes(None) == 0
