@@ -354,9 +354,17 @@ __device__ __forceinline__ void green_apply(const R* Ks, const R* xd,
                 for (int l = 0; l < 3; ++l) s += xd[j] * Ks[9 * (3 * i + j) + 3 * k + l] * xd[l];
             A[3 * i + k] = s;
         }
+    // Invert A / s with s = |trace A| and scale back: A itself reaches
+    // |xi|^2 C ~ 1e13 MPa/mm^2 near the Nyquist frequencies of a
+    // micrometre voxel, so det A (~A^3) would overflow FP32 there and zero
+    // M on those modes, which GMRES could then never reduce.
+    const R tr = fabs(A[0]) + fabs(A[4]) + fabs(A[8]);
+    const R is = tr > R(0) ? R(1) / tr : R(0);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) A[q] *= is;
     const R det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
                   A[2] * (A[3] * A[7] - A[4] * A[6]);
-    const R id = R(1) / det;
+    const R id = is / det;  // (A / s)^-1 / s = A^-1
     R Mi[9];
     Mi[0] = (A[4] * A[8] - A[5] * A[7]) * id;
     Mi[1] = (A[2] * A[7] - A[1] * A[8]) * id;
@@ -583,6 +591,8 @@ __device__ void dcgs_coefficients(int k, const double* d, const double* Hs, doub
         coef[2 * kMaxKrylov] = inu;
         coef[2 * kMaxKrylov + 1] = ddk * inu;
         slot[kSlotNu] = nu;
+        slot[kSlotAlpha] = alpha;
+        slot[kSlotA2] = aa;
     }
     if (k >= 1 && l <= k) {
         Hd[(size_t)(k - 1) * kHcol + l] = fin;

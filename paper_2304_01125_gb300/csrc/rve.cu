@@ -647,6 +647,8 @@ struct Impl {
                 r->launches += 2;
                 TRY(fetch(r, 1));
                 beta = std::sqrt(r->hred[0]);
+                if (r->verbose)
+                    std::fprintf(stderr, "  gmres restart: true |r|/|b| %.3e\n", beta / bn);
                 if (beta <= target) {
                     ok = true;
                     break;
@@ -687,8 +689,12 @@ struct Impl {
                 }
                 const double res = hess_lsq(Hm, m, kcols, beta, nullptr);
                 if (r->verbose)
-                    std::fprintf(stderr, "  gmres it %d |r|/|b| %.3e (|b| %.3e, h %.3e)\n", lin,
-                                 res / bn, bn, hn);
+                    std::fprintf(stderr,
+                                 "  gmres it %d |r|/|b| %.3e (|b| %.3e, h %.3e, nu %.3e, "
+                                 "|a|/|c| %.3e)\n",
+                                 lin, res / bn, bn, hn, slot[kSlotNu],
+                                 std::sqrt(std::max(slot[kSlotA2], 0.0) /
+                                           std::max(slot[kSlotAlpha], 1e-300)));
                 if (res <= target || hn == 0.0) {
                     ok = true;
                     break;

@@ -34,10 +34,12 @@ template <typename R> void tangent_apply(void* G, const void* K, const void* phi
 template <typename R> void contract(const void* T, const SGrid& g, void* w, cudaStream_t s);
 // Arnoldi step kernels (DCGS2, see kernels_spec.cu).  Hessenberg columns on
 // the device are kHcol doubles apart; the host slot holds the final column
-// k-1 at 0, the provisional column k at kSlotProv, nu_k at kSlotNu and
-// |c_{k+1}|^2 at kSlotNorm.
+// k-1 at 0, the provisional column k at kSlotProv, nu_k at kSlotNu,
+// |c_{k+1}|^2 at kSlotNorm, and alpha = |c_k|^2 and |a|^2 (kSlotAlpha,
+// kSlotA2) for the solver trace.
 constexpr int kHcol = kMaxKrylov + 1;
-constexpr int kSlotProv = 40, kSlotNorm = 80, kSlotNu = 81, kSlotLen = 82;
+constexpr int kSlotProv = 40, kSlotNorm = 80, kSlotNu = 81, kSlotAlpha = 82, kSlotA2 = 83,
+              kSlotLen = 84;
 template <typename R> void dcgs_dots(const void* c, const void* z, const void* V, size_t vstride, int k, const SGrid& g, const Red& red, double* Hd, double* Hp, double* slot, double* coef, cudaStream_t s);
 template <typename R> void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* coef, const double* Kbar, const SGrid& g, void* G, const Red& red, cudaStream_t s);
 template <typename R> void norm2(const void* v, const SGrid& g, const Red& red, cudaStream_t s);

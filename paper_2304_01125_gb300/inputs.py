@@ -125,23 +125,34 @@ def precrack_plane(n, x_range, y, value=1.0):
 def uniaxial_cycle_program(amplitude, inc_per_cycle, cycles, axis=1, eps_rate=1e-3):
     """Fully reversed (R = -1) triangle wave 0 -> +a -> 0 -> -a -> 0 per cycle,
     equal strain steps, dt = |d eps| / eps_rate.  Returns a list of
-    (Fbar_target (9,), dt) with Fbar = I + eps e_axis (x) e_axis."""
-    assert inc_per_cycle % 4 == 0
-    q = inc_per_cycle // 4
-    de = amplitude / q
+    (Fbar_target (9,), dt) with Fbar = I + eps e_axis (x) e_axis.  When
+    inc_per_cycle is not a multiple of 4 the wave is sampled at equal time
+    steps i / inc_per_cycle with dt = 4a / (eps_rate inc_per_cycle) (the
+    peaks then fall between increments)."""
+    assert inc_per_cycle >= 1 and cycles >= 1
     eps = [0.0]
-    for _ in range(cycles):
-        for k in range(1, q + 1):
-            eps.append(k * de)
-        for k in range(q - 1, -q - 1, -1):
-            eps.append(k * de)
-        for k in range(-q + 1, 1):
-            eps.append(k * de)
+    if inc_per_cycle % 4 == 0:
+        q = inc_per_cycle // 4
+        de = amplitude / q
+        for _ in range(cycles):
+            for k in range(1, q + 1):
+                eps.append(k * de)
+            for k in range(q - 1, -q - 1, -1):
+                eps.append(k * de)
+            for k in range(-q + 1, 1):
+                eps.append(k * de)
+    else:
+        for i in range(1, inc_per_cycle * cycles + 1):
+            t = (i % inc_per_cycle) / inc_per_cycle
+            tri = 4 * t if t <= 0.25 else (2 - 4 * t if t <= 0.75 else 4 * t - 4)
+            eps.append(amplitude * tri)
     prog = []
+    dt_equal = 4.0 * amplitude / (eps_rate * inc_per_cycle)
     for i in range(1, len(eps)):
         F = np.eye(3)
         F[axis, axis] += eps[i]
-        prog.append((F.reshape(9).copy(), abs(eps[i] - eps[i - 1]) / eps_rate))
+        dt = abs(eps[i] - eps[i - 1]) / eps_rate if inc_per_cycle % 4 == 0 else dt_equal
+        prog.append((F.reshape(9).copy(), dt))
     return prog
 
 
