@@ -125,13 +125,16 @@ def precrack_plane(n, x_range, y, value=1.0):
 def uniaxial_cycle_program(amplitude, inc_per_cycle, cycles, axis=1, eps_rate=1e-3):
     """Fully reversed (R = -1) triangle wave 0 -> +a -> 0 -> -a -> 0 per cycle,
     equal strain steps, dt = |d eps| / eps_rate.  Returns a list of
-    (Fbar_target (9,), dt) with Fbar = I + eps e_axis (x) e_axis.  When
-    inc_per_cycle is not a multiple of 4 the wave is sampled at equal time
-    steps i / inc_per_cycle with dt = 4a / (eps_rate inc_per_cycle) (the
-    peaks then fall between increments)."""
-    assert inc_per_cycle >= 1 and cycles >= 1
+    (Fbar_target (9,), dt) with Fbar = I + eps e_axis (x) e_axis.
+    inc_per_cycle = 4q samples the wave at t = i / inc_per_cycle; 4q + 2
+    samples it at t = (i - 1/2) / inc_per_cycle, which puts both peaks on
+    samples and keeps every step at 4a / inc_per_cycle (the first is half
+    that), so no increment holds the strain (Delta Fbar = 0 leaves the
+    relative Newton test with nothing but round-off to compare against).
+    Other counts are rejected."""
+    assert cycles >= 1
     eps = [0.0]
-    if inc_per_cycle % 4 == 0:
+    if inc_per_cycle >= 4 and inc_per_cycle % 4 == 0:
         q = inc_per_cycle // 4
         de = amplitude / q
         for _ in range(cycles):
@@ -141,18 +144,18 @@ def uniaxial_cycle_program(amplitude, inc_per_cycle, cycles, axis=1, eps_rate=1e
                 eps.append(k * de)
             for k in range(-q + 1, 1):
                 eps.append(k * de)
-    else:
+    elif inc_per_cycle >= 2 and inc_per_cycle % 4 == 2:
         for i in range(1, inc_per_cycle * cycles + 1):
-            t = (i % inc_per_cycle) / inc_per_cycle
+            t = ((i - 0.5) % inc_per_cycle) / inc_per_cycle
             tri = 4 * t if t <= 0.25 else (2 - 4 * t if t <= 0.75 else 4 * t - 4)
             eps.append(amplitude * tri)
+    else:
+        raise ValueError("increments per cycle must be 4q or 4q + 2")
     prog = []
-    dt_equal = 4.0 * amplitude / (eps_rate * inc_per_cycle)
     for i in range(1, len(eps)):
         F = np.eye(3)
         F[axis, axis] += eps[i]
-        dt = abs(eps[i] - eps[i - 1]) / eps_rate if inc_per_cycle % 4 == 0 else dt_equal
-        prog.append((F.reshape(9).copy(), dt))
+        prog.append((F.reshape(9).copy(), abs(eps[i] - eps[i - 1]) / eps_rate))
     return prog
 
 

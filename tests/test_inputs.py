@@ -21,15 +21,21 @@ def test_cycle_program_multiple_of_four_hits_the_peaks():
     assert np.allclose(dts, (a / 10) / rate)
 
 
-def test_cycle_program_equal_time_sampling():
+def test_cycle_program_4q_plus_2_hits_the_peaks_without_holds():
     a, rate = 0.006, 1e-3
     prog = I.uniaxial_cycle_program(a, 30, 2, eps_rate=rate)
     e = _eps(prog)
     assert len(prog) == 60
-    assert np.all(np.abs(e) <= a + 1e-15)
-    assert np.allclose(e[29::30], 0.0, atol=1e-15)  # each cycle ends at zero strain
-    dts = np.array([dt for _, dt in prog])
-    assert np.all(dts > 0) and np.allclose(dts, 4 * a / (rate * 30))
-    # the strain rate never exceeds the nominal one
+    assert np.isclose(e.max(), a) and np.isclose(e.min(), -a)
+    assert np.allclose(e[7::30], a) and np.allclose(e[22::30], -a)
     de = np.abs(np.diff(np.concatenate([[0.0], e])))
-    assert np.all(de <= rate * dts + 1e-15)
+    step = 4 * a / 30
+    assert np.isclose(de[0], step / 2) and np.allclose(de[1:], step)  # no zero increments
+    dts = np.array([dt for _, dt in prog])
+    assert np.allclose(dts, de / rate)
+
+
+def test_cycle_program_rejects_odd_counts():
+    import pytest
+    with pytest.raises(ValueError):
+        I.uniaxial_cycle_program(0.006, 31, 1)
