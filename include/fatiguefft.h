@@ -76,14 +76,20 @@ typedef struct {
  * ratios, tol_newton on ||grad du||inf / ||F - F_t||inf, tol_lin relative
  * GMRES residual, tol_pf relative phase-field CG residual, tol_local the
  * local slip-law residual (MPa).  max_* are iteration caps; restart is the
- * GMRES restart length (<= 64).  prec selects FP64 or the mixed path (FP32
- * fields, transforms and constitutive update; FP64 reductions, dot products,
- * norms and compensated history sums). */
+ * GMRES restart length (clamped to [1, 31]).  prec selects FP64 or the mixed
+ * path (FP32 fields, transforms and constitutive update; FP64 reductions,
+ * dot products, norms and compensated history sums).  max_cutbacks (an
+ * extension; the paper's Algorithm 1 has none, 0 = off): when run_increment
+ * does not converge, the increment is restarted from the committed state as
+ * two halves (Fbar and dt halved, each committed), recursively up to this
+ * depth (0..10, else FFT_ERR_ARG at init_rve); smaller steps stiffen the rate-dependent consistent tangent of
+ * plastic voxels and so ease the Krylov solves. */
 typedef struct {
     double tol_stag, tol_newton, tol_lin, tol_pf, tol_local;
     int max_stag, max_newton, max_lin, max_pf, max_local, restart;
     fft_precision prec;
     void* cuda_stream; /* cudaStream_t */
+    int max_cutbacks;
 } fft_options;
 
 /* Per-increment statistics (accumulated since apply_increment). */
@@ -93,6 +99,7 @@ typedef struct {
     double res_F, res_phi; /* last Algorithm 1 ratios */
     double Pbar[9];        /* volume average of g(phi) P at the current iterate */
     long cracked;          /* voxels with phi >= 0.9 */
+    int cutbacks;          /* halvings taken by run_increment (max_cutbacks) */
 } fft_stats;
 
 /* Field identifiers for fields_out / fields_in (component count). */

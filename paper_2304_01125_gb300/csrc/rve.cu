@@ -919,7 +919,8 @@ struct Impl {
         return FFT_OK;
     }
 
-    static fft_status run_increment(fft_rve_s* r, const double* Fbar, double dt, fft_stats* st) {
+    // Algorithm 1 for one increment, committed when converged.
+    static fft_status run_once(fft_rve_s* r, const double* Fbar, double dt, fft_stats* st) {
         TRY(apply_increment(r, Fbar, dt));
         for (int i = 0; i < r->opt.max_stag; ++i) {
             TRY(solve_equilibrium(r, st));
@@ -927,6 +928,32 @@ struct Impl {
             if (r->converged) return commit(r);
         }
         FAIL(r, FFT_ERR_NOT_CONVERGED, "staggered loop reached max_stag = %d", r->opt.max_stag);
+    }
+
+    // The increment as two halves from the committed state (a failed
+    // attempt leaves it untouched: apply_increment restarts from F_t, phi_t
+    // and the committed history), each halved again on failure down to
+    // depth max_cutbacks.
+    static fft_status run_halves(fft_rve_s* r, const double* Fbar, double dt, fft_stats* st,
+                                 int depth) {
+        if (st) st->cutbacks += 1;
+        double Fmid[9];
+        for (int c = 0; c < 9; ++c) Fmid[c] = 0.5 * (r->Fbar_t[c] + Fbar[c]);
+        const double* tgt[2] = {Fmid, Fbar};
+        for (int h = 0; h < 2; ++h) {
+            fft_status s = run_once(r, tgt[h], 0.5 * dt, st);
+            if (s == FFT_ERR_NOT_CONVERGED && depth < r->opt.max_cutbacks)
+                s = run_halves(r, tgt[h], 0.5 * dt, st, depth + 1);
+            if (s != FFT_OK) return s;
+        }
+        return FFT_OK;
+    }
+
+    static fft_status run_increment(fft_rve_s* r, const double* Fbar, double dt, fft_stats* st) {
+        const fft_status s = run_once(r, Fbar, dt, st);
+        if (s != FFT_ERR_NOT_CONVERGED || r->opt.max_cutbacks <= 0) return s;
+        if (r->verbose) std::fprintf(stderr, "  increment not converged: cutting back\n");
+        return run_halves(r, Fbar, dt, st, 1);
     }
 
     static fft_status fields_out(fft_rve_s* r, int field, double* d) {
@@ -1081,6 +1108,7 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
     }
     if (!(grid->h > 0) || (opt->prec != FFT_PREC_FP64 && opt->prec != FFT_PREC_MIXED))
         return FFT_ERR_ARG;
+    if (opt->max_cutbacks < 0 || opt->max_cutbacks > 10) return FFT_ERR_ARG;
     fft_rve_s* r = new fft_rve_s();
     r->prec = opt->prec;
     r->esz = opt->prec == FFT_PREC_FP64 ? 8 : 4;

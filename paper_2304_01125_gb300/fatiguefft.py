@@ -50,14 +50,15 @@ class Options(C.Structure):
                 ("tol_pf", C.c_double), ("tol_local", C.c_double),
                 ("max_stag", C.c_int), ("max_newton", C.c_int), ("max_lin", C.c_int),
                 ("max_pf", C.c_int), ("max_local", C.c_int), ("restart", C.c_int),
-                ("prec", C.c_int), ("cuda_stream", C.c_void_p)]
+                ("prec", C.c_int), ("cuda_stream", C.c_void_p), ("max_cutbacks", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("stag_it", C.c_int), ("newton_it", C.c_int), ("lin_it_total", C.c_int),
                 ("pf_it_total", C.c_int), ("local_fail", C.c_int), ("converged", C.c_int),
                 ("skipped_equilibrium", C.c_int), ("res_F", C.c_double),
-                ("res_phi", C.c_double), ("Pbar", C.c_double * 9), ("cracked", C.c_long)]
+                ("res_phi", C.c_double), ("Pbar", C.c_double * 9), ("cracked", C.c_long),
+                ("cutbacks", C.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -149,6 +150,7 @@ def _options(opts, prec, stream):
         setattr(o, k, int(opts[k]))
     o.prec = FFT_PREC_FP64 if prec in ("fp64", FFT_PREC_FP64) else FFT_PREC_MIXED
     o.cuda_stream = stream or None
+    o.max_cutbacks = int(opts.get("max_cutbacks", 0))
     return o
 
 

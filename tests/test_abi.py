@@ -53,6 +53,11 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu():
                       C.byref(o), None, None) == FF.FFT_ERR_ARG
     assert L.init_rve(None, C.byref(g), gid.ctypes.data, 1, eul.ctypes.data, C.byref(m),
                       C.byref(o), None, None) == FF.FFT_ERR_ARG
+    o.max_cutbacks = 11  # beyond the documented depth
+    g.n[:] = (4, 2, 2)
+    assert L.init_rve(C.byref(h), C.byref(g), gid.ctypes.data, 1, eul.ctypes.data, C.byref(m),
+                      C.byref(o), None, None) == FF.FFT_ERR_ARG
+    o.max_cutbacks = 0
     # beyond 32-bit spectral indexing, and an extent above 4096: rejected
     # before the grain ids are read
     for n in ((4096, 4096, 64), (8192, 1, 1)):

@@ -82,3 +82,39 @@ def test_batch_rejects_shared_or_default_streams():
             FF.Batch(group)
     for r in (a, c, d):
         r.close()
+
+
+def test_cutback_recovers_a_batch_rve_at_peak_load():
+    """One of the batched-workload RVEs (96^3, 43 grains) at the first 0.6 %
+    peak: restarted GMRES on the full-step tangent stalls (the plastic
+    voxels' rate-dependent tangent is orders softer than the averaged one);
+    with max_cutbacks the increment is redone as halves and converges, and
+    the macroscopic state is the requested one."""
+    import torch
+    c = I.CONFIGS["batch32"]
+    cfgs = I.batch_configs(seed=c["seed"], count=c["count"], sizes=c["sizes"],
+                           grains=c["grains"])
+    prog = I.uniaxial_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"])
+    x = cfgs[26]
+    mat = I.material("baseline")
+    res = {}
+    for cut in (0, 4):
+        r = FF.RVE(x["n"], H, x["grain_ids"], x["euler"], mat,
+                   I.solver_options("paper", max_lin=300, max_cutbacks=cut), prec="mixed",
+                   stream=torch.cuda.Stream())
+        for k in range(7):
+            s, st = r.run_increment(*prog[k])
+            assert st["cutbacks"] == 0
+        Ft_before = r.field("Ft")
+        Fb, dt = prog[7]
+        s, st = r.run_increment(Fb, dt, check=False)
+        res[cut] = (s, st["cutbacks"])
+        if cut == 0:
+            assert s == FF.FFT_ERR_NOT_CONVERGED
+            assert np.array_equal(r.field("Ft"), Ft_before)  # nothing committed
+        else:
+            assert s == FF.FFT_OK and st["cutbacks"] >= 1
+            F = r.field("F")
+            assert np.abs(F.mean(axis=1) - Fb).max() < 1e-7
+            assert np.array_equal(r.field("Ft"), F)
+        r.close()
