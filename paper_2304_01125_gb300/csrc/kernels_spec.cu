@@ -16,6 +16,7 @@
 // Every reduction kernel runs kRedBlocks blocks; each block writes one FP64
 // partial per value and the last block to finish combines them in a fixed
 // order (deterministic results, no separate finalisation launch).
+#include "bulk.cuh"
 #include "common.cuh"
 #include "spec.h"
 
@@ -593,6 +594,7 @@ __device__ void dcgs_coefficients(int k, const double* d, const double* Hs, doub
         slot[kSlotNu] = nu;
         slot[kSlotAlpha] = alpha;
         slot[kSlotA2] = aa;
+        slot[kSlotErr] = 0.0;  // the pipelined kernels overwrite it with their error word
     }
     if (k >= 1 && l <= k) {
         Hd[(size_t)(k - 1) * kHcol + l] = fin;
@@ -615,7 +617,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_dcgs_dots(const typename Tr<R>:
                                                            const typename Tr<R>::Cx* V,
                                                            size_t vstride, int k, SGrid g,
                                                            Red red, double* Hd, double* Hp,
-                                                           double* slot, double* coef) {
+                                                           double* slot, double* coef,
+                                                           const int* err) {
     typedef typename Tr<R>::Cx Cx;
     constexpr int U = NQ <= 4 ? 4 : (NQ <= 8 ? 2 : 1);
     constexpr int G = NQ < 8 ? NQ : 8;
@@ -681,21 +684,201 @@ __global__ void __launch_bounds__(kThreads, 2) k_dcgs_dots(const typename Tr<R>:
         }
         __syncthreads();
         if (threadIdx.x < 32) dcgs_coefficients(k, red.out, s_H, Hd, Hp, slot, coef);
+        // the pipelined update pass's error word, reported in the slot
+        if (threadIdx.x == 0 && err) slot[kSlotErr] = (double)*(volatile const int*)err;
     }
 }
+// ------------------------------------------- pipelined Arnoldi update pass
+// The same update as k_dcgs_update, with c_k, z and the basis streamed
+// through a ring of kBulkS shared-memory stages filled by bulk asynchronous
+// copies: one thread issues the copies kBulkS stages ahead and every thread
+// consumes a stage once its mbarrier phase completes, so the bytes in flight
+// per SM are set by the ring, not by registers.  Each CTA owns a contiguous
+// run of tpc tiles of kUpdT frequencies (all three components).  Used when
+// every copy is 16-byte aligned (Nh even, or complex FP64).  A wait that
+// runs out sets *err (reported to the host) and the CTA stops consuming,
+// takes part in the reduction with what it has, and waits (again bounded)
+// for its own copies still in flight before it exits.  (The dot pass keeps
+// its register-streaming kernel: a pipelined version's per-stage
+// synchronisation outweighed the deeper pipeline.)
+constexpr int kBulkS = 12;  // ring stages
+constexpr int kUpdT = 128;  // frequencies per tile
+
+// bounded wait for the last copy issued into every stage (issued copies in all)
+__device__ __forceinline__ void bulk_drain(uint64_t* full, int issued) {
+    for (int s = 0; s < kBulkS && s < issued; ++s) {
+        const int last = s + ((issued - 1 - s) / kBulkS) * kBulkS;
+        mbar_wait(&full[s], (unsigned)(last / kBulkS) & 1u);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kUpdT) k_dcgs_update_bulk(
+    typename Tr<R>::Cx* V, size_t vstride, int k, const typename Tr<R>::Cx* z,
+    const double* coef, const double* Kbar, SGrid g, typename Tr<R>::Cx* G, int tpc, Red red,
+    int* err) {
+    typedef typename Tr<R>::Cx Cx;
+    extern __shared__ __align__(128) unsigned char dyn[];
+    Cx* buf = reinterpret_cast<Cx*>(dyn);  // [kBulkS][3][kUpdT]
+    __shared__ __align__(8) uint64_t full[kBulkS];
+    __shared__ R s_a[kMaxKrylov], s_e[kMaxKrylov];
+    __shared__ R Ks[81];
+    const unsigned Nh = (unsigned)g.Nh;
+    const int ntiles = (int)((Nh + kUpdT - 1) / kUpdT);
+    const int t0 = blockIdx.x * tpc, t1 = min(t0 + tpc, ntiles);
+    const int nv = k + 2;  // c_k, z, q_0 .. q_{k-1}
+    const int total = t1 > t0 ? (t1 - t0) * nv : 0;
+    const int tid = threadIdx.x;
+    Cx* ck = V + (size_t)k * vstride;
+    Cx* cn = V + (size_t)(k + 1) * vstride;
+    int issued = 0;
+    auto issue = [&](int L) {
+        const int tile = t0 + L / nv, v = L % nv;
+        const unsigned e0 = (unsigned)tile * kUpdT;
+        const unsigned cnt = min((unsigned)kUpdT, Nh - e0);
+        const Cx* src = v == 0 ? ck : v == 1 ? z : V + (size_t)(v - 2) * vstride;
+        uint64_t* b = &full[L % kBulkS];
+        Cx* dst = buf + (size_t)(L % kBulkS) * 3 * kUpdT;
+        mbar_arrive_tx(b, 3 * cnt * (unsigned)sizeof(Cx));
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc)
+            bulk_load(dst + cc * kUpdT, src + (size_t)cc * Nh + e0, cnt * (unsigned)sizeof(Cx), b);
+        issued = L + 1;
+    };
+    for (int q = tid; q < 81; q += blockDim.x) Ks[q] = (R)Kbar[q];
+    for (int q = tid; q < k; q += blockDim.x) {
+        s_a[q] = (R)coef[q];
+        s_e[q] = (R)coef[kMaxKrylov + q];
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kBulkS; ++s) mbar_init(&full[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int L = 0; L < min(kBulkS, total); ++L) issue(L);
+    const R inu = (R)coef[2 * kMaxKrylov], cc = (R)coef[2 * kMaxKrylov + 1];
+    bool ok = true;
+    int L = 0;
+    R acc[1] = {R(0)};
+    for (int tile = t0; tile < t1; ++tile) {
+        const unsigned e = (unsigned)tile * kUpdT + tid;
+        Cx sa[3], se[3], cv[3], zv[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) sa[q].x = sa[q].y = se[q].x = se[q].y = 0;
+        for (int v = 0; v < nv; ++v) {
+            const int st = L % kBulkS;
+            if (ok && !mbar_wait(&full[st], (unsigned)(L / kBulkS) & 1u)) ok = false;
+            const Cx* b = buf + (size_t)st * 3 * kUpdT;
+            Cx x[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (ok && e < Nh) {
+                    x[q] = b[q * kUpdT + tid];
+                } else {
+                    x[q].x = x[q].y = 0;
+                }
+            }
+            if (v == 0) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) cv[q] = x[q];
+            } else if (v == 1) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) zv[q] = x[q];
+            } else {
+                const R ai = s_a[v - 2], ei = s_e[v - 2];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    sa[q].x += ai * x[q].x;
+                    sa[q].y += ai * x[q].y;
+                    se[q].x += ei * x[q].x;
+                    se[q].y += ei * x[q].y;
+                }
+            }
+            __syncthreads();
+            if (tid == 0 && ok && L + kBulkS < total) issue(L + kBulkS);
+            ++L;
+        }
+        if (ok && e < Nh) {
+            R xi[3], xd[3], wt;
+            hs_freq<R>(g, e, xi, xd, wt);
+            Cx nx[3];
+            R nn = 0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                Cx qk;
+                qk.x = (cv[q].x - sa[q].x) * inu;
+                qk.y = (cv[q].y - sa[q].y) * inu;
+                ck[(size_t)q * Nh + e] = qk;
+                nx[q].x = zv[q].x * inu - se[q].x - cv[q].x * cc;
+                nx[q].y = zv[q].y * inu - se[q].y - cv[q].y * cc;
+                cn[(size_t)q * Nh + e] = nx[q];
+                nn += nx[q].x * nx[q].x + nx[q].y * nx[q].y;
+            }
+            acc[0] += wt * nn;
+            Cx zz[3];
+            green_apply<R>(Ks, xd, nx, zz);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) G[(size_t)(3 * i + j) * Nh + e] = cmul_i(zz[i], xd[j]);
+        }
+    }
+    if (!ok) atomicExch(err, 1);
+    if (tid == 0 && !ok) bulk_drain(full, issued);
+    block_partials<1, kUpdT>(acc, 1, 0u, red.part);
+    grid_finish<kUpdT, 1>(red, 1, 0u, 1.0);
+}
+
+// Dynamic shared memory and the resident-CTA budget of the pipelined
+// kernels (set once per handle, outside any stream capture).
+template <typename R>
+static size_t upd_bulk_smem() {
+    return (size_t)kBulkS * 3 * kUpdT * sizeof(typename Tr<R>::Cx);
+}
+template <typename R>
+int dcgs_bulk_setup(BulkCfg& bc) {
+    int nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int su = (int)upd_bulk_smem<R>();
+    int nu = 0;
+    if (cudaFuncSetAttribute(k_dcgs_update_bulk<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             su) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nu, k_dcgs_update_bulk<R>, kUpdT, su) !=
+            cudaSuccess)
+        nu = 0;
+    cudaGetLastError();
+    // the reduction buffers hold kRedSlots x kRedBlocks partials
+    bc.upd_blocks = min(nu * nsm, kRedSlots * kRedBlocks);
+    return bc.upd_blocks > 0;
+}
+
+template <typename R>
+static inline bool bulk_aligned(const SGrid& g) {
+    return sizeof(typename Tr<R>::Cx) % 16 == 0 || g.Nh % 2 == 0;
+}
+
+static inline void tile_split(int ntiles, int maxb, int& tpc, int& nb) {
+    tpc = (ntiles + maxb - 1) / maxb;
+    if (tpc < 1) tpc = 1;
+    nb = (ntiles + tpc - 1) / tpc;
+}
+
 template <typename R>
 void dcgs_dots(const void* c, const void* z, const void* V, size_t vstride, int k,
                const SGrid& g, const Red& red, double* Hd, double* Hp, double* slot,
-               double* coef, cudaStream_t s) {
+               double* coef, const BulkCfg* bc, cudaStream_t s) {
     typedef typename Tr<R>::Cx Cx;
     const size_t n3 = 3 * g.Nh;
+    const Cx *cc = (const Cx*)c, *zz = (const Cx*)z, *VV = (const Cx*)V;
     size_t nb = (n3 + kThreads - 1) / kThreads;
     if (nb > 2 * 152) nb = 2 * 152;  // one wave of two blocks per SM
     const dim3 gr((unsigned)nb);
-    const Cx *cc = (const Cx*)c, *zz = (const Cx*)z, *VV = (const Cx*)V;
+    const int* err = bc ? bc->err : nullptr;
 #define DOTS(NQ)                                                                               \
     k_dcgs_dots<R, NQ><<<gr, kThreads, 0, s>>>(cc, zz, VV, vstride, k, g, red, Hd, Hp, slot, \
-                                               coef)
+                                               coef, err)
     if (k <= 0)
         DOTS(0);
     else if (k <= 4)
@@ -784,8 +967,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_dcgs_update(typename Tr<R>::Cx*
 }
 template <typename R>
 void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* coef,
-                 const double* Kbar, const SGrid& g, void* G, const Red& red, cudaStream_t s) {
+                 const double* Kbar, const SGrid& g, void* G, const Red& red, const BulkCfg* bc,
+                 cudaStream_t s) {
     typedef typename Tr<R>::Cx Cx;
+    if (bc && bulk_aligned<R>(g)) {
+        int tpc, nb;
+        tile_split((int)((g.Nh + kUpdT - 1) / kUpdT), bc->upd_blocks, tpc, nb);
+        k_dcgs_update_bulk<R><<<nb, kUpdT, upd_bulk_smem<R>(), s>>>(
+            (Cx*)V, vstride, k, (const Cx*)z, coef, Kbar, g, (Cx*)G, tpc, red, bc->err);
+        return;
+    }
     k_dcgs_update<R><<<grid_for(g.Nh), kThreads, 0, s>>>((Cx*)V, vstride, k, (const Cx*)z, coef,
                                                          Kbar, g, (Cx*)G, red);
 }
@@ -1190,9 +1381,11 @@ void fp_in(const double* Fp, const int32_t* grain, const double* Qg, void* Hpi, 
     template void contract<R>(const void*, const SGrid&, void*, cudaStream_t);                  \
     template void dcgs_dots<R>(const void*, const void*, const void*, size_t, int,              \
                                const SGrid&, const Red&, double*, double*, double*, double*,   \
-                               cudaStream_t);                                                   \
+                               const BulkCfg*, cudaStream_t);                                   \
     template void dcgs_update<R>(void*, size_t, int, const void*, const double*,                \
-                                 const double*, const SGrid&, void*, const Red&, cudaStream_t); \
+                                 const double*, const SGrid&, void*, const Red&,                \
+                                 const BulkCfg*, cudaStream_t);                                 \
+    template int dcgs_bulk_setup<R>(BulkCfg&);                                                  \
     template void norm2<R>(const void*, const SGrid&, const Red&, cudaStream_t);                \
     template void xupdate<R>(void*, const void*, size_t, int, const double*, const double*,     \
                              const SGrid&, cudaStream_t);                                       \

@@ -77,6 +77,10 @@ struct fft_rve_s {
     int prof_sample = 8;
     long long prof_tick = 0;
     int* dfail = nullptr;
+    // pipelined Arnoldi kernels (bulk copies into a shared-memory ring):
+    // resident-CTA budgets and the device error word of their bounded waits
+    BulkCfg bulk{};
+    bool use_bulk = false;
     double* stage = nullptr;  // device staging for host fields_out / fields_in
     size_t stage_bytes = 0;
     std::vector<void*> allocs;
@@ -563,13 +567,14 @@ struct Impl {
         e = prof_begin(r, KF_MDOT);
         double* Hp = r->Hd + (size_t)kMaxKrylov * kHcol;
         double* coef = Hp + (size_t)kMaxKrylov * kHcol;
+        const BulkCfg* bc = r->use_bulk ? &r->bulk : nullptr;
         dcgs_dots<R>(V + (size_t)k * vs, r->w, V, vs, k, r->g, red_at(r, r->red), r->Hd, Hp,
-                     dslot, coef, r->st);
+                     dslot, coef, bc, r->st);
         prof_end(r, KF_MDOT, e, Nh * 2 * es * 3 * (k + 2));
         // q_k final, c_{k+1} and the next gradient spectrum
         e = prof_begin(r, KF_GSUPD);
         dcgs_update<R>(V, vs, k, r->w, coef, r->Kbar, r->g, r->cb9,
-                       red_at(r, dslot + kSlotNorm), r->st);
+                       red_at(r, dslot + kSlotNorm), bc, r->st);
         prof_end(r, KF_GSUPD, e, Nh * 2 * es * 3 * (k + 2 + 2 + 3));
         double* slot = r->hslot + (size_t)(k % 2) * kSlot;
         CK(r, cudaMemcpyAsync(slot, dslot, kSlotLen * sizeof(double), cudaMemcpyDeviceToHost,
@@ -670,6 +675,8 @@ struct Impl {
                 CK(r, cudaEventSynchronize(r->slot_ev[k % 2]));
                 prof_collect_if_done(r);
                 const double* slot = r->hslot + (size_t)(k % 2) * kSlot;
+                if (slot[kSlotErr] != 0.0)
+                    FAIL(r, FFT_ERR_CUDA, "a bulk-copy wait in the Arnoldi step timed out");
                 for (int i = 0; i < kSlotLen; ++i)
                     if (!std::isfinite(slot[i]))
                         FAIL(r, FFT_ERR_NONFINITE, "non-finite Krylov coefficient (step %d)",
@@ -719,6 +726,11 @@ struct Impl {
         }
         *its = lin;
         CK(r, cudaGetLastError());
+        if (r->use_bulk) {
+            int e = 0;
+            CK(r, cudaMemcpy(&e, r->bulk.err, sizeof(int), cudaMemcpyDeviceToHost));
+            if (e) FAIL(r, FFT_ERR_CUDA, "a bulk-copy wait in the Arnoldi step timed out");
+        }
         if (!ok) FAIL(r, FFT_ERR_NOT_CONVERGED, "GMRES reached max_lin = %d", r->opt.max_lin);
         return FFT_OK;
     }
@@ -1211,6 +1223,7 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
     AL(r->dzero, kMaxRestart * sizeof(double));
     AL(r->counter, sizeof(unsigned));
     AL(r->dfail, sizeof(int));
+    AL(r->bulk.err, sizeof(int));
     if (elastic_only) AL(r->elastic, N);
 #undef AL
     if (cudaMallocHost((void**)&r->hred, kRedSlots * sizeof(double)) != cudaSuccess ||
@@ -1233,6 +1246,14 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
         cudaMemcpyAsync(r->elastic, elastic_only, N, cudaMemcpyHostToDevice, r->st);
     cudaMemsetAsync(r->dzero, 0, kMaxRestart * sizeof(double), r->st);
     cudaMemsetAsync(r->counter, 0, sizeof(unsigned), r->st);
+    cudaMemsetAsync(r->bulk.err, 0, sizeof(int), r->st);
+    {
+        // FATIGUEFFT_BULK=0 keeps the register-streaming Arnoldi kernels
+        const char* bv = std::getenv("FATIGUEFFT_BULK");
+        const bool want = !(bv && bv[0] == '0');
+        r->use_bulk = want && (r->prec == FFT_PREC_FP64 ? dcgs_bulk_setup<double>(r->bulk)
+                                                        : dcgs_bulk_setup<float>(r->bulk));
+    }
     upload_slip_table(r->st);
     // cuFFT plans: dims slowest-first (n2, n1, n0); 9-field batches use the
     // contiguous component-major layout.

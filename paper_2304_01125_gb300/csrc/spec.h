@@ -35,13 +35,24 @@ template <typename R> void contract(const void* T, const SGrid& g, void* w, cuda
 // Arnoldi step kernels (DCGS2, see kernels_spec.cu).  Hessenberg columns on
 // the device are kHcol doubles apart; the host slot holds the final column
 // k-1 at 0, the provisional column k at kSlotProv, nu_k at kSlotNu,
-// |c_{k+1}|^2 at kSlotNorm, and alpha = |c_k|^2 and |a|^2 (kSlotAlpha,
-// kSlotA2) for the solver trace.
+// |c_{k+1}|^2 at kSlotNorm, alpha = |c_k|^2 and |a|^2 (kSlotAlpha,
+// kSlotA2) for the solver trace, and the pipelined kernels' error word at
+// kSlotErr.
 constexpr int kHcol = kMaxKrylov + 1;
 constexpr int kSlotProv = 40, kSlotNorm = 80, kSlotNu = 81, kSlotAlpha = 82, kSlotA2 = 83,
-              kSlotLen = 84;
-template <typename R> void dcgs_dots(const void* c, const void* z, const void* V, size_t vstride, int k, const SGrid& g, const Red& red, double* Hd, double* Hp, double* slot, double* coef, cudaStream_t s);
-template <typename R> void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* coef, const double* Kbar, const SGrid& g, void* G, const Red& red, cudaStream_t s);
+              kSlotErr = 84, kSlotLen = 85;
+// Resident-CTA budget of the pipelined (bulk-copy) update pass and the
+// device error word of its bounded waits; the launchers below take them
+// when given (NULL: the register-streaming kernels; the dot pass always
+// streams through registers and only reports the error word).
+// dcgs_bulk_setup returns 0 if the pipelined kernel cannot be used.
+struct BulkCfg {
+    int upd_blocks;
+    int* err;
+};
+template <typename R> int dcgs_bulk_setup(BulkCfg& bc);
+template <typename R> void dcgs_dots(const void* c, const void* z, const void* V, size_t vstride, int k, const SGrid& g, const Red& red, double* Hd, double* Hp, double* slot, double* coef, const BulkCfg* bc, cudaStream_t s);
+template <typename R> void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* coef, const double* Kbar, const SGrid& g, void* G, const Red& red, const BulkCfg* bc, cudaStream_t s);
 template <typename R> void norm2(const void* v, const SGrid& g, const Red& red, cudaStream_t s);
 template <typename R> void xupdate(void* x, const void* V, size_t vstride, int k, const double* y, const double* Kbar, const SGrid& g, cudaStream_t s);
 template <typename R> void axpby(void* out, const void* a, const void* b, double alpha, double beta, size_t n, cudaStream_t s);

@@ -291,6 +291,35 @@ def test_graph_replay_matches_direct_launches(prec, monkeypatch):
         assert np.array_equal(out[0][1][f], out[1][1][f]), f
 
 
+@pytest.mark.parametrize("prec", PREC)
+def test_pipelined_arnoldi_kernels_match_register_streaming(prec, monkeypatch):
+    """The Arnoldi step with the basis streamed through shared memory by bulk
+    copies (the default where Nh is even) against the register-streaming
+    kernels: same iteration counts within one per solve and the same fields
+    to the Krylov tolerance (their dot products sum in different orders)."""
+    n = (8, 6, 6)  # Nh = 5 * 6 * 6, even
+    gid, eul = I.voronoi(n, 3, 23)
+    mat = dict(MAT, tau_c0=250.0)
+    prog = I.uniaxial_cycle_program(0.006, 24, 1)[:4]
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("FATIGUEFFT_BULK", flag)
+        r = FF.RVE(n, H, gid, eul, mat, opts_for(prec), prec=prec, stream=stream())
+        its = []
+        for Fb, dt in prog:
+            _, st = r.run_increment(Fb, dt)
+            its.append(st["lin_it_total"])
+        out.append((its, {f: r.field(f) for f in ("F", "P", "Fp")}))
+        r.close()
+    (ia, fa), (ib, fb) = out
+    assert sum(ia) > 0 and all(abs(x - y) <= 2 for x, y in zip(ia, ib)), (ia, ib)
+    eye = np.eye(3).reshape(9, 1)
+    tol = 1e-9 if prec == "fp64" else 1e-4
+    for f in fa:
+        a, b = (fa[f] - eye, fb[f] - eye) if f in ("F", "Fp") else (fa[f], fb[f])
+        assert rel(a, b, floor=FLOOR[f] * np.sqrt(b.size)) < tol, f
+
+
 # ----------------------------------------------------------- failure paths
 def test_call_order_errors():
     n = (4, 4, 4)
