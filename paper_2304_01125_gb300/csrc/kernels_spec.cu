@@ -194,29 +194,28 @@ void gnd_rho(const void* Lam, const int32_t* grain, const double* Qg, const doub
 }
 
 // -------------------------------------------------------- averaged tangent
-// Kbar = <g(phi) K> (Eq. avstiff).  2-D grid: block row y sums entries
-// 9y .. 9y + 8 (a few voxels per thread in the bulk type, FP64 across
-// threads and blocks); the last block of the grid writes all 81 means.
+// Kbar = <g(phi) K> (Eq. avstiff).  One row of kRedBlocks blocks; each
+// thread walks its voxels and issues the 81 component loads of a voxel
+// together (independent, coalesced across the warp), accumulating in the
+// bulk type; blocks combine in FP64 and the last block writes the means.
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_kbar(const R* K, const R* phi, R kres, size_t N,
                                                    Red red) {
-    const int y = blockIdx.y;
-    const R* Ky = K + (size_t)9 * y * N;
-    R acc[9];
+    R acc[81];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) acc[c] = 0;
+    for (int c = 0; c < 81; ++c) acc[c] = 0;
     GRID_STRIDE(v, N) {
         const R om = R(1) - phi[v];
         const R gv = om * om + kres;
 #pragma unroll
-        for (int c = 0; c < 9; ++c) acc[c] += gv * Ky[(size_t)c * N + v];
+        for (int c = 0; c < 81; ++c) acc[c] += gv * K[(size_t)c * N + v];
     }
-    block_partials<9, kThreads>(acc, 9, 0u, red.part + (size_t)9 * y * gridDim.x);
+    block_partials<81, kThreads>(acc, 81, 0u, red.part);
     grid_finish<kThreads, 81>(red, 81, 0u, 1.0 / (double)N);
 }
 template <typename R>
 void kbar(const void* K, const void* phi, double kres, size_t N, const Red& red, cudaStream_t s) {
-    k_kbar<R><<<dim3(2 * 152, 9), kThreads, 0, s>>>((const R*)K, (const R*)phi, (R)kres, N, red);
+    k_kbar<R><<<kRedBlocks, kThreads, 0, s>>>((const R*)K, (const R*)phi, (R)kres, N, red);
 }
 
 // ------------------------------------------------------------------ residual
@@ -672,6 +671,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_dcgs_dots(const typename Tr<R>:
             acc[2] += wt[u] * (zv[u].x * zv[u].x + zv[u].y * zv[u].y);
         }
     }
+    // the update pass (launched as a programmatic dependent) may start
+    // prefetching the basis while this grid reduces and forms coefficients
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     block_partials<3 + 2 * NQ, kThreads>(acc, 3 + 2 * k, 0u, red.part);
     if (grid_finish<kThreads, 3 + 2 * NQ>(red, 3 + 2 * k, 0u, 1.0)) {
         // the last block: stage the Hessenberg columns the step needs, then
@@ -746,17 +748,23 @@ __global__ void __launch_bounds__(kUpdT) k_dcgs_update_bulk(
         issued = L + 1;
     };
     for (int q = tid; q < 81; q += blockDim.x) Ks[q] = (R)Kbar[q];
-    for (int q = tid; q < k; q += blockDim.x) {
-        s_a[q] = (R)coef[q];
-        s_e[q] = (R)coef[kMaxKrylov + q];
-    }
     if (tid == 0) {
         for (int s = 0; s < kBulkS; ++s) mbar_init(&full[s], 1);
         mbar_fence_init();
     }
     __syncthreads();
+    // c_k, z and the basis were written before the dot pass started, so the
+    // ring can fill while that pass (this grid's programmatic predecessor)
+    // still runs; the coefficients, the outputs (slot k is the dot pass's
+    // input) and the shared reduction buffers wait for its completion
     if (tid == 0)
         for (int L = 0; L < min(kBulkS, total); ++L) issue(L);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    for (int q = tid; q < k; q += blockDim.x) {
+        s_a[q] = (R)coef[q];
+        s_e[q] = (R)coef[kMaxKrylov + q];
+    }
+    __syncthreads();
     const R inu = (R)coef[2 * kMaxKrylov], cc = (R)coef[2 * kMaxKrylov + 1];
     bool ok = true;
     int L = 0;
@@ -973,8 +981,18 @@ void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* co
     if (bc && bulk_aligned<R>(g)) {
         int tpc, nb;
         tile_split((int)((g.Nh + kUpdT - 1) / kUpdT), bc->upd_blocks, tpc, nb);
-        k_dcgs_update_bulk<R><<<nb, kUpdT, upd_bulk_smem<R>(), s>>>(
-            (Cx*)V, vstride, k, (const Cx*)z, coef, Kbar, g, (Cx*)G, tpc, red, bc->err);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)nb);
+        cfg.blockDim = dim3(kUpdT);
+        cfg.dynamicSmemBytes = upd_bulk_smem<R>();
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_dcgs_update_bulk<R>, (Cx*)V, vstride, k, (const Cx*)z, coef,
+                           Kbar, g, (Cx*)G, tpc, red, bc->err);
         return;
     }
     k_dcgs_update<R><<<grid_for(g.Nh), kThreads, 0, s>>>((Cx*)V, vstride, k, (const Cx*)z, coef,
