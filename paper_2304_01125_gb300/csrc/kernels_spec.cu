@@ -499,7 +499,7 @@ void tangent_apply(void* G, const void* K, const void* phi, double kres, size_t 
 //   A M q_k = (z - Q_{k+1} Hbar a) / nu,
 // so the column k coefficients follow from a, b, alpha = c_k.c_k,
 // beta = c_k.z and Hbar alone.  Per GMRES step: C2R, tangent apply, R2C,
-// contraction, k_dcgs_dots, k_dcgs_update.
+// contraction fused with the dot pass (k_contract_dots), k_dcgs_update.
 //
 // The Krylov vectors are 3 Nh complex entries in one flat, component-major
 // array; the Hermitian weight of flat entry f depends on kx = (f mod Nh) mod
@@ -542,7 +542,7 @@ void contract(const void* T, const SGrid& g, void* w, cudaStream_t s) {
     k_contract<R><<<grid_for(g.Nh), kThreads, 0, s>>>((const Cx*)T, g, (Cx*)w);
 }
 
-// Coefficients of DCGS2 step k from the dots d (layout of k_dcgs_dots) and
+// Coefficients of DCGS2 step k from the dots d (layout above) and
 // the Hessenberg columns (one warp, FP64):
 //   nu = sqrt(alpha - |a|^2)          (|c_k - Q_k a|; 0 on breakdown)
 //   column k-1, final:  Hp[k-1] + a (rows < k), nu (row k)
@@ -606,71 +606,14 @@ __device__ void dcgs_coefficients(int k, const double* d, const double* Hs, doub
 }
 
 // Dots of step k: out[0] = alpha = c.c, out[1] = beta = c.z, out[2] = z.z,
-// out[3 + 2i] = a_i = q_i.c, out[4 + 2i] = b_i = q_i.z (i < k <= NQ).  Each
-// thread streams its entries once (U entries per trip, all loads issued
-// before use) and keeps the 3 + 2k sums in registers; blocks combine in FP64
-// and the last block forms the step's coefficients (dcgs_coefficients).
+// out[3 + 2i] = a_i = q_i.c, out[4 + 2i] = b_i = q_i.z (i < k <= NQ), held
+// per thread in registers and combined across blocks in FP64.
+// Tail of the dot pass: block partials, the last block's combine, the
+// Hessenberg staging and the step coefficients (dcgs_coefficients).
 template <typename R, int NQ>
-__global__ void __launch_bounds__(kThreads, 2) k_dcgs_dots(const typename Tr<R>::Cx* c,
-                                                           const typename Tr<R>::Cx* z,
-                                                           const typename Tr<R>::Cx* V,
-                                                           size_t vstride, int k, SGrid g,
-                                                           Red red, double* Hd, double* Hp,
-                                                           double* slot, double* coef,
-                                                           const int* err) {
-    typedef typename Tr<R>::Cx Cx;
-    constexpr int U = NQ <= 4 ? 4 : (NQ <= 8 ? 2 : 1);
-    constexpr int G = NQ < 8 ? NQ : 8;
-    R acc[3 + 2 * NQ];
-#pragma unroll
-    for (int v = 0; v < 3 + 2 * NQ; ++v) acc[v] = 0;
-    const unsigned n3 = (unsigned)(3 * g.Nh);
-    const unsigned stride = gridDim.x * kThreads;
-    for (unsigned f0 = blockIdx.x * kThreads + threadIdx.x; f0 < n3; f0 += U * stride) {
-        Cx cv[U], zv[U];
-        R wt[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const unsigned f = f0 + u * stride;
-            if (f < n3) {
-                cv[u] = c[f];
-                zv[u] = z[f];
-                wt[u] = (R)hs_weight(g, f);
-            } else {
-                cv[u].x = cv[u].y = zv[u].x = zv[u].y = 0;
-                wt[u] = 0;
-            }
-        }
-        // basis vectors in groups of up to 8 loads in flight (bounded registers)
-#pragma unroll
-        for (int i0 = 0; i0 < NQ; i0 += 8) {
-            Cx q[U][G > 0 ? G : 1];
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-#pragma unroll
-                for (int t = 0; t < G; ++t) {
-                    const unsigned f = f0 + u * stride;
-                    if (i0 + t < k && f < n3) {
-                        q[u][t] = V[(size_t)(i0 + t) * vstride + f];
-                    } else {
-                        q[u][t].x = q[u][t].y = 0;
-                    }
-                }
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-#pragma unroll
-                for (int t = 0; t < G; ++t) {
-                    acc[3 + 2 * (i0 + t)] += wt[u] * (q[u][t].x * cv[u].x + q[u][t].y * cv[u].y);
-                    acc[4 + 2 * (i0 + t)] += wt[u] * (q[u][t].x * zv[u].x + q[u][t].y * zv[u].y);
-                }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            acc[0] += wt[u] * (cv[u].x * cv[u].x + cv[u].y * cv[u].y);
-            acc[1] += wt[u] * (cv[u].x * zv[u].x + cv[u].y * zv[u].y);
-            acc[2] += wt[u] * (zv[u].x * zv[u].x + zv[u].y * zv[u].y);
-        }
-    }
+__device__ __forceinline__ void dots_finish(const R (&acc)[3 + 2 * NQ], int k, const Red& red,
+                                            double* Hd, double* Hp, double* slot, double* coef,
+                                            const int* err) {
     // the update pass (launched as a programmatic dependent) may start
     // prefetching the basis while this grid reduces and forms coefficients
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -690,21 +633,109 @@ __global__ void __launch_bounds__(kThreads, 2) k_dcgs_dots(const typename Tr<R>:
         if (threadIdx.x == 0 && err) slot[kSlotErr] = (double)*(volatile const int*)err;
     }
 }
+
+// The GMRES operator's last step fused with the dot pass: per frequency,
+// z = -div(T) projected onto real fields (as k_contract) is stored and, in
+// the same pass, alpha = c.c, beta = c.z, |z|^2, a_i = q_i.c and
+// b_i = q_i.z accumulate (the dot layout above); the tail forms the step's
+// coefficients.  Saves the contraction's launch and tail and the re-read of
+// z and c.
+template <typename R, int NQ>
+__global__ void __launch_bounds__(kThreads, 2) k_contract_dots(
+    const typename Tr<R>::Cx* T, SGrid g, typename Tr<R>::Cx* w, const typename Tr<R>::Cx* c,
+    const typename Tr<R>::Cx* V, size_t vstride, int k, Red red, double* Hd, double* Hp,
+    double* slot, double* coef, const int* err) {
+    typedef typename Tr<R>::Cx Cx;
+    constexpr int G = NQ < 8 ? NQ : 8;
+    R acc[3 + 2 * NQ];
+#pragma unroll
+    for (int v = 0; v < 3 + 2 * NQ; ++v) acc[v] = 0;
+    const size_t Nh = g.Nh;
+    GRID_STRIDE(e, Nh) {
+        R xi[3], xd[3], wt;
+        hs_freq<R>(g, e, xi, xd, wt);
+        Cx zc[3], cv[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) cv[q] = c[q * Nh + e];
+        div3_real<R>(T, g, e, xd, R(-1), zc);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            w[q * Nh + e] = zc[q];
+            acc[0] += wt * (cv[q].x * cv[q].x + cv[q].y * cv[q].y);
+            acc[1] += wt * (cv[q].x * zc[q].x + cv[q].y * zc[q].y);
+            acc[2] += wt * (zc[q].x * zc[q].x + zc[q].y * zc[q].y);
+        }
+#pragma unroll
+        for (int i0 = 0; i0 < NQ; i0 += 8) {
+            Cx qv[G > 0 ? G : 1][3];
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if (i0 + t < k) {
+                        qv[t][q] = V[(size_t)(i0 + t) * vstride + q * Nh + e];
+                    } else {
+                        qv[t][q].x = qv[t][q].y = 0;
+                    }
+                }
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    acc[3 + 2 * (i0 + t)] += wt * (qv[t][q].x * cv[q].x + qv[t][q].y * cv[q].y);
+                    acc[4 + 2 * (i0 + t)] += wt * (qv[t][q].x * zc[q].x + qv[t][q].y * zc[q].y);
+                }
+        }
+    }
+    dots_finish<R, NQ>(acc, k, red, Hd, Hp, slot, coef, err);
+}
+template <typename R>
+void contract_dots(const void* T, const SGrid& g, void* w, const void* c, const void* V,
+                   size_t vstride, int k, const Red& red, double* Hd, double* Hp, double* slot,
+                   double* coef, const BulkCfg* bc, cudaStream_t s) {
+    typedef typename Tr<R>::Cx Cx;
+    const Cx *TT = (const Cx*)T, *cc = (const Cx*)c, *VV = (const Cx*)V;
+    Cx* ww = (Cx*)w;
+    const int* err = bc ? bc->err : nullptr;
+#define CDOTS(NQ)                                                                           \
+    k_contract_dots<R, NQ><<<kRedBlocks, kThreads, 0, s>>>(TT, g, ww, cc, VV, vstride, k, red, \
+                                                           Hd, Hp, slot, coef, err)
+    if (k <= 0)
+        CDOTS(0);
+    else if (k <= 4)
+        CDOTS(4);
+    else if (k <= 8)
+        CDOTS(8);
+    else if (k <= 16)
+        CDOTS(16);
+    else
+        CDOTS(kMaxKrylov);
+#undef CDOTS
+}
+
 // ------------------------------------------- pipelined Arnoldi update pass
 // The same update as k_dcgs_update, with c_k, z and the basis streamed
 // through a ring of kBulkS shared-memory stages filled by bulk asynchronous
 // copies: one thread issues the copies kBulkS stages ahead and every thread
 // consumes a stage once its mbarrier phase completes, so the bytes in flight
 // per SM are set by the ring, not by registers.  Each CTA owns a contiguous
-// run of tpc tiles of kUpdT frequencies (all three components).  Used when
+// run of tpc tiles of kUpdT frequencies (all three components); 256
+// frequencies and 8 stages measured fastest of {64, 128, 256} x {8, 12, 16}
+// at 64^3.  Used when
 // every copy is 16-byte aligned (Nh even, or complex FP64).  A wait that
 // runs out sets *err (reported to the host) and the CTA stops consuming,
 // takes part in the reduction with what it has, and waits (again bounded)
 // for its own copies still in flight before it exits.  (The dot pass keeps
 // its register-streaming kernel: a pipelined version's per-stage
 // synchronisation outweighed the deeper pipeline.)
-constexpr int kBulkS = 12;  // ring stages
-constexpr int kUpdT = 128;  // frequencies per tile
+#ifndef FATIGUEFFT_UPD_STAGES
+#define FATIGUEFFT_UPD_STAGES 8
+#endif
+#ifndef FATIGUEFFT_UPD_TILE
+#define FATIGUEFFT_UPD_TILE 256
+#endif
+constexpr int kBulkS = FATIGUEFFT_UPD_STAGES;  // ring stages
+constexpr int kUpdT = FATIGUEFFT_UPD_TILE;     // frequencies per tile (= threads per CTA)
 
 // bounded wait for the last copy issued into every stage (issued copies in all)
 __device__ __forceinline__ void bulk_drain(uint64_t* full, int issued) {
@@ -728,7 +759,7 @@ __global__ void __launch_bounds__(kUpdT) k_dcgs_update_bulk(
     const unsigned Nh = (unsigned)g.Nh;
     const int ntiles = (int)((Nh + kUpdT - 1) / kUpdT);
     const int t0 = blockIdx.x * tpc, t1 = min(t0 + tpc, ntiles);
-    const int nv = k + 2;  // c_k, z, q_0 .. q_{k-1}
+    const int nv = k + 2;  // per tile: c_k, q_0 .. q_{k-1}, then z (see below)
     const int total = t1 > t0 ? (t1 - t0) * nv : 0;
     const int tid = threadIdx.x;
     Cx* ck = V + (size_t)k * vstride;
@@ -738,7 +769,7 @@ __global__ void __launch_bounds__(kUpdT) k_dcgs_update_bulk(
         const int tile = t0 + L / nv, v = L % nv;
         const unsigned e0 = (unsigned)tile * kUpdT;
         const unsigned cnt = min((unsigned)kUpdT, Nh - e0);
-        const Cx* src = v == 0 ? ck : v == 1 ? z : V + (size_t)(v - 2) * vstride;
+        const Cx* src = v == 0 ? ck : v == nv - 1 ? z : V + (size_t)(v - 1) * vstride;
         uint64_t* b = &full[L % kBulkS];
         Cx* dst = buf + (size_t)(L % kBulkS) * 3 * kUpdT;
         mbar_arrive_tx(b, 3 * cnt * (unsigned)sizeof(Cx));
@@ -753,13 +784,17 @@ __global__ void __launch_bounds__(kUpdT) k_dcgs_update_bulk(
         mbar_fence_init();
     }
     __syncthreads();
-    // c_k, z and the basis were written before the dot pass started, so the
-    // ring can fill while that pass (this grid's programmatic predecessor)
-    // still runs; the coefficients, the outputs (slot k is the dot pass's
-    // input) and the shared reduction buffers wait for its completion
+    // c_k and the basis were written before the dot pass (this grid's
+    // programmatic predecessor) started, so their copies may start while it
+    // still runs; z (its output), the coefficients, the outputs (slot k is
+    // its input) and the shared reduction buffers wait for its completion.
+    // z is the last load of each tile, so the first tile's z bounds the
+    // early copies.
     if (tid == 0)
-        for (int L = 0; L < min(kBulkS, total); ++L) issue(L);
+        for (int L = 0; L < min(min(kBulkS, total), nv - 1); ++L) issue(L);
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (tid == 0)
+        for (int L = issued; L < min(kBulkS, total); ++L) issue(L);
     for (int q = tid; q < k; q += blockDim.x) {
         s_a[q] = (R)coef[q];
         s_e[q] = (R)coef[kMaxKrylov + q];
@@ -790,11 +825,11 @@ __global__ void __launch_bounds__(kUpdT) k_dcgs_update_bulk(
             if (v == 0) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q) cv[q] = x[q];
-            } else if (v == 1) {
+            } else if (v == nv - 1) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q) zv[q] = x[q];
             } else {
-                const R ai = s_a[v - 2], ei = s_e[v - 2];
+                const R ai = s_a[v - 1], ei = s_e[v - 1];
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     sa[q].x += ai * x[q].x;
@@ -873,34 +908,8 @@ static inline void tile_split(int ntiles, int maxb, int& tpc, int& nb) {
     nb = (ntiles + tpc - 1) / tpc;
 }
 
-template <typename R>
-void dcgs_dots(const void* c, const void* z, const void* V, size_t vstride, int k,
-               const SGrid& g, const Red& red, double* Hd, double* Hp, double* slot,
-               double* coef, const BulkCfg* bc, cudaStream_t s) {
-    typedef typename Tr<R>::Cx Cx;
-    const size_t n3 = 3 * g.Nh;
-    const Cx *cc = (const Cx*)c, *zz = (const Cx*)z, *VV = (const Cx*)V;
-    size_t nb = (n3 + kThreads - 1) / kThreads;
-    if (nb > 2 * 152) nb = 2 * 152;  // one wave of two blocks per SM
-    const dim3 gr((unsigned)nb);
-    const int* err = bc ? bc->err : nullptr;
-#define DOTS(NQ)                                                                               \
-    k_dcgs_dots<R, NQ><<<gr, kThreads, 0, s>>>(cc, zz, VV, vstride, k, g, red, Hd, Hp, slot, \
-                                               coef, err)
-    if (k <= 0)
-        DOTS(0);
-    else if (k <= 4)
-        DOTS(4);
-    else if (k <= 8)
-        DOTS(8);
-    else if (k <= 16)
-        DOTS(16);
-    else
-        DOTS(kMaxKrylov);
-#undef DOTS
-}
 
-// Update of step k with the coefficients from k_dcgs_dots (coef):
+// Update of step k with the coefficients from k_contract_dots (coef):
 //   q_k = (c_k - Q_k a) / nu                     -> slot k (in place)
 //   c_{k+1} = z / nu - Q_k e - c_k dd_k / nu     -> slot k + 1
 //   G = (M c_{k+1}) (x) i xi                     -> the next step's gradient
@@ -1397,13 +1406,13 @@ void fp_in(const double* Fp, const int32_t* grain, const double* Qg, void* Hpi, 
     template void tangent_apply<R>(void*, const void*, const void*, double, size_t,             \
                                    cudaStream_t);                                               \
     template void contract<R>(const void*, const SGrid&, void*, cudaStream_t);                  \
-    template void dcgs_dots<R>(const void*, const void*, const void*, size_t, int,              \
-                               const SGrid&, const Red&, double*, double*, double*, double*,   \
-                               const BulkCfg*, cudaStream_t);                                   \
     template void dcgs_update<R>(void*, size_t, int, const void*, const double*,                \
                                  const double*, const SGrid&, void*, const Red&,                \
                                  const BulkCfg*, cudaStream_t);                                 \
     template int dcgs_bulk_setup<R>(BulkCfg&);                                                  \
+    template void contract_dots<R>(const void*, const SGrid&, void*, const void*, const void*,  \
+                                   size_t, int, const Red&, double*, double*, double*, double*, \
+                                   const BulkCfg*, cudaStream_t);                               \
     template void norm2<R>(const void*, const SGrid&, const Red&, cudaStream_t);                \
     template void xupdate<R>(void*, const void*, size_t, int, const double*, const double*,     \
                              const SGrid&, cudaStream_t);                                       \

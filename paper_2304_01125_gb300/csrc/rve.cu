@@ -560,17 +560,15 @@ struct Impl {
         tangent_apply<R>(r->rb9, r->K, r->phi, r->mat.k_res, r->g.N, r->st);
         prof_end(r, KF_TANGENT, e, N * es * (9 + 81 + 1 + 9));
         TRY(fwd9(r));
-        e = prof_begin(r, KF_CONTRACT);
-        contract<R>(r->cb9, r->g, r->w, r->st);
-        prof_end(r, KF_CONTRACT, e, Nh * 2 * es * (9 + 3));
-        // one pass over q_0 .. q_{k-1}, c_k and z: alpha, beta, a, b
+        // z = -div T (stored to w) and, in the same pass over c_k and
+        // q_0 .. q_{k-1}: alpha, beta, a, b and the step's coefficients
         e = prof_begin(r, KF_MDOT);
         double* Hp = r->Hd + (size_t)kMaxKrylov * kHcol;
         double* coef = Hp + (size_t)kMaxKrylov * kHcol;
         const BulkCfg* bc = r->use_bulk ? &r->bulk : nullptr;
-        dcgs_dots<R>(V + (size_t)k * vs, r->w, V, vs, k, r->g, red_at(r, r->red), r->Hd, Hp,
-                     dslot, coef, bc, r->st);
-        prof_end(r, KF_MDOT, e, Nh * 2 * es * 3 * (k + 2));
+        contract_dots<R>(r->cb9, r->g, r->w, V + (size_t)k * vs, V, vs, k, red_at(r, r->red),
+                         r->Hd, Hp, dslot, coef, bc, r->st);
+        prof_end(r, KF_MDOT, e, Nh * 2 * es * (9 + 3 + 3 * (k + 1)));
         // q_k final, c_{k+1} and the next gradient spectrum
         e = prof_begin(r, KF_GSUPD);
         dcgs_update<R>(V, vs, k, r->w, coef, r->Kbar, r->g, r->cb9,
@@ -579,7 +577,7 @@ struct Impl {
         double* slot = r->hslot + (size_t)(k % 2) * kSlot;
         CK(r, cudaMemcpyAsync(slot, dslot, kSlotLen * sizeof(double), cudaMemcpyDeviceToHost,
                               r->st));
-        r->launches += 4;
+        r->launches += 3;
         return FFT_OK;
     }
 

@@ -51,7 +51,9 @@ struct BulkCfg {
     int* err;
 };
 template <typename R> int dcgs_bulk_setup(BulkCfg& bc);
-template <typename R> void dcgs_dots(const void* c, const void* z, const void* V, size_t vstride, int k, const SGrid& g, const Red& red, double* Hd, double* Hp, double* slot, double* coef, const BulkCfg* bc, cudaStream_t s);
+// the contraction fused with the dot pass: w = -div T stored; alpha, beta,
+// |z|^2, a, b reduced and the step coefficients formed (kernels_spec.cu)
+template <typename R> void contract_dots(const void* T, const SGrid& g, void* w, const void* c, const void* V, size_t vstride, int k, const Red& red, double* Hd, double* Hp, double* slot, double* coef, const BulkCfg* bc, cudaStream_t s);
 template <typename R> void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* coef, const double* Kbar, const SGrid& g, void* G, const Red& red, const BulkCfg* bc, cudaStream_t s);
 template <typename R> void norm2(const void* v, const SGrid& g, const Red& red, cudaStream_t s);
 template <typename R> void xupdate(void* x, const void* V, size_t vstride, int k, const double* y, const double* Kbar, const SGrid& g, cudaStream_t s);
