@@ -169,6 +169,29 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
+def rank_barrier(ws, dev=None):
+    """Device synchronise (when dev is a CUDA device), then a process-group
+    barrier when more than one rank runs."""
+    import torch
+    if dev is not None and dev.type == "cuda":
+        torch.cuda.synchronize(dev)
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+
+
+def rank_max(x, ws, dev=None):
+    """x maximised over the ranks (the slowest rank's time); the reduction
+    tensor lives on dev (the rank's GPU under NCCL, the host under gloo)."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -199,18 +222,10 @@ def run_ours(a):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
     def barrier():
-        torch.cuda.synchronize(dev)
-        if ws > 1:
-            import torch.distributed as tdist
-            tdist.barrier()
+        rank_barrier(ws, dev)
 
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        import torch.distributed as tdist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(x, ws, dev)
 
     results = {}
     fields = {}
