@@ -22,6 +22,14 @@
 
 namespace fatfft {
 
+template <typename R> __device__ __forceinline__ R grid_tpl(const SGrid& g, int i);
+template <> __device__ __forceinline__ float grid_tpl<float>(const SGrid& g, int i) {
+    return i == 0 ? g.tpl0f : (i == 1 ? g.tpl1f : g.tpl2f);
+}
+template <> __device__ __forceinline__ double grid_tpl<double>(const SGrid& g, int i) {
+    return i == 0 ? g.tpl0 : (i == 1 ? g.tpl1 : g.tpl2);
+}
+
 // Frequency, derivative frequency and Hermitian weight of half-spectrum
 // entry e (32-bit index arithmetic: every grid here has Nh < 2^31).
 template <typename R>
@@ -35,9 +43,10 @@ __device__ __forceinline__ void hs_freq(const SGrid& g, size_t e64, R* xi, R* xi
     const int kz = (int)kz_;
     const int sy = ky < (g.n1 + 1) / 2 ? ky : ky - g.n1;
     const int sz = kz < (g.n2 + 1) / 2 ? kz : kz - g.n2;
-    xi[0] = (R)(g.tpl0 * kx);
-    xi[1] = (R)(g.tpl1 * sy);
-    xi[2] = (R)(g.tpl2 * sz);
+    // in the bulk type: FP32 kernels keep the frequency decode off the FP64 pipe
+    xi[0] = grid_tpl<R>(g, 0) * (R)kx;
+    xi[1] = grid_tpl<R>(g, 1) * (R)sy;
+    xi[2] = grid_tpl<R>(g, 2) * (R)sz;
     const bool nyx = (g.n0 % 2 == 0) && kx == g.n0 / 2;
     const bool nyy = (g.n1 % 2 == 0) && ky == g.n1 / 2;
     const bool nyz = (g.n2 % 2 == 0) && kz == g.n2 / 2;
@@ -501,25 +510,12 @@ void tangent_apply(void* G, const void* K, const void* phi, double kres, size_t 
 // beta = c_k.z and Hbar alone.  Per GMRES step: C2R, tangent apply, R2C,
 // contraction fused with the dot pass (k_contract_dots), k_dcgs_update.
 //
-// The Krylov vectors are 3 Nh complex entries in one flat, component-major
-// array; the Hermitian weight of flat entry f depends on kx = (f mod Nh) mod
-// n0h.  Hessenberg columns live on the device in FP64: Hd (final columns)
-// and Hp (provisional columns), column i at offset i * kHcol.
+// The Krylov vectors are 3 Nh complex entries, component-major (stride Nh),
+// weighted by the Hermitian weight of their frequency.  Hessenberg columns
+// live on the device in FP64: Hd (final columns) and Hp (provisional
+// columns), column i at offset i * kHcol.
 
-__device__ __forceinline__ float hs_weight(const SGrid& g, unsigned f) {
-    const unsigned Nh = (unsigned)g.Nh, n0h = (unsigned)g.n0h;
-    const unsigned e = f - Nh * fdiv(f, g.fd_Nh);
-    const unsigned kx = e - n0h * fdiv(e, g.fd_n0h);
-    const bool nyx = (g.n0 % 2 == 0) && (int)kx == g.n0 / 2;
-    return (kx == 0 || nyx) ? 1.0f : 2.0f;
-}
 
-inline int tile_blocks(size_t n3, int items) {
-    const size_t tile = (size_t)items * kThreads;
-    size_t t = (n3 + tile - 1) / tile;
-    if (t > (size_t)(8 * 152)) t = 8 * 152;
-    return (int)(t < 1 ? 1 : t);
-}
 
 // w = -div(T) = -sum_j i xi_j T_ij (the sign that makes the operator
 // positive), projected onto real fields.

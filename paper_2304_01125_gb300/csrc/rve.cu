@@ -1145,6 +1145,9 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
     g.tpl0 = 2 * M_PI / (g.n0 * grid->h);
     g.tpl1 = 2 * M_PI / (g.n1 * grid->h);
     g.tpl2 = 2 * M_PI / (g.n2 * grid->h);
+    g.tpl0f = (float)g.tpl0;
+    g.tpl1f = (float)g.tpl1;
+    g.tpl2f = (float)g.tpl2;
     g.fd_n0h = make_fastdiv((uint32_t)g.n0h);
     g.fd_n1 = make_fastdiv((uint32_t)g.n1);
     g.fd_Nh = make_fastdiv((uint32_t)g.Nh);

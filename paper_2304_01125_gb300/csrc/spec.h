@@ -10,12 +10,13 @@
 
 namespace fatfft {
 
-// Grid and half-spectrum geometry; tpl_i = 2 pi / L_i; dividers for the
+// Grid and half-spectrum geometry; tpl_i = 2 pi / L_i (FP64 and FP32); dividers for the
 // index decode of half-spectrum entries.
 struct SGrid {
     int n0, n1, n2, n0h;
     size_t N, Nh;
     double tpl0, tpl1, tpl2;
+    float tpl0f, tpl1f, tpl2f;  // the same in FP32 (the FP64 pipe is narrow on this GPU)
     FastDiv fd_n0h, fd_n1, fd_Nh;
 };
 struct Mat9 {
