@@ -242,6 +242,15 @@ void batch_destroy(fft_batch_t b);
 /* Kernel launches issued by this handle since creation (for accounting). */
 long long rve_kernel_launches(fft_rve_t r);
 
+/* Library self-test (no counterpart in the paper): the bounded mbarrier
+ * wait that guards the pipelined Krylov update pass, run on a barrier that
+ * nothing completes with a limit of `rounds` try-wait rounds (1..65536).
+ * Returns 1 when the wait gave up as it must (the kernel then records an
+ * error instead of spinning), 2 if it wrongly reported completion, -1 on a
+ * CUDA error, -2 for a bad argument.  Uses the current device and stream 0;
+ * allocates one int. */
+int fft_selftest_bounded_wait(unsigned rounds);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1386,6 +1386,31 @@ void fp_in(const double* Fp, const int32_t* grain, const double* Qg, void* Hpi, 
     k_fp_in<R><<<grid_for(N), kThreads, 0, s>>>(Fp, grain, Qg, (R*)Hpi, N);
 }
 
+// ------------------------------------------------------ bounded-wait self-test
+// One warp waits on an mbarrier that nothing arrives on: the bounded wait
+// must give up after `limit` rounds (out = 1), not spin; out = 2 would mean
+// it reported a phase that never completed.
+__global__ void k_selftest_wait(int* out, unsigned limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const bool done = mbar_wait(&bar, 0u, limit);
+    if (threadIdx.x == 0) out[0] = done ? 2 : 1;
+}
+int selftest_bounded_wait(unsigned limit) {
+    int* d = nullptr;
+    int h = 0;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return -1;
+    k_selftest_wait<<<1, 32>>>(d, limit);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e == cudaSuccess ? h : -1;
+}
+
 // ------------------------------------------------------- instantiations
 #define INST(R)                                                                                \
     template void add_uniform<R>(void*, const void*, const double*, size_t, cudaStream_t);      \

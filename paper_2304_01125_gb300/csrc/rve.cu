@@ -1420,6 +1420,11 @@ fft_status rve_profile_read(fft_rve_t r, double* ms, long long* counts, double* 
 
 long long rve_kernel_launches(fft_rve_t r) { return r ? r->launches : 0; }
 
+int fft_selftest_bounded_wait(unsigned rounds) {
+    if (rounds == 0 || rounds > (1u << 16)) return -2;
+    return fatfft::selftest_bounded_wait(rounds);
+}
+
 }  // extern "C"
 
 // Library-internal accessors for the batch driver (batch.cu).

@@ -52,6 +52,8 @@ struct BulkCfg {
     int* err;
 };
 template <typename R> int dcgs_bulk_setup(BulkCfg& bc);
+// one warp's bounded wait on a barrier nothing completes: 1 = gave up, 2 = reported done
+int selftest_bounded_wait(unsigned limit);
 // the contraction fused with the dot pass: w = -div T stored; alpha, beta,
 // |z|^2, a, b reduced and the step coefficients formed (kernels_spec.cu)
 template <typename R> void contract_dots(const void* T, const SGrid& g, void* w, const void* c, const void* V, size_t vstride, int k, const Red& red, double* Hd, double* Hp, double* slot, double* coef, const BulkCfg* bc, cudaStream_t s);

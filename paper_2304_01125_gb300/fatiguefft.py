@@ -29,7 +29,7 @@ SYMBOLS = ["init_rve", "apply_increment", "solve_equilibrium", "update_damage",
            "eval_gnd", "solve_phase_field", "rve_device_bytes", "rve_destroy", "fft_last_error",
            "rve_kernel_launches", "rve_profile", "rve_profile_read",
            "degraded_average_noalloc", "batch_create", "batch_run_increment", "batch_size",
-           "batch_destroy"]
+           "batch_destroy", "fft_selftest_bounded_wait"]
 KERNEL_FAMILIES = ["constitutive", "tangent_apply", "precond_grad", "contract", "gmres_dot",
                    "gs_update", "gmres_xupdate", "kbar", "residual", "f_update", "phase_field",
                    "gnd", "cufft_9field", "cufft_scalar", "reductions", "other"]
@@ -112,6 +112,8 @@ def load(path=LIB_PATH):
     L.batch_size.restype = C.c_int
     L.batch_destroy.argtypes = [vp]
     L.batch_destroy.restype = None
+    L.fft_selftest_bounded_wait.argtypes = [C.c_uint]
+    L.fft_selftest_bounded_wait.restype = C.c_int
     L.fft_last_error.argtypes = [vp]
     L.fft_last_error.restype = C.c_char_p
     for t in ("init_rve", "apply_increment", "solve_equilibrium", "update_damage",

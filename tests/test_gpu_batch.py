@@ -118,3 +118,19 @@ def test_cutback_recovers_a_batch_rve_at_peak_load():
             assert np.abs(F.mean(axis=1) - Fb).max() < 1e-7
             assert np.array_equal(r.field("Ft"), F)
         r.close()
+
+
+def test_bounded_wait_gives_up_on_a_barrier_nothing_completes():
+    """The pipelined update pass's mbarrier waits are bounded: on a barrier
+    that no copy completes, the wait returns after its round limit (and the
+    context stays usable: a solve runs afterwards)."""
+    import time
+    L = FF.load()
+    t0 = time.time()
+    assert L.fft_selftest_bounded_wait(256) == 1
+    assert time.time() - t0 < 30
+    assert L.fft_selftest_bounded_wait(0) == -2
+    r = _make((6, 6, 6), 5, "mixed")
+    s, _ = r.run_increment(*I.uniaxial_cycle_program(0.004, 8, 1)[0])
+    assert s == FF.FFT_OK
+    r.close()
