@@ -100,6 +100,8 @@ typedef struct {
     double Pbar[9];        /* volume average of g(phi) P at the current iterate */
     long cracked;          /* voxels with phi >= 0.9 */
     int cutbacks;          /* halvings taken by run_increment (max_cutbacks) */
+    int mixed_it;          /* outer rounds of the mixed stress/strain control */
+    double Fbar[9];        /* macroscopic F (row-major) after the last damage update */
 } fft_stats;
 
 /* Field identifiers for fields_out / fields_in (component count). */
@@ -141,6 +143,27 @@ fft_status apply_increment(fft_rve_t r, const double Fbar_target[9], double dt);
 /* One "solve Eq. momentum" line of Algorithm 1: Newton-Krylov at the current
  * phase field phi_{i-1}.  Skipped (F_i = F_{i-1}) when phi has not changed
  * since the previous solve of this increment.  Accumulates into st. */
+/* Mixed stress/strain control (the paper's mixed-control extension of the
+ * FFT solver, Sec. 3.1; the outer iteration is this library's reading):
+ * mask[c] != 0 prescribes component c (row-major) of the volume-averaged
+ * degraded first Piola stress, <g(phi) P>_c = Pbar[c] (MPa; Pbar may be NULL
+ * for zero), and frees that component of the macroscopic F, whose value in
+ * Fbar[c] is the initial guess; mask[c] == 0 prescribes Fbar[c] as in
+ * apply_increment.  After each converged Newton solve the stress-controlled
+ * components are corrected by Kbar_SS dF_S = -(<gP> - Pbar)_S with the
+ * averaged tangent Kbar = <g K>, dF added uniformly, until
+ * max_S |<gP> - Pbar| <= tol_newton * max(max_c |<gP>_c|, 1 MPa); more than
+ * max_newton rounds give FFT_ERR_NOT_CONVERGED.  The solved F is reported in
+ * fft_stats.Fbar and committed with the increment.  run_increment_mixed is
+ * run_increment with this control (no cut-back).  For uniaxial stress prefer
+ * prescribing the lateral normal stresses and the off-diagonal F (no shear,
+ * no rotation): prescribed shear stresses leave the rigid rotation to the
+ * weak geometric stiffness, so the stress tolerance bounds it only loosely. */
+fft_status apply_increment_mixed(fft_rve_t r, const double Fbar[9], const double Pbar[9],
+                                 const int32_t mask[9], double dt);
+fft_status run_increment_mixed(fft_rve_t r, const double Fbar[9], const double Pbar[9],
+                               const int32_t mask[9], double dt, fft_stats* st);
+
 fft_status solve_equilibrium(fft_rve_t r, fft_stats* st);
 
 /* The "solve Eq. phase" and clamp lines of Algorithm 1 at F_i: evaluates the

@@ -33,11 +33,13 @@ class Stats(C.Structure):
     _fields_ = [("stag_it", C.c_int), ("newton_it", C.c_int), ("lin_it_total", C.c_int),
                 ("pf_it_total", C.c_int), ("local_fail", C.c_int), ("converged", C.c_int),
                 ("skipped_equilibrium", C.c_int), ("res_F", C.c_double),
-                ("res_phi", C.c_double), ("Pbar", C.c_double * 9), ("cracked", C.c_long)]
+                ("res_phi", C.c_double), ("Pbar", C.c_double * 9), ("cracked", C.c_long),
+                ("mixed_it", C.c_int), ("Fbar", C.c_double * 9)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["Pbar"] = list(self.Pbar)
+        d["Fbar"] = list(self.Fbar)
         return d
 
 
@@ -89,6 +91,8 @@ def lib():
             getattr(L, fn).argtypes = [C.c_void_p, C.POINTER(Stats)]
         L.orc_commit.argtypes = [C.c_void_p]
         L.orc_run_increment.argtypes = [C.c_void_p, _dp, C.c_double, C.POINTER(Stats)]
+        L.orc_run_increment_mixed.argtypes = [C.c_void_p, _dp, _dp, C.POINTER(C.c_int),
+                                              C.c_double, C.POINTER(Stats)]
         L.orc_fields_out.argtypes = [C.c_void_p, C.c_int, _dp]
         L.orc_fields_in.argtypes = [C.c_void_p, C.c_int, _dp]
         _LIB = L
@@ -256,10 +260,19 @@ class RVE:
     def commit(self):
         return lib().orc_commit(self._h)
 
-    def run_increment(self, Fbar, dt):
+    def run_increment(self, Fbar, dt, Pbar=None, stress_mask=None):
+        """One increment; with stress_mask (9 flags), the flagged components
+        of the macroscopic first Piola stress are prescribed (Pbar, default 0)
+        and the matching components of Fbar are solved for (mixed control)."""
         st = Stats()
-        s = lib().orc_run_increment(self._h, np.ascontiguousarray(Fbar, dtype=np.float64)
-                                    .reshape(9), float(dt), C.byref(st))
+        F = np.ascontiguousarray(Fbar, dtype=np.float64).reshape(9)
+        if stress_mask is None:
+            s = lib().orc_run_increment(self._h, F, float(dt), C.byref(st))
+        else:
+            P = np.ascontiguousarray(np.zeros(9) if Pbar is None else Pbar,
+                                     dtype=np.float64).reshape(9)
+            m = (C.c_int * 9)(*[int(bool(x)) for x in np.asarray(stress_mask).reshape(9)])
+            s = lib().orc_run_increment_mixed(self._h, F, P, m, float(dt), C.byref(st))
         return s, st.as_dict()
 
     def field(self, name):

@@ -71,6 +71,8 @@ typedef struct {
     double res_F, res_phi;
     double Pbar[9];
     long cracked;
+    int mixed_it;     /* outer rounds of the mixed stress/strain control */
+    double Fbar[9];   /* macroscopic F at the end of the last damage update */
 } orc_stats;
 
 /* Per-voxel constitutive result (Sec. 2.1, 2.3). */
@@ -145,6 +147,18 @@ int orc_solve_equilibrium(orc_rve* r, orc_stats* st);
 int orc_update_damage(orc_rve* r, orc_stats* st);
 int orc_commit(orc_rve* r);
 int orc_run_increment(orc_rve* r, const double Fbar[9], double dt, orc_stats* st);
+/* Mixed stress/strain control (the paper's mixed-control extension, Sec. 3.1;
+ * reading: an outer Newton on the stress-controlled macroscopic components):
+ * mask[c] = 1 makes component c of Pbar prescribed (Pstar[c]) and that
+ * component of Fbar free (Fbar[c] is its initial value); mask[c] = 0
+ * prescribes Fbar[c] as in orc_apply_increment.  After each converged
+ * Newton solve, Kbar_SS dF_S = -(<gP> - Pstar)_S with Kbar = <g K> is solved
+ * and dF added uniformly, until max_S |<gP> - Pstar| <= tol_newton *
+ * max(max|<gP>|, 1 MPa) (at most max_newton rounds). */
+int orc_apply_increment_mixed(orc_rve* r, const double Fbar[9], const double Pstar[9],
+                              const int mask[9], double dt);
+int orc_run_increment_mixed(orc_rve* r, const double Fbar[9], const double Pstar[9],
+                            const int mask[9], double dt, orc_stats* st);
 
 /* field ids shared in meaning (not in code) with the GPU library */
 enum {

@@ -298,6 +298,9 @@ struct orc_rve {
     // trial history at the current iterate (from the last damage update)
     std::vector<double> FpL_tr, rho_tr, Wp_tr, Gs_tr, Hmax_tr, Wcrit_tr, gam_tr, drive, We, Pund;
     double Fbar_t[9], Fbar[9], dt;
+    bool mixed = false;  // mixed stress/strain control (orc_apply_increment_mixed)
+    int mask[9] = {0};
+    double Pstar[9] = {0};
     int state, stag_it;
     bool phi_changed, skipped, converged;
 };
@@ -470,6 +473,7 @@ int orc_commit(orc_rve* r) {
 
 int orc_apply_increment(orc_rve* r, const double Fbar[9], double dt) {
     if (r->state == ST_DAMAGE && r->converged) orc_commit(r);
+    r->mixed = false;
     const size_t N = r->N;
     for (int c = 0; c < 9; ++c) {
         const double d = Fbar[c] - r->Fbar_t[c];
@@ -486,18 +490,11 @@ int orc_apply_increment(orc_rve* r, const double Fbar[9], double dt) {
     return 0;
 }
 
-int orc_solve_equilibrium(orc_rve* r, orc_stats* st) {
-    if (r->state != ST_APPLIED && r->state != ST_DAMAGE) return -7;
+// Newton iteration on the fluctuation at the current macroscopic F (Eq.
+// newton with the Krylov solver of Sec. 3.1).
+static int newton_solve(orc_rve* r, orc_stats* st) {
     const size_t N = r->N;
     const bool naive = r->o.use_naive_dft != 0;
-    r->Fprev = r->F;
-    r->skipped = false;
-    r->state = ST_EQUIL;
-    if (r->stag_it >= 1 && !r->phi_changed) {
-        r->skipped = true;
-        if (st) st->skipped_equilibrium = 1;
-        return 0;
-    }
     const Freq& f = r->f;
     std::vector<double> K;
     std::vector<double> Ks(81 * N), Pg(9 * N);
@@ -707,6 +704,89 @@ int orc_solve_equilibrium(orc_rve* r, orc_stats* st) {
     return status;
 }
 
+// Solve the n x n system A x = b (row-major) by Gaussian elimination with
+// partial pivoting; false if singular.
+static bool dense_solve(int n, std::vector<double> A, std::vector<double>& b) {
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r2 = c + 1; r2 < n; ++r2)
+            if (std::fabs(A[r2 * n + c]) > std::fabs(A[p * n + c])) p = r2;
+        if (A[p * n + c] == 0.0) return false;
+        if (p != c) {
+            for (int k = 0; k < n; ++k) std::swap(A[c * n + k], A[p * n + k]);
+            std::swap(b[c], b[p]);
+        }
+        for (int r2 = c + 1; r2 < n; ++r2) {
+            const double m = A[r2 * n + c] / A[c * n + c];
+            for (int k = c; k < n; ++k) A[r2 * n + k] -= m * A[c * n + k];
+            b[r2] -= m * b[c];
+        }
+    }
+    for (int c = n - 1; c >= 0; --c) {
+        double v = b[c];
+        for (int k = c + 1; k < n; ++k) v -= A[c * n + k] * b[k];
+        b[c] = v / A[c * n + c];
+    }
+    return true;
+}
+
+int orc_solve_equilibrium(orc_rve* r, orc_stats* st) {
+    if (r->state != ST_APPLIED && r->state != ST_DAMAGE) return -7;
+    const size_t N = r->N;
+    r->Fprev = r->F;
+    r->skipped = false;
+    r->state = ST_EQUIL;
+    if (r->stag_it >= 1 && !r->phi_changed) {
+        r->skipped = true;
+        if (st) st->skipped_equilibrium = 1;
+        return 0;
+    }
+    for (int outer = 0;; ++outer) {
+        const int s = newton_solve(r, st);
+        if (s) return s;
+        if (!r->mixed) return 0;
+        // mixed control: <gP> and Kbar = <gK> at the converged F, then a
+        // Newton step on the stress-controlled macroscopic components
+        std::vector<double> K;
+        const int nf = cp_all(r, &K, false);
+        if (st) st->local_fail += nf;
+        double Pbar[9] = {0}, Kbar[81] = {0};
+        for (size_t v = 0; v < N; ++v) {
+            const double g = gdeg(r, r->phi[v]);
+            for (int c = 0; c < 9; ++c) Pbar[c] += g * r->Pund[c * N + v];
+            for (int c = 0; c < 81; ++c) Kbar[c] += g * K[81 * v + c];
+        }
+        double pmax = 0, res = 0;
+        int S[9], ns = 0;
+        for (int c = 0; c < 9; ++c) {
+            Pbar[c] /= (double)N;
+            pmax = std::max(pmax, std::fabs(Pbar[c]));
+            if (r->mask[c]) {
+                S[ns++] = c;
+                res = std::max(res, std::fabs(Pbar[c] - r->Pstar[c]));
+            }
+        }
+        for (int c = 0; c < 81; ++c) Kbar[c] /= (double)N;
+        if (st) st->mixed_it = outer + 1;
+        if (std::getenv("ORACLE_VERBOSE"))
+            std::fprintf(stderr, "mixed %d |Pbar - P*|_S %.3e (max|Pbar| %.3e)\n", outer, res,
+                         pmax);
+        if (res <= r->o.tol_newton * std::max(pmax, 1.0)) return 0;
+        if (outer + 1 >= r->o.max_newton) return -5;
+        std::vector<double> A(ns * ns), d(ns);
+        for (int a = 0; a < ns; ++a) {
+            d[a] = -(Pbar[S[a]] - r->Pstar[S[a]]);
+            for (int b = 0; b < ns; ++b) A[a * ns + b] = Kbar[9 * S[a] + S[b]];
+        }
+        if (!dense_solve(ns, A, d)) return -6;
+        for (int a = 0; a < ns; ++a) {
+            const int c = S[a];
+            r->Fbar[c] += d[a];
+            for (size_t v = 0; v < N; ++v) r->F[c * N + v] += d[a];
+        }
+    }
+}
+
 int orc_update_damage(orc_rve* r, orc_stats* st) {
     if (r->state != ST_EQUIL) return -7;
     const size_t N = r->N;
@@ -757,8 +837,42 @@ int orc_update_damage(orc_rve* r, orc_stats* st) {
         long cr = 0;
         for (size_t v = 0; v < N; ++v) cr += r->phi[v] >= 0.9;
         st->cracked = cr;
+        std::memcpy(st->Fbar, r->Fbar, sizeof(r->Fbar));
     }
     return 0;
+}
+
+int orc_apply_increment_mixed(orc_rve* r, const double Fbar[9], const double Pstar[9],
+                              const int mask[9], double dt) {
+    const int s = orc_apply_increment(r, Fbar, dt);
+    if (s) return s;
+    int ns = 0;
+    for (int c = 0; c < 9; ++c) {
+        r->mask[c] = mask[c] ? 1 : 0;
+        r->Pstar[c] = Pstar ? Pstar[c] : 0.0;
+        ns += r->mask[c];
+    }
+    r->mixed = ns > 0;
+    return 0;
+}
+
+static int run_loop(orc_rve* r, orc_stats* st) {
+    for (int i = 0; i < r->o.max_stag; ++i) {
+        int s = orc_solve_equilibrium(r, st);
+        if (s) return s;
+        s = orc_update_damage(r, st);
+        if (s) return s;
+        if (r->converged) return orc_commit(r);
+    }
+    return -5;
+}
+
+int orc_run_increment_mixed(orc_rve* r, const double Fbar[9], const double Pstar[9],
+                            const int mask[9], double dt, orc_stats* st) {
+    if (st) std::memset(st, 0, sizeof(*st));
+    const int s = orc_apply_increment_mixed(r, Fbar, Pstar, mask, dt);
+    if (s) return s;
+    return run_loop(r, st);
 }
 
 int orc_run_increment(orc_rve* r, const double Fbar[9], double dt, orc_stats* st) {

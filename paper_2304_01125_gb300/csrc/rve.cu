@@ -104,6 +104,10 @@ struct fft_rve_s {
     long long prof_cnt[16] = {0};
     // Algorithm 1 bookkeeping
     double Fbar_t[9], Fbar[9], dt = 0;
+    // mixed stress/strain control (apply_increment_mixed)
+    bool mixed = false;
+    int mask[9] = {0};
+    double Pstar[9] = {0};
     int state = ST_NEW, stag_it = 0;
     bool phi_changed = true, skipped = false, converged = false, cp_valid = false;
     bool verbose = false;  // FATIGUEFFT_VERBOSE: solver traces on stderr
@@ -745,6 +749,89 @@ struct Impl {
             if (st) st->skipped_equilibrium = 1;
             return FFT_OK;
         }
+        for (int outer = 0;; ++outer) {
+            TRY(newton_solve(r, st));
+            if (!r->mixed) return FFT_OK;
+            bool done = false;
+            TRY(mixed_step(r, st, outer, &done));
+            if (done) return FFT_OK;
+        }
+    }
+
+    // Mixed control, one outer round after a converged Newton solve: the
+    // mean degraded stress <gP> and Kbar = <gK> at the current F, then
+    // Kbar_SS dF_S = -(<gP> - P*)_S on the stress-controlled components S
+    // (solved on the host) and dF added uniformly to F.  done when
+    // max_S |<gP> - P*| <= tol_newton max(max|<gP>|, 1 MPa).
+    static fft_status mixed_step(fft_rve_s* r, fft_stats* st, int outer, bool* done) {
+        const size_t N = r->g.N;
+        int nf = 0;
+        TRY(cp(r, false, &nf));
+        if (st) st->local_fail += nf;
+        kbar<R>(r->K, r->phi, r->mat.k_res, N, red_at(r, r->Kbar), r->st);
+        stag_stats<R>(r->H, r->Hprev, r->Ht, r->P, r->phi, r->mat.k_res, N, red_at(r, r->red),
+                      r->st);
+        r->launches += 2;
+        CK(r, cudaMemcpyAsync(r->hred + 16, r->Kbar, 81 * sizeof(double),
+                              cudaMemcpyDeviceToHost, r->st));
+        TRY(fetch(r, 11));
+        const double* Pb = r->hred + 2;  // <gP>, from the statistics kernel
+        const double* Kb = r->hred + 16;
+        double pmax = 0, res = 0;
+        int S[9], ns = 0;
+        for (int c = 0; c < 9; ++c) {
+            pmax = std::max(pmax, std::fabs(Pb[c]));
+            if (r->mask[c]) {
+                S[ns++] = c;
+                res = std::max(res, std::fabs(Pb[c] - r->Pstar[c]));
+            }
+        }
+        if (st) st->mixed_it = outer + 1;
+        if (r->verbose)
+            std::fprintf(stderr, "  mixed %d |<gP> - P*|_S %.3e (max|<gP>| %.3e)\n", outer, res,
+                         pmax);
+        if (res <= r->opt.tol_newton * std::max(pmax, 1.0)) {
+            *done = true;
+            return FFT_OK;
+        }
+        if (outer + 1 >= r->opt.max_newton)
+            FAIL(r, FFT_ERR_NOT_CONVERGED, "mixed control reached max_newton = %d rounds",
+                 r->opt.max_newton);
+        // Gauss-Jordan with partial pivoting on [Kbar_SS | -(<gP> - P*)_S]
+        double A[9][10];
+        for (int a = 0; a < ns; ++a) {
+            for (int b = 0; b < ns; ++b) A[a][b] = Kb[9 * S[a] + S[b]];
+            A[a][ns] = r->Pstar[S[a]] - Pb[S[a]];
+        }
+        for (int c = 0; c < ns; ++c) {
+            int p = c;
+            for (int a = c + 1; a < ns; ++a)
+                if (std::fabs(A[a][c]) > std::fabs(A[p][c])) p = a;
+            if (!(std::fabs(A[p][c]) > 0))
+                FAIL(r, FFT_ERR_NONFINITE, "mixed control: singular averaged tangent block");
+            if (p != c)
+                for (int b = 0; b <= ns; ++b) std::swap(A[c][b], A[p][b]);
+            for (int a = 0; a < ns; ++a) {
+                if (a == c) continue;
+                const double m = A[a][c] / A[c][c];
+                for (int b = c; b <= ns; ++b) A[a][b] -= m * A[c][b];
+            }
+        }
+        double d[9] = {0};
+        for (int a = 0; a < ns; ++a) {
+            d[S[a]] = A[a][ns] / A[a][a];
+            r->Fbar[S[a]] += d[S[a]];
+        }
+        add_uniform<R>(r->H, r->H, d, N, r->st);
+        r->launches += 1;
+        r->cp_valid = false;
+        return FFT_OK;
+    }
+
+    // Newton iteration on the fluctuation at the current macroscopic F
+    // (Eq. newton with GMRES, Sec. 3.1).
+    static fft_status newton_solve(fft_rve_s* r, fft_stats* st) {
+        const size_t N = r->g.N;
         for (int it = 0; it < r->opt.max_newton; ++it) {
             if (!r->cp_valid) {
                 int nf = 0;
@@ -890,12 +977,28 @@ struct Impl {
             st->converged = r->converged;
             for (int c = 0; c < 9; ++c) st->Pbar[c] = r->hred[2 + c];
             st->cracked = (long)o4[3];
+            std::memcpy(st->Fbar, r->Fbar, sizeof(r->Fbar));
         }
+        return FFT_OK;
+    }
+
+    static fft_status apply_increment_mixed(fft_rve_s* r, const double* Fbar,
+                                            const double* Pstar, const int32_t* mask,
+                                            double dt) {
+        TRY(apply_increment(r, Fbar, dt));
+        int ns = 0;
+        for (int c = 0; c < 9; ++c) {
+            r->mask[c] = mask[c] ? 1 : 0;
+            r->Pstar[c] = Pstar ? Pstar[c] : 0.0;
+            ns += r->mask[c];
+        }
+        r->mixed = ns > 0;
         return FFT_OK;
     }
 
     static fft_status apply_increment(fft_rve_s* r, const double* Fbar, double dt) {
         if (r->state == ST_DAMAGE && r->converged) TRY(commit(r));
+        r->mixed = false;
         double d[9];
         for (int c = 0; c < 9; ++c) {
             d[c] = Fbar[c] - r->Fbar_t[c];
@@ -932,6 +1035,14 @@ struct Impl {
     // Algorithm 1 for one increment, committed when converged.
     static fft_status run_once(fft_rve_s* r, const double* Fbar, double dt, fft_stats* st) {
         TRY(apply_increment(r, Fbar, dt));
+        return stag_loop(r, st);
+    }
+    static fft_status run_increment_mixed(fft_rve_s* r, const double* Fbar, const double* Pstar,
+                                          const int32_t* mask, double dt, fft_stats* st) {
+        TRY(apply_increment_mixed(r, Fbar, Pstar, mask, dt));
+        return stag_loop(r, st);
+    }
+    static fft_status stag_loop(fft_rve_s* r, fft_stats* st) {
         for (int i = 0; i < r->opt.max_stag; ++i) {
             TRY(solve_equilibrium(r, st));
             TRY(update_damage(r, st));
@@ -1292,6 +1403,21 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
 fft_status apply_increment(fft_rve_t r, const double Fbar_target[9], double dt) {
     if (!r || !Fbar_target || !(dt >= 0)) return FFT_ERR_ARG;
     return DISPATCH(r, apply_increment(r, Fbar_target, dt));
+}
+
+fft_status apply_increment_mixed(fft_rve_t r, const double Fbar[9], const double Pbar[9],
+                                 const int32_t mask[9], double dt) {
+    if (!r || !Fbar || !mask || !(dt >= 0)) return FFT_ERR_ARG;
+    return DISPATCH(r, apply_increment_mixed(r, Fbar, Pbar, mask, dt));
+}
+
+fft_status run_increment_mixed(fft_rve_t r, const double Fbar[9], const double Pbar[9],
+                               const int32_t mask[9], double dt, fft_stats* st) {
+    if (!r || !Fbar || !mask || !(dt >= 0)) return FFT_ERR_ARG;
+    if (st) std::memset(st, 0, sizeof(*st));
+    fft_status s = DISPATCH(r, run_increment_mixed(r, Fbar, Pbar, mask, dt, st));
+    if (s == FFT_OK && cudaStreamSynchronize(r->st) != cudaSuccess) return FFT_ERR_CUDA;
+    return s;
 }
 
 fft_status solve_equilibrium(fft_rve_t r, fft_stats* st) {

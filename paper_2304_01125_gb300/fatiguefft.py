@@ -29,7 +29,8 @@ SYMBOLS = ["init_rve", "apply_increment", "solve_equilibrium", "update_damage",
            "eval_gnd", "solve_phase_field", "rve_device_bytes", "rve_destroy", "fft_last_error",
            "rve_kernel_launches", "rve_profile", "rve_profile_read",
            "degraded_average_noalloc", "batch_create", "batch_run_increment", "batch_size",
-           "batch_destroy", "fft_selftest_bounded_wait"]
+           "batch_destroy", "fft_selftest_bounded_wait", "apply_increment_mixed",
+           "run_increment_mixed"]
 KERNEL_FAMILIES = ["constitutive", "tangent_apply", "precond_grad", "contract", "gmres_dot",
                    "gs_update", "gmres_xupdate", "kbar", "residual", "f_update", "phase_field",
                    "gnd", "cufft_9field", "cufft_scalar", "reductions", "other"]
@@ -58,11 +59,12 @@ class Stats(C.Structure):
                 ("pf_it_total", C.c_int), ("local_fail", C.c_int), ("converged", C.c_int),
                 ("skipped_equilibrium", C.c_int), ("res_F", C.c_double),
                 ("res_phi", C.c_double), ("Pbar", C.c_double * 9), ("cracked", C.c_long),
-                ("cutbacks", C.c_int)]
+                ("cutbacks", C.c_int), ("mixed_it", C.c_int), ("Fbar", C.c_double * 9)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["Pbar"] = list(self.Pbar)
+        d["Fbar"] = list(self.Fbar)
         return d
 
 
@@ -85,6 +87,9 @@ def load(path=LIB_PATH):
     L.update_damage.argtypes = [vp, C.POINTER(Stats)]
     L.commit_increment.argtypes = [vp]
     L.run_increment.argtypes = [vp, dp, C.c_double, C.POINTER(Stats)]
+    L.apply_increment_mixed.argtypes = [vp, dp, dp, C.POINTER(C.c_int32), C.c_double]
+    L.run_increment_mixed.argtypes = [vp, dp, dp, C.POINTER(C.c_int32), C.c_double,
+                                      C.POINTER(Stats)]
     L.fields_out.argtypes = [vp, C.c_int, C.c_void_p, C.c_size_t, C.c_int]
     L.fields_in.argtypes = [vp, C.c_int, C.c_void_p, C.c_size_t]
     L.eval_constitutive.argtypes = [vp, C.c_double, C.c_int, C.POINTER(C.c_int)]
@@ -118,7 +123,8 @@ def load(path=LIB_PATH):
     L.fft_last_error.restype = C.c_char_p
     for t in ("init_rve", "apply_increment", "solve_equilibrium", "update_damage",
               "commit_increment", "run_increment", "fields_out", "fields_in",
-              "eval_constitutive", "eval_gnd", "solve_phase_field"):
+              "eval_constitutive", "eval_gnd", "solve_phase_field", "apply_increment_mixed",
+              "run_increment_mixed"):
         getattr(L, t).restype = C.c_int
     _lib = L
     return L
@@ -228,13 +234,26 @@ class RVE:
     def commit_increment(self):
         return self._check("commit_increment", load().commit_increment(self._h))
 
-    def run_increment(self, Fbar, dt, check=True):
+    def run_increment(self, Fbar, dt, check=True, Pbar=None, stress_mask=None):
+        """One increment (run_increment).  With stress_mask (9 flags) the
+        flagged components of the mean degraded first Piola stress are
+        prescribed (Pbar, default 0) and the matching components of Fbar
+        (initial guesses) are solved for (run_increment_mixed)."""
         F = np.ascontiguousarray(Fbar, dtype=np.float64).reshape(9)
         st = Stats()
-        s = load().run_increment(self._h, F.ctypes.data_as(C.POINTER(C.c_double)), float(dt),
-                                 C.byref(st))
+        fp = F.ctypes.data_as(C.POINTER(C.c_double))
+        if stress_mask is None:
+            s = load().run_increment(self._h, fp, float(dt), C.byref(st))
+            call = "run_increment"
+        else:
+            P = np.ascontiguousarray(np.zeros(9) if Pbar is None else Pbar,
+                                     dtype=np.float64).reshape(9)
+            m = (C.c_int32 * 9)(*[int(bool(x)) for x in np.asarray(stress_mask).reshape(9)])
+            s = load().run_increment_mixed(self._h, fp, P.ctypes.data_as(C.POINTER(C.c_double)),
+                                           m, float(dt), C.byref(st))
+            call = "run_increment_mixed"
         if check:
-            self._check("run_increment", s)
+            self._check(call, s)
         return s, st.as_dict()
 
     def field(self, name):

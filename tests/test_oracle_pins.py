@@ -556,3 +556,38 @@ def test_precrack_mirror_symmetry():
         for j in range(3):
             assert np.abs(F[i, j] - sign[i, j] * Fm[i, j]).max() < 1e-12
     assert np.abs(F[0, 1]).max() > 1e-6  # the crack does perturb the field
+
+
+def test_mixed_control_uniaxial_stress_closed_form():
+    """Mixed stress/strain control (the paper's mixed-control extension):
+    a [100] single crystal, F22 = 1 + eps prescribed and the other eight
+    components of the mean first Piola stress held at zero, tiny eps so the
+    response is linear elastic.  Cubic elasticity gives the lateral strains
+    -C12 / (C11 + C12) eps, no shear, and the axial stress
+    E100 eps = (C11 - C12)(C11 + 2 C12) / (C11 + C12) eps."""
+    mat = I.material("baseline")
+    n = (4, 4, 4)
+    gid, eul = I.single_crystal(n)
+    r = O.RVE(n, I.VOXEL_MM, gid, eul, mat, I.solver_options("parity64"))
+    eps = 1e-5
+    F = np.eye(3).reshape(9).copy()
+    F[4] += eps
+    mask = np.ones(9, dtype=int)
+    mask[4] = 0
+    s, st = r.run_increment(F, eps / 1e-3, Pbar=np.zeros(9), stress_mask=mask)
+    assert s == 0 and st["mixed_it"] >= 1
+    C11, C12 = mat["C11"], mat["C12"]
+    Fb = np.array(st["Fbar"]).reshape(3, 3)
+    lat = -C12 / (C11 + C12) * eps
+    assert abs(Fb[0, 0] - 1 - lat) < 2e-3 * abs(lat)
+    assert abs(Fb[2, 2] - 1 - lat) < 2e-3 * abs(lat)
+    off = Fb - np.diag(np.diag(Fb))
+    assert np.abs(off).max() < 1e-12
+    P = np.array(st["Pbar"]).reshape(3, 3)
+    E100 = (C11 - C12) * (C11 + 2 * C12) / (C11 + C12)
+    assert abs(P[1, 1] - E100 * eps) < 2e-3 * E100 * eps
+    Pl = P.copy()
+    Pl[1, 1] = 0
+    assert np.abs(Pl).max() < 1e-7 * abs(P[1, 1])
+    # the mean F of the field is the solved macroscopic F
+    assert np.abs(r.field("F").mean(axis=1) - Fb.reshape(9)).max() < 1e-13
