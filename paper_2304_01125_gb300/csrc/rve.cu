@@ -1368,17 +1368,22 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
     }
     upload_slip_table(r->st);
     // cuFFT plans: dims slowest-first (n2, n1, n0); 9-field batches use the
-    // contiguous component-major layout.
-    int dims[3] = {g.n2, g.n1, g.n0};
+    // contiguous component-major layout.  Leading unit extents are dropped
+    // (a 2-D plate n2 = 1 gets a rank-2 plan over the same layout).
+    int dims3[3] = {g.n2, g.n1, g.n0};
+    int lead = 0;
+    while (lead < 2 && dims3[lead] == 1) ++lead;
+    int* dims = dims3 + lead;
+    const int rank = 3 - lead;
     const cufftType tf = r->prec == FFT_PREC_FP64 ? CUFFT_D2Z : CUFFT_R2C;
     const cufftType ti = r->prec == FFT_PREC_FP64 ? CUFFT_Z2D : CUFFT_C2R;
-    if (cufftPlanMany(&r->r2c9, 3, dims, nullptr, 1, (int)N, nullptr, 1, (int)Nh, tf, 9) !=
+    if (cufftPlanMany(&r->r2c9, rank, dims, nullptr, 1, (int)N, nullptr, 1, (int)Nh, tf, 9) !=
             CUFFT_SUCCESS ||
-        cufftPlanMany(&r->c2r9, 3, dims, nullptr, 1, (int)Nh, nullptr, 1, (int)N, ti, 9) !=
+        cufftPlanMany(&r->c2r9, rank, dims, nullptr, 1, (int)Nh, nullptr, 1, (int)N, ti, 9) !=
             CUFFT_SUCCESS ||
-        cufftPlanMany(&r->r2c1, 3, dims, nullptr, 1, (int)N, nullptr, 1, (int)Nh, tf, 1) !=
+        cufftPlanMany(&r->r2c1, rank, dims, nullptr, 1, (int)N, nullptr, 1, (int)Nh, tf, 1) !=
             CUFFT_SUCCESS ||
-        cufftPlanMany(&r->c2r1, 3, dims, nullptr, 1, (int)Nh, nullptr, 1, (int)N, ti, 1) !=
+        cufftPlanMany(&r->c2r1, rank, dims, nullptr, 1, (int)Nh, nullptr, 1, (int)N, ti, 1) !=
             CUFFT_SUCCESS) {
         release(r);
         delete r;

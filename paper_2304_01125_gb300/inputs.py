@@ -122,6 +122,75 @@ def precrack_plane(n, x_range, y, value=1.0):
     return phi.reshape(-1), mask.reshape(-1)
 
 
+def soft_region(n, x_range, y_range, phi=None, mask=None):
+    """Soft elastic region: phase field 1 and plasticity off on x in x_range,
+    y in y_range (inclusive) and every z, added to ``phi`` / ``mask`` when
+    given.  Its stiffness is g(1) = k (Sec. 4.1's pre-crack, Sec. 4.5's
+    free-surface buffer)."""
+    n0, n1, n2 = n
+    ph = np.zeros((n2, n1, n0)) if phi is None else phi.reshape(n2, n1, n0).copy()
+    ph[:, y_range[0]:y_range[1] + 1, x_range[0]:x_range[1] + 1] = 1.0
+    m = (ph > 0).astype(np.uint8)
+    if mask is not None:
+        m |= mask.reshape(n2, n1, n0).astype(np.uint8)
+    return ph.reshape(-1), m.reshape(-1)
+
+
+def plate_precrack(n, length, thickness=2):
+    """Central pre-crack of a plate: a soft region ``length`` voxels along x
+    and ``thickness`` voxels along y, centred in the cell (Sec. 4.1: a
+    central crack normal to the loading axis y)."""
+    n0, n1, _ = n
+    x0 = (n0 - length) // 2
+    y0 = n1 // 2 - thickness // 2
+    return soft_region(n, (x0, x0 + length - 1), (y0, y0 + thickness - 1))
+
+
+def free_surface_buffer(n, thickness, phi=None, mask=None):
+    """Free surfaces normal to y in the periodic cell: soft layers at
+    y < thickness and y >= n1 - thickness (Sec. 4.5's buffer layers)."""
+    n0, n1, _ = n
+    phi, mask = soft_region(n, (0, n0 - 1), (0, thickness - 1), phi, mask)
+    return soft_region(n, (0, n0 - 1), (n1 - thickness, n1 - 1), phi, mask)
+
+
+def edge_notch(n, depth, width=2, thickness=0, phi=None, mask=None):
+    """A notch from the lower free surface (inside a buffer of ``thickness``
+    layers) into the sample at x = n0 / 2: ``width`` voxels along x, reaching
+    ``depth`` voxels past the buffer along y."""
+    n0 = n[0]
+    x0 = n0 // 2 - width // 2
+    return soft_region(n, (x0, x0 + width - 1), (thickness, thickness + depth - 1), phi, mask)
+
+
+def bicrystal(n, boundary, euler_a, euler_b):
+    """Periodic bicrystal plate: grain 1 is the band between two parallel
+    grain boundaries, grain 0 the rest.  ``boundary`` = "perpendicular"
+    (boundaries y = n1/4 and 3 n1/4, normal to the loading axis y) or
+    "45" (boundaries x + y = n/4 and 3n/4 mod n, at 45 degrees to y; needs
+    n0 = n1).  Returns grain ids (int32, x fastest) and Euler angles (2, 3)."""
+    n0, n1, n2 = n
+    z, y, x = np.meshgrid(np.arange(n2), np.arange(n1), np.arange(n0), indexing="ij")
+    if boundary == "perpendicular":
+        g = (y >= n1 // 4) & (y < n1 // 4 + n1 // 2)
+    elif boundary == "45":
+        if n0 != n1:
+            raise ValueError("a periodic 45 degree boundary needs n0 = n1")
+        s = (x + y) % n0
+        g = (s >= n0 // 4) & (s < n0 // 4 + n0 // 2)
+    else:
+        raise ValueError(boundary)
+    return g.astype(np.int32).reshape(-1), np.array([euler_a, euler_b], dtype=np.float64)
+
+
+# Bunge angles (Q = Rz(phi1) Rx(Phi) Rz(phi2), lattice -> sample) that put a
+# lattice direction along the sample y axis: [010] (the cube orientation) and
+# [1 1 -1] (a <111> direction: Q^T e_y = (sin phi2 cos Phi, cos phi2 cos Phi,
+# -sin Phi) with phi2 = 45 deg, sin Phi = 1 / sqrt 3).
+EULER_Y100 = (0.0, 0.0, 0.0)
+EULER_Y111 = (0.0, math.asin(1.0 / math.sqrt(3.0)), math.pi / 4)
+
+
 def uniaxial_cycle_program(amplitude, inc_per_cycle, cycles, axis=1, eps_rate=1e-3):
     """Fully reversed (R = -1) triangle wave 0 -> +a -> 0 -> -a -> 0 per cycle,
     equal strain steps, dt = |d eps| / eps_rate.  Returns a list of
@@ -159,7 +228,56 @@ def uniaxial_cycle_program(amplitude, inc_per_cycle, cycles, axis=1, eps_rate=1e
     return prog
 
 
-# The five workloads: grids, grain counts, loading (Sec. 4 shapes).
+def pulsating_cycle_program(eps_max, inc_per_cycle, cycles, axis=1, eps_rate=1e-3):
+    """Strain ratio R = 0 triangle wave 0 -> eps_max -> 0 per cycle (Sec. 4's
+    loading), equal strain steps of 2 eps_max / inc_per_cycle sampled at
+    t = i / inc_per_cycle (the peak and the zero are samples, no increment
+    holds the strain), dt = |d eps| / eps_rate.  inc_per_cycle must be even.
+    Returns a list of (Fbar_target (9,), dt) with Fbar_target =
+    I + eps e_axis (x) e_axis; under uniaxial stress only the axial component
+    is a target, the lateral ones are solved for."""
+    assert cycles >= 1
+    if inc_per_cycle < 2 or inc_per_cycle % 2:
+        raise ValueError("increments per cycle must be even")
+    q = inc_per_cycle // 2
+    de = eps_max / q
+    eps = [0.0]
+    for _ in range(cycles):
+        eps += [k * de for k in range(1, q + 1)] + [k * de for k in range(q - 1, -1, -1)]
+    prog = []
+    for i in range(1, len(eps)):
+        F = np.eye(3)
+        F[axis, axis] += eps[i]
+        prog.append((F.reshape(9).copy(), abs(eps[i] - eps[i - 1]) / eps_rate))
+    return prog
+
+
+def uniaxial_stress_mask(axis=1):
+    """Stress mask (9,) for uniaxial stress along ``axis``: the two lateral
+    normal stresses prescribed (zero), the axial stretch and the off-diagonal
+    F prescribed (no shear, no rigid rotation)."""
+    m = np.zeros(9, dtype=np.int32)
+    for c in range(3):
+        if c != axis:
+            m[4 * c] = 1
+    return m
+
+
+def increment_args(cfg, k, Fbar_prev=None):
+    """(args, kwargs) of ``run_increment`` for increment k of a config's
+    loading.  Strain control: ((Fbar, dt), {}).  Under a stress mask the
+    stress-controlled components of Fbar start from the previous increment's
+    solved values (``Fbar_prev``, the stats' Fbar; the target's at the first
+    increment) and Pbar / stress_mask are passed."""
+    Fb, dt = cfg["program"][k]
+    m = cfg.get("stress_mask")
+    if m is None:
+        return (Fb, dt), {}
+    guess = Fb.copy() if Fbar_prev is None else np.where(m == 1, Fbar_prev, Fb)
+    return (guess, dt), {"Pbar": np.array(cfg["Pbar"], dtype=np.float64), "stress_mask": m}
+
+
+# The workloads: grids, grain counts, loading (Sec. 4 shapes).
 CONFIGS = {
     "sx16": dict(n=(16, 16, 16), grains=1, amplitude=0.005, inc_per_cycle=20, cycles=1,
                  precrack=True, seed=1001),
@@ -169,6 +287,22 @@ CONFIGS = {
                     cycles=10, precrack=False, seed=1003),
     "batch32": dict(sizes=(32, 48, 64, 96), count=32, grains=(20, 150), amplitude=0.006,
                     inc_per_cycle=30, cycles=2, seed=2000),
+    "poly64_r0": dict(n=(64, 64, 64), grains=50, amplitude=0.02, inc_per_cycle=40, cycles=2,
+                      precrack=False, seed=1002, ratio=0, control="uniaxial_stress"),
+    # 2-D plates (one voxel thick, plane stress through mixed control)
+    "plate256_sx100": dict(n=(256, 256, 1), plate="single", euler=EULER_Y100, crack=64,
+                           amplitude=0.02, inc_per_cycle=40, cycles=2, ratio=0, seed=0),
+    "plate256_sx111": dict(n=(256, 256, 1), plate="single", euler=EULER_Y111, crack=64,
+                           amplitude=0.02, inc_per_cycle=40, cycles=2, ratio=0, seed=0),
+    "plate256_bx90": dict(n=(256, 256, 1), plate="bicrystal", boundary="perpendicular",
+                          amplitude=0.02, inc_per_cycle=40, cycles=2, ratio=0,
+                          seed=1006),
+    "plate256_bx45": dict(n=(256, 256, 1), plate="bicrystal", boundary="45",
+                          amplitude=0.02, inc_per_cycle=40, cycles=2, ratio=0,
+                          seed=1006),
+    "plate256x128_notch": dict(n=(256, 128, 1), plate="notched", grains=40, buffer=8,
+                               notch=16, amplitude=0.01, inc_per_cycle=40, cycles=2, ratio=0,
+                               seed=1007),
     "poly256": dict(n=(256, 256, 256), grains=1000, amplitude=0.007, inc_per_cycle=40,
                     cycles=5, precrack=False, seed=1005),
 }
@@ -182,6 +316,8 @@ def build_config(name, n_override=None):
     is given."""
     c = CONFIGS[name]
     n = tuple(n_override) if n_override else c["n"]
+    if "plate" in c:
+        return _plate_config(c, n)
     if c["grains"] == 1:
         gid, eul = single_crystal(n)
     else:
@@ -191,9 +327,45 @@ def build_config(name, n_override=None):
         s = n[0] / 16.0
         x0, x1 = int(round(6 * s)), int(round(10 * s)) - 1
         phi0, mask = precrack_plane(n, (x0, x1), n[1] // 2)
-    prog = uniaxial_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"])
+    if c.get("ratio", -1) == 0:
+        prog = pulsating_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"])
+    else:
+        prog = uniaxial_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"])
+    out = dict(n=n, h=VOXEL_MM, grain_ids=gid, euler=eul, phi0=phi0, elastic_only=mask,
+               program=prog, stress_mask=None, Pbar=None)
+    if c.get("control") == "uniaxial_stress":
+        out["stress_mask"] = uniaxial_stress_mask(1)
+        out["Pbar"] = np.zeros(9)
+    return out
+
+
+def _plate_config(c, n):
+    """Plates of Sec. 4 (2-D, one voxel thick): single crystal with a central
+    soft pre-crack (length scaled with n0), periodic bicrystal, notched
+    polycrystal between free-surface buffer layers (loaded along x).  Plane
+    stress: the lateral in-plane and the out-of-plane normal mean stresses
+    are held at zero."""
+    phi0 = mask = None
+    axis = 1
+    if c["plate"] == "single":
+        gid, eul = single_crystal(n, c["euler"])
+        phi0, mask = plate_precrack(n, max(2, c["crack"] * n[0] // 256))
+    elif c["plate"] == "bicrystal":
+        rng = np.random.default_rng(c["seed"])
+        ea, eb = random_orientations(rng, 2)
+        gid, eul = bicrystal(n, c["boundary"], ea, eb)
+    else:
+        gid, eul = voronoi(n, c["grains"], c["seed"])
+        b = max(1, c["buffer"] * n[1] // 128)
+        phi0, mask = free_surface_buffer(n, b)
+        phi0, mask = edge_notch(n, max(1, c["notch"] * n[1] // 128), 2, b, phi0, mask)
+        axis = 0
+    if c.get("ratio", -1) == 0:
+        prog = pulsating_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"], axis)
+    else:
+        prog = uniaxial_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"], axis)
     return dict(n=n, h=VOXEL_MM, grain_ids=gid, euler=eul, phi0=phi0, elastic_only=mask,
-                program=prog)
+                program=prog, stress_mask=uniaxial_stress_mask(axis), Pbar=np.zeros(9))
 
 
 def batch_configs(seed=2000, count=32, sizes=(32, 48, 64, 96), grains=(20, 150)):

@@ -217,31 +217,20 @@ def test_ragged_odd_grid(prec):
     _run_pair(n, gid, eul, prog, prec, mat=mat)
 
 
-@pytest.mark.parametrize("prec", PREC)
-def test_mixed_control_uniaxial_stress(prec):
-    """Mixed stress/strain control: F22 follows the cycle, the lateral normal
-    stresses P11 = P33 = 0 and the off-diagonal F is held at zero (no shear,
-    no rotation: holding all eight other stresses at zero instead ties the
-    rigid rotation to the stress tolerance through the weak geometric
-    stiffness), on a plastic polycrystal.
-
-    The solved macroscopic F is checked against the oracle running the same
-    control.  The outer stop leaves each lateral mean stress anywhere within
-    tol_newton |P| of zero, and at the onset of plasticity that offset is
-    amplified in the plastic fields, so the fields are checked against a
-    second oracle instance driven under strain control along the solved F
-    sequence: the state a mixed increment ends in is the equilibrium at its
-    final F."""
-    n = (6, 6, 6)
-    gid, eul = I.voronoi(n, 3, 11)
-    mat = dict(MAT, tau_c0=250.0)
-    prog = I.uniaxial_cycle_program(0.006, 24, 1)[:4]
-    mask = np.zeros(9, dtype=int)
-    mask[0] = mask[8] = 1
+def _mixed_parity(prec, n, gid, eul, mat, prog, mask, phi0=None, elastic=None):
+    """Drive the GPU and the oracle under the same mixed control; the solved
+    macroscopic F against the oracle's own mixed control, the fields against
+    a second oracle instance strain-controlled along the GPU's solved F
+    sequence (the state a mixed increment ends in is the equilibrium at its
+    final F: the outer stop leaves each stress-controlled mean anywhere within
+    tol_newton |P| of its target, and at the onset of plasticity that offset
+    is amplified in the plastic fields, so two independent mixed runs differ
+    by more than the round-off bar)."""
     opts = opts_for(prec)
-    g = FF.RVE(n, H, gid, eul, mat, opts, prec=prec, stream=stream())
-    o = O.RVE(n, H, gid, eul, mat, I.solver_options("parity64"))
-    ofol = O.RVE(n, H, gid, eul, mat, I.solver_options("parity64"))
+    kw = dict(phi0=phi0, elastic_only=elastic)
+    g = FF.RVE(n, H, gid, eul, mat, opts, prec=prec, stream=stream(), **kw)
+    o = O.RVE(n, H, gid, eul, mat, I.solver_options("parity64"), **kw)
+    ofol = O.RVE(n, H, gid, eul, mat, I.solver_options("parity64"), **kw)
     Fg = Fo = None
     for k, (Fb, dt) in enumerate(prog):
         guess_g = Fb.copy() if Fg is None else np.where(mask == 1, Fg, Fb)
@@ -257,10 +246,93 @@ def test_mixed_control_uniaxial_stress(prec):
         tol = 1e-9 if prec == "fp64" else 1e-6
         assert np.abs(Fg - Fo).max() < tol * max(1.0, np.abs(Fo - np.eye(3).reshape(9)).max() / 1e-3)
         P = np.array(stg["Pbar"])
-        assert max(abs(P[0]), abs(P[8])) <= 1.01 * opts["tol_newton"] * max(np.abs(P).max(), 1.0)
+        assert np.abs(P[mask == 1]).max() <= 1.01 * opts["tol_newton"] * max(np.abs(P).max(), 1.0)
+    g.close()
+    return o, Fo
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_mixed_control_uniaxial_stress(prec):
+    """Mixed stress/strain control: F22 follows the cycle, the lateral normal
+    stresses P11 = P33 = 0 and the off-diagonal F is held at zero (no shear,
+    no rotation: holding all eight other stresses at zero instead ties the
+    rigid rotation to the stress tolerance through the weak geometric
+    stiffness), on a plastic 6^3 polycrystal, four increments into
+    plasticity."""
+    n = (6, 6, 6)
+    gid, eul = I.voronoi(n, 3, 11)
+    mat = dict(MAT, tau_c0=250.0)
+    prog = I.uniaxial_cycle_program(0.006, 24, 1)[:4]
+    o, Fo = _mixed_parity(prec, n, gid, eul, mat, prog, I.uniaxial_stress_mask(1))
     assert Fo[0] < 1.0 and Fo[8] < 1.0  # lateral contraction under axial tension
     assert np.abs(o.field("Fp") - np.eye(3).reshape(9, 1)).max() > 1e-6  # plastic by the end
-    g.close()
+
+
+GENERIC = (0.3, 0.9, 1.7)  # Bunge angles with no symmetric multi-slip along y
+
+
+@pytest.mark.parametrize("config,euler,tau_c0,prec", [
+    ("plate256_sx100", None, 250.0, "fp64"),
+    ("plate256_sx100", GENERIC, 350.0, "fp64"),
+    ("plate256_sx100", GENERIC, 350.0, "mixed"),
+    ("plate256_bx45", None, 350.0, "fp64"),
+    ("plate256_bx45", None, 350.0, "mixed")])
+def test_plate_plane_stress(config, euler, tau_c0, prec):
+    """2-D plates (16 x 16 x 1: rank-2 transforms, xi_z = 0) under plane
+    stress on the R = 0 loading, five increments, into plasticity, against
+    the oracle: the single crystal with its central soft pre-crack (the [100]
+    orientation of Sec. 4.1, and a generic one) and the periodic bicrystal
+    with boundaries at 45 degrees to the load.
+
+    [100] along y loads eight slip systems equally: in the nearly
+    rate-independent slip law (Delta V / k T of about 76 per MPa) the split of
+    the slip among them, and with it the plastic spin, is fixed by the rate
+    term far below FP32 round-off, so only the FP64 path is held to it; the
+    mixed path is checked on the generic orientation, where the split is
+    well conditioned."""
+    n = (16, 16, 1)
+    cfg = I.build_config(config, n_override=n)
+    eul = cfg["euler"] if euler is None else np.array([euler], dtype=np.float64)
+    mat = dict(MAT, tau_c0=tau_c0)
+    o, Fo = _mixed_parity(prec, n, cfg["grain_ids"], eul, mat, cfg["program"][:5],
+                          cfg["stress_mask"], cfg["phi0"], cfg["elastic_only"])
+    assert Fo[0] < 1.0 and Fo[8] < 1.0
+    assert np.abs(o.field("Fp") - np.eye(3).reshape(9, 1)).max() > 1e-6
+
+
+def test_notched_plate_with_free_surfaces():
+    """Notched polycrystal plate between free-surface buffer layers (soft,
+    stiffness g(1) = k across the whole width), loaded along x under plane
+    stress at the linear tolerance 1e-3 of Sec. 4.5.  Against a Green
+    preconditioner built on the averaged tangent such a laminate takes
+    hundreds of Krylov iterations per Newton step, too many for the oracle
+    at a size that still has a notch, so this is a behavioural test of the
+    GPU path in both precisions: the increments converge, the mean of F is
+    the solved macroscopic F, the prescribed mean stresses are held, and the
+    two precisions solve the same macroscopic F to within the tolerances."""
+    n = (32, 16, 1)
+    cfg = I.build_config("plate256x128_notch", n_override=n)
+    opts = I.solver_options("paper", tol_lin=1e-3, tol_newton=1e-4, tol_stag=1e-4)
+    kw = dict(phi0=cfg["phi0"], elastic_only=cfg["elastic_only"])
+    m = cfg["stress_mask"]
+    solved = {}
+    for prec in PREC:
+        g = FF.RVE(n, H, cfg["grain_ids"], cfg["euler"], MAT, opts, prec=prec, stream=stream(),
+                   **kw)
+        F = None
+        for k in range(3):
+            a, kwg = I.increment_args(cfg, k, F)
+            s, st = g.run_increment(*a, **kwg)
+            assert s == 0
+            F = np.array(st["Fbar"])
+            assert np.abs(g.field("F").mean(axis=1) - F).max() < (1e-13 if prec == "fp64" else 1e-7)
+            P = np.array(st["Pbar"])
+            assert np.abs(P[m == 1]).max() <= 1.01 * opts["tol_newton"] * np.abs(P).max()
+        solved[prec] = F
+        g.close()
+    eps = np.abs(solved["fp64"] - np.eye(3).reshape(9)).max()
+    assert np.abs(solved["mixed"] - solved["fp64"]).max() < 1e-2 * eps
+    assert solved["fp64"][0] > 1.0 and solved["fp64"][8] < 1.0
 
 
 @pytest.mark.parametrize("prec", PREC)

@@ -1,7 +1,10 @@
 """Seeded input generators (host logic shared by the tests, smoke and the
-benchmark): the R = -1 triangle-wave loading programs."""
+benchmark): the loading programs, the stress masks and the plate
+microstructures."""
 import numpy as np
+import pytest
 
+import oracle as O
 from paper_2304_01125_gb300 import inputs as I
 
 
@@ -39,3 +42,78 @@ def test_cycle_program_rejects_odd_counts():
     import pytest
     with pytest.raises(ValueError):
         I.uniaxial_cycle_program(0.006, 31, 1)
+
+
+def test_pulsating_program():
+    """R = 0 loading of Sec. 4: 0 -> eps_max -> 0 per cycle, equal steps,
+    peak and zero sampled, no increment that holds the strain."""
+    prog = I.pulsating_cycle_program(0.02, 8, 2)
+    eps = np.array([F[4] - 1.0 for F, _ in prog])
+    assert np.allclose(eps, [0.005, 0.01, 0.015, 0.02, 0.015, 0.01, 0.005, 0.0] * 2)
+    assert min(eps) >= 0.0 and abs(eps.max() - 0.02) < 1e-15
+    assert np.allclose([dt for _, dt in prog], 0.005 / 1e-3)
+    F = prog[0][0].reshape(3, 3)
+    assert np.array_equal(F - np.diag(np.diag(F)), np.zeros((3, 3))) and F[0, 0] == F[2, 2] == 1
+    with pytest.raises(ValueError):
+        I.pulsating_cycle_program(0.02, 7, 1)
+
+
+def test_stress_mask_and_increment_args():
+    m = I.uniaxial_stress_mask(1)
+    assert m.tolist() == [1, 0, 0, 0, 0, 0, 0, 0, 1]
+    assert I.uniaxial_stress_mask(0).tolist() == [0, 0, 0, 0, 1, 0, 0, 0, 1]
+    cfg = I.build_config("poly64_r0", n_override=(4, 4, 4))
+    assert np.array_equal(cfg["stress_mask"], m)
+    (F0, dt0), kw = I.increment_args(cfg, 0)
+    assert np.array_equal(F0, cfg["program"][0][0]) and np.array_equal(kw["stress_mask"], m)
+    prev = np.eye(3).reshape(9) + 0.1
+    (F1, _), _ = I.increment_args(cfg, 1, prev)
+    assert np.array_equal(F1[m == 1], prev[m == 1])
+    assert np.array_equal(F1[m == 0], cfg["program"][1][0][m == 0])
+    strain = I.build_config("poly64", n_override=(4, 4, 4))
+    assert strain["stress_mask"] is None
+    (Fs, _), kws = I.increment_args(strain, 0, prev)
+    assert kws == {} and np.array_equal(Fs, strain["program"][0][0])
+
+
+def test_bicrystal_geometry():
+    n = (16, 16, 1)
+    for b in ("perpendicular", "45"):
+        gid, eul = I.bicrystal(n, b, (0, 0, 0), (1, 1, 1))
+        g = gid.reshape(16, 16)  # (y, x)
+        assert g.sum() == 128 and eul.shape == (2, 3)
+    gid, _ = I.bicrystal(n, "perpendicular", (0, 0, 0), (1, 1, 1))
+    g = gid.reshape(16, 16)
+    assert np.all(g == g[:, :1]) and g[:, 0].tolist() == [0] * 4 + [1] * 8 + [0] * 4
+    gid, _ = I.bicrystal(n, "45", (0, 0, 0), (1, 1, 1))
+    g = gid.reshape(16, 16)
+    assert np.array_equal(g, np.roll(np.roll(g, 1, axis=1), -1, axis=0))  # boundaries along x + y
+    with pytest.raises(ValueError):
+        I.bicrystal((16, 8, 1), "45", (0, 0, 0), (1, 1, 1))
+
+
+def test_y111_orientation():
+    """EULER_Y111 puts a <111> lattice direction on the sample y axis."""
+    Q = O.euler_to_Q(I.EULER_Y111)
+    d = Q.T @ np.array([0.0, 1.0, 0.0])
+    assert np.allclose(np.abs(d), 1 / np.sqrt(3), atol=1e-15)
+    assert np.allclose(O.euler_to_Q(I.EULER_Y100), np.eye(3))
+
+
+def test_plate_configs():
+    for name in ("plate256_sx100", "plate256_sx111", "plate256_bx90", "plate256_bx45",
+                 "plate256x128_notch"):
+        c = I.build_config(name)
+        assert c["n"][2] == 1 and c["stress_mask"] is not None
+        assert c["grain_ids"].size == int(np.prod(c["n"]))
+    c = I.build_config("plate256_sx100")
+    phi = c["phi0"].reshape(256, 256)
+    ys, xs = np.nonzero(phi)
+    assert (xs.min(), xs.max(), ys.min(), ys.max()) == (96, 159, 127, 128)
+    assert np.array_equal(c["elastic_only"], (c["phi0"] > 0).astype(np.uint8))
+    c = I.build_config("plate256x128_notch")
+    phi = c["phi0"].reshape(128, 256)
+    assert np.all(phi[:8] == 1) and np.all(phi[120:] == 1) and np.all(phi[8:120, :100] == 0)
+    assert np.all(phi[8:24, 127:129] == 1) and np.all(phi[24:120, 127:129] == 0)
+    assert c["stress_mask"].tolist() == [0, 0, 0, 0, 1, 0, 0, 0, 1]
+    assert c["program"][0][0][0] > 1.0 and c["program"][0][0][4] == 1.0

@@ -591,3 +591,39 @@ def test_mixed_control_uniaxial_stress_closed_form():
     assert np.abs(Pl).max() < 1e-7 * abs(P[1, 1])
     # the mean F of the field is the solved macroscopic F
     assert np.abs(r.field("F").mean(axis=1) - Fb.reshape(9)).max() < 1e-13
+
+
+def test_plate_matches_extruded_cell():
+    """A one-voxel-thick periodic plate (n2 = 1, every frequency has xi_z = 0)
+    under plane stress (mixed control, P11 = P33 = 0, in-plane uniaxial F22)
+    equals, to round-off, a three-voxel-thick cell with the same in-plane
+    microstructure extruded along z, whose fields are z-uniform by symmetry:
+    F, P, F_p, rho_SSD and the GND density from the plastic F_p of the
+    previous increments."""
+    mat = dict(I.material("baseline"), tau_c0=150.0)
+    n2, n3 = (8, 6, 1), (8, 6, 3)
+    gid, eul = I.voronoi(n2, 3, 7)
+    gid3 = np.tile(gid.reshape(1, 6, 8), (3, 1, 1)).reshape(-1)
+    opts = I.solver_options("paper")
+    a = O.RVE(n2, I.VOXEL_MM, gid, eul, mat, opts)
+    b = O.RVE(n3, I.VOXEL_MM, gid3, eul, mat, opts)
+    m = I.uniaxial_stress_mask(1)
+    Fa = Fb_ = None
+    for k, (Fb, dt) in enumerate(I.uniaxial_cycle_program(0.006, 24, 1)[:4]):
+        ga = Fb.copy() if Fa is None else np.where(m == 1, Fa, Fb)
+        gb = Fb.copy() if Fb_ is None else np.where(m == 1, Fb_, Fb)
+        sa, sta = a.run_increment(ga, dt, Pbar=np.zeros(9), stress_mask=m)
+        sb, stb = b.run_increment(gb, dt, Pbar=np.zeros(9), stress_mask=m)
+        assert sa == 0 and sb == 0 and sta["mixed_it"] == stb["mixed_it"]
+        Fa, Fb_ = np.array(sta["Fbar"]), np.array(stb["Fbar"])
+        assert np.abs(Fa - Fb_).max() < 1e-14
+    floor = {"F": 1e-4, "P": 1.0, "Fp": 1e-7, "rho_gnd": 1e2, "rho_ssd": 1e2}
+    for f, fl in floor.items():
+        A = a.field(f).reshape(-1, 1, 6, 8)
+        B = b.field(f).reshape(-1, 3, 6, 8)
+        if f in ("F", "Fp"):
+            eye = np.eye(3).reshape(9, 1, 1, 1)
+            A, B = A - eye, B - eye
+        assert np.abs(B - A).max() <= 1e-10 * max(np.abs(A).max(), fl), f
+    assert np.abs(a.field("rho_gnd")).max() > 1e3  # the plastic F_p is curl-carrying
+    assert abs(np.array(sta["Pbar"])[8]) <= opts["tol_newton"] * abs(sta["Pbar"][4])
