@@ -80,10 +80,14 @@ typedef struct {
  * path (FP32 fields, transforms and constitutive update; FP64 reductions,
  * dot products, norms and compensated history sums).  max_cutbacks (an
  * extension; the paper's Algorithm 1 has none, 0 = off): when run_increment
- * does not converge, the increment is restarted from the committed state as
- * two halves (Fbar and dt halved, each committed), recursively up to this
- * depth (0..10, else FFT_ERR_ARG at init_rve); smaller steps stiffen the rate-dependent consistent tangent of
- * plastic voxels and so ease the Krylov solves. */
+ * or run_increment_mixed does not converge, the increment is restarted from
+ * the committed state as two halves of the step, each committed: the first
+ * to the midpoint of the committed and the requested Fbar, the second to the
+ * request (under mixed control its stress-controlled components start from
+ * the solved midpoint), dt halved; recursively up to this depth (0..10, else
+ * FFT_ERR_ARG at init_rve).  Smaller steps keep Newton within reach of the
+ * solution and stiffen the rate-dependent consistent tangent of plastic
+ * voxels, which eases the Krylov solves. */
 typedef struct {
     double tol_stag, tol_newton, tol_lin, tol_pf, tol_local;
     int max_stag, max_newton, max_lin, max_pf, max_local, restart;
@@ -155,10 +159,11 @@ fft_status apply_increment(fft_rve_t r, const double Fbar_target[9], double dt);
  * max_S |<gP> - Pbar| <= tol_newton * max(max_c |<gP>_c|, 1 MPa); more than
  * max_newton rounds give FFT_ERR_NOT_CONVERGED.  The solved F is reported in
  * fft_stats.Fbar and committed with the increment.  run_increment_mixed is
- * run_increment with this control (no cut-back).  For uniaxial stress prefer
- * prescribing the lateral normal stresses and the off-diagonal F (no shear,
- * no rotation): prescribed shear stresses leave the rigid rotation to the
- * weak geometric stiffness, so the stress tolerance bounds it only loosely. */
+ * run_increment with this control (with cut-back, max_cutbacks).  For
+ * uniaxial stress prefer prescribing the lateral normal stresses and the
+ * off-diagonal F (no shear, no rotation): prescribed shear stresses leave the
+ * rigid rotation to the weak geometric stiffness, so the stress tolerance
+ * bounds it only loosely. */
 fft_status apply_increment_mixed(fft_rve_t r, const double Fbar[9], const double Pbar[9],
                                  const int32_t mask[9], double dt);
 fft_status run_increment_mixed(fft_rve_t r, const double Fbar[9], const double Pbar[9],

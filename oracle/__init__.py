@@ -26,7 +26,7 @@ class Options(C.Structure):
                 ("tol_pf", C.c_double), ("tol_local", C.c_double),
                 ("max_stag", C.c_int), ("max_newton", C.c_int), ("max_lin", C.c_int),
                 ("max_pf", C.c_int), ("max_local", C.c_int), ("restart", C.c_int),
-                ("use_naive_dft", C.c_int), ("n_threads", C.c_int)]
+                ("use_naive_dft", C.c_int), ("n_threads", C.c_int), ("max_cutbacks", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -34,7 +34,7 @@ class Stats(C.Structure):
                 ("pf_it_total", C.c_int), ("local_fail", C.c_int), ("converged", C.c_int),
                 ("skipped_equilibrium", C.c_int), ("res_F", C.c_double),
                 ("res_phi", C.c_double), ("Pbar", C.c_double * 9), ("cracked", C.c_long),
-                ("mixed_it", C.c_int), ("Fbar", C.c_double * 9)]
+                ("mixed_it", C.c_int), ("Fbar", C.c_double * 9), ("cutbacks", C.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -118,6 +118,7 @@ def options(opts, naive=False, threads=0):
         setattr(o, k, int(opts[k]))
     o.use_naive_dft = 1 if naive else 0
     o.n_threads = int(threads)
+    o.max_cutbacks = int(opts.get("max_cutbacks", 0))
     return o
 
 

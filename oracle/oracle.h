@@ -63,6 +63,8 @@ typedef struct {
     int restart;            /* GMRES restart length */
     int use_naive_dft;      /* 1: every transform is the O(N^2) DFT */
     int n_threads;          /* 0: hardware concurrency */
+    int max_cutbacks;       /* 0: off; else a non-converged increment is redone as two
+                               halves from the committed state, down to this depth */
 } orc_options;
 
 typedef struct {
@@ -73,6 +75,7 @@ typedef struct {
     long cracked;
     int mixed_it;     /* outer rounds of the mixed stress/strain control */
     double Fbar[9];   /* macroscopic F at the end of the last damage update */
+    int cutbacks;     /* halvings taken (max_cutbacks) */
 } orc_stats;
 
 /* Per-voxel constitutive result (Sec. 2.1, 2.3). */

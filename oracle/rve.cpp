@@ -867,26 +867,51 @@ static int run_loop(orc_rve* r, orc_stats* st) {
     return -5;
 }
 
-int orc_run_increment_mixed(orc_rve* r, const double Fbar[9], const double Pstar[9],
-                            const int mask[9], double dt, orc_stats* st) {
-    if (st) std::memset(st, 0, sizeof(*st));
-    const int s = orc_apply_increment_mixed(r, Fbar, Pstar, mask, dt);
+// One attempt at an increment, committed when converged; mask = nullptr is
+// strain control.
+static int attempt(orc_rve* r, const double Fbar[9], const double* Pstar, const int* mask,
+                   double dt, orc_stats* st) {
+    const int s = mask ? orc_apply_increment_mixed(r, Fbar, Pstar, mask, dt)
+                       : orc_apply_increment(r, Fbar, dt);
     if (s) return s;
     return run_loop(r, st);
 }
 
-int orc_run_increment(orc_rve* r, const double Fbar[9], double dt, orc_stats* st) {
-    if (st) std::memset(st, 0, sizeof(*st));
-    int s = orc_apply_increment(r, Fbar, dt);
+// Cut-back (an extension of Algorithm 1, off unless max_cutbacks > 0): an
+// increment that does not converge is redone from the committed state as two
+// halves of the step, the first to the midpoint of the committed and the
+// requested macroscopic F, the second to the request with its
+// stress-controlled components started from the solved midpoint; each half
+// is halved again on failure, down to depth max_cutbacks.
+static int halves(orc_rve* r, const double Fbar[9], const double* Pstar, const int* mask,
+                  double dt, orc_stats* st, int depth) {
+    if (st) st->cutbacks += 1;
+    double mid[9], last[9];
+    for (int c = 0; c < 9; ++c) mid[c] = 0.5 * (r->Fbar_t[c] + Fbar[c]);
+    int s = attempt(r, mid, Pstar, mask, 0.5 * dt, st);
+    if (s == -5 && depth < r->o.max_cutbacks) s = halves(r, mid, Pstar, mask, 0.5 * dt, st, depth + 1);
     if (s) return s;
-    for (int i = 0; i < r->o.max_stag; ++i) {
-        s = orc_solve_equilibrium(r, st);
-        if (s) return s;
-        s = orc_update_damage(r, st);
-        if (s) return s;
-        if (r->converged) return orc_commit(r);
-    }
-    return -5;
+    for (int c = 0; c < 9; ++c) last[c] = (mask && mask[c]) ? r->Fbar_t[c] : Fbar[c];
+    s = attempt(r, last, Pstar, mask, 0.5 * dt, st);
+    if (s == -5 && depth < r->o.max_cutbacks) s = halves(r, last, Pstar, mask, 0.5 * dt, st, depth + 1);
+    return s;
+}
+
+static int run_with_cutbacks(orc_rve* r, const double Fbar[9], const double* Pstar,
+                             const int* mask, double dt, orc_stats* st) {
+    if (st) std::memset(st, 0, sizeof(*st));
+    const int s = attempt(r, Fbar, Pstar, mask, dt, st);
+    if (s != -5 || r->o.max_cutbacks <= 0) return s;
+    return halves(r, Fbar, Pstar, mask, dt, st, 1);
+}
+
+int orc_run_increment_mixed(orc_rve* r, const double Fbar[9], const double Pstar[9],
+                            const int mask[9], double dt, orc_stats* st) {
+    return run_with_cutbacks(r, Fbar, Pstar, mask, dt, st);
+}
+
+int orc_run_increment(orc_rve* r, const double Fbar[9], double dt, orc_stats* st) {
+    return run_with_cutbacks(r, Fbar, nullptr, nullptr, dt, st);
 }
 
 int orc_fields_out(const orc_rve* r, int field, double* dst) {

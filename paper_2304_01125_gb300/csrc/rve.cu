@@ -1032,14 +1032,14 @@ struct Impl {
         return FFT_OK;
     }
 
-    // Algorithm 1 for one increment, committed when converged.
-    static fft_status run_once(fft_rve_s* r, const double* Fbar, double dt, fft_stats* st) {
-        TRY(apply_increment(r, Fbar, dt));
-        return stag_loop(r, st);
-    }
-    static fft_status run_increment_mixed(fft_rve_s* r, const double* Fbar, const double* Pstar,
-                                          const int32_t* mask, double dt, fft_stats* st) {
-        TRY(apply_increment_mixed(r, Fbar, Pstar, mask, dt));
+    // Algorithm 1 for one increment, committed when converged; mask = nullptr
+    // is strain control, otherwise the mixed control of apply_increment_mixed.
+    static fft_status run_once(fft_rve_s* r, const double* Fbar, const double* Pstar,
+                               const int32_t* mask, double dt, fft_stats* st) {
+        if (mask)
+            TRY(apply_increment_mixed(r, Fbar, Pstar, mask, dt));
+        else
+            TRY(apply_increment(r, Fbar, dt));
         return stag_loop(r, st);
     }
     static fft_status stag_loop(fft_rve_s* r, fft_stats* st) {
@@ -1054,27 +1054,32 @@ struct Impl {
     // The increment as two halves from the committed state (a failed
     // attempt leaves it untouched: apply_increment restarts from F_t, phi_t
     // and the committed history), each halved again on failure down to
-    // depth max_cutbacks.
-    static fft_status run_halves(fft_rve_s* r, const double* Fbar, double dt, fft_stats* st,
-                                 int depth) {
+    // depth max_cutbacks.  The first half goes to the midpoint of the
+    // committed and the requested macroscopic F, the second to the request;
+    // under mixed control the second half's stress-controlled components
+    // start from the solved midpoint.
+    static fft_status run_halves(fft_rve_s* r, const double* Fbar, const double* Pstar,
+                                 const int32_t* mask, double dt, fft_stats* st, int depth) {
         if (st) st->cutbacks += 1;
-        double Fmid[9];
-        for (int c = 0; c < 9; ++c) Fmid[c] = 0.5 * (r->Fbar_t[c] + Fbar[c]);
-        const double* tgt[2] = {Fmid, Fbar};
+        double tgt[2][9];
+        for (int c = 0; c < 9; ++c) tgt[0][c] = 0.5 * (r->Fbar_t[c] + Fbar[c]);
         for (int h = 0; h < 2; ++h) {
-            fft_status s = run_once(r, tgt[h], 0.5 * dt, st);
+            if (h == 1)
+                for (int c = 0; c < 9; ++c) tgt[1][c] = (mask && mask[c]) ? r->Fbar_t[c] : Fbar[c];
+            fft_status s = run_once(r, tgt[h], Pstar, mask, 0.5 * dt, st);
             if (s == FFT_ERR_NOT_CONVERGED && depth < r->opt.max_cutbacks)
-                s = run_halves(r, tgt[h], 0.5 * dt, st, depth + 1);
+                s = run_halves(r, tgt[h], Pstar, mask, 0.5 * dt, st, depth + 1);
             if (s != FFT_OK) return s;
         }
         return FFT_OK;
     }
 
-    static fft_status run_increment(fft_rve_s* r, const double* Fbar, double dt, fft_stats* st) {
-        const fft_status s = run_once(r, Fbar, dt, st);
+    static fft_status run_increment(fft_rve_s* r, const double* Fbar, const double* Pstar,
+                                    const int32_t* mask, double dt, fft_stats* st) {
+        const fft_status s = run_once(r, Fbar, Pstar, mask, dt, st);
         if (s != FFT_ERR_NOT_CONVERGED || r->opt.max_cutbacks <= 0) return s;
         if (r->verbose) std::fprintf(stderr, "  increment not converged: cutting back\n");
-        return run_halves(r, Fbar, dt, st, 1);
+        return run_halves(r, Fbar, Pstar, mask, dt, st, 1);
     }
 
     static fft_status fields_out(fft_rve_s* r, int field, double* d) {
@@ -1420,7 +1425,7 @@ fft_status run_increment_mixed(fft_rve_t r, const double Fbar[9], const double P
                                const int32_t mask[9], double dt, fft_stats* st) {
     if (!r || !Fbar || !mask || !(dt >= 0)) return FFT_ERR_ARG;
     if (st) std::memset(st, 0, sizeof(*st));
-    fft_status s = DISPATCH(r, run_increment_mixed(r, Fbar, Pbar, mask, dt, st));
+    fft_status s = DISPATCH(r, run_increment(r, Fbar, Pbar, mask, dt, st));
     if (s == FFT_OK && cudaStreamSynchronize(r->st) != cudaSuccess) return FFT_ERR_CUDA;
     return s;
 }
@@ -1445,7 +1450,7 @@ fft_status commit_increment(fft_rve_t r) {
 fft_status run_increment(fft_rve_t r, const double Fbar_target[9], double dt, fft_stats* st) {
     if (!r || !Fbar_target || !(dt >= 0)) return FFT_ERR_ARG;
     if (st) std::memset(st, 0, sizeof(*st));
-    fft_status s = DISPATCH(r, run_increment(r, Fbar_target, dt, st));
+    fft_status s = DISPATCH(r, run_increment(r, Fbar_target, nullptr, nullptr, dt, st));
     if (s == FFT_OK && cudaStreamSynchronize(r->st) != cudaSuccess) return FFT_ERR_CUDA;
     return s;
 }

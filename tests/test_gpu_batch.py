@@ -120,6 +120,39 @@ def test_cutback_recovers_a_batch_rve_at_peak_load():
         r.close()
 
 
+def test_cutback_under_mixed_control_matches_oracle():
+    """Cut-back under mixed control (uniaxial stress): a single 0.6 % step
+    from rest that Newton cannot take whole (max_newton 6, at most 100
+    Krylov iterations per solve) is redone as halves; the FP64 path takes the
+    same halvings as the oracle and reaches its solved macroscopic F and
+    fields, the mixed path converges through halvings with the lateral
+    stresses held."""
+    import torch
+    import oracle as O
+    n = (6, 6, 6)
+    gid, eul = I.voronoi(n, 3, 11)
+    mat = dict(I.material("baseline"), tau_c0=250.0)
+    m = I.uniaxial_stress_mask(1)
+    Fb, dt = I.uniaxial_cycle_program(0.006, 4, 1)[0]
+    opts = I.solver_options("paper", max_newton=6, max_lin=100, max_cutbacks=3)
+    o = O.RVE(n, H, gid, eul, mat, opts)
+    so, sto = o.run_increment(Fb, dt, Pbar=np.zeros(9), stress_mask=m)
+    assert so == 0 and sto["cutbacks"] >= 1
+    for prec in ("fp64", "mixed"):
+        r = FF.RVE(n, H, gid, eul, mat, opts, prec=prec, stream=torch.cuda.Stream())
+        s, st = r.run_increment(Fb, dt, Pbar=np.zeros(9), stress_mask=m)
+        assert s == FF.FFT_OK and st["cutbacks"] >= 1
+        P = np.array(st["Pbar"])
+        assert np.abs(P[m == 1]).max() <= 1.01 * opts["tol_newton"] * np.abs(P).max()
+        if prec == "fp64":
+            assert st["cutbacks"] == sto["cutbacks"]
+            assert np.abs(np.array(st["Fbar"]) - np.array(sto["Fbar"])).max() < 1e-9
+            for f in ("F", "P", "Fp"):
+                a, b = r.field(f), o.field(f)
+                assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(b), f
+        r.close()
+
+
 def test_bounded_wait_gives_up_on_a_barrier_nothing_completes():
     """The pipelined update pass's mbarrier waits are bounded: on a barrier
     that no copy completes, the wait returns after its round limit (and the

@@ -627,3 +627,50 @@ def test_plate_matches_extruded_cell():
         assert np.abs(B - A).max() <= 1e-10 * max(np.abs(A).max(), fl), f
     assert np.abs(a.field("rho_gnd")).max() > 1e3  # the plastic F_p is curl-carrying
     assert abs(np.array(sta["Pbar"])[8]) <= opts["tol_newton"] * abs(sta["Pbar"][4])
+
+
+def test_cutback_equals_explicit_halves():
+    """Cut-back (max_cutbacks, an extension of Algorithm 1): a single 0.6 %
+    step from rest that Newton cannot take whole (max_newton 6, at most 100
+    Krylov iterations per solve) is redone as
+    halves of the step, recursively; the result equals, bit for bit, the
+    same halves requested one by one from a handle with cut-back off, by the
+    definition: the first half to the midpoint of the committed and the
+    requested macroscopic F, the second to the request."""
+    n = (6, 6, 6)
+    gid, eul = I.voronoi(n, 3, 11)
+    mat = dict(I.material("baseline"), tau_c0=250.0)
+    Fb, dt = I.uniaxial_cycle_program(0.006, 4, 1)[0]
+    a = O.RVE(n, I.VOXEL_MM, gid, eul, mat,
+              I.solver_options("paper", max_newton=6, max_lin=100, max_cutbacks=3))
+    s, st = a.run_increment(Fb, dt)
+    assert s == 0 and st["cutbacks"] >= 1
+    b = O.RVE(n, I.VOXEL_MM, gid, eul, mat,
+              I.solver_options("paper", max_newton=6, max_lin=100, max_cutbacks=0))
+    committed = [np.eye(3).reshape(9)]
+    halvings = [0]
+
+    def attempt(F, t):
+        s, _ = b.run_increment(F, t)
+        if s == 0:
+            committed[0] = F.copy()
+        return s
+
+    def halves(F, t, depth):
+        halvings[0] += 1
+        mid = 0.5 * (committed[0] + F)
+        s = attempt(mid, 0.5 * t)
+        if s == -5 and depth < 3:
+            s = halves(mid, 0.5 * t, depth + 1)
+        if s:
+            return s
+        s = attempt(F, 0.5 * t)
+        if s == -5 and depth < 3:
+            s = halves(F, 0.5 * t, depth + 1)
+        return s
+
+    assert attempt(Fb, dt) == -5
+    assert halves(Fb, dt, 1) == 0
+    assert halvings[0] == st["cutbacks"]
+    for f in ("F", "P", "Fp", "rho_ssd", "gamma", "Wp"):
+        assert np.array_equal(a.field(f), b.field(f)), f
