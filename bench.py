@@ -87,13 +87,45 @@ def ncu_traffic(family):
     return e.get("dram_bytes_per_launch")
 
 
+class Driver:
+    """Runs a workload's increments on one handle (GPU or oracle).  Under a
+    stress mask (uniaxial stress) the stress-controlled components of each
+    increment start from the previous increment's solved macroscopic F."""
+
+    def __init__(self, cfg):
+        self.cfg, self.F = cfg, None
+
+    def __call__(self, r, k):
+        args, kw = I.increment_args(self.cfg, k, self.F)
+        s, st = r.run_increment(*args, **kw)
+        if kw and s == 0:
+            self.F = np.array(st["Fbar"])
+        return s, st
+
+
+def workload_options(a, cfg):
+    """Solver options of a workload: the --tol preset; mixed-control
+    workloads (large plastic strains at the R = 0 peaks) with cut-back on."""
+    return I.solver_options(a.tol, **({} if cfg["stress_mask"] is None else
+                                      {"max_cutbacks": 4}))
+
+
+def workload_desc(name, cfg):
+    c = I.CONFIGS[name]
+    n = "x".join(str(x) for x in cfg["n"])
+    grains = c.get("grains", len(cfg["euler"]))
+    ctl = "uniaxial strain" if cfg["stress_mask"] is None else "uniaxial stress (mixed control)"
+    ratio = "R=0" if c.get("ratio", -1) == 0 else "R=-1"
+    return (f"{name}: {n} voxels, {grains} grains, {ratio} {ctl} {100 * c['amplitude']:g}%, "
+            f"{c['inc_per_cycle']} increments/cycle")
+
+
 def probe_dominant(FF, cfg, mat, opts, stream, prec):
     """Per-family kernel times over plastic increments of the workload
     (untimed, on a separate handle): the HBM-bound family with the largest
     total time is the one the timed region measures."""
     import torch
     n = cfg["n"]
-    prog = cfg["program"]
     # the probe is untimed: its graph replays are all timed (shares comparable
     # with an ncu launch list of the same window)
     old = os.environ.get("FATIGUEFFT_PROF_SAMPLE")
@@ -104,12 +136,13 @@ def probe_dominant(FF, cfg, mat, opts, stream, prec):
         del os.environ["FATIGUEFFT_PROF_SAMPLE"]
     else:
         os.environ["FATIGUEFFT_PROF_SAMPLE"] = old
+    drv = Driver(cfg)
     for k in range(8):
-        r.run_increment(*prog[k])
+        drv(r, k)
     r.profile(FF.KERNEL_FAMILIES)
     torch.cuda.nvtx.range_push(f"probe_{prec}")  # the window of the committed ncu launch list
     for k in range(8, 14):
-        r.run_increment(*prog[k])
+        drv(r, k)
     bd = r.profile_read(reset=True)
     torch.cuda.nvtx.range_pop()
     r.close()
@@ -223,7 +256,7 @@ def run_ours(a):
     prog = cfg["program"]
     assert a.warmup + a.steps <= len(prog)
     mat = I.material("baseline")
-    opts = I.solver_options(a.tol)
+    opts = workload_options(a, cfg)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
@@ -239,8 +272,9 @@ def run_ours(a):
         dom, breakdown = probe_dominant(FF, cfg, mat, opts, stream, prec)
         r = FF.RVE(n, I.VOXEL_MM, cfg["grain_ids"], cfg["euler"], mat, opts, prec=prec,
                    stream=stream)
+        drv = Driver(cfg)
         for k in range(a.warmup):
-            r.run_increment(*prog[k])
+            drv(r, k)
         # only the dominant family is timed (CUDA events in the same stream)
         r.profile([dom])
         barrier()
@@ -256,7 +290,7 @@ def run_ours(a):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                s, st = r.run_increment(*prog[k])
+                s, st = drv(r, k)
                 e1.record(stream)
                 stats.append(st)
                 times.append((e0, e1))
@@ -294,8 +328,10 @@ def run_ours(a):
     # field read back to pinned host memory
     r = FF.RVE(n, I.VOXEL_MM, cfg["grain_ids"], cfg["euler"], mat, opts, prec="mixed",
                stream=stream)
+    drv = Driver(cfg)
     for k in range(a.warmup):
-        r.run_increment(*prog[k])
+        drv(r, k)
+    mixed_ctl = cfg["stress_mask"] is not None
     host_in = torch.empty((a.steps, 10), dtype=torch.float64).pin_memory()
     for i, k in enumerate(range(a.warmup, a.warmup + a.steps)):
         host_in[i, :9] = torch.from_numpy(prog[k][0])
@@ -305,7 +341,10 @@ def run_ours(a):
     t0 = time.perf_counter()
     for i in range(a.steps):
         row = host_in[i].numpy()
-        r.run_increment(row[:9], float(row[9]))
+        if mixed_ctl:  # the guess of the stress-controlled components is the last solved F
+            drv(r, a.warmup + i)
+        else:
+            r.run_increment(row[:9], float(row[9]))
         FF.load().fields_out(r._h, FF.FIELDS["phi"][0], host_out.data_ptr(), host_out.nbytes, 0)
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
@@ -346,8 +385,7 @@ def run_ours(a):
         "vs_baseline": None,
         "dtype": "f32+f64",
         "data": "synthetic (seeded periodic Voronoi, uniform SO(3) orientations)",
-        "config": {"workload": f"{a.config}: 64^3 voxels, 50 grains, R=-1 uniaxial strain "
-                               f"0.6%, 40 increments/cycle, increments {a.warmup + 1}-"
+        "config": {"workload": f"{workload_desc(a.config, cfg)}, increments {a.warmup + 1}-"
                                f"{a.warmup + a.steps}",
                    "tolerances": a.tol, "l2": L2_NOTE, "parallelism": f"replicas x{ws}"},
         "fp64": {"value": round(value64, 1), "ms_per_step": round(f64["total_ms"] / a.steps, 3),
@@ -355,7 +393,8 @@ def run_ours(a):
         "mixed_speedup_vs_fp64": round(value / value64, 3),
         "mixed_vs_fp64_rel_l2": errs,
         "e2e": {"value": round(ws * N * a.steps / e2e_s, 1), "unit": "voxel-increments/s",
-                "h2d_bytes_per_step": 80, "d2h_bytes_per_step": 8 * N},
+                "h2d_bytes_per_step": 80 + (72 + 36 if mixed_ctl else 0),
+                "d2h_bytes_per_step": 8 * N},
         "gpu_launches": int(mx["launches"]),
         "roofline": roof,
         "clocks": mx["clocks"],
@@ -509,17 +548,17 @@ def cpu_baseline(cfg, mat, opts, a, increments=1):
     OB.build()
     threads = os.cpu_count() or 1
     r = O.RVE(cfg["n"], I.VOXEL_MM, cfg["grain_ids"], cfg["euler"], mat, opts, threads=threads)
-    prog = cfg["program"]
+    drv = Driver(cfg)
     for k in range(a.warmup):
-        r.run_increment(*prog[k])
+        drv(r, k)
     N = int(np.prod(cfg["n"]))
     t0 = time.perf_counter()
     for k in range(a.warmup, a.warmup + increments):
-        r.run_increment(*prog[k])
+        drv(r, k)
     dt = time.perf_counter() - t0
     return {"value": round(N * increments / dt, 1), "unit": "voxel-increments/s",
             "cores": threads, "kind": "oracle",
-            "sample": f"{increments} increment(s) of the same 64^3 workload "
+            "sample": f"{increments} increment(s) of the same workload "
                       f"(increment {a.warmup + 1}), {dt:.1f} s"}
 
 
@@ -534,16 +573,16 @@ def run_reference(a):
     cfg = I.build_config(a.config)
     N = int(np.prod(cfg["n"]))
     mat = I.material("baseline")
-    opts = I.solver_options(a.tol)
+    opts = workload_options(a, cfg)
     threads = os.cpu_count() or 1
     r = O.RVE(cfg["n"], I.VOXEL_MM, cfg["grain_ids"], cfg["euler"], mat, opts, threads=threads)
-    prog = cfg["program"]
+    drv = Driver(cfg)
     for k in range(a.warmup):
-        r.run_increment(*prog[k])
+        drv(r, k)
     t0 = time.perf_counter()
     done = 0
     for k in range(a.warmup, a.warmup + a.steps):
-        r.run_increment(*prog[k])
+        drv(r, k)
         done += 1
         if time.perf_counter() - t0 > a.ref_budget_s:
             break
@@ -556,8 +595,8 @@ def run_reference(a):
         "steps_timed": done,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded periodic Voronoi, uniform SO(3) orientations)",
-        "config": {"workload": f"{a.config}: 64^3 voxels, 50 grains, increments "
-                               f"{a.warmup + 1}-{a.warmup + a.steps}", "tolerances": a.tol},
+        "config": {"workload": f"{workload_desc(a.config, cfg)}, increments {a.warmup + 1}-"
+                               f"{a.warmup + a.steps}", "tolerances": a.tol},
         "cpu_baseline": {"value": round(value, 1), "unit": "voxel-increments/s",
                          "cores": threads, "kind": "oracle",
                          "sample": f"{done} full increments of the workload (increments "
