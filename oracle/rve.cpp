@@ -492,6 +492,8 @@ int orc_apply_increment(orc_rve* r, const double Fbar[9], double dt) {
 
 // Newton iteration on the fluctuation at the current macroscopic F (Eq.
 // newton with the Krylov solver of Sec. 3.1).
+static const int kDampFrom = 4;
+
 static int newton_solve(orc_rve* r, orc_stats* st) {
     const size_t N = r->N;
     const bool naive = r->o.use_naive_dft != 0;
@@ -499,6 +501,7 @@ static int newton_solve(orc_rve* r, orc_stats* st) {
     std::vector<double> K;
     std::vector<double> Ks(81 * N), Pg(9 * N);
     int status = -5;
+    double alpha = 1.0, prev_ratio = 0.0;
     for (int it = 0; it < r->o.max_newton; ++it) {
         const int nf = cp_all(r, &K, false);
         if (st) {
@@ -688,18 +691,30 @@ static int newton_solve(orc_rve* r, orc_stats* st) {
                 std::vector<double> g(N);
                 inv_real(f, s, g.data(), naive);
                 for (size_t v = 0; v < N; ++v) {
-                    r->F[(3 * i + j) * N + v] += g[v];
+                    r->F[(3 * i + j) * N + v] += alpha * g[v];
                     gmax = std::max(gmax, std::fabs(g[v]));
                 }
             }
         const double dF = std::max(maxabs_diff(r->F, r->Ft), 1e-30);
+        const double ratio = gmax / dF;
         if (std::getenv("ORACLE_VERBOSE"))
-            std::fprintf(stderr, "newton %d |b| %.3e lin %d gmax %.3e ratio %.3e\n", it, bn,
-                         lin_it, gmax, gmax / dF);
-        if (gmax / dF < r->o.tol_newton) {
+            std::fprintf(stderr, "newton %d |b| %.3e lin %d gmax %.3e ratio %.3e alpha %.4f\n",
+                         it, bn, lin_it, gmax, ratio, alpha);
+        if (ratio < r->o.tol_newton) {
             status = 0;
             break;
         }
+        // Damping (an extension; the paper's Newton takes full steps): from
+        // the kDampFrom-th iteration on, an update after which the ratio did
+        // not fall halves the length of the next (down to 1/16); one that
+        // halved the ratio doubles it back (up to a full step).  This breaks
+        // the two-cycles a kink in the slip law's tangent can trap Newton
+        // in; a Newton iteration whose ratio keeps falling is untouched.
+        if (it + 1 >= kDampFrom && ratio >= prev_ratio)
+            alpha = std::max(0.5 * alpha, 1.0 / 16);
+        else if (ratio < 0.5 * prev_ratio)
+            alpha = std::min(2.0 * alpha, 1.0);
+        prev_ratio = ratio;
     }
     return status;
 }

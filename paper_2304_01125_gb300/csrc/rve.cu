@@ -829,9 +829,17 @@ struct Impl {
     }
 
     // Newton iteration on the fluctuation at the current macroscopic F
-    // (Eq. newton with GMRES, Sec. 3.1).
+    // (Eq. newton with GMRES, Sec. 3.1).  Damping (an extension; the paper's
+    // Newton takes full steps): from the kDampFrom-th iteration on, an update
+    // after which the ratio of the Newton test did not fall halves the length
+    // of the next (down to 1/16); one that halved the ratio doubles it back
+    // (up to a full step).  This breaks the two-cycles a kink in the slip
+    // law's tangent can trap Newton in; an iteration whose ratio keeps
+    // falling is untouched.  The test itself uses the full correction.
+    static constexpr int kDampFrom = 4;
     static fft_status newton_solve(fft_rve_s* r, fft_stats* st) {
         const size_t N = r->g.N;
+        double alpha = 1.0, prev_ratio = 0.0;
         for (int it = 0; it < r->opt.max_newton; ++it) {
             if (!r->cp_valid) {
                 int nf = 0;
@@ -857,7 +865,7 @@ struct Impl {
             if (st) st->lin_it_total += lin;
             if (s != FFT_OK) return s;
             e = prof_begin(r, KF_PRECOND);
-            precond_grad<R>(r->x, 1.0, nullptr, r->Kbar, r->g, r->cb9, 0, r->st);
+            precond_grad<R>(r->x, alpha, nullptr, r->Kbar, r->g, r->cb9, 0, r->st);
             prof_end(r, KF_PRECOND, e, (double)r->g.Nh * 2 * sizeof(R) * 12);
             TRY(inv9(r));
             e = prof_begin(r, KF_FUPD);
@@ -866,11 +874,19 @@ struct Impl {
             r->launches += 2;
             TRY(fetch(r, 2));
             r->cp_valid = false;
-            const double gmax = r->hred[0], dFt = std::max(r->hred[1], 1e-30);
+            // the applied update is alpha grad(du) (alpha a power of two)
+            const double gmax = r->hred[0] / alpha, dFt = std::max(r->hred[1], 1e-30);
+            const double ratio = gmax / dFt;
             if (r->verbose)
-                std::fprintf(stderr, "newton %d |b| %.3e |Phat| %.3e lin %d gmax %.3e ratio %.3e\n",
-                             it, bn, pn, lin, gmax, gmax / dFt);
-            if (gmax / dFt < r->opt.tol_newton) return FFT_OK;
+                std::fprintf(stderr,
+                             "newton %d |b| %.3e |Phat| %.3e lin %d gmax %.3e ratio %.3e alpha %.4f\n",
+                             it, bn, pn, lin, gmax, ratio, alpha);
+            if (ratio < r->opt.tol_newton) return FFT_OK;
+            if (it + 1 >= kDampFrom && ratio >= prev_ratio)
+                alpha = std::max(0.5 * alpha, 1.0 / 16);
+            else if (ratio < 0.5 * prev_ratio)
+                alpha = std::min(2.0 * alpha, 1.0);
+            prev_ratio = ratio;
         }
         FAIL(r, FFT_ERR_NOT_CONVERGED, "Newton reached max_newton = %d", r->opt.max_newton);
     }
