@@ -106,6 +106,62 @@ def voronoi(n, n_grains, seed, h=VOXEL_MM):
     return idx.astype(np.int32), euler
 
 
+def _power_assign(n, h, centres, w):
+    """Grain id per voxel: argmin_i |x - c_i|^2 - w_i under the minimum image
+    (separable over the axes), x fastest."""
+    L = np.array(n, dtype=np.float64) * h
+    d2 = []
+    for a in range(3):
+        x = (np.arange(n[a]) + 0.5) * h
+        dx = x[:, None] - centres[None, :, a]
+        dx -= L[a] * np.round(dx / L[a])
+        d2.append(dx * dx)
+    out = np.empty((n[2], n[1], n[0]), dtype=np.int32)
+    base = d2[1][:, None, :] + d2[0][None, :, :] - w[None, None, :]  # (n1, n0, G)
+    for k in range(n[2]):
+        out[k] = np.argmin(base + d2[2][k][None, None, :], axis=2)
+    return out.reshape(-1)
+
+
+def lognormal_polycrystal(n, n_grains, sigma, seed, h=VOXEL_MM, iters=400):
+    """Periodic polycrystal with log-normal grain sizes (Sec. 4.3 and 4.4:
+    equivalent diameters log-normal, 0.1 standard deviation of the log).
+
+    Target equivalent diameters d_i = exp(sigma Z_i), scaled so that the
+    discs (n2 = 1, a plate) or balls they define fill the box; a periodic
+    Laguerre (power) tessellation, voxel -> argmin_i |x - c_i|^2 - w_i under
+    the minimum image with centres uniform in the box, whose weights are
+    moved towards the targets (w_i += eta (R_target^2 - R_cell^2) with R the
+    equivalent radius, eta 0.3 for the first half of ``iters`` rounds and 0.1
+    after) until every cell is within 2 % (or half a voxel) of its target.  Returns grain ids (int32, x
+    fastest), Euler angles (n_grains, 3) uniform on SO(3), and the target
+    diameters in mm."""
+    n = tuple(int(x) for x in n)
+    rng = np.random.default_rng(seed)
+    D = 2 if n[2] == 1 else 3
+    L = np.array(n, dtype=np.float64) * h
+    centres = rng.random((n_grains, 3)) * L
+    if D == 2:
+        centres[:, 2] = 0.5 * h
+    euler = random_orientations(rng, n_grains)
+    d = np.exp(sigma * rng.standard_normal(n_grains))
+    unit = math.pi / 4 if D == 2 else math.pi / 6  # measure of a unit-diameter disc / ball
+    d *= (np.prod(L[:D]) / (unit * np.sum(d ** D))) ** (1.0 / D)
+    vox = h ** D
+    r_t2 = (d / 2) ** 2
+    target = unit * d ** D / vox
+    w = np.zeros(n_grains)
+    for it in range(iters):
+        gid = _power_assign(n, h, centres, w)
+        cnt = np.bincount(gid, minlength=n_grains).astype(np.float64)
+        if np.all(np.abs(cnt - target) <= 0.02 * target + 0.5):
+            return gid, euler, d
+        r_c2 = (cnt * vox / unit) ** (2.0 / D) / 4
+        w += (0.3 if it < iters // 2 else 0.1) * (r_t2 - r_c2)
+    gid = _power_assign(n, h, centres, w)
+    return gid, euler, d
+
+
 def single_crystal(n, euler=(0.0, 0.0, 0.0)):
     N = int(np.prod(n))
     return np.zeros(N, dtype=np.int32), np.array([euler], dtype=np.float64)
@@ -300,6 +356,11 @@ CONFIGS = {
     "plate256_bx45": dict(n=(256, 256, 1), plate="bicrystal", boundary="45",
                           amplitude=0.02, inc_per_cycle=40, cycles=2, ratio=0,
                           seed=1006),
+    "plate256_poly62": dict(n=(256, 256, 1), plate="lognormal", grains=62, sigma=0.1,
+                            amplitude=0.02, inc_per_cycle=40, cycles=2, ratio=0, seed=1008),
+    "poly128_ln64": dict(n=(128, 128, 128), grains=64, sigma=0.1, amplitude=0.02,
+                         inc_per_cycle=40, cycles=2, precrack=False, seed=1009, ratio=0,
+                         control="uniaxial_stress"),
     "plate256x128_notch": dict(n=(256, 128, 1), plate="notched", grains=40, buffer=8,
                                notch=16, amplitude=0.01, inc_per_cycle=40, cycles=2, ratio=0,
                                seed=1007),
@@ -320,6 +381,8 @@ def build_config(name, n_override=None):
         return _plate_config(c, n)
     if c["grains"] == 1:
         gid, eul = single_crystal(n)
+    elif "sigma" in c:
+        gid, eul, _ = lognormal_polycrystal(n, c["grains"], c["sigma"], c["seed"])
     else:
         gid, eul = voronoi(n, c["grains"], c["seed"])
     phi0 = mask = None
@@ -341,7 +404,8 @@ def build_config(name, n_override=None):
 
 def _plate_config(c, n):
     """Plates of Sec. 4 (2-D, one voxel thick): single crystal with a central
-    soft pre-crack (length scaled with n0), periodic bicrystal, notched
+    soft pre-crack (length scaled with n0), periodic bicrystal, polycrystal
+    with log-normal grain sizes (Sec. 4.3), notched
     polycrystal between free-surface buffer layers (loaded along x).  Plane
     stress: the lateral in-plane and the out-of-plane normal mean stresses
     are held at zero."""
@@ -350,6 +414,8 @@ def _plate_config(c, n):
     if c["plate"] == "single":
         gid, eul = single_crystal(n, c["euler"])
         phi0, mask = plate_precrack(n, max(2, c["crack"] * n[0] // 256))
+    elif c["plate"] == "lognormal":
+        gid, eul, _ = lognormal_polycrystal(n, c["grains"], c["sigma"], c["seed"])
     elif c["plate"] == "bicrystal":
         rng = np.random.default_rng(c["seed"])
         ea, eb = random_orientations(rng, 2)

@@ -117,3 +117,36 @@ def test_plate_configs():
     assert np.all(phi[8:24, 127:129] == 1) and np.all(phi[24:120, 127:129] == 0)
     assert c["stress_mask"].tolist() == [0, 0, 0, 0, 1, 0, 0, 0, 1]
     assert c["program"][0][0][0] > 1.0 and c["program"][0][0][4] == 1.0
+
+
+@pytest.mark.parametrize("n,grains,sigma", [((96, 96, 1), 40, 0.3), ((32, 32, 32), 40, 0.5)])
+def test_lognormal_polycrystal(n, grains, sigma):
+    """Log-normal grain sizes (Sec. 4.3, 4.4): every grain present, each
+    cell's size within 2 % (or half a voxel) of its log-normal target, the
+    measured equivalent diameters carrying the targets' order and log spread,
+    and the targets filling the box."""
+    from scipy.stats import spearmanr
+    gid, eul, d = I.lognormal_polycrystal(n, grains, sigma, 3)
+    D = 2 if n[2] == 1 else 3
+    unit = np.pi / 4 if D == 2 else np.pi / 6
+    h = I.VOXEL_MM
+    cnt = np.bincount(gid, minlength=grains)
+    target = unit * d ** D / h ** D
+    assert gid.size == int(np.prod(n)) and eul.shape == (grains, 3)
+    assert np.all(cnt > 0) and np.all(np.abs(cnt - target) <= 0.02 * target + 0.5)
+    assert abs(target.sum() - gid.size) < 1e-6 * gid.size
+    de = (cnt * h ** D / unit) ** (1.0 / D)
+    assert spearmanr(d, de).correlation > 0.99
+    assert abs(np.log(de).std() - np.log(d).std()) < 0.02
+    g2, e2, d2 = I.lognormal_polycrystal(n, grains, sigma, 3)
+    assert np.array_equal(gid, g2) and np.array_equal(eul, e2)
+
+
+def test_lognormal_configs():
+    c = I.build_config("plate256_poly62", n_override=(64, 64, 1))
+    assert len(np.unique(c["grain_ids"])) == 62 and c["stress_mask"] is not None
+    c = I.build_config("poly128_ln64", n_override=(24, 24, 24))
+    assert len(np.unique(c["grain_ids"])) == 64
+    assert np.array_equal(c["stress_mask"], I.uniaxial_stress_mask(1))
+    eps = np.array([F[4] - 1.0 for F, _ in c["program"]])
+    assert abs(eps.max() - 0.02) < 1e-15 and eps.min() >= 0.0
