@@ -280,10 +280,10 @@ GENERIC = (0.3, 0.9, 1.7)  # Bunge angles with no symmetric multi-slip along y
     ("plate256_bx45", None, 350.0, "mixed", None)])
 def test_plate_plane_stress(config, euler, tau_c0, prec, tol):
     """2-D plates (16 x 16 x 1: rank-2 transforms, xi_z = 0) under plane
-    stress on the R = 0 loading, five increments, into plasticity, against
+    stress on the R = 0 loading, five increments into plasticity, against
     the oracle: the single crystal with its central soft pre-crack (the [100]
-    orientation of Sec. 4.1, and a generic one) and the periodic bicrystal
-    with boundaries at 45 degrees to the load.
+    orientation of Sec. 4.1, and a generic one, three increments) and the
+    periodic bicrystal with boundaries at 45 degrees to the load.
 
     [100] along y loads eight slip systems equally: in the nearly
     rate-independent slip law (Delta V / k T of about 76 per MPa) the split of
@@ -298,7 +298,8 @@ def test_plate_plane_stress(config, euler, tau_c0, prec, tol):
     cfg = I.build_config(config, n_override=n)
     eul = cfg["euler"] if euler is None else np.array([euler], dtype=np.float64)
     mat = dict(MAT, tau_c0=tau_c0)
-    o, Fo = _mixed_parity(prec, n, cfg["grain_ids"], eul, mat, cfg["program"][:5],
+    incs = 3 if euler is not None else 5  # the generic orientation yields at once
+    o, Fo = _mixed_parity(prec, n, cfg["grain_ids"], eul, mat, cfg["program"][:incs],
                           cfg["stress_mask"], cfg["phi0"], cfg["elastic_only"], tol)
     assert Fo[0] < 1.0 and Fo[8] < 1.0
     assert np.abs(o.field("Fp") - np.eye(3).reshape(9, 1)).max() > 1e-6
