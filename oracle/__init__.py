@@ -26,7 +26,8 @@ class Options(C.Structure):
                 ("tol_pf", C.c_double), ("tol_local", C.c_double),
                 ("max_stag", C.c_int), ("max_newton", C.c_int), ("max_lin", C.c_int),
                 ("max_pf", C.c_int), ("max_local", C.c_int), ("restart", C.c_int),
-                ("use_naive_dft", C.c_int), ("n_threads", C.c_int), ("max_cutbacks", C.c_int)]
+                ("use_naive_dft", C.c_int), ("n_threads", C.c_int), ("max_cutbacks", C.c_int),
+                ("derivative", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -119,6 +120,7 @@ def options(opts, naive=False, threads=0):
     o.use_naive_dft = 1 if naive else 0
     o.n_threads = int(threads)
     o.max_cutbacks = int(opts.get("max_cutbacks", 0))
+    o.derivative = {"spectral": 0, "willot": 1}[opts.get("derivative", "spectral")]
     return o
 
 

@@ -65,6 +65,8 @@ typedef struct {
     int n_threads;          /* 0: hardware concurrency */
     int max_cutbacks;       /* 0: off; else a non-converged increment is redone as two
                                halves from the committed state, down to this depth */
+    int derivative;         /* mechanical derivatives: 0 spectral (i xi, Sec. 3.1),
+                               1 Willot's rotated finite differences */
 } orc_options;
 
 typedef struct {

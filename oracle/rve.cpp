@@ -42,8 +42,10 @@ int cp_point(const orc_material& m, const M3& Q, const M3& F, const M3& FpL, dou
 struct Freq {
     int n[3];
     size_t N;
+    double h;
     std::vector<double> xi[3];   // full frequency per axis index
     std::vector<double> xid[3];  // derivative frequency (Nyquist -> 0)
+    std::vector<cplx> shift[3];  // exp(i xi h): a shift by one voxel along the axis
 };
 static Freq make_freq(const int n[3], double h) {
     Freq f;
@@ -58,10 +60,63 @@ static Freq make_freq(const int n[3], double h) {
             f.xi[d][mm] = 2.0 * M_PI * kk / L;
             const bool nyq = (n[d] % 2 == 0) && (kk == -n[d] / 2);
             f.xid[d][mm] = nyq ? 0.0 : f.xi[d][mm];
+            // exactly -1 at the Nyquist index, so that the rotated scheme's
+            // factor (1 + e) vanishes there (its null modes) without round-off
+            f.shift[d].push_back(nyq ? cplx(-1.0, 0.0) : std::polar(1.0, 2.0 * M_PI * kk / n[d]));
         }
     }
     f.N = (size_t)n[0] * n[1] * n[2];
+    f.h = h;
     return f;
+}
+
+// Willot's rotated finite-difference derivative (Willot 2015, Comptes Rendus
+// Mecanique 343): the forward difference along j averaged over the four cell
+// edges parallel to j, i.e. in Fourier D_j = (e_j - 1)/h prod_{l != j} (1 +
+// e_l)/2 with e_l = exp(i xi_l h).  It replaces i xi_j in the gradient; its
+// adjoint -conj(D_j) replaces i xi_j in the divergence.
+static inline void willot_symbol(const Freq& f, size_t v, cplx D[3]) {
+    const int idx[3] = {(int)(v % f.n[0]), (int)((v / f.n[0]) % f.n[1]),
+                        (int)(v / ((size_t)f.n[0] * f.n[1]))};
+    cplx e[3];
+    for (int d = 0; d < 3; ++d) e[d] = f.shift[d][idx[d]];
+    for (int j = 0; j < 3; ++j) {
+        cplx s = (e[j] - 1.0) / f.h;
+        for (int l = 0; l < 3; ++l)
+            if (l != j) s *= 0.5 * (1.0 + e[l]);
+        D[j] = s;
+    }
+}
+
+// Green preconditioner of the rotated scheme at one frequency:
+// [conj(D) . Kbar . D]^-1, a Hermitian 3 x 3 inverted by cofactors; zero
+// where D = 0 (the zero frequency and the scheme's null modes).
+static void green_willot(const double* Kbar, const cplx D[3], cplx Minv[9]) {
+    if (std::abs(D[0]) == 0 && std::abs(D[1]) == 0 && std::abs(D[2]) == 0) {
+        for (int i = 0; i < 9; ++i) Minv[i] = 0.0;
+        return;
+    }
+    cplx A[9];
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) {
+            cplx s = 0.0;
+            for (int j = 0; j < 3; ++j)
+                for (int l = 0; l < 3; ++l)
+                    s += std::conj(D[j]) * Kbar[9 * (3 * i + j) + 3 * k + l] * D[l];
+            A[3 * i + k] = s;
+        }
+    const cplx c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8],
+               c02 = A[3] * A[7] - A[4] * A[6];
+    const cplx det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    Minv[0] = c00 / det;
+    Minv[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+    Minv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+    Minv[3] = c01 / det;
+    Minv[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+    Minv[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+    Minv[6] = c02 / det;
+    Minv[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+    Minv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
 }
 static inline void kvec(const Freq& f, size_t v, double xi[3], double xid[3]) {
     const int a = v % f.n[0], b = (v / f.n[0]) % f.n[1], c = v / ((size_t)f.n[0] * f.n[1]);
@@ -500,6 +555,22 @@ static int newton_solve(orc_rve* r, orc_stats* st) {
     const Freq& f = r->f;
     std::vector<double> K;
     std::vector<double> Ks(81 * N), Pg(9 * N);
+    // derivative symbols: i xi_j (spectral, Nyquist dropped) or Willot's D_j
+    // for the gradient; i xi_j or -conj(D_j) for the divergence
+    const bool willot = r->o.derivative == 1;
+    auto dsym = [&](size_t v, int j) -> cplx {
+        if (willot) {
+            cplx D[3];
+            willot_symbol(f, v, D);
+            return D[j];
+        }
+        double xi[3], xid[3];
+        kvec(f, v, xi, xid);
+        return cplx(0.0, xid[j]);
+    };
+    auto dsym_div = [&](size_t v, int j) -> cplx {
+        return willot ? -std::conj(dsym(v, j)) : dsym(v, j);
+    };
     int status = -5;
     double alpha = 1.0, prev_ratio = 0.0;
     for (int it = 0; it < r->o.max_newton; ++it) {
@@ -526,8 +597,17 @@ static int newton_solve(orc_rve* r, orc_stats* st) {
             bvec[i].assign(N, 0.0);
             x[i].assign(N, 0.0);
         }
-        std::vector<double> Minv(9 * N);
+        std::vector<double> Minv(willot ? 0 : 9 * N);
+        std::vector<cplx> MinvW(willot ? 9 * N : 0);
         for (size_t v = 0; v < N; ++v) {
+            if (willot) {
+                cplx D[3];
+                willot_symbol(f, v, D);
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) bvec[i][v] -= Ph[3 * i + j][v] * std::conj(D[j]);
+                green_willot(Kbar, D, &MinvW[9 * v]);
+                continue;
+            }
             double xi[3], xid[3];
             kvec(f, v, xi, xid);
             for (int i = 0; i < 3; ++i)
@@ -539,7 +619,9 @@ static int newton_solve(orc_rve* r, orc_stats* st) {
             for (int i = 0; i < 3; ++i) out[i].assign(N, 0.0);
             for (size_t v = 0; v < N; ++v)
                 for (int i = 0; i < 3; ++i)
-                    for (int k = 0; k < 3; ++k) out[i][v] += Minv[9 * v + 3 * i + k] * in[k][v];
+                    for (int k = 0; k < 3; ++k)
+                        out[i][v] += (willot ? MinvW[9 * v + 3 * i + k] : Minv[9 * v + 3 * i + k]) *
+                                     in[k][v];
         };
         // A' u = -F{g K : F^-1{u (x) i xi}} . i xi
         auto apply_op = [&](const Vec3& u, Vec3& out) {
@@ -547,11 +629,7 @@ static int newton_solve(orc_rve* r, orc_stats* st) {
             for (int i = 0; i < 3; ++i)
                 for (int j = 0; j < 3; ++j) {
                     std::vector<cplx> s(N);
-                    for (size_t v = 0; v < N; ++v) {
-                        double xi[3], xid[3];
-                        kvec(f, v, xi, xid);
-                        s[v] = u[i][v] * cplx(0.0, xid[j]);
-                    }
+                    for (size_t v = 0; v < N; ++v) s[v] = u[i][v] * dsym(v, j);
                     inv_real(f, s, G.data() + (3 * i + j) * N, naive);
                 }
             for (size_t v = 0; v < N; ++v)
@@ -563,12 +641,9 @@ static int newton_solve(orc_rve* r, orc_stats* st) {
             std::vector<std::vector<cplx>> Th(9);
             for (int c = 0; c < 9; ++c) fwd(f, T.data() + c * N, Th[c], naive);
             for (int i = 0; i < 3; ++i) out[i].assign(N, 0.0);
-            for (size_t v = 0; v < N; ++v) {
-                double xi[3], xid[3];
-                kvec(f, v, xi, xid);
+            for (size_t v = 0; v < N; ++v)
                 for (int i = 0; i < 3; ++i)
-                    for (int j = 0; j < 3; ++j) out[i][v] -= Th[3 * i + j][v] * cplx(0.0, xid[j]);
-            }
+                    for (int j = 0; j < 3; ++j) out[i][v] -= Th[3 * i + j][v] * dsym_div(v, j);
         };
         auto dot = [&](const Vec3& a, const Vec3& b) {
             double s = 0;
@@ -588,12 +663,9 @@ static int newton_solve(orc_rve* r, orc_stats* st) {
         const double bn = std::sqrt(dot(bv, bv));
         // round-off scale of b: ||F{gP}_ij xi_j|| before the sum over j
         double pn = 0;
-        for (size_t v = 0; v < N; ++v) {
-            double xi[3], xid[3];
-            kvec(f, v, xi, xid);
+        for (size_t v = 0; v < N; ++v)
             for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) pn += std::norm(Ph[3 * i + j][v]) * xid[j] * xid[j];
-        }
+                for (int j = 0; j < 3; ++j) pn += std::norm(Ph[3 * i + j][v]) * std::norm(dsym(v, j));
         pn = std::sqrt(pn);
         const double target = std::max(r->o.tol_lin * bn, 1e-12 * pn);
         int lin_it = 0;
@@ -683,11 +755,7 @@ static int newton_solve(orc_rve* r, orc_stats* st) {
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) {
                 std::vector<cplx> s(N);
-                for (size_t v = 0; v < N; ++v) {
-                    double xi[3], xid[3];
-                    kvec(f, v, xi, xid);
-                    s[v] = x[i][v] * cplx(0.0, xid[j]);
-                }
+                for (size_t v = 0; v < N; ++v) s[v] = x[i][v] * dsym(v, j);
                 std::vector<double> g(N);
                 inv_real(f, s, g.data(), naive);
                 for (size_t v = 0; v < N; ++v) {

@@ -151,6 +151,9 @@ def _material(params):
 
 
 def _options(opts, prec, stream):
+    if opts.get("derivative", "spectral") != "spectral":
+        raise NotImplementedError("the CUDA path takes the spectral derivatives of Sec. 3.1 "
+                                  "only; Willot's rotated scheme is in the oracle")
     o = Options()
     for k in ("tol_stag", "tol_newton", "tol_lin", "tol_pf", "tol_local"):
         setattr(o, k, float(opts[k]))

@@ -76,3 +76,13 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu():
     assert L.run_increment_mixed(None, F9, None, m9, 1.0, None) == FF.FFT_ERR_ARG
     assert L.apply_increment_mixed(None, F9, None, None, 1.0) == FF.FFT_ERR_ARG
     assert L.rve_device_bytes(None) == 0
+
+
+def test_willot_derivatives_refused_by_the_cuda_binding():
+    """The CUDA path has spectral derivatives only: asking for Willot's
+    scheme fails before any handle is made instead of running spectral."""
+    import pytest
+    from paper_2304_01125_gb300 import fatiguefft as FF
+    from paper_2304_01125_gb300 import inputs as I
+    with pytest.raises(NotImplementedError):
+        FF._options(I.solver_options("paper", derivative="willot"), "mixed", None)
