@@ -775,3 +775,25 @@ def test_willot_matches_real_space_finite_differences(scheme):
         assert err < 1e-5
     else:
         assert err > 1e-3
+
+
+def test_damped_newton_passes_the_yield_plateau():
+    """The paper's loading (2 %, R = 0) under uniaxial stress on an 8^3,
+    50-grain cell: near 1.1 % strain the full-step Newton falls into a
+    two-cycle (the ratio of its test stuck near 0.2, |b| alternating between
+    two values); with the damping of the update on stagnation every
+    increment up to there converges without cut-back and holds the lateral
+    stresses at zero."""
+    cfg = I.build_config("poly64_r0", n_override=(8, 8, 8))
+    mat = I.material("baseline")
+    opts = I.solver_options("paper")
+    r = O.RVE(cfg["n"], I.VOXEL_MM, cfg["grain_ids"], cfg["euler"], mat, opts)
+    F = None
+    for k in range(12):
+        a, kw = I.increment_args(cfg, k, F)
+        s, st = r.run_increment(*a, **kw)
+        assert s == 0 and st["cutbacks"] == 0, (k, st)
+        F = np.array(st["Fbar"])
+        P = np.array(st["Pbar"])
+        assert max(abs(P[0]), abs(P[8])) <= opts["tol_newton"] * np.abs(P).max()
+    assert F[4] - 1.0 > 0.0119 and P[4] > 1000.0  # past the yield plateau
