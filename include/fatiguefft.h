@@ -194,6 +194,25 @@ fft_status fields_out(fft_rve_t r, int field, void* dst, size_t bytes, int dst_i
  * history sums restart with a zero compensation term. */
 fft_status fields_in(fft_rve_t r, int field, const double* src, size_t bytes);
 
+/* Checkpoint of the committed state (not in the paper; the state Algorithm 1
+ * carries from one increment to the next): F_t, F_p (lattice-frame inverse),
+ * phi_t and the FP64 history with its compensation terms, in the handle's
+ * precision, plus the committed macroscopic F.  Grain ids, orientations,
+ * material and options are not included: a checkpoint is loaded into a
+ * handle created with the same ones.
+ * state_save: dst == NULL sets *bytes to the size needed; otherwise *bytes
+ * is the capacity of dst (host memory, caller-owned), the checkpoint is
+ * written, *bytes set to its size and the stream synchronised.  A converged
+ * but uncommitted increment of the stage calls is not included.
+ * FFT_ERR_ARG: NULL handle or bytes, or capacity too small.
+ * state_load: restores a checkpoint of a handle with the same grid and
+ * precision (else FFT_ERR_ARG) as the committed state and the current
+ * iterate; the next increment then reproduces, bit for bit, the run the
+ * checkpoint was taken from.  Any earlier failed or uncommitted increment is
+ * discarded. */
+fft_status state_save(fft_rve_t r, void* dst, size_t* bytes);
+fft_status state_load(fft_rve_t r, const void* src, size_t bytes);
+
 /* Stage entry points (same kernels as the increment uses), for checking one
  * stage at a time.  eval_constitutive: constitutive update at the current F
  * with the committed history; with_history = 1 also evaluates W_e+, the

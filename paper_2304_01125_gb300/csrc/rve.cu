@@ -1233,6 +1233,37 @@ static fft_status ensure_stage(fft_rve_s* r, size_t bytes) {
     return FFT_OK;
 }
 
+// Checkpoint layout (state_save / state_load): a fixed header, then the
+// committed fields in the handle's bulk type (F_t 9N, the lattice-frame
+// F_p^-1 9N, phi_t N) and the FP64 history with its compensation terms
+// (HIST_SLOTS N).  These fix the next increment completely: the trial
+// history and F_p^-1 are rewritten before they are read, GMRES starts from
+// zero, the phase field from phi_t and rho_GND is recomputed from F_p.
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int32_t version, prec, n[3], esz;
+    uint64_t N;
+    double Fbar_t[9];
+};
+constexpr char kCkptMagic[8] = {'F', 'F', 'T', 'C', 'K', 'P', 'T', '1'};
+size_t ckpt_bytes(const fft_rve_s* r) {
+    const size_t N = r->g.N;
+    return sizeof(CkptHeader) + 19 * N * r->esz + (size_t)HIST_SLOTS * N * sizeof(double);
+}
+struct CkptPart {
+    void* dev;
+    size_t bytes;
+};
+void ckpt_parts(fft_rve_s* r, CkptPart out[4]) {
+    const size_t N = r->g.N;
+    out[0] = {r->Ht, 9 * N * r->esz};
+    out[1] = {r->Hpi_t, 9 * N * r->esz};
+    out[2] = {r->phi_t, N * r->esz};
+    out[3] = {r->hist_c, (size_t)HIST_SLOTS * N * sizeof(double)};
+}
+}  // namespace
+
 extern "C" {
 
 fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_ids, int n_grains,
@@ -1513,6 +1544,70 @@ fft_status fields_in(fft_rve_t r, int field, const double* src, size_t bytes) {
     if (s == FFT_OK) s = DISPATCH(r, fields_in(r, field, r->stage));
     if (cudaStreamSynchronize(r->st) != cudaSuccess && s == FFT_OK) s = FFT_ERR_CUDA;
     return s;
+}
+
+fft_status state_save(fft_rve_t r, void* dst, size_t* bytes) {
+    if (!r || !bytes) return FFT_ERR_ARG;
+    const size_t need = ckpt_bytes(r);
+    if (!dst) {
+        *bytes = need;
+        return FFT_OK;
+    }
+    if (*bytes < need) FAIL(r, FFT_ERR_ARG, "state_save: %zu bytes < %zu", *bytes, need);
+    CkptHeader h{};
+    std::memcpy(h.magic, kCkptMagic, sizeof(h.magic));
+    h.version = 1;
+    h.prec = r->prec;
+    h.n[0] = r->g.n0;
+    h.n[1] = r->g.n1;
+    h.n[2] = r->g.n2;
+    h.esz = (int32_t)r->esz;
+    h.N = r->g.N;
+    std::memcpy(h.Fbar_t, r->Fbar_t, sizeof(h.Fbar_t));
+    std::memcpy(dst, &h, sizeof(h));
+    char* p = (char*)dst + sizeof(h);
+    CkptPart parts[4];
+    ckpt_parts(r, parts);
+    for (const CkptPart& c : parts) {
+        CK(r, cudaMemcpyAsync(p, c.dev, c.bytes, cudaMemcpyDeviceToHost, r->st));
+        p += c.bytes;
+    }
+    CK(r, cudaStreamSynchronize(r->st));
+    *bytes = need;
+    return FFT_OK;
+}
+
+fft_status state_load(fft_rve_t r, const void* src, size_t bytes) {
+    if (!r || !src) return FFT_ERR_ARG;
+    CkptHeader h;
+    if (bytes < sizeof(h)) FAIL(r, FFT_ERR_ARG, "state_load: %zu bytes is no checkpoint", bytes);
+    std::memcpy(&h, src, sizeof(h));
+    if (std::memcmp(h.magic, kCkptMagic, sizeof(h.magic)) != 0 || h.version != 1)
+        FAIL(r, FFT_ERR_ARG, "state_load: not a checkpoint of this library");
+    if (h.prec != r->prec || h.esz != (int32_t)r->esz || h.n[0] != r->g.n0 ||
+        h.n[1] != r->g.n1 || h.n[2] != r->g.n2 || h.N != (uint64_t)r->g.N)
+        FAIL(r, FFT_ERR_ARG, "state_load: checkpoint of another grid or precision");
+    const size_t need = ckpt_bytes(r);
+    if (bytes < need) FAIL(r, FFT_ERR_ARG, "state_load: %zu bytes < %zu", bytes, need);
+    const char* p = (const char*)src + sizeof(h);
+    CkptPart parts[4];
+    ckpt_parts(r, parts);
+    for (const CkptPart& c : parts) {
+        CK(r, cudaMemcpyAsync(c.dev, p, c.bytes, cudaMemcpyHostToDevice, r->st));
+        p += c.bytes;
+    }
+    // the current iterate restarts at the committed state
+    CK(r, cudaMemcpyAsync(r->H, r->Ht, 9 * r->g.N * r->esz, cudaMemcpyDeviceToDevice, r->st));
+    CK(r, cudaMemcpyAsync(r->phi, r->phi_t, r->g.N * r->esz, cudaMemcpyDeviceToDevice, r->st));
+    CK(r, cudaStreamSynchronize(r->st));
+    std::memcpy(r->Fbar_t, h.Fbar_t, sizeof(r->Fbar_t));
+    std::memcpy(r->Fbar, h.Fbar_t, sizeof(r->Fbar));
+    r->state = ST_COMMITTED;
+    r->converged = false;
+    r->cp_valid = false;
+    r->mixed = false;
+    r->stag_it = 0;
+    return FFT_OK;
 }
 
 fft_status eval_constitutive(fft_rve_t r, double dt, int with_history, int* local_fail) {

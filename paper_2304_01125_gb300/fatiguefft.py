@@ -30,7 +30,7 @@ SYMBOLS = ["init_rve", "apply_increment", "solve_equilibrium", "update_damage",
            "rve_kernel_launches", "rve_profile", "rve_profile_read",
            "degraded_average_noalloc", "batch_create", "batch_run_increment", "batch_size",
            "batch_destroy", "fft_selftest_bounded_wait", "apply_increment_mixed",
-           "run_increment_mixed"]
+           "run_increment_mixed", "state_save", "state_load"]
 KERNEL_FAMILIES = ["constitutive", "tangent_apply", "precond_grad", "contract", "gmres_dot",
                    "gs_update", "gmres_xupdate", "kbar", "residual", "f_update", "phase_field",
                    "gnd", "cufft_9field", "cufft_scalar", "reductions", "other"]
@@ -92,6 +92,8 @@ def load(path=LIB_PATH):
                                       C.POINTER(Stats)]
     L.fields_out.argtypes = [vp, C.c_int, C.c_void_p, C.c_size_t, C.c_int]
     L.fields_in.argtypes = [vp, C.c_int, C.c_void_p, C.c_size_t]
+    L.state_save.argtypes = [vp, C.c_void_p, C.POINTER(C.c_size_t)]
+    L.state_load.argtypes = [vp, C.c_void_p, C.c_size_t]
     L.eval_constitutive.argtypes = [vp, C.c_double, C.c_int, C.POINTER(C.c_int)]
     L.eval_gnd.argtypes = [vp]
     L.solve_phase_field.argtypes = [vp, C.POINTER(C.c_int)]
@@ -124,7 +126,7 @@ def load(path=LIB_PATH):
     for t in ("init_rve", "apply_increment", "solve_equilibrium", "update_damage",
               "commit_increment", "run_increment", "fields_out", "fields_in",
               "eval_constitutive", "eval_gnd", "solve_phase_field", "apply_increment_mixed",
-              "run_increment_mixed"):
+              "run_increment_mixed", "state_save", "state_load"):
         getattr(L, t).restype = C.c_int
     _lib = L
     return L
@@ -258,6 +260,19 @@ class RVE:
         if check:
             self._check(call, s)
         return s, st.as_dict()
+
+    def state_save(self):
+        """Checkpoint of the committed state (state_save), as bytes."""
+        n = C.c_size_t(0)
+        self._check("state_save", load().state_save(self._h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check("state_save", load().state_save(self._h, buf, C.byref(n)))
+        return buf.raw[:n.value]
+
+    def state_load(self, data):
+        """Restore a checkpoint from state_save (state_load)."""
+        b = bytes(data)
+        self._check("state_load", load().state_load(self._h, b, len(b)))
 
     def field(self, name):
         fid, nc = FIELDS[name]

@@ -76,6 +76,9 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu():
     assert L.run_increment_mixed(None, F9, None, m9, 1.0, None) == FF.FFT_ERR_ARG
     assert L.apply_increment_mixed(None, F9, None, None, 1.0) == FF.FFT_ERR_ARG
     assert L.rve_device_bytes(None) == 0
+    nb = C.c_size_t(0)
+    assert L.state_save(None, None, C.byref(nb)) == FF.FFT_ERR_ARG
+    assert L.state_load(None, b"x" * 16, 16) == FF.FFT_ERR_ARG
 
 
 def test_willot_derivatives_refused_by_the_cuda_binding():

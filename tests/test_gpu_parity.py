@@ -532,3 +532,40 @@ def test_mixed_cracked_set_matches_fp64():
         assert np.array_equal((p64 >= thr)[clear], (p32 >= thr)[clear]), thr
     assert rel(fields["mixed"]["P"], fields["fp64"]["P"]) < 1e-3
     assert rel(p32, p64, floor=1e-4 * np.sqrt(p64.size)) < 5e-3
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_checkpoint_resume_is_bitwise(prec):
+    """state_save / state_load: three increments into plasticity, a
+    checkpoint, two more increments; a fresh handle loaded from the
+    checkpoint and given the same two increments ends in the same state bit
+    for bit (current and committed fields, the history sums, the last
+    increment's iteration counts).  A checkpoint of another grid is
+    refused."""
+    n = (8, 6, 5)
+    gid, eul = I.voronoi(n, 3, 21)
+    mat = dict(MAT, tau_c0=250.0)
+    prog = I.uniaxial_cycle_program(0.006, 24, 1)[:5]
+    opts = opts_for(prec)
+    a = FF.RVE(n, H, gid, eul, mat, opts, prec=prec, stream=stream())
+    for Fb, dt in prog[:3]:
+        a.run_increment(Fb, dt)
+    ck = a.state_save()
+    for Fb, dt in prog[3:]:
+        _, sta = a.run_increment(Fb, dt)
+    b = FF.RVE(n, H, gid, eul, mat, opts, prec=prec, stream=stream())
+    b.state_load(ck)
+    for Fb, dt in prog[3:]:
+        _, stb = b.run_increment(Fb, dt)
+    for f in ("F", "Ft", "P", "phi", "phi_t", "Fp", "rho_ssd", "rho_gnd", "Wp", "Gs", "Hmax",
+              "Wcrit", "gamma"):
+        assert np.array_equal(a.field(f), b.field(f)), f
+    for k in ("newton_it", "lin_it_total", "stag_it", "mixed_it"):
+        assert sta[k] == stb[k], k
+    assert np.abs(a.field("Fp") - np.eye(3).reshape(9, 1)).max() > 1e-6
+    c = FF.RVE((8, 6, 4), H, np.zeros(192, dtype=np.int32), eul[:1], mat, opts, prec=prec,
+               stream=stream())
+    with pytest.raises(FF.FFTError):
+        c.state_load(ck)
+    for r in (a, b, c):
+        r.close()
