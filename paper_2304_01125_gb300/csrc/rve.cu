@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "fatiguefft.h"
 #include "launch.h"
@@ -29,6 +31,27 @@ static_assert(kSlotLen <= kSlot, "host slot too small");
 static_assert(kDslot + kSlotLen <= kRedSlots, "device slot outside the reduction buffer");
 static_assert(3 + 2 * (kMaxKrylov - 1) <= kDslot, "Arnoldi dots overlap the device slot");
 }  // namespace
+
+// NVTX range over one stage of Algorithm 1, in the library's own domain
+// ("fatiguefft"), so that profilers show the stages without touching the
+// caller's default-domain ranges; a no-op without a tool attached.
+static nvtxDomainHandle_t nvtx_domain() {
+    static nvtxDomainHandle_t d = nvtxDomainCreateA("fatiguefft");
+    return d;
+}
+struct NvtxRange {
+    explicit NvtxRange(const char* name) {
+        nvtxEventAttributes_t a = {};
+        a.version = NVTX_VERSION;
+        a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+        a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+        a.message.ascii = name;
+        nvtxDomainRangePushEx(nvtx_domain(), &a);
+    }
+    ~NvtxRange() { nvtxDomainRangePop(nvtx_domain()); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct fft_rve_s {
     int prec = 0;
@@ -418,6 +441,7 @@ struct Impl {
     }
 
     static fft_status cp(fft_rve_s* r, bool hist, int* fails) {
+        NvtxRange nvtx_("constitutive");
         CPFields f;
         f.H = r->H;
         f.Hpi = r->Hpi_t;
@@ -628,6 +652,7 @@ struct Impl {
     // correction arrives with step k + 1 and is of the order of the FP
     // rounding of the first projection.
     static fft_status gmres(fft_rve_s* r, double bn, double pn, int* its) {
+        NvtxRange nvtx_("gmres");
         const size_t Nh = r->g.Nh, n3 = 3 * Nh;
         const double es = (double)sizeof(R);
         // round-off floor relative to the scale of the terms summed into b
@@ -738,6 +763,7 @@ struct Impl {
     }
 
     static fft_status solve_equilibrium(fft_rve_s* r, fft_stats* st) {
+        NvtxRange nvtx_("equilibrium");
         if (r->state != ST_APPLIED && r->state != ST_DAMAGE)
             FAIL(r, FFT_ERR_STATE, "solve_equilibrium before apply_increment");
         const size_t N = r->g.N;
@@ -764,6 +790,7 @@ struct Impl {
     // (solved on the host) and dF added uniformly to F.  done when
     // max_S |<gP> - P*| <= tol_newton max(max|<gP>|, 1 MPa).
     static fft_status mixed_step(fft_rve_s* r, fft_stats* st, int outer, bool* done) {
+        NvtxRange nvtx_("mixed_control");
         const size_t N = r->g.N;
         int nf = 0;
         TRY(cp(r, false, &nf));
@@ -940,6 +967,7 @@ struct Impl {
     // phase-field solve (or phi = phi_t when S = 0 everywhere) and clamp;
     // out: max|phi_new - phi_old|, max|phi_new - phi_t|, changed, cracked.
     static fft_status phase_field(fft_rve_s* r, int* iters, double* out4) {
+        NvtxRange nvtx_("phase_field");
         const size_t N = r->g.N;
         maxval<R>(r->drive, N, red_at(r, r->red), r->st);
         r->launches += 1;
@@ -958,6 +986,7 @@ struct Impl {
     }
 
     static fft_status update_damage(fft_rve_s* r, fft_stats* st) {
+        NvtxRange nvtx_("damage");
         if (r->state != ST_EQUIL) FAIL(r, FFT_ERR_STATE, "update_damage before solve_equilibrium");
         const size_t N = r->g.N;
         r->stag_it += 1;
@@ -1013,6 +1042,7 @@ struct Impl {
     }
 
     static fft_status apply_increment(fft_rve_s* r, const double* Fbar, double dt) {
+        NvtxRange nvtx_("apply_increment");
         if (r->state == ST_DAMAGE && r->converged) TRY(commit(r));
         r->mixed = false;
         double d[9];
@@ -1035,6 +1065,7 @@ struct Impl {
     }
 
     static fft_status commit(fft_rve_s* r) {
+        NvtxRange nvtx_("commit");
         if (r->state != ST_DAMAGE || !r->converged)
             FAIL(r, FFT_ERR_STATE, "commit without a converged increment");
         const size_t N = r->g.N;
