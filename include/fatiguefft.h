@@ -280,10 +280,16 @@ const char* fft_last_error(fft_rve_t r);
  * (row-major per handle), dt n doubles, stats n entries (may be NULL),
  * status n ints (may be NULL) receive each handle's own result; returns
  * FFT_OK or the first failing handle's status (the others still ran).
- * A failed handle behaves as after its own failed run_increment. */
+ * A failed handle behaves as after its own failed run_increment.
+ * batch_run_increment_mixed = run_increment_mixed on every handle, with the
+ * same layouts plus Pbar 9n doubles (may be NULL: zero targets) and mask 9n
+ * int32 (per handle as in run_increment_mixed; NULL: FFT_ERR_ARG). */
 fft_status batch_create(fft_batch_t* out, fft_rve_t const* rves, int n, int n_threads);
 fft_status batch_run_increment(fft_batch_t b, const double* Fbar, const double* dt,
                                fft_stats* stats, int* status);
+fft_status batch_run_increment_mixed(fft_batch_t b, const double* Fbar, const double* Pbar,
+                                     const int32_t* mask, const double* dt, fft_stats* stats,
+                                     int* status);
 int batch_size(fft_batch_t b);
 void batch_destroy(fft_batch_t b);
 /* Kernel launches issued by this handle since creation (for accounting). */

@@ -30,6 +30,8 @@ struct fft_batch_s {
     std::condition_variable cv_work, cv_done;
     // the current job
     const double* Fbar = nullptr;
+    const double* Pbar = nullptr;   // mixed control: nullable targets (9 per RVE)
+    const int32_t* mask = nullptr;  // mixed control: 9 flags per RVE; null = strain control
     const double* dt = nullptr;
     fft_stats* stats = nullptr;
     int* status = nullptr;
@@ -49,8 +51,12 @@ struct fft_batch_s {
                 lk.unlock();
                 int s = (int)FFT_ERR_CUDA;
                 if (cudaSetDevice(dev[i]) == cudaSuccess)
-                    s = (int)run_increment(rves[i], Fbar + 9 * (size_t)i, dt[i],
-                                           stats ? stats + i : nullptr);
+                    s = mask ? (int)run_increment_mixed(rves[i], Fbar + 9 * (size_t)i,
+                                                        Pbar ? Pbar + 9 * (size_t)i : nullptr,
+                                                        mask + 9 * (size_t)i, dt[i],
+                                                        stats ? stats + i : nullptr)
+                             : (int)run_increment(rves[i], Fbar + 9 * (size_t)i, dt[i],
+                                                  stats ? stats + i : nullptr);
                 lk.lock();
                 status[i] = s;
                 if (++done == (int)rves.size()) cv_done.notify_all();
@@ -89,8 +95,9 @@ fft_status batch_create(fft_batch_t* out, fft_rve_t const* rves, int n, int n_th
     return FFT_OK;
 }
 
-fft_status batch_run_increment(fft_batch_t b, const double* Fbar, const double* dt,
-                               fft_stats* stats, int* status) {
+static fft_status run_job(fft_batch_t b, const double* Fbar, const double* Pbar,
+                          const int32_t* mask, const double* dt, fft_stats* stats,
+                          int* status) {
     if (!b || !Fbar || !dt) return FFT_ERR_ARG;
     const int n = (int)b->rves.size();
     for (int i = 0; i < n; ++i)
@@ -99,6 +106,8 @@ fft_status batch_run_increment(fft_batch_t b, const double* Fbar, const double* 
     {
         std::unique_lock<std::mutex> lk(b->m);
         b->Fbar = Fbar;
+        b->Pbar = Pbar;
+        b->mask = mask;
         b->dt = dt;
         b->stats = stats;
         b->status = st.data();
@@ -113,6 +122,18 @@ fft_status batch_run_increment(fft_batch_t b, const double* Fbar, const double* 
     for (int i = 0; i < n; ++i)
         if (st[i] != (int)FFT_OK) return (fft_status)st[i];
     return FFT_OK;
+}
+
+fft_status batch_run_increment(fft_batch_t b, const double* Fbar, const double* dt,
+                               fft_stats* stats, int* status) {
+    return run_job(b, Fbar, nullptr, nullptr, dt, stats, status);
+}
+
+fft_status batch_run_increment_mixed(fft_batch_t b, const double* Fbar, const double* Pbar,
+                                     const int32_t* mask, const double* dt, fft_stats* stats,
+                                     int* status) {
+    if (!mask) return FFT_ERR_ARG;
+    return run_job(b, Fbar, Pbar, mask, dt, stats, status);
 }
 
 int batch_size(fft_batch_t b) { return b ? (int)b->rves.size() : 0; }

@@ -30,7 +30,7 @@ SYMBOLS = ["init_rve", "apply_increment", "solve_equilibrium", "update_damage",
            "rve_kernel_launches", "rve_profile", "rve_profile_read",
            "degraded_average_noalloc", "batch_create", "batch_run_increment", "batch_size",
            "batch_destroy", "fft_selftest_bounded_wait", "apply_increment_mixed",
-           "run_increment_mixed", "state_save", "state_load"]
+           "run_increment_mixed", "state_save", "state_load", "batch_run_increment_mixed"]
 KERNEL_FAMILIES = ["constitutive", "tangent_apply", "precond_grad", "contract", "gmres_dot",
                    "gs_update", "gmres_xupdate", "kbar", "residual", "f_update", "phase_field",
                    "gnd", "cufft_9field", "cufft_scalar", "reductions", "other"]
@@ -115,6 +115,9 @@ def load(path=LIB_PATH):
     L.batch_create.restype = C.c_int
     L.batch_run_increment.argtypes = [vp, dp, dp, C.POINTER(Stats), C.POINTER(C.c_int)]
     L.batch_run_increment.restype = C.c_int
+    L.batch_run_increment_mixed.argtypes = [vp, dp, dp, C.POINTER(C.c_int32), dp,
+                                            C.POINTER(Stats), C.POINTER(C.c_int)]
+    L.batch_run_increment_mixed.restype = C.c_int
     L.batch_size.argtypes = [vp]
     L.batch_size.restype = C.c_int
     L.batch_destroy.argtypes = [vp]
@@ -345,21 +348,35 @@ class Batch:
             raise FFTError("batch_create", s, "distinct handles, each with its own stream")
         self._h = h
 
-    def run_increment(self, Fbars, dts, check=True):
-        """Fbars: (n, 9) absolute macroscopic F per handle; dts: (n,).
+    def run_increment(self, Fbars, dts, check=True, Pbars=None, stress_masks=None):
+        """Fbars: (n, 9) absolute macroscopic F per handle; dts: (n,).  With
+        stress_masks (n, 9) flags, mixed control per handle
+        (batch_run_increment_mixed, Pbars (n, 9) or None for zero targets).
         Returns (status, per-handle statuses, per-handle stats dicts)."""
         n = len(self.rves)
+        dp = C.POINTER(C.c_double)
         F = np.ascontiguousarray(np.asarray(Fbars, dtype=np.float64).reshape(n, 9))
         dt = np.ascontiguousarray(np.asarray(dts, dtype=np.float64).reshape(n))
         stats = (Stats * n)()
         st = (C.c_int * n)()
-        s = load().batch_run_increment(self._h, F.ctypes.data_as(C.POINTER(C.c_double)),
-                                       dt.ctypes.data_as(C.POINTER(C.c_double)), stats, st)
+        if stress_masks is None:
+            call = "batch_run_increment"
+            s = load().batch_run_increment(self._h, F.ctypes.data_as(dp), dt.ctypes.data_as(dp),
+                                           stats, st)
+        else:
+            call = "batch_run_increment_mixed"
+            m = np.ascontiguousarray((np.asarray(stress_masks).reshape(n, 9) != 0)
+                                     .astype(np.int32))
+            P = np.ascontiguousarray(np.zeros((n, 9)) if Pbars is None else
+                                     np.asarray(Pbars, dtype=np.float64).reshape(n, 9))
+            s = load().batch_run_increment_mixed(
+                self._h, F.ctypes.data_as(dp), P.ctypes.data_as(dp),
+                m.ctypes.data_as(C.POINTER(C.c_int32)), dt.ctypes.data_as(dp), stats, st)
         per = list(st)
         if check and s != FFT_OK:
             bad = [i for i, x in enumerate(per) if x != FFT_OK]
             msg = load().fft_last_error(self.rves[bad[0]]._h).decode() if bad else ""
-            raise FFTError("batch_run_increment", s, f"handles {bad}: {msg}")
+            raise FFTError(call, s, f"handles {bad}: {msg}")
         return s, per, [x.as_dict() for x in stats]
 
     def close(self):

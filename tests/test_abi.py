@@ -71,6 +71,8 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu():
     assert L.batch_create(C.byref(b), arr, 1, 1) == FF.FFT_ERR_ARG
     assert L.batch_create(C.byref(b), arr, 0, 1) == FF.FFT_ERR_ARG
     assert L.batch_size(None) == 0
+    one = (C.c_double * 9)(*np.eye(3).reshape(9))
+    assert L.batch_run_increment_mixed(None, one, None, None, one, None, None) == FF.FFT_ERR_ARG
     F9 = (C.c_double * 9)(*np.eye(3).reshape(9))
     m9 = (C.c_int32 * 9)(*([1] * 9))
     assert L.run_increment_mixed(None, F9, None, m9, 1.0, None) == FF.FFT_ERR_ARG

@@ -51,6 +51,42 @@ def test_batch_matches_single_runs(prec):
         r.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_mixed_control_matches_single_runs(prec):
+    """batch_run_increment_mixed: three uneven grids under uniaxial stress
+    (lateral mean stresses zero), each handle's stress-controlled components
+    started from its own previous solved F, give the same bits as each
+    handle run alone with run_increment_mixed."""
+    grids = GRIDS[:3]
+    m = I.uniaxial_stress_mask(1)
+    prog = I.uniaxial_cycle_program(0.006, 24, 1)[:4]
+
+    def guesses(prev, Fb):
+        return [Fb.copy() if p is None else np.where(m == 1, p, Fb) for p in prev]
+
+    batch_rves = [_make(n, 60 + i, prec) for i, n in enumerate(grids)]
+    b = FF.Batch(batch_rves, threads=2)
+    prev = [None] * len(grids)
+    for Fb, dt in prog:
+        s, per, stats = b.run_increment(guesses(prev, Fb), [dt] * len(grids),
+                                        stress_masks=[m] * len(grids))
+        assert s == FF.FFT_OK and all(x["mixed_it"] >= 1 for x in stats)
+        prev = [np.array(x["Fbar"]) for x in stats]
+    b.close()
+    for i, n in enumerate(grids):
+        r = _make(n, 60 + i, prec)
+        p = None
+        for Fb, dt in prog:
+            _, st = r.run_increment(guesses([p], Fb)[0], dt, Pbar=np.zeros(9), stress_mask=m)
+            p = np.array(st["Fbar"])
+        assert np.array_equal(p, prev[i])
+        for f in ("F", "P", "Fp", "gamma"):
+            assert np.array_equal(r.field(f), batch_rves[i].field(f)), (n, f)
+        r.close()
+    for r in batch_rves:
+        r.close()
+
+
 def test_failing_handle_does_not_stop_the_others():
     prog = I.uniaxial_cycle_program(0.004, 8, 1)
     capped = I.solver_options("parity32", max_lin=1, tol_lin=1e-14)
