@@ -797,3 +797,51 @@ def test_damped_newton_passes_the_yield_plateau():
         P = np.array(st["Pbar"])
         assert max(abs(P[0]), abs(P[8])) <= opts["tol_newton"] * np.abs(P).max()
     assert F[4] - 1.0 > 0.0119 and P[4] > 1000.0  # past the yield plateau
+
+
+def test_mixed_cutback_equals_explicit_halves():
+    """Cut-back under mixed control (uniaxial stress), by the same
+    definition as under strain control plus its one addition: the second
+    half's stress-controlled components start from the solved midpoint.  A
+    single 0.6 % step from rest that fails whole equals, bit for bit, the
+    same halves requested one by one with cut-back off, each half's guess of
+    the lateral components built that way."""
+    n = (6, 6, 6)
+    gid, eul = I.voronoi(n, 3, 11)
+    mat = dict(I.material("baseline"), tau_c0=250.0)
+    m = I.uniaxial_stress_mask(1)
+    Fb, dt = I.uniaxial_cycle_program(0.006, 4, 1)[0]
+    kw = dict(max_newton=6, max_lin=100)
+    a = O.RVE(n, I.VOXEL_MM, gid, eul, mat, I.solver_options("paper", max_cutbacks=3, **kw))
+    s, st = a.run_increment(Fb, dt, Pbar=np.zeros(9), stress_mask=m)
+    assert s == 0 and st["cutbacks"] >= 1
+    b = O.RVE(n, I.VOXEL_MM, gid, eul, mat, I.solver_options("paper", max_cutbacks=0, **kw))
+    committed = [np.eye(3).reshape(9)]
+    halvings = [0]
+
+    def attempt(F, t):
+        s, st = b.run_increment(F, t, Pbar=np.zeros(9), stress_mask=m)
+        if s == 0:
+            committed[0] = np.array(st["Fbar"])
+        return s
+
+    def halves(F, t, depth):
+        halvings[0] += 1
+        mid = 0.5 * (committed[0] + F)
+        s = attempt(mid, 0.5 * t)
+        if s == -5 and depth < 3:
+            s = halves(mid, 0.5 * t, depth + 1)
+        if s:
+            return s
+        last = np.where(m == 1, committed[0], F)
+        s = attempt(last, 0.5 * t)
+        if s == -5 and depth < 3:
+            s = halves(last, 0.5 * t, depth + 1)
+        return s
+
+    assert attempt(Fb, dt) == -5
+    assert halves(Fb, dt, 1) == 0
+    assert halvings[0] == st["cutbacks"]
+    assert np.array_equal(committed[0], np.array(st["Fbar"]))
+    for f in ("F", "P", "Fp", "rho_ssd", "gamma"):
+        assert np.array_equal(a.field(f), b.field(f)), f
