@@ -75,7 +75,11 @@ typedef struct {
 /* Solver controls.  Tolerances (Sec. 3.1-3.2): tol_stag on the Algorithm 1
  * ratios, tol_newton on ||grad du||inf / ||F - F_t||inf, tol_lin relative
  * GMRES residual, tol_pf relative phase-field CG residual, tol_local the
- * local slip-law residual (MPa).  max_* are iteration caps; restart is the
+ * local slip-law residual (MPa).  The Newton update is damped (an
+ * extension; the paper takes full steps): from the 4th iteration, an update
+ * after which the tol_newton ratio did not fall halves the next update
+ * (down to 1/16), one that halved the ratio doubles it back; the ratio is
+ * always that of the full correction.  max_* are iteration caps; restart is the
  * GMRES restart length (clamped to [1, 31]).  prec selects FP64 or the mixed
  * path (FP32 fields, transforms and constitutive update; FP64 reductions,
  * dot products, norms and compensated history sums).  max_cutbacks (an
@@ -103,7 +107,7 @@ typedef struct {
     double res_F, res_phi; /* last Algorithm 1 ratios */
     double Pbar[9];        /* volume average of g(phi) P at the current iterate */
     long cracked;          /* voxels with phi >= 0.9 */
-    int cutbacks;          /* halvings taken by run_increment (max_cutbacks) */
+    int cutbacks;          /* halvings taken (max_cutbacks), either control */
     int mixed_it;          /* outer rounds of the mixed stress/strain control */
     double Fbar[9];        /* macroscopic F (row-major) after the last damage update */
 } fft_stats;
