@@ -5,6 +5,7 @@ check and by the CPU-baseline leg of ``bench.py``; never by the product path.
 The oracle restates the paper's equations plainly (own FFT, own slip tables,
 own solvers) and shares no code with the GPU library.
 """
+import contextlib
 import ctypes as C
 import os
 
@@ -60,44 +61,59 @@ _ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _up = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
 
 
+def _declare(L):
+    L.orc_fft3d.argtypes = [C.c_int * 3, _dp, C.c_int, C.c_int]
+    L.orc_material_paper.argtypes = [C.POINTER(Material)]
+    L.orc_euler_to_Q.argtypes = [_dp, _dp]
+    L.orc_fcc_systems.argtypes = [_dp, _dp]
+    L.orc_gnd_basis.argtypes = [_dp, _dp]
+    L.orc_cp_point.argtypes = [C.POINTER(Material), _dp, _dp, _dp, C.c_double, C.c_double,
+                               C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
+                               C.POINTER(CPResult)]
+    L.orc_we_plus.argtypes = [C.POINTER(Material), _dp]
+    L.orc_we_plus.restype = C.c_double
+    L.orc_sym_eig3.argtypes = [_dp, _dp, _dp]
+    L.orc_green_precond.argtypes = [_dp, _dp, _dp]
+    L.orc_gnd_field.argtypes = [C.c_int * 3, C.c_double, C.POINTER(Material), _dp, _dp,
+                                C.c_int, _dp, _dp]
+    L.orc_phase_field.argtypes = [C.c_int * 3, C.c_double, C.c_double, _dp, _dp, _dp,
+                                  C.c_double, C.c_int, C.c_int, _dp, C.POINTER(C.c_int)]
+    L.orc_rve_create.argtypes = [C.c_int * 3, C.c_double, _ip, C.c_int, _dp,
+                                 C.POINTER(Material), C.POINTER(Options), C.c_void_p,
+                                 C.c_void_p]
+    L.orc_rve_create.restype = C.c_void_p
+    L.orc_rve_destroy.argtypes = [C.c_void_p]
+    L.orc_apply_increment.argtypes = [C.c_void_p, _dp, C.c_double]
+    for fn in ("orc_solve_equilibrium", "orc_update_damage"):
+        getattr(L, fn).argtypes = [C.c_void_p, C.POINTER(Stats)]
+    L.orc_commit.argtypes = [C.c_void_p]
+    L.orc_run_increment.argtypes = [C.c_void_p, _dp, C.c_double, C.POINTER(Stats)]
+    L.orc_run_increment_mixed.argtypes = [C.c_void_p, _dp, _dp, C.POINTER(C.c_int),
+                                          C.c_double, C.POINTER(Stats)]
+    L.orc_fields_out.argtypes = [C.c_void_p, C.c_int, _dp]
+    L.orc_fields_in.argtypes = [C.c_void_p, C.c_int, _dp]
+    return L
+
+
 def lib():
     global _LIB
     if _LIB is None:
-        path = _build.build()
-        L = C.CDLL(path)
-        L.orc_fft3d.argtypes = [C.c_int * 3, _dp, C.c_int, C.c_int]
-        L.orc_material_paper.argtypes = [C.POINTER(Material)]
-        L.orc_euler_to_Q.argtypes = [_dp, _dp]
-        L.orc_fcc_systems.argtypes = [_dp, _dp]
-        L.orc_gnd_basis.argtypes = [_dp, _dp]
-        L.orc_cp_point.argtypes = [C.POINTER(Material), _dp, _dp, _dp, C.c_double, C.c_double,
-                                   C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
-                                   C.POINTER(CPResult)]
-        L.orc_we_plus.argtypes = [C.POINTER(Material), _dp]
-        L.orc_we_plus.restype = C.c_double
-        L.orc_sym_eig3.argtypes = [_dp, _dp, _dp]
-        L.orc_green_precond.argtypes = [_dp, _dp, _dp]
-        L.orc_gnd_field.argtypes = [C.c_int * 3, C.c_double, C.POINTER(Material), _dp, _dp,
-                                    C.c_int, _dp, _dp]
-        L.orc_phase_field.argtypes = [C.c_int * 3, C.c_double, C.c_double, _dp, _dp, _dp,
-                                      C.c_double, C.c_int, C.c_int, _dp, C.POINTER(C.c_int)]
-        L.orc_rve_create.argtypes = [C.c_int * 3, C.c_double, _ip, C.c_int, _dp,
-                                     C.POINTER(Material), C.POINTER(Options), C.c_void_p,
-                                     C.c_void_p]
-        L.orc_rve_create.restype = C.c_void_p
-        L.orc_rve_destroy.argtypes = [C.c_void_p]
-        for fn in ("orc_apply_increment",):
-            getattr(L, fn).argtypes = [C.c_void_p, _dp, C.c_double]
-        for fn in ("orc_solve_equilibrium", "orc_update_damage"):
-            getattr(L, fn).argtypes = [C.c_void_p, C.POINTER(Stats)]
-        L.orc_commit.argtypes = [C.c_void_p]
-        L.orc_run_increment.argtypes = [C.c_void_p, _dp, C.c_double, C.POINTER(Stats)]
-        L.orc_run_increment_mixed.argtypes = [C.c_void_p, _dp, _dp, C.POINTER(C.c_int),
-                                              C.c_double, C.POINTER(Stats)]
-        L.orc_fields_out.argtypes = [C.c_void_p, C.c_int, _dp]
-        L.orc_fields_in.argtypes = [C.c_void_p, C.c_int, _dp]
-        _LIB = L
+        _LIB = _declare(C.CDLL(_build.build()))
     return _LIB
+
+
+@contextlib.contextmanager
+def library(path):
+    """Route every call of this module through another build of the oracle
+    (the mutation tests load builds with a planted mistake) until the block
+    ends.  Handles created inside the block must be closed inside it."""
+    global _LIB
+    prev = lib()
+    _LIB = _declare(C.CDLL(os.path.abspath(path)))
+    try:
+        yield
+    finally:
+        _LIB = prev
 
 
 def _n3(n):

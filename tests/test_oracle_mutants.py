@@ -1,0 +1,53 @@
+"""Mutation checks of the oracle's pins: a plausible mistake planted in a
+copy of the oracle's sources (built on the CPU into a temporary folder) must
+make a pin fail.  The committed oracle is never modified.
+
+Each mutant names the passage whose restatement it breaks."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+import oracle as O
+from oracle import build as OB
+from test_oracle_pins import history_chain_check
+
+MUTANTS = {
+    # Eq. Gs / R10: the stored energy increment divides by the density after
+    # the increment's SSD growth, not before it
+    "gs_uses_old_rho": ("rve.cpp", "std::sqrt(rho_new + r->rho_gnd[v])",
+                        "std::sqrt(r->rho_t[v] + r->rho_gnd[v])"),
+    # Eq. crit / R9: W_crit is H_max + W_p at the event, not W_p alone
+    "wcrit_without_hmax": ("rve.cpp", "wc = r->Hmax_tr[v] + r->Wp_tr[v];",
+                           "wc = r->Wp_tr[v];"),
+    # Eq. zeta / A14: the drive uses the current W_e+, the maximum only
+    # enters W_crit
+    "drive_uses_hmax": ("rve.cpp", "(res.We_plus + r->Wp_tr[v]) / wc",
+                        "(r->Hmax_tr[v] + r->Wp_tr[v]) / wc"),
+}
+
+
+def _build_mutant(tmp, name):
+    fname, old, new = MUTANTS[name]
+    src = os.path.join(tmp, "src")
+    os.makedirs(src, exist_ok=True)
+    for f in OB.SOURCES + ["oracle.h", "oracle_internal.hpp"]:
+        shutil.copy(os.path.join(OB.HERE, f), src)
+    p = os.path.join(src, fname)
+    text = open(p).read()
+    assert text.count(old) == 1, (name, "the planted site must match exactly once")
+    open(p, "w").write(text.replace(old, new))
+    out = os.path.join(tmp, f"lib_{name}.so")
+    subprocess.run(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-pthread",
+                    *[os.path.join(src, s) for s in OB.SOURCES], "-o", out], check=True)
+    return out
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_history_pin_catches_mutant(name, tmp_path):
+    path = _build_mutant(str(tmp_path), name)
+    with O.library(path):
+        with pytest.raises(AssertionError):
+            history_chain_check()
+    history_chain_check()  # the committed oracle still passes

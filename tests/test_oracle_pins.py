@@ -845,3 +845,128 @@ def test_mixed_cutback_equals_explicit_halves():
     assert np.array_equal(committed[0], np.array(st["Fbar"]))
     for f in ("F", "P", "Fp", "rho_ssd", "gamma"):
         assert np.array_equal(a.field(f), b.field(f)), f
+
+
+# ------------------------------------------------ history and driving force
+# (shear, dilatation) history of a crystal in the lattice frame, shear along
+# FCC system 0: yield, a further push with a 0.05 % dilatation on top (which
+# resolves no shear on any system but raises W_e+, so that H_max stays above
+# the later W_e+), elastic unloading, reversed yield, a reversed push,
+# elastic unloading and re-yield (only system 0 ever slips; checked below).
+_HIST_SHEAR = ((2e-3, 0.0), (4e-3, 0.0), (6e-3, 5e-4), (4e-3, 0.0), (0.0, 0.0), (-4e-3, 0.0),
+               (-6e-3, 0.0), (-2e-3, 0.0), (2e-3, 0.0), (6e-3, 0.0), (3e-3, 0.0))
+
+
+def _bisect(f, lo, hi):
+    assert f(lo) < 0 < f(hi)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if f(mid) < 0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def _history_by_hand(m, g_crit, dt=1.0):
+    """The history of Sec. 2.1 and 2.3 for a homogeneous crystal (F = Fbar
+    everywhere, so grad F_p = 0 and rho_GND = 0) under _HIST_SHEAR, built
+    from quantities pinned elsewhere and written out here step by step:
+      dgamma (one active system) by bisection of the scalar slip law,
+      dW_p = tau dgamma, drho_SSD = lambda sqrt(2/3 dL:dL) with dL = dgamma P0,
+      G_s += xi dW_p / sqrt(rho_SSD,n+1 + rho_GND)            (Eq. Gs, R10),
+      W_e+ = 1/2 eps+ : C : eps+, eps = 1/2 ln(Fe Fe^T)      (Eq. decMiehe),
+      H_max = max over the committed states of W_e+          (Eq. crit),
+      W_crit = H_max + W_p at the first state with G_s >= G_crit (R9),
+      S = <(W_e+ + W_p) / W_crit - 1> with the current W_e+  (Eq. zeta),
+      phi = 2 S / (1 + 2 S) for a uniform drive, clamped by phi_t
+                                                   (Eqs. strpf, phase; Alg. 1).
+    Returns one dict per increment."""
+    s, n = O.fcc_systems()
+    P0 = np.outer(s[0], n[0])
+    kT = m["k_B"] * m["T"]
+    g0 = m["rho_m"] * m["b"] ** 2 * m["nu_D"] * np.exp(-m["dF"] / kT)
+    sT = kT / (m["dV"] * 1e-3)
+    tc = m["tau_c0"]
+    Fpi, rho, Wp, Gs, Hmax, Wc, phi = np.eye(3), m["rho_ssd0"], 0.0, 0.0, 0.0, 0.0, 0.0
+    out = []
+    for e, dil in _HIST_SHEAR:
+        F = (1.0 + dil) * (np.eye(3) + e * P0)
+
+        def tau(dg, a=0):
+            Fe = F @ Fpi @ (np.eye(3) - dg * P0)
+            S = cubic_apply_np(m, 0.5 * (Fe.T @ Fe - np.eye(3)))
+            return s[a] @ S @ n[a]
+
+        dg = 0.0
+        if abs(tau(0.0)) > tc:
+            sg = np.sign(tau(0.0))
+            dg = sg * _bisect(lambda x: x - dt * g0 * np.sinh((sg * tau(sg * x) - tc) / sT),
+                              0.0, 0.01)
+        t0 = tau(dg)
+        assert all(abs(tau(dg, a)) < tc for a in range(1, 12))  # one active system
+        Fpi = Fpi @ (np.eye(3) - dg * P0)
+        Fe = F @ Fpi
+        dW = t0 * dg
+        rho = rho + m["lambda_h"] * np.sqrt(2.0 / 3.0) * abs(dg) * np.linalg.norm(P0)
+        Wp += dW
+        Gs += m["xi_store"] * dW / np.sqrt(rho)
+        lam, V = np.linalg.eigh(Fe @ Fe.T)
+        ep = V @ np.diag(np.maximum(0.5 * np.log(lam), 0.0)) @ V.T
+        We = 0.5 * np.sum(ep * cubic_apply_np(m, ep))
+        Hmax = max(Hmax, We)
+        if Wc == 0.0 and Gs >= g_crit:
+            Wc = Hmax + Wp
+        S = max(0.0, (We + Wp) / Wc - 1.0) if Wc > 0 else 0.0
+        phi = max(phi, 2 * S / (1 + 2 * S))
+        out.append(dict(Fbar=F.reshape(9), dgamma=dg, rho_ssd=rho, Wp=Wp, Gs=Gs, We=We,
+                        Hmax=Hmax, Wcrit=Wc, drive=S, phi_t=phi))
+    return out
+
+
+def history_chain_check():
+    """Runs the oracle's Algorithm 1 on a 2 x 2 x 2 homogeneous crystal
+    through _HIST_SHEAR and compares every committed history field with
+    _history_by_hand.  G_crit is placed between G_s of the fifth and sixth
+    increments, so W_crit is set at reversed yield, after the tensile peak
+    (H_max > W_e+ there), and S is then positive at the reversed push and
+    zero again on unloading (W_e+ < H_max).  Raises AssertionError on any
+    mismatch (the mutation tests plant mistakes in the oracle and expect
+    one)."""
+    s, n = O.fcc_systems()
+    m, _, _, _, tc = _single_slip_case(1.0)
+    m = dict(m, G_crit=np.inf)
+    free = _history_by_hand(m, np.inf)
+    gs = [h["Gs"] for h in free]
+    assert gs[4] < gs[5]
+    m["G_crit"] = 0.5 * (gs[4] + gs[5])
+    ref = _history_by_hand(m, m["G_crit"])
+    # the sequence exercises what the pin is about
+    assert ref[5]["Wcrit"] > 0 and ref[4]["Wcrit"] == 0
+    assert ref[5]["Hmax"] > 1.05 * ref[5]["We"]
+    assert ref[6]["drive"] > 0 and ref[7]["drive"] == 0
+    assert ref[7]["Hmax"] + ref[7]["Wp"] > ref[7]["Wcrit"]
+    r = O.RVE((2, 2, 2), H, np.zeros(8, dtype=np.int32), np.zeros(3), m,
+              I.solver_options("parity64"))
+    try:
+        for k, h in enumerate(ref):
+            st, stats = r.run_increment(h["Fbar"], 1.0)
+            assert st == 0, (k, stats)
+            got = {f: r.field(f) for f in ("rho_ssd", "Wp", "Gs", "We", "Hmax", "Wcrit",
+                                            "drive", "phi_t")}
+            gam = r.field("gamma")
+            assert np.all(gam[1:] == 0)
+            for f, v in got.items():
+                assert np.ptp(v) == 0, (k, f)  # homogeneous
+                want = h[f]
+                assert abs(v[0] - want) <= 1e-9 * abs(want) + 1e-13, (k, f, v[0], want)
+    finally:
+        r.close()
+
+
+def test_history_and_driving_force_chain():
+    """Sec. 2.3 (Eqs. Gs, crit, zeta) with readings R9, R10 and A14: the
+    stored energy density, the maximum tensile energy across a load reversal,
+    the W_crit event and its value, and the driving force from the current
+    W_e+, against a hand-built chain on a homogeneous crystal."""
+    history_chain_check()
