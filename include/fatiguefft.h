@@ -86,9 +86,13 @@ typedef struct {
  * extension; the paper's Algorithm 1 has none, 0 = off): when run_increment
  * or run_increment_mixed does not converge, the increment is restarted from
  * the committed state as two halves of the step, each committed: the first
- * to the midpoint of the committed and the requested Fbar, the second to the
- * request (under mixed control its stress-controlled components start from
- * the solved midpoint), dt halved; recursively up to this depth (0..10, else
+ * to the midpoint of the committed and the requested Fbar (under mixed
+ * control, with the stress-controlled components aimed at the midpoint of
+ * the committed and the requested stress; the committed stress is the
+ * previous increment's target on components it held by stress, its mean
+ * <g P> on the others), the second to the request (under mixed control its
+ * stress-controlled components of F start from the solved midpoint), dt
+ * halved; recursively up to this depth (0..10, else
  * FFT_ERR_ARG at init_rve).  Smaller steps keep Newton within reach of the
  * solution and stiffen the rate-dependent consistent tangent of plastic
  * voxels, which eases the Krylov solves. */
@@ -209,9 +213,10 @@ fft_status fields_in(fft_rve_t r, int field, const double* src, size_t bytes);
  * written, *bytes set to its size and the stream synchronised.  A converged
  * but uncommitted increment of the stage calls is not included.
  * FFT_ERR_ARG: NULL handle or bytes, or capacity too small.
- * state_load: restores a checkpoint of a handle with the same grid and
- * precision (else FFT_ERR_ARG) as the committed state and the current
- * iterate; the next increment then reproduces, bit for bit, the run the
+ * state_load: restores a checkpoint of a handle with the same grid,
+ * precision, grain ids, orientations, soft-region mask and material (the
+ * checkpoint carries a hash of these; else FFT_ERR_ARG) as the committed
+ * state and the current iterate; the next increment then reproduces, bit for bit, the run the
  * checkpoint was taken from.  Any earlier failed or uncommitted increment is
  * discarded. */
 fft_status state_save(fft_rve_t r, void* dst, size_t* bytes);
@@ -261,7 +266,10 @@ fft_status rve_profile_read(fft_rve_t r, double* ms, long long* counts, double* 
  * the process exits), sized for ncomp <= 81; a larger ncomp, N = 0 or a null
  * pointer returns FFT_ERR_ARG without launching anything.  The first call on
  * each device (with that device current) looks up the array's device
- * address, so make that first call before any stream capture.  All calls on
+ * address, so make that first call before any stream capture.  The address
+ * is kept until the process exits: do not call this function again on a
+ * device after resetting it (cudaDeviceReset or a re-created primary
+ * context), since the array then lives elsewhere.  All calls on
  * a device share the array: calls whose work overlaps on the GPU (other
  * streams, other threads) race and must be serialised by the caller.  Each
  * call overwrites every partial it later reads, so no clearing is needed. */
@@ -284,7 +292,9 @@ const char* fft_last_error(fft_rve_t r);
  * (row-major per handle), dt n doubles, stats n entries (may be NULL),
  * status n ints (may be NULL) receive each handle's own result; returns
  * FFT_OK or the first failing handle's status (the others still ran).
- * A failed handle behaves as after its own failed run_increment.
+ * A failed handle behaves as after its own failed run_increment.  Calls on
+ * one batch from several host threads are serialised (each waits for the
+ * previous one to finish).
  * batch_run_increment_mixed = run_increment_mixed on every handle, with the
  * same layouts plus Pbar 9n doubles (may be NULL: zero targets) and mask 9n
  * int32 (per handle as in run_increment_mixed; NULL: FFT_ERR_ARG). */

@@ -356,6 +356,10 @@ struct orc_rve {
     bool mixed = false;  // mixed stress/strain control (orc_apply_increment_mixed)
     int mask[9] = {0};
     double Pstar[9] = {0};
+    // mean degraded stress <g P> at the last damage update, and the committed
+    // macroscopic stress: the target on stress-controlled components, the
+    // mean on the others (the start of a halved stress path under cut-back)
+    double Pbar_cur[9] = {0}, Pbar_t[9] = {0};
     int state, stag_it;
     bool phi_changed, skipped, converged;
 };
@@ -522,6 +526,7 @@ int orc_commit(orc_rve* r) {
     r->Ft = r->F;
     r->phi_t = r->phi;
     std::memcpy(r->Fbar_t, r->Fbar, sizeof(r->Fbar));
+    for (int c = 0; c < 9; ++c) r->Pbar_t[c] = (r->mixed && r->mask[c]) ? r->Pstar[c] : r->Pbar_cur[c];
     r->state = ST_COMMITTED;
     return 0;
 }
@@ -908,15 +913,16 @@ int orc_update_damage(orc_rve* r, orc_stats* st) {
     const bool cF = dF <= r->o.tol_stag * std::max(dFt, 1e-12);
     const bool cP = dphi <= r->o.tol_stag * std::max(dphit, 1e-12);
     r->converged = cF && cP;
+    for (int c = 0; c < 9; ++c) {
+        double s2 = 0;
+        for (size_t v = 0; v < N; ++v) s2 += gdeg(r, r->phi[v]) * r->Pund[c * N + v];
+        r->Pbar_cur[c] = s2 / (double)N;
+    }
     if (st) {
         st->res_F = dF / std::max(dFt, 1e-12);
         st->res_phi = dphi / std::max(dphit, 1e-12);
         st->converged = r->converged;
-        for (int c = 0; c < 9; ++c) {
-            double s2 = 0;
-            for (size_t v = 0; v < N; ++v) s2 += gdeg(r, r->phi[v]) * r->Pund[c * N + v];
-            st->Pbar[c] = s2 / (double)N;
-        }
+        for (int c = 0; c < 9; ++c) st->Pbar[c] = r->Pbar_cur[c];
         long cr = 0;
         for (size_t v = 0; v < N; ++v) cr += r->phi[v] >= 0.9;
         st->cracked = cr;
@@ -962,17 +968,23 @@ static int attempt(orc_rve* r, const double Fbar[9], const double* Pstar, const 
 
 // Cut-back (an extension of Algorithm 1, off unless max_cutbacks > 0): an
 // increment that does not converge is redone from the committed state as two
-// halves of the step, the first to the midpoint of the committed and the
-// requested macroscopic F, the second to the request with its
-// stress-controlled components started from the solved midpoint; each half
-// is halved again on failure, down to depth max_cutbacks.
+// halves of the load step, each half taking half of the change: the first
+// to the midpoint of the committed and the requested macroscopic F and, on
+// stress-controlled components, to the midpoint of the committed and the
+// requested stress; the second to the request, with its stress-controlled
+// components of F started from the solved midpoint.  Each half is halved
+// again on failure, down to depth max_cutbacks.
 static int halves(orc_rve* r, const double Fbar[9], const double* Pstar, const int* mask,
                   double dt, orc_stats* st, int depth) {
     if (st) st->cutbacks += 1;
-    double mid[9], last[9];
-    for (int c = 0; c < 9; ++c) mid[c] = 0.5 * (r->Fbar_t[c] + Fbar[c]);
-    int s = attempt(r, mid, Pstar, mask, 0.5 * dt, st);
-    if (s == -5 && depth < r->o.max_cutbacks) s = halves(r, mid, Pstar, mask, 0.5 * dt, st, depth + 1);
+    double mid[9], last[9], Pmid[9];
+    for (int c = 0; c < 9; ++c) {
+        mid[c] = 0.5 * (r->Fbar_t[c] + Fbar[c]);
+        const double Pc = Pstar ? Pstar[c] : 0.0;
+        Pmid[c] = (mask && mask[c]) ? 0.5 * (r->Pbar_t[c] + Pc) : Pc;
+    }
+    int s = attempt(r, mid, Pmid, mask, 0.5 * dt, st);
+    if (s == -5 && depth < r->o.max_cutbacks) s = halves(r, mid, Pmid, mask, 0.5 * dt, st, depth + 1);
     if (s) return s;
     for (int c = 0; c < 9; ++c) last[c] = (mask && mask[c]) ? r->Fbar_t[c] : Fbar[c];
     s = attempt(r, last, Pstar, mask, 0.5 * dt, st);

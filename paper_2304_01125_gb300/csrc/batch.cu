@@ -26,6 +26,7 @@ struct fft_batch_s {
     std::vector<int> dev;
     std::vector<int> order;  // indices, largest grid first
     std::vector<std::thread> pool;
+    std::mutex call;  // one batch call at a time (the job fields below are shared)
     std::mutex m;
     std::condition_variable cv_work, cv_done;
     // the current job
@@ -103,6 +104,7 @@ static fft_status run_job(fft_batch_t b, const double* Fbar, const double* Pbar,
     for (int i = 0; i < n; ++i)
         if (!(dt[i] >= 0)) return FFT_ERR_ARG;
     std::vector<int> st(n, (int)FFT_OK);
+    std::lock_guard<std::mutex> serial(b->call);
     {
         std::unique_lock<std::mutex> lk(b->m);
         b->Fbar = Fbar;

@@ -66,7 +66,10 @@ extern "C" fft_status degraded_average_noalloc(const double* X, int ncomp, const
     double* part = nullptr;
     {
         // First call on this device: look up the device address of the
-        // scratch array (its name is only a placeholder in host code).
+        // scratch array (its name is only a placeholder in host code).  The
+        // address is kept for the life of the process; it does not survive
+        // a reset of the device (cudaDeviceReset, a re-created primary
+        // context), after which the module is loaded again elsewhere.
         std::lock_guard<std::mutex> lock(g_na_mutex);
         if (!g_na_ptr[dev]) {
             void* p = nullptr;

@@ -131,6 +131,13 @@ struct fft_rve_s {
     bool mixed = false;
     int mask[9] = {0};
     double Pstar[9] = {0};
+    // mean degraded stress <g P> at the last damage update, and the committed
+    // macroscopic stress: the target on stress-controlled components, the
+    // mean on the others (the start of a halved stress path under cut-back)
+    double Pbar_cur[9] = {0}, Pbar_t[9] = {0};
+    // hash of the grain ids, orientations, soft-region mask and material
+    // (a checkpoint loads only into a handle with the same set-up)
+    uint64_t setup_hash = 0;
     int state = ST_NEW, stag_it = 0;
     bool phi_changed = true, skipped = false, converged = false, cp_valid = false;
     bool verbose = false;  // FATIGUEFFT_VERBOSE: solver traces on stderr
@@ -804,6 +811,10 @@ struct Impl {
         TRY(fetch(r, 11));
         const double* Pb = r->hred + 2;  // <gP>, from the statistics kernel
         const double* Kb = r->hred + 16;
+        for (int c = 0; c < 81; ++c)
+            if (!std::isfinite(Kb[c]))
+                FAIL(r, FFT_ERR_NONFINITE,
+                     "mixed control: non-finite averaged tangent entry %d (Kbar = <g K>)", c);
         double pmax = 0, res = 0;
         int S[9], ns = 0;
         for (int c = 0; c < 9; ++c) {
@@ -1016,6 +1027,7 @@ struct Impl {
         r->phi_changed = o4[2] > 0;
         const double tol = r->opt.tol_stag;
         r->converged = dF <= tol * std::max(dFt, 1e-12) && dphi <= tol * std::max(dphit, 1e-12);
+        for (int c = 0; c < 9; ++c) r->Pbar_cur[c] = r->hred[2 + c];
         if (st) {
             st->res_F = dF / std::max(dFt, 1e-12);
             st->res_phi = dphi / std::max(dphit, 1e-12);
@@ -1074,6 +1086,8 @@ struct Impl {
         CK(r, cudaMemcpyAsync(r->Ht, r->H, 9 * N * sizeof(R), cudaMemcpyDeviceToDevice, r->st));
         CK(r, cudaMemcpyAsync(r->phi_t, r->phi, N * sizeof(R), cudaMemcpyDeviceToDevice, r->st));
         std::memcpy(r->Fbar_t, r->Fbar, sizeof(r->Fbar));
+        for (int c = 0; c < 9; ++c)
+            r->Pbar_t[c] = (r->mixed && r->mask[c]) ? r->Pstar[c] : r->Pbar_cur[c];
         r->state = ST_COMMITTED;
         r->cp_valid = false;
         return FFT_OK;
@@ -1101,21 +1115,27 @@ struct Impl {
     // The increment as two halves from the committed state (a failed
     // attempt leaves it untouched: apply_increment restarts from F_t, phi_t
     // and the committed history), each halved again on failure down to
-    // depth max_cutbacks.  The first half goes to the midpoint of the
-    // committed and the requested macroscopic F, the second to the request;
-    // under mixed control the second half's stress-controlled components
-    // start from the solved midpoint.
+    // depth max_cutbacks.  Each half takes half of the load change: the
+    // first goes to the midpoint of the committed and the requested
+    // macroscopic F and, on stress-controlled components, to the midpoint
+    // of the committed and the requested stress; the second to the request,
+    // its stress-controlled components of F started from the solved
+    // midpoint.
     static fft_status run_halves(fft_rve_s* r, const double* Fbar, const double* Pstar,
                                  const int32_t* mask, double dt, fft_stats* st, int depth) {
         if (st) st->cutbacks += 1;
-        double tgt[2][9];
-        for (int c = 0; c < 9; ++c) tgt[0][c] = 0.5 * (r->Fbar_t[c] + Fbar[c]);
+        double tgt[2][9], Ptgt[2][9];
+        for (int c = 0; c < 9; ++c) {
+            tgt[0][c] = 0.5 * (r->Fbar_t[c] + Fbar[c]);
+            Ptgt[1][c] = Pstar ? Pstar[c] : 0.0;
+            Ptgt[0][c] = (mask && mask[c]) ? 0.5 * (r->Pbar_t[c] + Ptgt[1][c]) : Ptgt[1][c];
+        }
         for (int h = 0; h < 2; ++h) {
             if (h == 1)
                 for (int c = 0; c < 9; ++c) tgt[1][c] = (mask && mask[c]) ? r->Fbar_t[c] : Fbar[c];
-            fft_status s = run_once(r, tgt[h], Pstar, mask, 0.5 * dt, st);
+            fft_status s = run_once(r, tgt[h], Ptgt[h], mask, 0.5 * dt, st);
             if (s == FFT_ERR_NOT_CONVERGED && depth < r->opt.max_cutbacks)
-                s = run_halves(r, tgt[h], Pstar, mask, 0.5 * dt, st, depth + 1);
+                s = run_halves(r, tgt[h], Ptgt[h], mask, 0.5 * dt, st, depth + 1);
             if (s != FFT_OK) return s;
         }
         return FFT_OK;
@@ -1276,8 +1296,20 @@ struct CkptHeader {
     int32_t version, prec, n[3], esz;
     uint64_t N;
     double Fbar_t[9];
+    double Pbar_t[9];     // committed macroscopic stress (cut-back under mixed control)
+    uint64_t setup_hash;  // grain ids, orientations, soft regions, material
 };
 constexpr char kCkptMagic[8] = {'F', 'F', 'T', 'C', 'K', 'P', 'T', '1'};
+constexpr int32_t kCkptVersion = 2;
+// 64-bit FNV-1a over a byte range, chained through h
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
 size_t ckpt_bytes(const fft_rve_s* r) {
     const size_t N = r->g.N;
     return sizeof(CkptHeader) + 19 * N * r->esz + (size_t)HIST_SLOTS * N * sizeof(double);
@@ -1351,6 +1383,15 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
             delete r;
             return FFT_ERR_ARG;
         }
+    {
+        uint64_t hs = 14695981039346656037ull;
+        hs = fnv1a(hs, grain_ids, N * sizeof(int32_t));
+        hs = fnv1a(hs, euler, 3 * (size_t)n_grains * sizeof(double));
+        hs = fnv1a(hs, mat, sizeof(*mat));
+        const uint8_t none = 0xff;
+        hs = elastic_only ? fnv1a(hs, elastic_only, N) : fnv1a(hs, &none, 1);
+        r->setup_hash = hs;
+    }
     // constitutive constants (MPa, mm, s); tau*dV in N mm = 1e-3 J
     const double kT = mat->k_B * mat->T;
     r->cpp.C11 = mat->C11;
@@ -1587,7 +1628,7 @@ fft_status state_save(fft_rve_t r, void* dst, size_t* bytes) {
     if (*bytes < need) FAIL(r, FFT_ERR_ARG, "state_save: %zu bytes < %zu", *bytes, need);
     CkptHeader h{};
     std::memcpy(h.magic, kCkptMagic, sizeof(h.magic));
-    h.version = 1;
+    h.version = kCkptVersion;
     h.prec = r->prec;
     h.n[0] = r->g.n0;
     h.n[1] = r->g.n1;
@@ -1595,6 +1636,8 @@ fft_status state_save(fft_rve_t r, void* dst, size_t* bytes) {
     h.esz = (int32_t)r->esz;
     h.N = r->g.N;
     std::memcpy(h.Fbar_t, r->Fbar_t, sizeof(h.Fbar_t));
+    std::memcpy(h.Pbar_t, r->Pbar_t, sizeof(h.Pbar_t));
+    h.setup_hash = r->setup_hash;
     std::memcpy(dst, &h, sizeof(h));
     char* p = (char*)dst + sizeof(h);
     CkptPart parts[4];
@@ -1613,11 +1656,15 @@ fft_status state_load(fft_rve_t r, const void* src, size_t bytes) {
     CkptHeader h;
     if (bytes < sizeof(h)) FAIL(r, FFT_ERR_ARG, "state_load: %zu bytes is no checkpoint", bytes);
     std::memcpy(&h, src, sizeof(h));
-    if (std::memcmp(h.magic, kCkptMagic, sizeof(h.magic)) != 0 || h.version != 1)
+    if (std::memcmp(h.magic, kCkptMagic, sizeof(h.magic)) != 0 || h.version != kCkptVersion)
         FAIL(r, FFT_ERR_ARG, "state_load: not a checkpoint of this library");
     if (h.prec != r->prec || h.esz != (int32_t)r->esz || h.n[0] != r->g.n0 ||
         h.n[1] != r->g.n1 || h.n[2] != r->g.n2 || h.N != (uint64_t)r->g.N)
         FAIL(r, FFT_ERR_ARG, "state_load: checkpoint of another grid or precision");
+    if (h.setup_hash != r->setup_hash)
+        FAIL(r, FFT_ERR_ARG,
+             "state_load: checkpoint of another microstructure or material (grain ids, "
+             "orientations, soft regions or material constants differ)");
     const size_t need = ckpt_bytes(r);
     if (bytes < need) FAIL(r, FFT_ERR_ARG, "state_load: %zu bytes < %zu", bytes, need);
     const char* p = (const char*)src + sizeof(h);
@@ -1633,6 +1680,7 @@ fft_status state_load(fft_rve_t r, const void* src, size_t bytes) {
     CK(r, cudaStreamSynchronize(r->st));
     std::memcpy(r->Fbar_t, h.Fbar_t, sizeof(r->Fbar_t));
     std::memcpy(r->Fbar, h.Fbar_t, sizeof(r->Fbar));
+    std::memcpy(r->Pbar_t, h.Pbar_t, sizeof(r->Pbar_t));
     r->state = ST_COMMITTED;
     r->converged = false;
     r->cp_valid = false;

@@ -189,6 +189,41 @@ def test_cutback_under_mixed_control_matches_oracle():
         r.close()
 
 
+def test_cutback_with_a_changing_stress_target_matches_oracle():
+    """Cut-back under mixed control when the stress target moves between
+    increments (lateral stresses 0 -> -40 MPa with a step from 0.3 to
+    0.7 %): each half takes half of the stress change; the FP64 path takes
+    the oracle's halvings and reaches its solved macroscopic F and fields."""
+    import torch
+    import oracle as O
+    n = (6, 6, 6)
+    gid, eul = I.voronoi(n, 3, 11)
+    mat = dict(I.material("baseline"), tau_c0=250.0)
+    m = I.uniaxial_stress_mask(1)
+    prog = I.uniaxial_cycle_program(0.006, 8, 1)
+    P1 = np.zeros(9)
+    P1[0] = P1[8] = -40.0
+    Fb = prog[1][0].copy()
+    Fb[4] += 0.001
+    opts = I.solver_options("paper", max_newton=10, max_lin=100, max_cutbacks=3)
+    o = O.RVE(n, H, gid, eul, mat, opts)
+    r = FF.RVE(n, H, gid, eul, mat, opts, prec="fp64", stream=torch.cuda.Stream())
+    res = []
+    for h in (o, r):
+        s, st = h.run_increment(prog[0][0], prog[0][1], Pbar=np.zeros(9), stress_mask=m)
+        assert s == 0
+        guess = np.where(m == 1, np.array(st["Fbar"]), Fb)
+        s, st = h.run_increment(guess, 4.0, Pbar=P1, stress_mask=m)
+        assert s == 0 and st["cutbacks"] >= 1
+        res.append(st)
+    assert res[0]["cutbacks"] == res[1]["cutbacks"]
+    assert np.abs(np.array(res[0]["Fbar"]) - np.array(res[1]["Fbar"])).max() < 1e-9
+    for f in ("F", "P", "Fp"):
+        a, b = r.field(f), o.field(f)
+        assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(b), f
+    r.close()
+
+
 def test_bounded_wait_gives_up_on_a_barrier_nothing_completes():
     """The pipelined update pass's mbarrier waits are bounded: on a barrier
     that no copy completes, the wait returns after its round limit (and the

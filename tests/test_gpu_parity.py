@@ -540,8 +540,8 @@ def test_checkpoint_resume_is_bitwise(prec):
     checkpoint, two more increments; a fresh handle loaded from the
     checkpoint and given the same two increments ends in the same state bit
     for bit (current and committed fields, the history sums, the last
-    increment's iteration counts).  A checkpoint of another grid is
-    refused."""
+    increment's iteration counts).  A checkpoint of another grid, material
+    or set of orientations is refused."""
     n = (8, 6, 5)
     gid, eul = I.voronoi(n, 3, 21)
     mat = dict(MAT, tau_c0=250.0)
@@ -567,5 +567,12 @@ def test_checkpoint_resume_is_bitwise(prec):
                stream=stream())
     with pytest.raises(FF.FFTError):
         c.state_load(ck)
-    for r in (a, b, c):
+    # nor one of the same grid with other material constants or orientations
+    d = FF.RVE(n, H, gid, eul, dict(mat, tau_c0=251.0), opts, prec=prec, stream=stream())
+    with pytest.raises(FF.FFTError):
+        d.state_load(ck)
+    e = FF.RVE(n, H, gid, eul[::-1].copy(), mat, opts, prec=prec, stream=stream())
+    with pytest.raises(FF.FFTError):
+        e.state_load(ck)
+    for r in (a, b, c, d, e):
         r.close()

@@ -970,3 +970,72 @@ def test_history_and_driving_force_chain():
     the W_crit event and its value, and the driving force from the current
     W_e+, against a hand-built chain on a homogeneous crystal."""
     history_chain_check()
+
+
+def test_mixed_cutback_halves_a_changing_stress_target():
+    """Cut-back under mixed control when the stress target changes between
+    increments: each half takes half of the load change, so the first half
+    aims the stress-controlled components at the midpoint of the committed
+    target (the previous increment's) and the new one.  An increment that
+    fails whole (a step from 0.3 to 0.7 % with the lateral stresses moving
+    from 0 to -40 MPa) equals, bit for bit, the same halves requested one by one with
+    cut-back off, each half's targets built that way."""
+    n = (6, 6, 6)
+    gid, eul = I.voronoi(n, 3, 11)
+    mat = dict(I.material("baseline"), tau_c0=250.0)
+    m = I.uniaxial_stress_mask(1)
+    prog = I.uniaxial_cycle_program(0.006, 8, 1)
+    P0, P1 = np.zeros(9), np.zeros(9)
+    P1[0] = P1[8] = -40.0
+    kw = dict(max_newton=10, max_lin=100)
+    a = O.RVE(n, I.VOXEL_MM, gid, eul, mat, I.solver_options("paper", max_cutbacks=3, **kw))
+    b = O.RVE(n, I.VOXEL_MM, gid, eul, mat, I.solver_options("paper", max_cutbacks=0, **kw))
+    # a first, small increment at zero lateral stress, taken whole by both
+    F1 = prog[0][0]
+    s, st1 = a.run_increment(F1, prog[0][1], Pbar=P0, stress_mask=m)
+    assert s == 0 and st1["cutbacks"] == 0
+    s, stb = b.run_increment(F1, prog[0][1], Pbar=P0, stress_mask=m)
+    assert s == 0
+    committed = [np.array(stb["Fbar"]), P0.copy()]
+    # then a large step that also moves the lateral stress target
+    Fb = prog[1][0].copy()
+    Fb[4] += 0.001
+    dt = 4.0
+    guess = np.where(m == 1, committed[0], Fb)
+    s, st = a.run_increment(guess, dt, Pbar=P1, stress_mask=m)
+    assert s == 0 and st["cutbacks"] >= 1
+    halvings = [0]
+
+    def attempt(F, P, t):
+        s, stx = b.run_increment(F, t, Pbar=P, stress_mask=m)
+        if s == 0:
+            committed[0] = np.array(stx["Fbar"])
+            committed[1] = P.copy()
+        return s
+
+    def halves(F, P, t, depth):
+        halvings[0] += 1
+        mid = 0.5 * (committed[0] + F)
+        Pm = np.where(m == 1, 0.5 * (committed[1] + P), P)
+        s = attempt(mid, Pm, 0.5 * t)
+        if s == -5 and depth < 3:
+            s = halves(mid, Pm, 0.5 * t, depth + 1)
+        if s:
+            return s
+        last = np.where(m == 1, committed[0], F)
+        s = attempt(last, P, 0.5 * t)
+        if s == -5 and depth < 3:
+            s = halves(last, P, 0.5 * t, depth + 1)
+        return s
+
+    assert attempt(guess, P1, dt) == -5
+    assert halves(guess, P1, dt, 1) == 0
+    assert halvings[0] == st["cutbacks"]
+    assert np.array_equal(committed[0], np.array(st["Fbar"]))
+    for f in ("F", "P", "Fp", "rho_ssd", "gamma"):
+        assert np.array_equal(a.field(f), b.field(f)), f
+    # the lateral stresses reached the new target within the mixed-control
+    # stop rule, tol_newton max|<gP>|
+    Pm = a.field("P").mean(axis=1)
+    band = 5e-3 * np.abs(Pm).max()
+    assert abs(Pm[0] + 40.0) <= band and abs(Pm[8] + 40.0) <= band
