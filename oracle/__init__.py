@@ -235,6 +235,10 @@ class RVE:
                  naive=False, threads=0):
         self.n = tuple(int(x) for x in n)
         self.N = int(np.prod(self.n))
+        if not threads:
+            # the oracle starts its threads for every parallel loop, which
+            # outweighs the work of a loop over fewer than ~32k voxels
+            threads = 1 if self.N < 32768 else (os.cpu_count() or 1)
         self._m = material(params)
         self._o = options(opts, naive, threads)
         g = np.ascontiguousarray(grain_ids, dtype=np.int32).reshape(-1)

@@ -243,6 +243,20 @@ void degrade(const void* P, const void* phi, double kres, void* out, size_t N, c
                                                   N);
 }
 
+// Offset of field c at half-spectrum entry e in the interleaved layout of
+// the fused x pass: (9 r + c) n0h + kx for the row r = ky + n1 kz of e.
+__device__ __forceinline__ size_t il_at(const SGrid& g, size_t e64, int c) {
+    const unsigned e = (unsigned)e64;
+    const unsigned n0h = (unsigned)g.n0h;
+    const unsigned rest = fdiv(e, g.fd_n0h);
+    return ((size_t)rest * 9 + c) * n0h + (e - rest * n0h);
+}
+// Offset of field c at entry e: component-major, or interleaved (IL).
+template <bool IL>
+__device__ __forceinline__ size_t fld_at(const SGrid& g, size_t e, int c) {
+    return IL ? il_at(g, e, c) : (size_t)c * g.Nh + e;
+}
+
 // Partner of a half-spectrum entry on the kx = 0 plane (or kx = n0/2 for an
 // even n0): the entry holding the conjugate frequency (-ky, -kz).  Returns
 // false for entries off those planes.
@@ -268,19 +282,18 @@ __device__ __forceinline__ bool hs_partner(const SGrid& g, size_t e64, size_t& p
 // k and -k coincide, have zero multipliers).  Its entries are loaded with
 // the entry's own (off the planes p = e, a cache hit), so no lane waits for
 // a second round of loads.
-template <typename R>
+template <typename R, bool IL = false>
 __device__ __forceinline__ void div3_real(const typename Tr<R>::Cx* T, const SGrid& g, size_t e,
                                           const R* xd, R sign, typename Tr<R>::Cx* out) {
     typedef typename Tr<R>::Cx Cx;
     size_t p;
     const bool hp = hs_partner(g, e, p);
     if (!hp) p = e;
-    const size_t Nh = g.Nh;
     Cx te[9], tp[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-        te[q] = T[q * Nh + e];
-        tp[q] = T[q * Nh + p];
+        te[q] = T[fld_at<IL>(g, e, q)];
+        tp[q] = T[fld_at<IL>(g, p, q)];
     }
     const R xp[3] = {xd[0], -xd[1], -xd[2]};
 #pragma unroll
@@ -393,7 +406,7 @@ __device__ __forceinline__ void green_apply(const R* Ks, const R* xd,
 
 // v = scale * vin (optionally stored to vout); z = M(xi) v when use_pre,
 // else z = v; G_ij = z_i i xi_j, the 9-component spectrum of grad z.
-template <typename R>
+template <typename R, bool IL>
 __global__ void __launch_bounds__(kThreads, 3) k_precond_grad(const typename Tr<R>::Cx* vin,
                                                               R scale, typename Tr<R>::Cx* vout,
                                                               const double* Kbar, SGrid g,
@@ -423,15 +436,19 @@ __global__ void __launch_bounds__(kThreads, 3) k_precond_grad(const typename Tr<
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) G[(3 * i + j) * Nh + e] = cmul_i(z[i], xd[j]);
+            for (int j = 0; j < 3; ++j) G[fld_at<IL>(g, e, 3 * i + j)] = cmul_i(z[i], xd[j]);
     }
 }
 template <typename R>
 void precond_grad(const void* vin, double scale, void* vout, const double* Kbar, const SGrid& g,
-                  void* G, int use_pre, cudaStream_t s) {
+                  void* G, int use_pre, cudaStream_t s, int il) {
     typedef typename Tr<R>::Cx Cx;
-    k_precond_grad<R><<<grid_for(g.Nh), kThreads, 0, s>>>((const Cx*)vin, (R)scale, (Cx*)vout,
-                                                          Kbar, g, (Cx*)G, use_pre);
+    if (il)
+        k_precond_grad<R, true><<<grid_for(g.Nh), kThreads, 0, s>>>(
+            (const Cx*)vin, (R)scale, (Cx*)vout, Kbar, g, (Cx*)G, use_pre);
+    else
+        k_precond_grad<R, false><<<grid_for(g.Nh), kThreads, 0, s>>>(
+            (const Cx*)vin, (R)scale, (Cx*)vout, Kbar, g, (Cx*)G, use_pre);
 }
 
 // tau = g(phi) K : grad z in place (grad z arrives scaled by N from the
@@ -636,7 +653,7 @@ __device__ __forceinline__ void dots_finish(const R (&acc)[3 + 2 * NQ], int k, c
 // b_i = q_i.z accumulate (the dot layout above); the tail forms the step's
 // coefficients.  Saves the contraction's launch and tail and the re-read of
 // z and c.
-template <typename R, int NQ>
+template <typename R, int NQ, bool IL>
 __global__ void __launch_bounds__(kThreads, 2) k_contract_dots(
     const typename Tr<R>::Cx* T, SGrid g, typename Tr<R>::Cx* w, const typename Tr<R>::Cx* c,
     const typename Tr<R>::Cx* V, size_t vstride, int k, Red red, double* Hd, double* Hp,
@@ -653,7 +670,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_contract_dots(
         Cx zc[3], cv[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) cv[q] = c[q * Nh + e];
-        div3_real<R>(T, g, e, xd, R(-1), zc);
+        div3_real<R, IL>(T, g, e, xd, R(-1), zc);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             w[q * Nh + e] = zc[q];
@@ -688,14 +705,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_contract_dots(
 template <typename R>
 void contract_dots(const void* T, const SGrid& g, void* w, const void* c, const void* V,
                    size_t vstride, int k, const Red& red, double* Hd, double* Hp, double* slot,
-                   double* coef, const BulkCfg* bc, cudaStream_t s) {
+                   double* coef, const BulkCfg* bc, cudaStream_t s, int il) {
     typedef typename Tr<R>::Cx Cx;
     const Cx *TT = (const Cx*)T, *cc = (const Cx*)c, *VV = (const Cx*)V;
     Cx* ww = (Cx*)w;
     const int* err = bc ? bc->err : nullptr;
-#define CDOTS(NQ)                                                                           \
-    k_contract_dots<R, NQ><<<kRedBlocks, kThreads, 0, s>>>(TT, g, ww, cc, VV, vstride, k, red, \
-                                                           Hd, Hp, slot, coef, err)
+#define CDOTS(NQ)                                                                             \
+    do {                                                                                      \
+        if (il)                                                                               \
+            k_contract_dots<R, NQ, true><<<kRedBlocks, kThreads, 0, s>>>(                     \
+                TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err);                 \
+        else                                                                                  \
+            k_contract_dots<R, NQ, false><<<kRedBlocks, kThreads, 0, s>>>(                    \
+                TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err);                 \
+    } while (0)
     if (k <= 0)
         CDOTS(0);
     else if (k <= 4)
@@ -741,7 +764,7 @@ __device__ __forceinline__ void bulk_drain(uint64_t* full, int issued) {
     }
 }
 
-template <typename R>
+template <typename R, bool IL>
 __global__ void __launch_bounds__(kUpdT) k_dcgs_update_bulk(
     typename Tr<R>::Cx* V, size_t vstride, int k, const typename Tr<R>::Cx* z,
     const double* coef, const double* Kbar, SGrid g, typename Tr<R>::Cx* G, int tpc, Red red,
@@ -855,12 +878,14 @@ __global__ void __launch_bounds__(kUpdT) k_dcgs_update_bulk(
                 nn += nx[q].x * nx[q].x + nx[q].y * nx[q].y;
             }
             acc[0] += wt * nn;
-            Cx zz[3];
-            green_apply<R>(Ks, xd, nx, zz);
+            if (G) {
+                Cx zz[3];
+                green_apply<R>(Ks, xd, nx, zz);
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+                for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int j = 0; j < 3; ++j) G[(size_t)(3 * i + j) * Nh + e] = cmul_i(zz[i], xd[j]);
+                    for (int j = 0; j < 3; ++j) G[fld_at<IL>(g, e, 3 * i + j)] = cmul_i(zz[i], xd[j]);
+            }
         }
     }
     if (!ok) atomicExch(err, 1);
@@ -882,10 +907,12 @@ int dcgs_bulk_setup(BulkCfg& bc) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int su = (int)upd_bulk_smem<R>();
     int nu = 0;
-    if (cudaFuncSetAttribute(k_dcgs_update_bulk<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             su) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nu, k_dcgs_update_bulk<R>, kUpdT, su) !=
-            cudaSuccess)
+    if (cudaFuncSetAttribute(k_dcgs_update_bulk<R, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, su) != cudaSuccess ||
+        cudaFuncSetAttribute(k_dcgs_update_bulk<R, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, su) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nu, k_dcgs_update_bulk<R, false>, kUpdT,
+                                                      su) != cudaSuccess)
         nu = 0;
     cudaGetLastError();
     // the reduction buffers hold kRedSlots x kRedBlocks partials
@@ -910,7 +937,7 @@ static inline void tile_split(int ntiles, int maxb, int& tpc, int& nb) {
 //   c_{k+1} = z / nu - Q_k e - c_k dd_k / nu     -> slot k + 1
 //   G = (M c_{k+1}) (x) i xi                     -> the next step's gradient
 // and out[0] = |c_{k+1}|^2.
-template <typename R>
+template <typename R, bool IL>
 __global__ void __launch_bounds__(kThreads, 2) k_dcgs_update(typename Tr<R>::Cx* V,
                                                              size_t vstride, int k,
                                                              const typename Tr<R>::Cx* z,
@@ -968,12 +995,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_dcgs_update(typename Tr<R>::Cx*
             nn += nx[c].x * nx[c].x + nx[c].y * nx[c].y;
         }
         acc[0] += wt * nn;
-        Cx zz[3];
-        green_apply<R>(Ks, xd, nx, zz);
+        if (G) {
+            Cx zz[3];
+            green_apply<R>(Ks, xd, nx, zz);
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+            for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) G[(3 * i + j) * Nh + e] = cmul_i(zz[i], xd[j]);
+                for (int j = 0; j < 3; ++j) G[fld_at<IL>(g, e, 3 * i + j)] = cmul_i(zz[i], xd[j]);
+        }
     }
     block_partials<1, kThreads>(acc, 1, 0u, red.part);
     grid_finish<kThreads, 1>(red, 1, 0u, 1.0);
@@ -981,7 +1010,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dcgs_update(typename Tr<R>::Cx*
 template <typename R>
 void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* coef,
                  const double* Kbar, const SGrid& g, void* G, const Red& red, const BulkCfg* bc,
-                 cudaStream_t s) {
+                 cudaStream_t s, int il) {
     typedef typename Tr<R>::Cx Cx;
     if (bc && bulk_aligned<R>(g)) {
         int tpc, nb;
@@ -996,12 +1025,20 @@ void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* co
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        cudaLaunchKernelEx(&cfg, k_dcgs_update_bulk<R>, (Cx*)V, vstride, k, (const Cx*)z, coef,
-                           Kbar, g, (Cx*)G, tpc, red, bc->err);
+        if (il)
+            cudaLaunchKernelEx(&cfg, k_dcgs_update_bulk<R, true>, (Cx*)V, vstride, k,
+                               (const Cx*)z, coef, Kbar, g, (Cx*)G, tpc, red, bc->err);
+        else
+            cudaLaunchKernelEx(&cfg, k_dcgs_update_bulk<R, false>, (Cx*)V, vstride, k,
+                               (const Cx*)z, coef, Kbar, g, (Cx*)G, tpc, red, bc->err);
         return;
     }
-    k_dcgs_update<R><<<grid_for(g.Nh), kThreads, 0, s>>>((Cx*)V, vstride, k, (const Cx*)z, coef,
-                                                         Kbar, g, (Cx*)G, red);
+    if (il)
+        k_dcgs_update<R, true><<<grid_for(g.Nh), kThreads, 0, s>>>(
+            (Cx*)V, vstride, k, (const Cx*)z, coef, Kbar, g, (Cx*)G, red);
+    else
+        k_dcgs_update<R, false><<<grid_for(g.Nh), kThreads, 0, s>>>(
+            (Cx*)V, vstride, k, (const Cx*)z, coef, Kbar, g, (Cx*)G, red);
 }
 
 // x += M (sum_i y_i V_i)  (right-preconditioned GMRES update)
@@ -1423,17 +1460,17 @@ int selftest_bounded_wait(unsigned limit) {
     template void degrade<R>(const void*, const void*, double, void*, size_t, cudaStream_t);    \
     template void residual<R>(const void*, const SGrid&, void*, const Red&, cudaStream_t);      \
     template void precond_grad<R>(const void*, double, void*, const double*, const SGrid&,      \
-                                  void*, int, cudaStream_t);                                    \
+                                  void*, int, cudaStream_t, int);                               \
     template void tangent_apply<R>(void*, const void*, const void*, double, size_t,             \
                                    cudaStream_t);                                               \
     template void contract<R>(const void*, const SGrid&, void*, cudaStream_t);                  \
     template void dcgs_update<R>(void*, size_t, int, const void*, const double*,                \
                                  const double*, const SGrid&, void*, const Red&,                \
-                                 const BulkCfg*, cudaStream_t);                                 \
+                                 const BulkCfg*, cudaStream_t, int);                            \
     template int dcgs_bulk_setup<R>(BulkCfg&);                                                  \
     template void contract_dots<R>(const void*, const SGrid&, void*, const void*, const void*,  \
                                    size_t, int, const Red&, double*, double*, double*, double*, \
-                                   const BulkCfg*, cudaStream_t);                               \
+                                   const BulkCfg*, cudaStream_t, int);                          \
     template void norm2<R>(const void*, const SGrid&, const Red&, cudaStream_t);                \
     template void xupdate<R>(void*, const void*, size_t, int, const double*, const double*,     \
                              const SGrid&, cudaStream_t);                                       \

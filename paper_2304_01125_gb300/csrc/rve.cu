@@ -104,6 +104,14 @@ struct fft_rve_s {
     // resident-CTA budgets and the device error word of their bounded waits
     BulkCfg bulk{};
     bool use_bulk = false;
+    // fused x pass of the Arnoldi step (inverse real transform along x,
+    // tangent apply, forward real transform in one kernel) between batched
+    // 2-D transforms over (z, y) of the interleaved spectrum layout; off
+    // for grids it does not support or with FATIGUEFFT_FUSED=0
+    FusedX fx{};
+    bool use_fused = false;
+    cufftHandle yz = 0;
+    bool yz_plan = false;
     double* stage = nullptr;  // device staging for host fields_out / fields_in
     size_t stage_bytes = 0;
     std::vector<void*> allocs;
@@ -283,7 +291,10 @@ static fft_status dalloc(fft_rve_s* r, void** p, size_t bytes) {
 // ---------------------------------------------------------------- cuFFT
 template <typename R> struct FFT;
 template <> struct FFT<float> {
-    static constexpr cufftType R2C = CUFFT_R2C, C2R = CUFFT_C2R;
+    static constexpr cufftType R2C = CUFFT_R2C, C2R = CUFFT_C2R, C2C = CUFFT_C2C;
+    static cufftResult c2c(cufftHandle p, void* io, int dir) {
+        return cufftExecC2C(p, (cufftComplex*)io, (cufftComplex*)io, dir);
+    }
     static cufftResult fwd(cufftHandle p, void* i, void* o) {
         return cufftExecR2C(p, (cufftReal*)i, (cufftComplex*)o);
     }
@@ -292,7 +303,10 @@ template <> struct FFT<float> {
     }
 };
 template <> struct FFT<double> {
-    static constexpr cufftType R2C = CUFFT_D2Z, C2R = CUFFT_Z2D;
+    static constexpr cufftType R2C = CUFFT_D2Z, C2R = CUFFT_Z2D, C2C = CUFFT_Z2Z;
+    static cufftResult c2c(cufftHandle p, void* io, int dir) {
+        return cufftExecZ2Z(p, (cufftDoubleComplex*)io, (cufftDoubleComplex*)io, dir);
+    }
     static cufftResult fwd(cufftHandle p, void* i, void* o) {
         return cufftExecD2Z(p, (cufftDoubleReal*)i, (cufftDoubleComplex*)o);
     }
@@ -523,7 +537,8 @@ struct Impl {
         if (j == 0) {
             const double Nh = (double)r->g.Nh, es = (double)sizeof(R);
             cudaEvent_t e = prof_begin(r, KF_PRECOND);
-            precond_grad<R>(src, scale, r->V, r->Kbar, r->g, r->cb9, 1, r->st);
+            precond_grad<R>(src, scale, r->V, r->Kbar, r->g, r->cb9, 1, r->st,
+                            r->use_fused ? 1 : 0);
             prof_end(r, KF_PRECOND, e, Nh * 2 * es * (3 + 3 + 9));
             r->launches += 1;
         }
@@ -590,25 +605,52 @@ struct Impl {
         Cx* V = (Cx*)r->V;
         double* dslot = r->red + kDslot;
         cudaEvent_t e;
-        TRY(inv9(r));
-        e = prof_begin(r, KF_TANGENT);
-        tangent_apply<R>(r->rb9, r->K, r->phi, r->mat.k_res, r->g.N, r->st);
-        prof_end(r, KF_TANGENT, e, N * es * (9 + 81 + 1 + 9));
-        TRY(fwd9(r));
-        // z = -div T (stored to w) and, in the same pass over c_k and
-        // q_0 .. q_{k-1}: alpha, beta, a, b and the step's coefficients
-        e = prof_begin(r, KF_MDOT);
         double* Hp = r->Hd + (size_t)kMaxKrylov * kHcol;
         double* coef = Hp + (size_t)kMaxKrylov * kHcol;
         const BulkCfg* bc = r->use_bulk ? &r->bulk : nullptr;
-        contract_dots<R>(r->cb9, r->g, r->w, V + (size_t)k * vs, V, vs, k, red_at(r, r->red),
-                         r->Hd, Hp, dslot, coef, bc, r->st);
-        prof_end(r, KF_MDOT, e, Nh * 2 * es * (9 + 3 + 3 * (k + 1)));
-        // q_k final, c_{k+1} and the next gradient spectrum
-        e = prof_begin(r, KF_GSUPD);
-        dcgs_update<R>(V, vs, k, r->w, coef, r->Kbar, r->g, r->cb9,
-                       red_at(r, dslot + kSlotNorm), bc, r->st);
-        prof_end(r, KF_GSUPD, e, Nh * 2 * es * 3 * (k + 2 + 2 + 3));
+        if (r->use_fused) {
+            // the gradient spectrum (interleaved layout) to (kx, y, z) by the
+            // batched 2-D inverse transform, then the fused x pass (inverse
+            // real transform, tangent apply, forward real transform), then
+            // the batched 2-D forward transform
+            e = prof_begin(r, KF_FFT9);
+            CKF(r, FFT<R>::c2c(r->yz, r->cb9, CUFFT_INVERSE));
+            prof_end(r, KF_FFT9, e);
+            e = prof_begin(r, KF_TANGENT);
+            fused_xpass<R>(r->fx, r->cb9, r->K, r->phi, r->mat.k_res, r->g, r->st);
+            prof_end(r, KF_TANGENT, e, Nh * 2 * es * 18 + N * es * 82);
+            e = prof_begin(r, KF_FFT9);
+            CKF(r, FFT<R>::c2c(r->yz, r->cb9, CUFFT_FORWARD));
+            prof_end(r, KF_FFT9, e);
+            // z = -div T (stored to w) and, in the same pass over c_k and
+            // q_0 .. q_{k-1}: alpha, beta, a, b and the step's coefficients
+            e = prof_begin(r, KF_MDOT);
+            contract_dots<R>(r->cb9, r->g, r->w, V + (size_t)k * vs, V, vs, k,
+                             red_at(r, r->red), r->Hd, Hp, dslot, coef, bc, r->st, 1);
+            prof_end(r, KF_MDOT, e, Nh * 2 * es * (9 + 3 + 3 * (k + 1)));
+            // q_k final, c_{k+1} and the next gradient spectrum
+            e = prof_begin(r, KF_GSUPD);
+            dcgs_update<R>(V, vs, k, r->w, coef, r->Kbar, r->g, r->cb9,
+                           red_at(r, dslot + kSlotNorm), bc, r->st, 1);
+            prof_end(r, KF_GSUPD, e, Nh * 2 * es * 3 * (k + 2 + 2 + 3));
+        } else {
+            TRY(inv9(r));
+            e = prof_begin(r, KF_TANGENT);
+            tangent_apply<R>(r->rb9, r->K, r->phi, r->mat.k_res, r->g.N, r->st);
+            prof_end(r, KF_TANGENT, e, N * es * (9 + 81 + 1 + 9));
+            TRY(fwd9(r));
+            // z = -div T (stored to w) and, in the same pass over c_k and
+            // q_0 .. q_{k-1}: alpha, beta, a, b and the step's coefficients
+            e = prof_begin(r, KF_MDOT);
+            contract_dots<R>(r->cb9, r->g, r->w, V + (size_t)k * vs, V, vs, k,
+                             red_at(r, r->red), r->Hd, Hp, dslot, coef, bc, r->st);
+            prof_end(r, KF_MDOT, e, Nh * 2 * es * (9 + 3 + 3 * (k + 1)));
+            // q_k final, c_{k+1} and the next gradient spectrum
+            e = prof_begin(r, KF_GSUPD);
+            dcgs_update<R>(V, vs, k, r->w, coef, r->Kbar, r->g, r->cb9,
+                           red_at(r, dslot + kSlotNorm), bc, r->st);
+            prof_end(r, KF_GSUPD, e, Nh * 2 * es * 3 * (k + 2 + 2 + 3));
+        }
         double* slot = r->hslot + (size_t)(k % 2) * kSlot;
         CK(r, cudaMemcpyAsync(slot, dslot, kSlotLen * sizeof(double), cudaMemcpyDeviceToHost,
                               r->st));
@@ -1249,6 +1291,7 @@ static void release(fft_rve_s* r) {
     for (auto e : r->prof_pool) cudaEventDestroy(e);
     r->prof_pool.clear();
     drop_graphs(r);
+    if (r->yz_plan) cufftDestroy(r->yz);
     if (r->plans) {
         cufftDestroy(r->r2c9);
         cufftDestroy(r->c2r9);
@@ -1489,6 +1532,43 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
         const bool want = !(bv && bv[0] == '0');
         r->use_bulk = want && (r->prec == FFT_PREC_FP64 ? dcgs_bulk_setup<double>(r->bulk)
                                                         : dcgs_bulk_setup<float>(r->bulk));
+    }
+    {
+        // FATIGUEFFT_FUSED=1 selects the fused x pass in the Arnoldi step
+        // (measured slower than the library 3-D transforms with the separate
+        // tangent apply at 64^3: the strided batched 2-D transforms cost more
+        // than the transform passes they replace); grids whose n0 is not a
+        // power of two (or with n1 = n2 = 1) always use the library path
+        const char* fv = std::getenv("FATIGUEFFT_FUSED");
+        const bool want = (fv && fv[0] == '1') && (g.n1 > 1 || g.n2 > 1);
+        const bool f64 = r->prec == FFT_PREC_FP64;
+        if (want && (f64 ? fused_x_plan<double>(r->fx, g) : fused_x_plan<float>(r->fx, g))) {
+            void* tw = nullptr;
+            s = dalloc(r, &tw, (size_t)g.n0 * cs);
+            if (s != FFT_OK) {
+                release(r);
+                delete r;
+                return s;
+            }
+            std::vector<unsigned char> host((size_t)g.n0 * cs);
+            if (f64)
+                fused_x_twiddles<double>(g.n0, host.data());
+            else
+                fused_x_twiddles<float>(g.n0, host.data());
+            cudaMemcpy(tw, host.data(), host.size(), cudaMemcpyHostToDevice);
+            r->fx.tw = tw;
+            // batched 2-D transform over (z, y) of the interleaved layout:
+            // batch b = 9 kx-runs of n0h, element stride 9 n0h
+            int n2d[2] = {g.n2, g.n1};
+            const int lead2 = g.n2 == 1 ? 1 : 0;
+            const int st9 = 9 * g.n0h;
+            if (cufftPlanMany(&r->yz, 2 - lead2, n2d + lead2, n2d + lead2, st9, 1, n2d + lead2,
+                              st9, 1, f64 ? CUFFT_Z2Z : CUFFT_C2C, st9) == CUFFT_SUCCESS) {
+                r->yz_plan = true;
+                cufftSetStream(r->yz, r->st);
+                r->use_fused = true;
+            }
+        }
     }
     upload_slip_table(r->st);
     // cuFFT plans: dims slowest-first (n2, n1, n0); 9-field batches use the

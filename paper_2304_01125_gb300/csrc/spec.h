@@ -30,7 +30,8 @@ template <typename R> void gnd_rho(const void* Lam, const int32_t* grain, const 
 template <typename R> void kbar(const void* K, const void* phi, double kres, size_t N, const Red& red, cudaStream_t s);
 template <typename R> void degrade(const void* P, const void* phi, double kres, void* out, size_t N, cudaStream_t s);
 template <typename R> void residual(const void* Ph, const SGrid& g, void* b, const Red& red, cudaStream_t s);
-template <typename R> void precond_grad(const void* vin, double scale, void* vout, const double* Kbar, const SGrid& g, void* G, int use_pre, cudaStream_t s);
+// il = 1 writes G in the interleaved layout of the fused x pass
+template <typename R> void precond_grad(const void* vin, double scale, void* vout, const double* Kbar, const SGrid& g, void* G, int use_pre, cudaStream_t s, int il = 0);
 template <typename R> void tangent_apply(void* G, const void* K, const void* phi, double kres, size_t N, cudaStream_t s);
 template <typename R> void contract(const void* T, const SGrid& g, void* w, cudaStream_t s);
 // Arnoldi step kernels (DCGS2, see kernels_spec.cu).  Hessenberg columns on
@@ -56,9 +57,27 @@ template <typename R> int dcgs_bulk_setup(BulkCfg& bc);
 int selftest_bounded_wait(unsigned limit);
 // the contraction fused with the dot pass: w = -div T stored; alpha, beta,
 // |z|^2, a, b reduced and the step coefficients formed (kernels_spec.cu)
-template <typename R> void contract_dots(const void* T, const SGrid& g, void* w, const void* c, const void* V, size_t vstride, int k, const Red& red, double* Hd, double* Hp, double* slot, double* coef, const BulkCfg* bc, cudaStream_t s);
-template <typename R> void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* coef, const double* Kbar, const SGrid& g, void* G, const Red& red, const BulkCfg* bc, cudaStream_t s);
+// il = 1: T (and, for the update, G) in the interleaved layout of the
+// fused x pass
+template <typename R> void contract_dots(const void* T, const SGrid& g, void* w, const void* c, const void* V, size_t vstride, int k, const Red& red, double* Hd, double* Hp, double* slot, double* coef, const BulkCfg* bc, cudaStream_t s, int il = 0);
+template <typename R> void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* coef, const double* Kbar, const SGrid& g, void* G, const Red& red, const BulkCfg* bc, cudaStream_t s, int il = 0);
 template <typename R> void norm2(const void* v, const SGrid& g, const Red& red, cudaStream_t s);
+
+// Fused x pass of the Arnoldi step (kernels_fft.cu): inverse real
+// transform along x of the 9 gradient components, tangent apply and forward
+// real transform, per block of rows of the interleaved spectrum layout
+// ((9 r + c) n0h + kx for row r = y + n1 z, field c); the transforms along
+// y and z are a batched 2-D library transform over that layout.
+constexpr int kFftMaxLen = 512;  // longest x line of the fused pass
+struct FusedX {
+    int ok;          // the grid is supported (else the library 3-D transforms are used)
+    int rb, lpw;     // rows per block, (row, field) lines per warp
+    size_t smem;     // dynamic shared memory per block
+    const void* tw;  // device twiddle table exp(-2 pi i t / n0), t < n0
+};
+template <typename R> int fused_x_plan(FusedX& p, const SGrid& g);
+template <typename R> void fused_x_twiddles(int n, void* host);
+template <typename R> void fused_xpass(const FusedX& p, void* G, const void* K, const void* phi, double kres, const SGrid& g, cudaStream_t s);
 template <typename R> void xupdate(void* x, const void* V, size_t vstride, int k, const double* y, const double* Kbar, const SGrid& g, cudaStream_t s);
 template <typename R> void axpby(void* out, const void* a, const void* b, double alpha, double beta, size_t n, cudaStream_t s);
 template <typename R> void fupdate(void* H, const void* G, const void* Ht, size_t N, const Red& red, cudaStream_t s);

@@ -51,7 +51,7 @@ def solver_options(preset="paper", **overrides):
     ``parity64``: tight tolerances for FP64 parity.  ``parity32``: the
     tightest the FP32-bulk path reaches reliably.
     """
-    base = {"max_stag": 50, "max_newton": 25, "max_lin": 2000, "max_pf": 500, "max_local": 100,
+    base = {"max_stag": 300, "max_newton": 25, "max_lin": 2000, "max_pf": 500, "max_local": 100,
             "restart": 30, "max_cutbacks": 0}
     if preset == "paper":
         o = dict(tol_stag=5e-3, tol_newton=5e-3, tol_lin=1e-5, tol_pf=1e-5, tol_local=1e-9)

@@ -8,7 +8,9 @@ Each line holds the increment index, its status, dt, the macroscopic F and
 the mean degraded first Piola stress, the iteration counts of the staggered
 loop, Newton, GMRES and the phase field, local failures, cut-backs, mixed
 control rounds and the cracked-voxel count; with --phi-max also the largest
-phase-field value (one field read per increment).  Under a stress mask
+phase-field value, stored energy density G_s and the number of voxels whose
+W_crit is set (field reads per increment).  --mat and --opt override
+material constants and solver options (KEY=VALUE, repeatable).  Under a stress mask
 (uniaxial stress, plane stress of the plates) the stress-controlled
 components of each increment start from the previous solved F.  The run
 stops at the first increment that fails.  --checkpoint writes the state
@@ -44,6 +46,8 @@ def drive(rve, cfg, increments, emit, phi_max=False):
         rec["Pbar"] = [float(x) for x in st["Pbar"]]
         if phi_max and s == 0:
             rec["phi_max"] = float(np.max(rve.field("phi")))
+            rec["gs_max"] = float(np.max(rve.field("Gs")))
+            rec["wcrit_set"] = int(np.count_nonzero(rve.field("Wcrit")))
         emit(rec)
         if s != 0:
             break
@@ -64,6 +68,8 @@ def main(argv=None):
     p.add_argument("--phi-max", action="store_true")
     p.add_argument("--out", default="-", help="JSON lines file (- for stdout)")
     p.add_argument("--checkpoint", default=None, help="write state_save here at the end")
+    p.add_argument("--mat", action="append", default=[], help="material override KEY=VALUE")
+    p.add_argument("--opt", action="append", default=[], help="solver option override KEY=VALUE")
     a = p.parse_args(argv)
     if a.config == "batch32":
         p.error("batch32 is a set of RVEs: use bench.py --config batch32")
@@ -73,8 +79,17 @@ def main(argv=None):
     n = tuple(int(x) for x in a.n.split(",")) if a.n else None
     cfg = I.build_config(a.config, n_override=n)
     over = {} if a.max_cutbacks is None else {"max_cutbacks": a.max_cutbacks}
+    for kv in a.opt:
+        k, v = kv.split("=", 1)
+        over[k] = type(I.solver_options(a.tol)[k])(float(v))
     opts = I.solver_options(a.tol, **over)
-    rve = FF.RVE(cfg["n"], cfg["h"], cfg["grain_ids"], cfg["euler"], I.material("baseline"),
+    mat = I.material("baseline")
+    for kv in a.mat:
+        k, v = kv.split("=", 1)
+        if k not in mat:
+            p.error(f"unknown material constant {k}")
+        mat[k] = float(v)
+    rve = FF.RVE(cfg["n"], cfg["h"], cfg["grain_ids"], cfg["euler"], mat,
                  opts, prec=a.prec, stream=torch.cuda.Stream(), phi0=cfg["phi0"],
                  elastic_only=cfg["elastic_only"])
     out = sys.stdout if a.out == "-" else open(a.out, "w")

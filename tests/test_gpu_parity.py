@@ -445,6 +445,48 @@ def test_pipelined_arnoldi_kernels_match_register_streaming(prec, monkeypatch):
         assert rel(a, b, floor=FLOOR[f] * np.sqrt(b.size)) < tol, f
 
 
+@pytest.mark.parametrize("prec", PREC)
+@pytest.mark.parametrize("n", [(8, 6, 6), (16, 12, 9), (32, 8, 1), (16, 16, 16), (64, 5, 7)])
+def test_fused_x_pass_matches_library_transforms(prec, n, monkeypatch):
+    """The Arnoldi step's fused x pass (inverse real transform along x of the
+    9 gradient components, tangent apply and forward real transform in one
+    kernel, between batched 2-D transforms over (z, y) of the interleaved
+    spectrum layout; selected by FATIGUEFFT_FUSED=1 where n0 is a power of
+    two) against the
+    same step with the library 3-D transforms and the separate tangent
+    apply: the same iteration counts within two per solve and the same
+    fields to the Krylov tolerance, on grids with odd, radix-3 and unit
+    (plate) y/z extents.  The tangent family's algorithmic bytes per launch
+    show which path ran."""
+    gid, eul = I.voronoi(n, 3, 29)
+    mat = dict(MAT, tau_c0=250.0)
+    prog = I.uniaxial_cycle_program(0.006, 24, 1)[:4]
+    N = int(np.prod(n))
+    Nh = (n[0] // 2 + 1) * n[1] * n[2]
+    es = 8 if prec == "fp64" else 4
+    per_launch = {"1": Nh * 2 * es * 18 + N * es * 82, "0": N * es * 100}
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("FATIGUEFFT_FUSED", flag)
+        r = FF.RVE(n, H, gid, eul, mat, opts_for(prec), prec=prec, stream=stream())
+        r.profile(["tangent_apply"])
+        its = []
+        for Fb, dt in prog:
+            _, st = r.run_increment(Fb, dt)
+            its.append(st["lin_it_total"])
+        ms, cnt, by = r.profile_read()["tangent_apply"]
+        assert cnt > 0 and abs(by / cnt - per_launch[flag]) < 1e-6 * per_launch[flag], flag
+        out.append((its, {f: r.field(f) for f in ("F", "P", "Fp")}))
+        r.close()
+    (ia, fa), (ib, fb) = out
+    assert sum(ia) > 0 and all(abs(x - y) <= 2 for x, y in zip(ia, ib)), (ia, ib)
+    eye = np.eye(3).reshape(9, 1)
+    tol = 1e-9 if prec == "fp64" else 1e-4
+    for f in fa:
+        a, b = (fa[f] - eye, fb[f] - eye) if f in ("F", "Fp") else (fa[f], fb[f])
+        assert rel(a, b, floor=FLOOR[f] * np.sqrt(b.size)) < tol, f
+
+
 # ----------------------------------------------------------- failure paths
 def test_call_order_errors():
     n = (4, 4, 4)
@@ -470,14 +512,90 @@ def test_iteration_cap_is_reported(prec):
 
 
 # ------------------------------------------------- full size, sampled
+# ------------------------------------------- the benchmark's configurations
+_ORACLE_TRACKS = {}
+
+
+def _oracle_track(name, cfg, opts, incs, keep):
+    """Oracle fields after each increment in `keep` of a config's loading
+    (computed once per module run and shared by both precisions)."""
+    key = (name, incs, tuple(sorted(opts.items())))
+    if key not in _ORACLE_TRACKS:
+        o = O.RVE(cfg["n"], H, cfg["grain_ids"], cfg["euler"], MAT, opts, phi0=cfg["phi0"],
+                  elastic_only=cfg["elastic_only"])
+        snaps = {}
+        for k, (Fb, dt) in enumerate(cfg["program"][:incs]):
+            s, st = o.run_increment(Fb, dt)
+            assert s == 0, (name, k, st)
+            if k in keep:
+                snaps[k] = ({f: o.field(f) for f in FIELDS_CMP}, st)
+        o.close()
+        _ORACLE_TRACKS[key] = snaps
+    return _ORACLE_TRACKS[key]
+
+
+class _Snap:
+    def __init__(self, fields):
+        self.f = fields
+
+    def field(self, name):
+        return self.f[name]
+
+
 @pytest.mark.parametrize("prec", PREC)
-@pytest.mark.parametrize("config,incs", [("poly64", 2), ("poly128", 6)])
+def test_sx16_config_every_increment(prec):
+    """The 16^3 pre-cracked [100] crystal exactly as configured (one grain,
+    the 4 x 16 crack plane at mid-height held at phi = 1 without slip), one
+    R = -1 cycle at 0.5 % in 20 increments: every field after every
+    increment against the oracle, FP64 at the tight preset to 1e-9, the
+    mixed path to 1e-4."""
+    cfg = I.build_config("sx16")
+    incs = len(cfg["program"])
+    track = _oracle_track("sx16", cfg, I.solver_options("parity64"), incs, set(range(incs)))
+    g = FF.RVE(cfg["n"], H, cfg["grain_ids"], cfg["euler"], MAT, opts_for(prec), prec=prec,
+               phi0=cfg["phi0"], elastic_only=cfg["elastic_only"], stream=stream())
+    for k, (Fb, dt) in enumerate(cfg["program"]):
+        s, _ = g.run_increment(Fb, dt)
+        assert s == 0
+        _compare(g, _Snap(track[k][0]), prec, k)
+    g.close()
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_poly64_benchmark_increments_fieldwise(prec):
+    """The timed workload (64^3, 50 grains, 0.6 % R = -1, 40 increments per
+    cycle) in the benchmark's own configuration (its tolerances, a side
+    stream, graph-replayed GMRES columns): increments 1-8, the last three
+    plastic, compared field by field at every voxel with the oracle run at
+    the same tolerances.  Both solves stop at the same tolerances along
+    different Krylov paths, so both precisions are held to 1e-4 per field
+    (the bound the mixed path is held to; F, P, F_p, rho_SSD, phi, W_p,
+    G_s, gamma, W_crit)."""
+    cfg = I.build_config("poly64")
+    opts = I.solver_options("paper")
+    keep = (5, 6, 7)
+    track = _oracle_track("poly64", cfg, opts, 8, set(keep))
+    assert np.abs(track[5][0]["Fp"] - np.eye(3).reshape(9, 1)).max() > 0  # plastic from inc 6
+    g = FF.RVE(cfg["n"], H, cfg["grain_ids"], cfg["euler"], MAT, opts, prec=prec,
+               stream=stream())
+    errs = {}
+    for k, (Fb, dt) in enumerate(cfg["program"][:8]):
+        s, _ = g.run_increment(Fb, dt)
+        assert s == 0
+        if k in keep:
+            errs[k] = _compare(g, _Snap(track[k][0]), prec, k, tol=1e-4)
+    print(prec, {k: {f: f"{v:.1e}" for f, v in e.items()} for k, e in errs.items()})
+    g.close()
+
+
+@pytest.mark.parametrize("prec", PREC)
+@pytest.mark.parametrize("config,incs", [("poly128", 6)])
 def test_full_size_sampled(prec, config, incs):
-    """The timed workload (64^3, 50 grains) and the 128^3 / 200-grain one in
-    the benchmark's launch configuration: a few increments (into plasticity
-    for 128^3), then the constitutive update at 64 sampled voxels against
-    the oracle, and the invariants <F> = Fbar and phi_t <= phi <= 1 over the
-    whole grid."""
+    """The 128^3 / 200-grain polycrystal in the benchmark's launch
+    configuration (too large for the oracle's full solve in a test): six
+    increments into plasticity, then the constitutive update at 64 sampled
+    voxels against the oracle, and the invariants <F> = Fbar and
+    phi_t <= phi <= 1 over the whole grid."""
     cfg = I.build_config(config)
     n, gid, eul = cfg["n"], cfg["grain_ids"], cfg["euler"]
     r = FF.RVE(n, H, gid, eul, MAT, I.solver_options("paper"), prec=prec, stream=stream())
