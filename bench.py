@@ -50,6 +50,7 @@ def args_():
     p.add_argument("--config", default=CONFIG_NAME)
     p.add_argument("--tol", default="paper", choices=["paper", "parity32", "parity64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-damage-window", action="store_true")
     p.add_argument("--verbose", action="store_true")
     p.add_argument("--ref-budget-s", type=float, default=150.0,
                    help="--impl reference: stop timing the oracle after this many seconds")
@@ -104,10 +105,13 @@ class Driver:
 
 
 def workload_options(a, cfg):
-    """Solver options of a workload: the --tol preset; mixed-control
-    workloads (large plastic strains at the R = 0 peaks) with cut-back on."""
-    return I.solver_options(a.tol, **({} if cfg["stress_mask"] is None else
-                                      {"max_cutbacks": 4}))
+    """Solver options of a workload: the --tol preset with the config's own
+    overrides; mixed-control workloads (large plastic strains at the R = 0
+    peaks) with cut-back on."""
+    over = dict(cfg.get("options", {}))
+    if cfg["stress_mask"] is not None:
+        over.setdefault("max_cutbacks", 4)
+    return I.solver_options(a.tol, **over)
 
 
 def workload_desc(name, cfg):
@@ -238,6 +242,65 @@ def dist():
     return ws, rank, local
 
 
+# A damage-active window of the timed workload's grid (poly64_damage:
+# softer slip, full storage of the plastic work, small G_crit): increments
+# DAMAGE_WINDOW[0] .. DAMAGE_WINDOW[1] - 1 (0-based) of the first tensile
+# half take the first plastic steps, set W_crit and nucleate damage.
+DAMAGE_CONFIG = "poly64_damage"
+DAMAGE_WINDOW = (4, 8)
+
+
+def damage_window(FF, a, stream, flush):
+    """The mixed path on a damage-active window: voxel-increments/s, the
+    phase-field PCG iterations and the phase-field kernels' achieved bytes/s
+    (CUDA events per launch, algorithmic bytes) against the copy peak."""
+    import torch
+    cfg = I.build_config(DAMAGE_CONFIG)
+    n, N = cfg["n"], int(np.prod(cfg["n"]))
+    mat = I.material("baseline", **cfg["material"])
+    opts = workload_options(a, cfg)
+    r = FF.RVE(n, I.VOXEL_MM, cfg["grain_ids"], cfg["euler"], mat, opts, prec="mixed",
+               stream=stream)
+    drv = Driver(cfg)
+    w0, w1 = DAMAGE_WINDOW
+    for k in range(w0):
+        drv(r, k)
+    r.profile(["phase_field"])
+    ms, stats = [], []
+    with torch.cuda.stream(stream):
+        for k in range(w0, w1):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s, st = drv(r, k)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            stats.append(st)
+    pf = r.profile_read(reset=True).get("phase_field", (0.0, 0, 0.0))
+    r.profile([])
+    cracked = stats[-1]["cracked"]
+    phimax = float(np.max(r.field("phi")))
+    r.close()
+    hbm, kind = peaks()
+    gbs = pf[2] / pf[0] / 1e6 if pf[0] > 0 else None
+    return {"workload": f"{workload_desc(DAMAGE_CONFIG, cfg)}, tau_c0 250 MPa, xi_store 1, "
+                        f"G_crit 7e-4 N/mm, increments {w0 + 1}-{w1}",
+            "value": round(N * len(ms) / (sum(ms) / 1e3), 1), "unit": "voxel-increments/s",
+            "ms_per_step": round(sum(ms) / len(ms), 3), "prec": "mixed",
+            "iterations": {"staggered": sum(st["stag_it"] for st in stats),
+                           "newton": sum(st["newton_it"] for st in stats),
+                           "gmres": sum(st["lin_it_total"] for st in stats),
+                           "phase_field": sum(st["pf_it_total"] for st in stats)},
+            "phi_max": round(phimax, 4), "cracked": int(cracked),
+            "phase_field_kernels": {"launches": int(pf[1]), "ms": round(pf[0], 3),
+                                    "algorithmic_bytes": int(pf[2]),
+                                    "achieved_gbs": round(gbs, 1) if gbs else None,
+                                    "frac": round(gbs / hbm, 4) if gbs else None,
+                                    "peak_kind": kind}}
+
+
 def run_ours(a):
     import torch
 
@@ -255,7 +318,7 @@ def run_ours(a):
     n, N = cfg["n"], int(np.prod(cfg["n"]))
     prog = cfg["program"]
     assert a.warmup + a.steps <= len(prog)
-    mat = I.material("baseline")
+    mat = I.material("baseline", **cfg.get("material", {}))
     opts = workload_options(a, cfg)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -391,6 +454,11 @@ def run_ours(a):
         "fp64": {"value": round(value64, 1), "ms_per_step": round(f64["total_ms"] / a.steps, 3),
                  "dominant_kernel": f64["dominant"]},
         "mixed_speedup_vs_fp64": round(value / value64, 3),
+        # the same at equal Krylov work: time per GMRES iteration (the mixed
+        # path stops GMRES at an FP32 round-off floor and runs fewer)
+        "mixed_speedup_vs_fp64_per_gmres_iteration": round(
+            (f64["total_ms"] / max(1, sum(s["lin_it_total"] for s in f64["stats"]))) /
+            (mx["total_ms"] / max(1, sum(s["lin_it_total"] for s in mx["stats"]))), 3),
         "mixed_vs_fp64_rel_l2": errs,
         "e2e": {"value": round(ws * N * a.steps / e2e_s, 1), "unit": "voxel-increments/s",
                 "h2d_bytes_per_step": 80 + (72 + 36 if mixed_ctl else 0),
@@ -414,6 +482,8 @@ def run_ours(a):
                 for k, v in results[p]["breakdown"].items() if v[2] > 0 and v[0] > 0}
             for p in results},
     }
+    if a.config == CONFIG_NAME and not a.no_damage_window:
+        line["damage_window"] = damage_window(FF, a, stream, flush)
     if ws == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, mat, opts, a)
     return line
@@ -572,7 +642,7 @@ def run_reference(a):
     OB.build()
     cfg = I.build_config(a.config)
     N = int(np.prod(cfg["n"]))
-    mat = I.material("baseline")
+    mat = I.material("baseline", **cfg.get("material", {}))
     opts = workload_options(a, cfg)
     threads = os.cpu_count() or 1
     r = O.RVE(cfg["n"], I.VOXEL_MM, cfg["grain_ids"], cfg["euler"], mat, opts, threads=threads)

@@ -102,6 +102,16 @@ typedef struct {
     fft_precision prec;
     void* cuda_stream; /* cudaStream_t */
     int max_cutbacks;
+    /* Derivatives of the mechanical operators (gradient, divergence and the
+     * Green preconditioner of Eq. precf): 0 = the spectral i xi of Sec. 3.1;
+     * 1 = Willot's rotated finite differences, the discrete derivative the
+     * paper cites against the Gibbs oscillations of the spectral one:
+     * D_j = (e_j - 1)/h prod_{l != j} (1 + e_l)/2, e_l = exp(i xi_l h), in
+     * place of i xi_j in the gradient, -conj(D_j) in the divergence, and the
+     * Green block [conj(D) . Kbar . D]^-1 (zero where D = 0).  The Nye curl
+     * and the phase-field Laplacian stay spectral.  Other values:
+     * FFT_ERR_ARG at init_rve. */
+    int derivative;
 } fft_options;
 
 /* Per-increment statistics (accumulated since apply_increment). */

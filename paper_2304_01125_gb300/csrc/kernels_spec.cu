@@ -64,6 +64,58 @@ __device__ __forceinline__ Cx cmul_i(Cx a, decltype(a.x) s) {  // a * (i s)
     return r;
 }
 
+template <typename Cx>
+__device__ __forceinline__ Cx cmul(Cx a, Cx b) {
+    Cx r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+// Willot's rotated-scheme gradient symbols at half-spectrum entry e:
+// D_j = (e_j - 1)/h prod_{l != j} (1 + e_l)/2 with e_l = exp(2 pi i k_l / n_l)
+// (the forward difference along j averaged over the four cell edges
+// parallel to j).  sinpi/cospi are exact at the Nyquist index (e = -1), so
+// the factors (1 + e) vanish there exactly: the scheme's null modes.
+template <typename R> __device__ __forceinline__ void sincospi_r(R a, R* s, R* c);
+template <> __device__ __forceinline__ void sincospi_r<float>(float a, float* s, float* c) {
+    sincospif(a, s, c);
+}
+template <> __device__ __forceinline__ void sincospi_r<double>(double a, double* s, double* c) {
+    sincospi(a, s, c);
+}
+template <typename R>
+__device__ __forceinline__ void willot_D(const SGrid& g, size_t e64, typename Tr<R>::Cx* D) {
+    typedef typename Tr<R>::Cx Cx;
+    const unsigned e = (unsigned)e64;
+    const unsigned n0h = (unsigned)g.n0h, n1 = (unsigned)g.n1;
+    const unsigned rest = fdiv(e, g.fd_n0h);
+    const unsigned kx = e - rest * n0h;
+    const unsigned kz = fdiv(rest, g.fd_n1);
+    const unsigned ky = rest - kz * n1;
+    const unsigned k[3] = {kx, ky, kz};
+    const int n[3] = {g.n0, g.n1, g.n2};
+    Cx ev[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sincospi_r<R>(R(2 * k[d]) / R(n[d]), &ev[d].y, &ev[d].x);
+    const R ih = sizeof(R) == 8 ? (R)g.ih : (R)g.ihf;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        Cx s;
+        s.x = (ev[j].x - R(1)) * ih;
+        s.y = ev[j].y * ih;
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            if (l == j) continue;
+            Cx h;
+            h.x = R(0.5) * (R(1) + ev[l].x);
+            h.y = R(0.5) * ev[l].y;
+            s = cmul(s, h);
+        }
+        D[j] = s;
+    }
+}
+
 #define GRID_STRIDE(i, n) \
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
 
@@ -295,6 +347,37 @@ __device__ __forceinline__ void div3_real(const typename Tr<R>::Cx* T, const SGr
         te[q] = T[fld_at<IL>(g, e, q)];
         tp[q] = T[fld_at<IL>(g, p, q)];
     }
+    if (g.willot) {
+        // divergence symbols S_j = -conj(D_j) (the adjoint of the rotated
+        // gradient); the partner's are conj(S_j)
+        Cx D[3];
+        willot_D<R>(g, e, D);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            Cx s, r;
+            s.x = s.y = r.x = r.y = 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                Cx S;
+                S.x = -D[j].x;
+                S.y = D[j].y;
+                const Cx t = cmul(te[3 * i + j], S);
+                s.x += t.x;
+                s.y += t.y;
+                S.y = -S.y;
+                const Cx u = cmul(tp[3 * i + j], S);
+                r.x += u.x;
+                r.y += u.y;
+            }
+            out[i].x = sign * s.x;
+            out[i].y = sign * s.y;
+            if (hp) {
+                out[i].x = R(0.5) * (out[i].x + sign * r.x);
+                out[i].y = R(0.5) * (out[i].y - sign * r.y);
+            }
+        }
+        return;
+    }
     const R xp[3] = {xd[0], -xd[1], -xd[2]};
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -332,13 +415,21 @@ __global__ void k_residual(const typename Tr<R>::Cx* Ph, SGrid g, typename Tr<R>
         Cx s[3];
         div3_real<R>(Ph, g, e, xd, R(1), s);
 #pragma unroll
+        R d2[3] = {xd[0] * xd[0], xd[1] * xd[1], xd[2] * xd[2]};
+        if (g.willot) {
+            Cx D[3];
+            willot_D<R>(g, e, D);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) d2[j] = D[j].x * D[j].x + D[j].y * D[j].y;
+        }
+#pragma unroll
         for (int i = 0; i < 3; ++i) {
             b[i * Nh + e] = s[i];
             acc[0] += w * (s[i].x * s[i].x + s[i].y * s[i].y);
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 const Cx q = Ph[(3 * i + j) * Nh + e];
-                acc[1] += w * (q.x * q.x + q.y * q.y) * xd[j] * xd[j];
+                acc[1] += w * (q.x * q.x + q.y * q.y) * d2[j];
             }
         }
     }
@@ -404,6 +495,110 @@ __device__ __forceinline__ void green_apply(const R* Ks, const R* xd,
     }
 }
 
+// The Green preconditioner of Willot's scheme, [conj(D) . Kbar . D]^-1 (a
+// complex 3 x 3, inverted by cofactors after scaling by its trace as above);
+// zero where every symbol vanishes (the mean and the scheme's null modes).
+template <typename R>
+__device__ __forceinline__ void green_apply_w(const R* Ks, const typename Tr<R>::Cx* D,
+                                              const typename Tr<R>::Cx* v,
+                                              typename Tr<R>::Cx* z) {
+    typedef typename Tr<R>::Cx Cx;
+    const R dn = fabs(D[0].x) + fabs(D[0].y) + fabs(D[1].x) + fabs(D[1].y) + fabs(D[2].x) +
+                 fabs(D[2].y);
+    if (dn == R(0)) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) z[i].x = z[i].y = 0;
+        return;
+    }
+    Cx A[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            Cx s;
+            s.x = s.y = 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                Cx cj = D[j];
+                cj.y = -cj.y;
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    const R kk = Ks[9 * (3 * i + j) + 3 * k + l];
+                    const Cx t = cmul(cj, D[l]);
+                    s.x += kk * t.x;
+                    s.y += kk * t.y;
+                }
+            }
+            A[3 * i + k] = s;
+        }
+    const R tr = fabs(A[0].x) + fabs(A[4].x) + fabs(A[8].x) + fabs(A[0].y) + fabs(A[4].y) +
+                 fabs(A[8].y);
+    const R is = R(1) / tr;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        A[q].x *= is;
+        A[q].y *= is;
+    }
+    auto sub = [](Cx a, Cx b) {
+        Cx r;
+        r.x = a.x - b.x;
+        r.y = a.y - b.y;
+        return r;
+    };
+    Cx C[9];  // cofactors, transposed (the adjugate)
+    C[0] = sub(cmul(A[4], A[8]), cmul(A[5], A[7]));
+    C[1] = sub(cmul(A[2], A[7]), cmul(A[1], A[8]));
+    C[2] = sub(cmul(A[1], A[5]), cmul(A[2], A[4]));
+    C[3] = sub(cmul(A[5], A[6]), cmul(A[3], A[8]));
+    C[4] = sub(cmul(A[0], A[8]), cmul(A[2], A[6]));
+    C[5] = sub(cmul(A[2], A[3]), cmul(A[0], A[5]));
+    C[6] = sub(cmul(A[3], A[7]), cmul(A[4], A[6]));
+    C[7] = sub(cmul(A[1], A[6]), cmul(A[0], A[7]));
+    C[8] = sub(cmul(A[0], A[4]), cmul(A[1], A[3]));
+    Cx det = cmul(A[0], C[0]);
+    const Cx d1 = cmul(A[1], C[3]), d2 = cmul(A[2], C[6]);
+    det.x += d1.x + d2.x;
+    det.y += d1.y + d2.y;
+    // 1/det times the scale 1/tr: (A/tr)^-1 / tr = A^-1
+    const R dd = det.x * det.x + det.y * det.y;
+    Cx id;
+    id.x = det.x / dd * is;
+    id.y = -det.y / dd * is;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        Cx acc;
+        acc.x = acc.y = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const Cx t = cmul(C[3 * i + k], v[k]);
+            acc.x += t.x;
+            acc.y += t.y;
+        }
+        z[i] = cmul(acc, id);
+    }
+}
+
+// z = M v with the Green preconditioner of the grid's derivative scheme;
+// D receives Willot's symbols when that scheme is selected.
+template <typename R>
+__device__ __forceinline__ void green_any(const SGrid& g, size_t e, const R* Ks, const R* xd,
+                                          const typename Tr<R>::Cx* v, typename Tr<R>::Cx* z,
+                                          typename Tr<R>::Cx* D) {
+    if (g.willot) {
+        willot_D<R>(g, e, D);
+        green_apply_w<R>(Ks, D, v, z);
+    } else {
+        green_apply<R>(Ks, xd, v, z);
+    }
+}
+// gradient entry z_i d_j: d_j = i xi_j (spectral) or Willot's D_j
+template <typename R>
+__device__ __forceinline__ typename Tr<R>::Cx grad_sym(const SGrid& g, typename Tr<R>::Cx z,
+                                                       const R* xd,
+                                                       const typename Tr<R>::Cx* D, int j) {
+    return g.willot ? cmul(z, D[j]) : cmul_i(z, xd[j]);
+}
+
 // v = scale * vin (optionally stored to vout); z = M(xi) v when use_pre,
 // else z = v; G_ij = z_i i xi_j, the 9-component spectrum of grad z.
 template <typename R, bool IL>
@@ -427,16 +622,19 @@ __global__ void __launch_bounds__(kThreads, 3) k_precond_grad(const typename Tr<
             v[i].y *= scale;
             if (vout) vout[i * Nh + e] = v[i];
         }
+        Cx D[3];
         if (use_pre) {
-            green_apply<R>(Ks, xd, v, z);
+            green_any<R>(g, e, Ks, xd, v, z, D);
         } else {
+            if (g.willot) willot_D<R>(g, e, D);
 #pragma unroll
             for (int i = 0; i < 3; ++i) z[i] = v[i];
         }
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) G[fld_at<IL>(g, e, 3 * i + j)] = cmul_i(z[i], xd[j]);
+            for (int j = 0; j < 3; ++j)
+                G[fld_at<IL>(g, e, 3 * i + j)] = grad_sym<R>(g, z[i], xd, D, j);
     }
 }
 template <typename R>
@@ -623,8 +821,8 @@ __device__ void dcgs_coefficients(int k, const double* d, const double* Hs, doub
 // per thread in registers and combined across blocks in FP64.
 // Tail of the dot pass: block partials, the last block's combine, the
 // Hessenberg staging and the step coefficients (dcgs_coefficients).
-template <typename R, int NQ>
-__device__ __forceinline__ void dots_finish(const R (&acc)[3 + 2 * NQ], int k, const Red& red,
+template <typename A, int NQ>
+__device__ __forceinline__ void dots_finish(const A (&acc)[3 + 2 * NQ], int k, const Red& red,
                                             double* Hd, double* Hp, double* slot, double* coef,
                                             const int* err) {
     // the update pass (launched as a programmatic dependent) may start
@@ -653,14 +851,17 @@ __device__ __forceinline__ void dots_finish(const R (&acc)[3 + 2 * NQ], int k, c
 // b_i = q_i.z accumulate (the dot layout above); the tail forms the step's
 // coefficients.  Saves the contraction's launch and tail and the re-read of
 // z and c.
-template <typename R, int NQ, bool IL>
+// A is the per-thread accumulator type: the bulk type R by default, or FP64
+// (products and sums, FATIGUEFFT_DOT64=1) to measure what the FP32 partial
+// sums of the mixed path cost in accuracy.
+template <typename R, int NQ, bool IL, typename A>
 __global__ void __launch_bounds__(kThreads, 2) k_contract_dots(
     const typename Tr<R>::Cx* T, SGrid g, typename Tr<R>::Cx* w, const typename Tr<R>::Cx* c,
     const typename Tr<R>::Cx* V, size_t vstride, int k, Red red, double* Hd, double* Hp,
     double* slot, double* coef, const int* err) {
     typedef typename Tr<R>::Cx Cx;
     constexpr int G = NQ < 8 ? NQ : 8;
-    R acc[3 + 2 * NQ];
+    A acc[3 + 2 * NQ];
 #pragma unroll
     for (int v = 0; v < 3 + 2 * NQ; ++v) acc[v] = 0;
     const size_t Nh = g.Nh;
@@ -674,9 +875,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_contract_dots(
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             w[q * Nh + e] = zc[q];
-            acc[0] += wt * (cv[q].x * cv[q].x + cv[q].y * cv[q].y);
-            acc[1] += wt * (cv[q].x * zc[q].x + cv[q].y * zc[q].y);
-            acc[2] += wt * (zc[q].x * zc[q].x + zc[q].y * zc[q].y);
+            acc[0] += (A)wt * ((A)cv[q].x * (A)cv[q].x + (A)cv[q].y * (A)cv[q].y);
+            acc[1] += (A)wt * ((A)cv[q].x * (A)zc[q].x + (A)cv[q].y * (A)zc[q].y);
+            acc[2] += (A)wt * ((A)zc[q].x * (A)zc[q].x + (A)zc[q].y * (A)zc[q].y);
         }
 #pragma unroll
         for (int i0 = 0; i0 < NQ; i0 += 8) {
@@ -695,17 +896,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_contract_dots(
             for (int t = 0; t < G; ++t)
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    acc[3 + 2 * (i0 + t)] += wt * (qv[t][q].x * cv[q].x + qv[t][q].y * cv[q].y);
-                    acc[4 + 2 * (i0 + t)] += wt * (qv[t][q].x * zc[q].x + qv[t][q].y * zc[q].y);
+                    acc[3 + 2 * (i0 + t)] += (A)wt * ((A)qv[t][q].x * (A)cv[q].x +
+                                                      (A)qv[t][q].y * (A)cv[q].y);
+                    acc[4 + 2 * (i0 + t)] += (A)wt * ((A)qv[t][q].x * (A)zc[q].x +
+                                                      (A)qv[t][q].y * (A)zc[q].y);
                 }
         }
     }
-    dots_finish<R, NQ>(acc, k, red, Hd, Hp, slot, coef, err);
+    dots_finish<A, NQ>(acc, k, red, Hd, Hp, slot, coef, err);
 }
 template <typename R>
 void contract_dots(const void* T, const SGrid& g, void* w, const void* c, const void* V,
                    size_t vstride, int k, const Red& red, double* Hd, double* Hp, double* slot,
-                   double* coef, const BulkCfg* bc, cudaStream_t s, int il) {
+                   double* coef, const BulkCfg* bc, cudaStream_t s, int il, int dot64) {
     typedef typename Tr<R>::Cx Cx;
     const Cx *TT = (const Cx*)T, *cc = (const Cx*)c, *VV = (const Cx*)V;
     Cx* ww = (Cx*)w;
@@ -713,10 +916,13 @@ void contract_dots(const void* T, const SGrid& g, void* w, const void* c, const 
 #define CDOTS(NQ)                                                                             \
     do {                                                                                      \
         if (il)                                                                               \
-            k_contract_dots<R, NQ, true><<<kRedBlocks, kThreads, 0, s>>>(                     \
+            k_contract_dots<R, NQ, true, R><<<kRedBlocks, kThreads, 0, s>>>(                  \
+                TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err);                 \
+        else if (dot64)                                                                       \
+            k_contract_dots<R, NQ, false, double><<<kRedBlocks, kThreads, 0, s>>>(            \
                 TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err);                 \
         else                                                                                  \
-            k_contract_dots<R, NQ, false><<<kRedBlocks, kThreads, 0, s>>>(                    \
+            k_contract_dots<R, NQ, false, R><<<kRedBlocks, kThreads, 0, s>>>(                 \
                 TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err);                 \
     } while (0)
     if (k <= 0)
@@ -879,12 +1085,13 @@ __global__ void __launch_bounds__(kUpdT) k_dcgs_update_bulk(
             }
             acc[0] += wt * nn;
             if (G) {
-                Cx zz[3];
-                green_apply<R>(Ks, xd, nx, zz);
+                Cx zz[3], D[3];
+                green_any<R>(g, e, Ks, xd, nx, zz, D);
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) G[fld_at<IL>(g, e, 3 * i + j)] = cmul_i(zz[i], xd[j]);
+                    for (int j = 0; j < 3; ++j)
+                        G[fld_at<IL>(g, e, 3 * i + j)] = grad_sym<R>(g, zz[i], xd, D, j);
             }
         }
     }
@@ -996,12 +1203,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_dcgs_update(typename Tr<R>::Cx*
         }
         acc[0] += wt * nn;
         if (G) {
-            Cx zz[3];
-            green_apply<R>(Ks, xd, nx, zz);
+            Cx zz[3], D[3];
+            green_any<R>(g, e, Ks, xd, nx, zz, D);
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int j = 0; j < 3; ++j) G[fld_at<IL>(g, e, 3 * i + j)] = cmul_i(zz[i], xd[j]);
+                for (int j = 0; j < 3; ++j)
+                    G[fld_at<IL>(g, e, 3 * i + j)] = grad_sym<R>(g, zz[i], xd, D, j);
         }
     }
     block_partials<1, kThreads>(acc, 1, 0u, red.part);
@@ -1065,7 +1273,8 @@ __global__ void k_xupdate(typename Tr<R>::Cx* x, const typename Tr<R>::Cx* V, si
                 c[i].y += yq * v.y;
             }
         }
-        green_apply<R>(Ks, xd, c, z);
+        Cx D[3];
+        green_any<R>(g, e, Ks, xd, c, z, D);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             Cx xv = x[i * Nh + e];
@@ -1470,7 +1679,7 @@ int selftest_bounded_wait(unsigned limit) {
     template int dcgs_bulk_setup<R>(BulkCfg&);                                                  \
     template void contract_dots<R>(const void*, const SGrid&, void*, const void*, const void*,  \
                                    size_t, int, const Red&, double*, double*, double*, double*, \
-                                   const BulkCfg*, cudaStream_t, int);                          \
+                                   const BulkCfg*, cudaStream_t, int, int);                     \
     template void norm2<R>(const void*, const SGrid&, const Red&, cudaStream_t);                \
     template void xupdate<R>(void*, const void*, size_t, int, const double*, const double*,     \
                              const SGrid&, cudaStream_t);                                       \

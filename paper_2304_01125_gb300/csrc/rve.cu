@@ -149,6 +149,9 @@ struct fft_rve_s {
     int state = ST_NEW, stag_it = 0;
     bool phi_changed = true, skipped = false, converged = false, cp_valid = false;
     bool verbose = false;  // FATIGUEFFT_VERBOSE: solver traces on stderr
+    // FATIGUEFFT_DOT64=1: the Arnoldi dot pass forms its per-thread products
+    // and partial sums in FP64 (a measurement of the FP32 partials' effect)
+    bool dot64 = false;
     std::string err;
 };
 
@@ -643,7 +646,8 @@ struct Impl {
             // q_0 .. q_{k-1}: alpha, beta, a, b and the step's coefficients
             e = prof_begin(r, KF_MDOT);
             contract_dots<R>(r->cb9, r->g, r->w, V + (size_t)k * vs, V, vs, k,
-                             red_at(r, r->red), r->Hd, Hp, dslot, coef, bc, r->st);
+                             red_at(r, r->red), r->Hd, Hp, dslot, coef, bc, r->st, 0,
+                             r->dot64 ? 1 : 0);
             prof_end(r, KF_MDOT, e, Nh * 2 * es * (9 + 3 + 3 * (k + 1)));
             // q_k final, c_{k+1} and the next gradient spectrum
             e = prof_begin(r, KF_GSUPD);
@@ -977,21 +981,31 @@ struct Impl {
     static fft_status pcg_phase(fft_rve_s* r, int* iters) {
         const size_t N = r->g.N;
         const double l2 = r->mat.ell * r->mat.ell;
+        // algorithmic bytes: a real field, a half-spectrum scalar field
+        const double fb = (double)N * sizeof(R), sb = (double)r->g.Nh * 2 * sizeof(R);
         *iters = 0;
         CK(r, cudaMemcpyAsync(r->pfx, r->phi, N * sizeof(R), cudaMemcpyDeviceToDevice, r->st));
         TRY(fwd1(r, r->pfx));
+        cudaEvent_t e = prof_begin(r, KF_PF);
         pf_spec<R>(r->cb9, r->g, l2, 0, r->st);
+        prof_end(r, KF_PF, e, 2 * sb);
         TRY(inv1(r, r->pfq));
+        e = prof_begin(r, KF_PF);
         pf_init<R>(r->pfx, r->pfq, r->drive, r->pfr, N, red_at(r, r->red), r->st);
+        prof_end(r, KF_PF, e, 4 * fb);
         r->launches += 2;
         TRY(fetch(r, 2));
         const double bn = std::sqrt(r->hred[1]);
         if (std::sqrt(r->hred[0]) <= r->opt.tol_pf * bn) return FFT_OK;
         auto precond = [&]() -> fft_status {
             TRY(fwd1(r, r->pfr));
+            cudaEvent_t e1 = prof_begin(r, KF_PF);
             pf_spec<R>(r->cb9, r->g, l2, 1, r->st);
+            prof_end(r, KF_PF, e1, 2 * sb);
             TRY(inv1(r, r->pfz));
+            e1 = prof_begin(r, KF_PF);
             rdot<R>(r->pfr, r->pfz, N, red_at(r, r->red), r->st);
+            prof_end(r, KF_PF, e1, 2 * fb);
             r->launches += 2;
             return fetch(r, 1);
         };
@@ -1001,17 +1015,23 @@ struct Impl {
         CK(r, cudaMemcpyAsync(r->pft, r->pfr, N * sizeof(R), cudaMemcpyDeviceToDevice, r->st));
         for (int it = 1; it <= r->opt.max_pf; ++it) {
             *iters = it;
+            e = prof_begin(r, KF_PF);
             pf_q<R>(r->pft, r->pfp, r->drive, r->pfq, N, red_at(r, r->red), r->st);
+            prof_end(r, KF_PF, e, 4 * fb);
             TRY(fetch(r, 1));
             const double alpha = rz / r->hred[0];
+            e = prof_begin(r, KF_PF);
             pf_xr<R>(r->pfx, r->pfr, r->pfp, r->pfq, alpha, N, red_at(r, r->red), r->st);
+            prof_end(r, KF_PF, e, 6 * fb);
             r->launches += 2;
             TRY(fetch(r, 1));
             if (std::sqrt(r->hred[0]) <= r->opt.tol_pf * bn) return FFT_OK;
             TRY(precond());
             const double beta = r->hred[0] / rz;
             rz = r->hred[0];
+            e = prof_begin(r, KF_PF);
             pf_pt<R>(r->pfp, r->pft, r->pfz, r->pfr, beta, N, r->st);
+            prof_end(r, KF_PF, e, 6 * fb);
             r->launches += 1;
         }
         FAIL(r, FFT_ERR_NOT_CONVERGED, "phase-field CG reached max_pf = %d", r->opt.max_pf);
@@ -1031,7 +1051,9 @@ struct Impl {
         } else {
             TRY(pcg_phase(r, iters));
         }
+        cudaEvent_t e = prof_begin(r, KF_PF);
         pf_clamp<R>(r->pfx, r->phi_t, r->phi, N, red_at(r, r->red), r->st);
+        prof_end(r, KF_PF, e, 4.0 * N * sizeof(R));
         r->launches += 1;
         TRY(fetch(r, 4));
         for (int i = 0; i < 4; ++i) out4[i] = r->hred[i];
@@ -1388,10 +1410,15 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
     if (!(grid->h > 0) || (opt->prec != FFT_PREC_FP64 && opt->prec != FFT_PREC_MIXED))
         return FFT_ERR_ARG;
     if (opt->max_cutbacks < 0 || opt->max_cutbacks > 10) return FFT_ERR_ARG;
+    if (opt->derivative != 0 && opt->derivative != 1) return FFT_ERR_ARG;
     fft_rve_s* r = new fft_rve_s();
     r->prec = opt->prec;
     r->esz = opt->prec == FFT_PREC_FP64 ? 8 : 4;
     r->verbose = std::getenv("FATIGUEFFT_VERBOSE") != nullptr;
+    {
+        const char* dv = std::getenv("FATIGUEFFT_DOT64");
+        r->dot64 = dv && dv[0] == '1';
+    }
     {
         const char* gv = std::getenv("FATIGUEFFT_GRAPHS");
         r->graphs = !(gv && gv[0] == '0');
@@ -1420,6 +1447,9 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
     g.fd_n0h = make_fastdiv((uint32_t)g.n0h);
     g.fd_n1 = make_fastdiv((uint32_t)g.n1);
     g.fd_Nh = make_fastdiv((uint32_t)g.Nh);
+    g.willot = opt->derivative;
+    g.ih = 1.0 / grid->h;
+    g.ihf = (float)g.ih;
     const size_t N = g.N, Nh = g.Nh;
     for (size_t v = 0; v < N; ++v)
         if (grain_ids[v] < 0 || grain_ids[v] >= n_grains) {

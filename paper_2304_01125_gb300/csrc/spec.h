@@ -18,6 +18,12 @@ struct SGrid {
     double tpl0, tpl1, tpl2;
     float tpl0f, tpl1f, tpl2f;  // the same in FP32 (the FP64 pipe is narrow on this GPU)
     FastDiv fd_n0h, fd_n1, fd_Nh;
+    // derivatives of the mechanical operators: 0 = spectral i xi (Sec. 3.1),
+    // 1 = Willot's rotated finite differences (the discrete alternative the
+    // paper cites against Gibbs oscillations); 1/h in FP64 and FP32
+    int willot;
+    double ih;
+    float ihf;
 };
 struct Mat9 {
     double a[9];
@@ -59,7 +65,9 @@ int selftest_bounded_wait(unsigned limit);
 // |z|^2, a, b reduced and the step coefficients formed (kernels_spec.cu)
 // il = 1: T (and, for the update, G) in the interleaved layout of the
 // fused x pass
-template <typename R> void contract_dots(const void* T, const SGrid& g, void* w, const void* c, const void* V, size_t vstride, int k, const Red& red, double* Hd, double* Hp, double* slot, double* coef, const BulkCfg* bc, cudaStream_t s, int il = 0);
+// dot64 = 1: per-thread products and partial sums in FP64 (default: the
+// bulk type, FP64 from the block combine on)
+template <typename R> void contract_dots(const void* T, const SGrid& g, void* w, const void* c, const void* V, size_t vstride, int k, const Red& red, double* Hd, double* Hp, double* slot, double* coef, const BulkCfg* bc, cudaStream_t s, int il = 0, int dot64 = 0);
 template <typename R> void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* coef, const double* Kbar, const SGrid& g, void* G, const Red& red, const BulkCfg* bc, cudaStream_t s, int il = 0);
 template <typename R> void norm2(const void* v, const SGrid& g, const Red& red, cudaStream_t s);
 

@@ -51,7 +51,10 @@ class Options(C.Structure):
                 ("tol_pf", C.c_double), ("tol_local", C.c_double),
                 ("max_stag", C.c_int), ("max_newton", C.c_int), ("max_lin", C.c_int),
                 ("max_pf", C.c_int), ("max_local", C.c_int), ("restart", C.c_int),
-                ("prec", C.c_int), ("cuda_stream", C.c_void_p), ("max_cutbacks", C.c_int)]
+                ("prec", C.c_int), ("cuda_stream", C.c_void_p), ("max_cutbacks", C.c_int),
+                ("derivative", C.c_int)]
+
+DERIVATIVES = {"spectral": 0, "willot": 1}
 
 
 class Stats(C.Structure):
@@ -156,9 +159,9 @@ def _material(params):
 
 
 def _options(opts, prec, stream):
-    if opts.get("derivative", "spectral") != "spectral":
-        raise NotImplementedError("the CUDA path takes the spectral derivatives of Sec. 3.1 "
-                                  "only; Willot's rotated scheme is in the oracle")
+    d = opts.get("derivative", "spectral")
+    if d not in DERIVATIVES:
+        raise ValueError(f"derivative scheme {d!r}: one of {sorted(DERIVATIVES)}")
     o = Options()
     for k in ("tol_stag", "tol_newton", "tol_lin", "tol_pf", "tol_local"):
         setattr(o, k, float(opts[k]))
@@ -167,6 +170,7 @@ def _options(opts, prec, stream):
     o.prec = FFT_PREC_FP64 if prec in ("fp64", FFT_PREC_FP64) else FFT_PREC_MIXED
     o.cuda_stream = stream or None
     o.max_cutbacks = int(opts.get("max_cutbacks", 0))
+    o.derivative = DERIVATIVES[d]
     return o
 
 

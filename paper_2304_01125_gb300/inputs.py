@@ -366,6 +366,22 @@ CONFIGS = {
                                seed=1007),
     "poly256": dict(n=(256, 256, 256), grains=1000, amplitude=0.007, inc_per_cycle=40,
                     cycles=5, precrack=False, seed=1005),
+    # the timed workload with damage switched on early (softer slip,
+    # full storage of the plastic work, G_crit reached at the first tensile
+    # peak): the drive turns positive in the second cycle
+    "poly64_damage": dict(n=(64, 64, 64), grains=50, amplitude=0.006, inc_per_cycle=40,
+                          cycles=3, precrack=False, seed=1002,
+                          material=dict(tau_c0=250.0, xi_store=1.0, G_crit=7e-4),
+                          options=dict(max_cutbacks=4)),
+    # the 128^3 / 200-grain polycrystal with the stored-energy fraction
+    # calibrated (reading A4) so that W_crit is reached in its second cycle;
+    # cut-back at the load peaks, and the phase-field solve converged far
+    # below the staggered tolerance (its error otherwise decides the
+    # staggered test while damage grows slowly)
+    "poly128_damage": dict(n=(128, 128, 128), grains=200, amplitude=0.007, inc_per_cycle=40,
+                           cycles=10, precrack=False, seed=1003,
+                           material=dict(xi_store=0.25),
+                           options=dict(max_cutbacks=4, tol_pf=1e-8)),
 }
 
 
@@ -395,7 +411,8 @@ def build_config(name, n_override=None):
     else:
         prog = uniaxial_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"])
     out = dict(n=n, h=VOXEL_MM, grain_ids=gid, euler=eul, phi0=phi0, elastic_only=mask,
-               program=prog, stress_mask=None, Pbar=None)
+               program=prog, stress_mask=None, Pbar=None, material=dict(c.get("material", {})),
+               options=dict(c.get("options", {})))
     if c.get("control") == "uniaxial_stress":
         out["stress_mask"] = uniaxial_stress_mask(1)
         out["Pbar"] = np.zeros(9)
@@ -431,7 +448,8 @@ def _plate_config(c, n):
     else:
         prog = uniaxial_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"], axis)
     return dict(n=n, h=VOXEL_MM, grain_ids=gid, euler=eul, phi0=phi0, elastic_only=mask,
-                program=prog, stress_mask=uniaxial_stress_mask(axis), Pbar=np.zeros(9))
+                program=prog, stress_mask=uniaxial_stress_mask(axis), Pbar=np.zeros(9),
+                material={}, options={})
 
 
 def batch_configs(seed=2000, count=32, sizes=(32, 48, 64, 96), grains=(20, 150)):

@@ -14,7 +14,8 @@ material constants and solver options (KEY=VALUE, repeatable).  Under a stress m
 (uniaxial stress, plane stress of the plates) the stress-controlled
 components of each increment start from the previous solved F.  The run
 stops at the first increment that fails.  --checkpoint writes the state
-(state_save) after the last converged increment.
+(state_save) after the last converged increment; --fields-out writes the
+final phase field and W_crit (NumPy .npz, FP32).
 """
 import argparse
 import json
@@ -68,6 +69,7 @@ def main(argv=None):
     p.add_argument("--phi-max", action="store_true")
     p.add_argument("--out", default="-", help="JSON lines file (- for stdout)")
     p.add_argument("--checkpoint", default=None, help="write state_save here at the end")
+    p.add_argument("--fields-out", default=None, help="write phi and Wcrit (.npz) at the end")
     p.add_argument("--mat", action="append", default=[], help="material override KEY=VALUE")
     p.add_argument("--opt", action="append", default=[], help="solver option override KEY=VALUE")
     a = p.parse_args(argv)
@@ -78,12 +80,14 @@ def main(argv=None):
 
     n = tuple(int(x) for x in a.n.split(",")) if a.n else None
     cfg = I.build_config(a.config, n_override=n)
-    over = {} if a.max_cutbacks is None else {"max_cutbacks": a.max_cutbacks}
+    over = dict(cfg.get("options", {}))
+    if a.max_cutbacks is not None:
+        over["max_cutbacks"] = a.max_cutbacks
     for kv in a.opt:
         k, v = kv.split("=", 1)
         over[k] = type(I.solver_options(a.tol)[k])(float(v))
     opts = I.solver_options(a.tol, **over)
-    mat = I.material("baseline")
+    mat = I.material("baseline", **cfg.get("material", {}))
     for kv in a.mat:
         k, v = kv.split("=", 1)
         if k not in mat:
@@ -100,6 +104,9 @@ def main(argv=None):
         if a.checkpoint:
             with open(a.checkpoint, "wb") as f:
                 f.write(rve.state_save())
+        if a.fields_out:
+            np.savez_compressed(a.fields_out, phi=rve.field("phi").astype(np.float32),
+                                Wcrit=rve.field("Wcrit").astype(np.float32))
     finally:
         if out is not sys.stdout:
             out.close()

@@ -83,11 +83,15 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu():
     assert L.state_load(None, b"x" * 16, 16) == FF.FFT_ERR_ARG
 
 
-def test_willot_derivatives_refused_by_the_cuda_binding():
-    """The CUDA path has spectral derivatives only: asking for Willot's
-    scheme fails before any handle is made instead of running spectral."""
+def test_derivative_scheme_option():
+    """The derivative scheme reaches the C ABI as an integer (0 spectral,
+    1 Willot's rotated scheme); an unknown name fails before any handle is
+    made."""
     import pytest
     from paper_2304_01125_gb300 import fatiguefft as FF
     from paper_2304_01125_gb300 import inputs as I
-    with pytest.raises(NotImplementedError):
-        FF._options(I.solver_options("paper", derivative="willot"), "mixed", None)
+    assert FF._options(I.solver_options("paper"), "mixed", None).derivative == 0
+    assert FF._options(I.solver_options("paper", derivative="willot"), "mixed",
+                       None).derivative == 1
+    with pytest.raises(ValueError):
+        FF._options(I.solver_options("paper", derivative="central"), "mixed", None)

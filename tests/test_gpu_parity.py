@@ -167,22 +167,26 @@ def _compare(gpu, orc, prec, tag, tol=None):
         out[f] = rel(a, b, floor=FLOOR[f] * np.sqrt(b.size))
     if tol is None:
         tol = 1e-9 if prec == "fp64" else 1e-4
-    bad = {k: v for k, v in out.items() if not v < tol}
+    if not isinstance(tol, dict):
+        tol = {f: tol for f in out}
+    bad = {k: v for k, v in out.items() if not v < tol[k]}
     assert not bad, (tag, bad, out)
     return out
 
 
-def _run_pair(n, gid, eul, prog, prec, mat=MAT, phi0=None, mask=None, opts=None):
+def _run_pair(n, gid, eul, prog, prec, mat=MAT, phi0=None, mask=None, opts=None, tol=None):
     opts = opts or opts_for(prec)
     g = FF.RVE(n, H, gid, eul, mat, opts, prec=prec, phi0=phi0, elastic_only=mask,
                stream=stream())
-    o = O.RVE(n, H, gid, eul, mat, I.solver_options("parity64"), phi0=phi0, elastic_only=mask)
+    o = O.RVE(n, H, gid, eul, mat,
+              I.solver_options("parity64", derivative=opts.get("derivative", "spectral")),
+              phi0=phi0, elastic_only=mask)
     hist = []
     for k, (Fb, dt) in enumerate(prog):
         sg, stg = g.run_increment(Fb, dt)
         so, sto = o.run_increment(Fb, dt)
         assert so == 0 and sg == 0
-        hist.append((_compare(g, o, prec, k), stg, sto))
+        hist.append((_compare(g, o, prec, k, tol), stg, sto))
     return g, o, hist
 
 
@@ -206,6 +210,40 @@ def test_increments_polycrystal_plasticity_and_damage(prec):
     assert o.field("gamma").max() > 0
     if prec == "fp64":
         assert o.field("phi_t").max() > 0.05
+
+
+@pytest.mark.parametrize("prec", PREC)
+@pytest.mark.parametrize("n", [(8, 6, 5), (12, 12, 1)])
+def test_willot_derivatives_match_oracle(prec, n):
+    """Willot's rotated finite differences (R33) in place of the spectral
+    derivatives in the gradient, the divergence and the Green block, on a
+    plastic polycrystal with a soft elastic region (a stiffness contrast of
+    10^5 across it), on a grid with even and odd extents and on a plate:
+    every field after four increments against the oracle's rotated scheme,
+    FP64 1e-9 and mixed 1e-4 (on the plate the plastic history F_p, rho_SSD
+    and gamma of the mixed path 3e-4: it yields in these increments, where
+    the FP32 local solve's tolerance shows, as on the spectral plates); the
+    scheme changes the answer (the spectral solution differs from it by
+    far more than that)."""
+    gid, eul = I.voronoi(n, 3, 17)
+    mat = dict(MAT, tau_c0=250.0)
+    phi0, mask = I.precrack_plane(n, (2, n[0] // 2), n[1] // 2)
+    prog = I.uniaxial_cycle_program(0.006, 24, 1)[:4]
+    tol = None
+    if prec == "mixed" and n[2] == 1:
+        tol = {f: (3e-4 if f in ("Fp", "rho_ssd", "gamma", "Wp", "Gs") else 1e-4)
+               for f in FIELDS_CMP}
+    g, o, hist = _run_pair(n, gid, eul, prog, prec, mat=mat, phi0=phi0, mask=mask,
+                           opts=opts_for(prec, derivative="willot"), tol=tol)
+    assert np.abs(g.field("Fp") - np.eye(3).reshape(9, 1)).max() > 1e-6  # plastic
+    s = FF.RVE(n, H, gid, eul, mat, opts_for(prec), prec=prec, phi0=phi0, elastic_only=mask,
+               stream=stream())
+    for Fb, dt in prog:
+        s.run_increment(Fb, dt)
+    assert rel(s.field("F") - np.eye(3).reshape(9, 1),
+               g.field("F") - np.eye(3).reshape(9, 1)) > 1e-3
+    for h in (g, o, s):
+        h.close()
 
 
 @pytest.mark.parametrize("prec", PREC)
@@ -309,20 +347,30 @@ def test_plate_plane_stress(config, euler, tau_c0, prec, tol):
 
 def test_notched_plate_with_free_surfaces():
     """Notched polycrystal plate between free-surface buffer layers (soft,
-    stiffness g(1) = k across the whole width), loaded along x under plane
-    stress at the linear tolerance 1e-3 of Sec. 4.5.  Against a Green
-    preconditioner built on the averaged tangent such a laminate takes
-    hundreds of Krylov iterations per Newton step, too many for the oracle
-    at a size that still has a notch, so this is a behavioural test of the
-    GPU path in both precisions: the increments converge, the mean of F is
-    the solved macroscopic F, the prescribed mean stresses are held, and the
-    two precisions solve the same macroscopic F to within the tolerances."""
+    stiffness g(1) = k across the whole width, Sec. 4.5), loaded along x
+    under plane stress at the paper's linear tolerance 1e-3 for it (the
+    buffers make each Newton step take hundreds of Krylov iterations):
+    three increments of a 32 x 16 x 1 plate against the oracle at the same
+    tolerances.  Both solvers follow the same Krylov iterates, so the FP64
+    path's solved macroscopic F agrees to 1e-7 of the strain and its fields
+    to 1e-5; the mixed path is held to 1e-3 of the strain and 1e-3 on the
+    fields (the loose linear tolerance leaves its FP32 iterates free to part
+    from FP64's by that much).  The mean of F is the solved macroscopic F
+    and the prescribed mean stresses are held."""
     n = (32, 16, 1)
     cfg = I.build_config("plate256x128_notch", n_override=n)
     opts = I.solver_options("paper", tol_lin=1e-3, tol_newton=1e-4, tol_stag=1e-4)
     kw = dict(phi0=cfg["phi0"], elastic_only=cfg["elastic_only"])
     m = cfg["stress_mask"]
-    solved = {}
+    o = O.RVE(n, H, cfg["grain_ids"], cfg["euler"], MAT, opts, **kw)
+    ref, F = [], None
+    for k in range(3):
+        a, kwg = I.increment_args(cfg, k, F)
+        s, st = o.run_increment(*a, **kwg)
+        assert s == 0
+        F = np.array(st["Fbar"])
+        ref.append((F, o.field("F"), o.field("P")))
+    o.close()
     for prec in PREC:
         g = FF.RVE(n, H, cfg["grain_ids"], cfg["euler"], MAT, opts, prec=prec, stream=stream(),
                    **kw)
@@ -332,14 +380,18 @@ def test_notched_plate_with_free_surfaces():
             s, st = g.run_increment(*a, **kwg)
             assert s == 0
             F = np.array(st["Fbar"])
+            Fo, Ffo, Pfo = ref[k]
+            eps = np.abs(Fo - np.eye(3).reshape(9)).max()
             assert np.abs(g.field("F").mean(axis=1) - F).max() < (1e-13 if prec == "fp64" else 1e-7)
             P = np.array(st["Pbar"])
             assert np.abs(P[m == 1]).max() <= 1.01 * opts["tol_newton"] * np.abs(P).max()
-        solved[prec] = F
+            tF, tf = (1e-7, 1e-5) if prec == "fp64" else (1e-3, 1e-3)
+            errF = np.abs(F - Fo).max() / eps
+            errs = (rel(g.field("F") - np.eye(3).reshape(9, 1), Ffo - np.eye(3).reshape(9, 1)),
+                    rel(g.field("P"), Pfo))
+            print(prec, k, f"Fbar {errF:.2e} F {errs[0]:.2e} P {errs[1]:.2e}")
+            assert errF < tF and max(errs) < tf, (prec, k, errF, errs)
         g.close()
-    eps = np.abs(solved["fp64"] - np.eye(3).reshape(9)).max()
-    assert np.abs(solved["mixed"] - solved["fp64"]).max() < 1e-2 * eps
-    assert solved["fp64"][0] > 1.0 and solved["fp64"][8] < 1.0
 
 
 @pytest.mark.parametrize("prec", PREC)
@@ -588,6 +640,32 @@ def test_poly64_benchmark_increments_fieldwise(prec):
     g.close()
 
 
+def test_fp32_partial_dot_sums_change_nothing_measurable(monkeypatch):
+    """The mixed path's Arnoldi dot pass forms its per-thread products and
+    partial sums in FP32 (FP64 from the block combine on).  Against the same
+    pass with FP64 products and partial sums (FATIGUEFFT_DOT64=1) on the
+    timed workload's increments 1-8 (64^3, the last three plastic): the same
+    GMRES iteration counts within one per increment, and fields equal to
+    1e-6 (F - I, P) -- far below the 1e-4 the mixed path is held to."""
+    cfg = I.build_config("poly64")
+    opts = I.solver_options("paper")
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("FATIGUEFFT_DOT64", flag)
+        r = FF.RVE(cfg["n"], H, cfg["grain_ids"], cfg["euler"], MAT, opts, prec="mixed",
+                   stream=stream())
+        its = []
+        for Fb, dt in cfg["program"][:8]:
+            _, st = r.run_increment(Fb, dt)
+            its.append(st["lin_it_total"])
+        out.append((its, r.field("F") - np.eye(3).reshape(9, 1), r.field("P")))
+        r.close()
+    (ia, Fa, Pa), (ib, Fb_, Pb) = out
+    print("gmres its FP64 partials", ia, "FP32 partials", ib, "F", rel(Fb_, Fa), "P", rel(Pb, Pa))
+    assert all(abs(x - y) <= 1 for x, y in zip(ia, ib)), (ia, ib)
+    assert rel(Fb_, Fa) < 1e-6 and rel(Pb, Pa) < 1e-6
+
+
 @pytest.mark.parametrize("prec", PREC)
 @pytest.mark.parametrize("config,incs", [("poly128", 6)])
 def test_full_size_sampled(prec, config, incs):
@@ -620,36 +698,113 @@ def test_full_size_sampled(prec, config, incs):
     r.close()
 
 
-def test_mixed_cracked_set_matches_fp64():
-    """Damage nucleates (W_crit reached early: G_crit small, full storage
-    fraction) in a 24^3 four-grain polycrystal at the fifth increment; the
-    mixed path's damaged (phi >= 0.05), half-broken and cracked (phi >= 0.9)
-    voxel sets equal the FP64 path's wherever phi is not within 1e-3 of the
-    threshold.  The fields are held to 5e-3 (damage) and 1e-3 (degraded
-    stress, which follows g(phi)) here, not 1e-4: W_crit freezes at the step where G_s (accumulated
-    from FP32 slip increments) first exceeds G_crit, and the drive
-    S = W / W_crit - 1 divides that difference by W / W_crit - 1, small
-    right after nucleation.  (Later increments, with a 10^5 stiffness
-    contrast across the cracked voxels, are beyond what the averaged-tangent
-    Green preconditioner converges in either precision.)"""
+def _damage12():
+    """The damaged-regime workload of tests/golden/make_damage12.py and the
+    oracle trajectory that script stored."""
+    import importlib.util
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    spec = importlib.util.spec_from_file_location("make_damage12",
+                                                  os.path.join(here, "make_damage12.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod, np.load(os.path.join(here, "damage12.npz"))
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_damage_growth_matches_oracle(prec):
+    """Crack nucleation and growth (Sec. 2.3, Eqs. zeta, phase; Algorithm 1)
+    on a 12^3 four-grain polycrystal with W_crit reached at the first
+    tensile peak: damage appears at increment 25, grows through 28, runs
+    across the cell at a fixed load at 29 (64 staggered iterations) and
+    spreads at 30 (32).  Every increment converges.  Against the oracle's
+    trajectory (stored by the golden script):
+      * FP64: phi after increments 25-30 to 1e-9, the degraded stress after
+        28 and 30 to 1e-6 (stored in FP32), and the staggered iteration
+        counts of every increment equal the oracle's;
+      * mixed: phi after 25-29 and the stress after 28 to 1e-4 (phi
+        relative to max(||phi||, 0.01 sqrt N): at nucleation phi is 5e-3 at
+        most and its differences 1e-6); after 30, where the second
+        unstable increment has taken the FP32 path a tolerance-level
+        distance (tol_stag 5e-3) from the FP64 one, 5e-4 on phi and 5e-3 on
+        the stress (measured 1.7e-4 and 1.7e-3);
+      * the cracked set (phi >= 0.9) identical wherever phi is not within
+        1e-3 of the threshold (FP64), within 1 % of its size (mixed)."""
+    mod, ref = _damage12()
+    gid, eul, mat, prog, opts = mod.setup()
+    r = FF.RVE(mod.N_GRID, H, gid, eul, mat, opts, prec=prec, stream=stream())
+    stats = []
+    last = len(prog) - 1
+    for k, (Fb, dt) in enumerate(prog):
+        s, st = r.run_increment(Fb, dt, check=False)
+        assert s == 0, (k, FF.load().fft_last_error(r._h).decode())
+        stats.append(st)
+        if k in mod.KEEP_PHI:
+            phi, phio = r.field("phi"), ref[f"phi_{k}"]
+            if prec == "fp64":
+                tol, floor = 1e-9, 1e-4
+            else:
+                tol, floor = (5e-4 if k == last else 1e-4), 1e-2
+            err = rel(phi, phio, floor=floor * np.sqrt(phio.size))
+            assert err < tol, (k, err)
+            clear = np.abs(phio - 0.9) > 1e-3
+            diff = int(np.sum((phi >= 0.9)[clear] != (phio >= 0.9)[clear]))
+            if prec == "fp64":
+                assert diff == 0, k
+            else:
+                assert diff <= 0.01 * max(int(np.sum(phio >= 0.9)), 1), (k, diff)
+        if k in mod.KEEP_P:
+            P, Po = r.field("P"), ref[f"P_{k}"].astype(np.float64)
+            tol = 1e-6 if prec == "fp64" else (5e-3 if k == last else 1e-4)
+            assert rel(P, Po) < tol, (k, rel(P, Po))
+    so = ref["stats"]
+    assert so[-1][4] > 0 and stats[-1]["cracked"] > 0  # the cell did crack
+    if prec == "fp64":
+        assert [st["stag_it"] for st in stats] == [int(x) for x in so[:, 0]]
+    r.close()
+
+
+def test_mixed_cracked_set_matches_fp64_at_24():
+    """The same damaged regime on a 24^3 four-grain polycrystal (beyond the
+    oracle's reach in a test: unstable growth takes 150 staggered
+    iterations there): damage nucleates within the first cycle and grows
+    through the second; both precisions converge through increment 27,
+    where the crack runs across the cell at a fixed load.  From nucleation
+    to increment 26 the mixed path's phase field and degraded stress agree
+    with FP64's to 1e-4 (phi relative to max(||phi||, 0.01 sqrt N)); at
+    the unstable increment 27 to 5e-4 (both paths stop their staggered
+    iterations at tol_stag 5e-3 along different round-off); the damaged
+    (phi >= 0.05), half-broken and cracked (phi >= 0.9) voxel sets agree
+    at every increment wherever phi is not within 1e-3 of the threshold.
+    (Past it the two paths take different cut-back decisions and part.)"""
+    mod, _ = _damage12()
     n = (24, 24, 24)
     gid, eul = I.voronoi(n, 4, 31)
-    mat = dict(MAT, tau_c0=250.0, G_crit=1e-9, xi_store=1.0)
-    prog = I.uniaxial_cycle_program(0.006, 24, 1)[:5]
-    fields = {}
+    _, _, mat, _, opts = mod.setup()
+    prog = I.uniaxial_cycle_program(0.006, 24, 2)[:27]
+    runs = {}
     for prec in PREC:
-        r = FF.RVE(n, H, gid, eul, mat, I.solver_options("paper"), prec=prec, stream=stream())
-        for Fb, dt in prog:
-            r.run_increment(Fb, dt)
-        fields[prec] = {f: r.field(f) for f in ("phi", "P")}
+        r = FF.RVE(n, H, gid, eul, mat, opts, prec=prec, stream=stream())
+        snaps = []
+        for k, (Fb, dt) in enumerate(prog):
+            s, st = r.run_increment(Fb, dt, check=False)
+            assert s == 0, (prec, k, FF.load().fft_last_error(r._h).decode())
+            snaps.append((r.field("phi"), r.field("P"), st["cracked"], st["stag_it"]))
+        runs[prec] = snaps
         r.close()
-    p64, p32 = fields["fp64"]["phi"], fields["mixed"]["phi"]
-    assert (p64 >= 0.9).sum() > 0
-    for thr in (0.05, 0.5, 0.9):
-        clear = np.abs(p64 - thr) > 1e-3
-        assert np.array_equal((p64 >= thr)[clear], (p32 >= thr)[clear]), thr
-    assert rel(fields["mixed"]["P"], fields["fp64"]["P"]) < 1e-3
-    assert rel(p32, p64, floor=1e-4 * np.sqrt(p64.size)) < 5e-3
+    assert runs["fp64"][-1][2] > 0  # cracked voxels at the end
+    nuc = min(k for k, (p, _, _, _) in enumerate(runs["fp64"]) if p.max() > 0)
+    assert len(prog) - nuc >= 6  # at least five increments past nucleation
+    assert runs["fp64"][-1][3] > 50  # the last one is the unstable growth
+    for k in range(nuc, len(prog)):
+        p64, P64 = runs["fp64"][k][:2]
+        p32, P32 = runs["mixed"][k][:2]
+        tol = 5e-4 if k == len(prog) - 1 else 1e-4
+        for thr in (0.05, 0.5, 0.9):
+            clear = np.abs(p64 - thr) > 1e-3
+            assert np.array_equal((p64 >= thr)[clear], (p32 >= thr)[clear]), (k, thr)
+        ep, eP = rel(p32, p64, floor=1e-2 * np.sqrt(p64.size)), rel(P32, P64)
+        print("24^3", k, f"phi {ep:.2e} P {eP:.2e}")
+        assert ep < tol and eP < tol, (k, ep, eP)
 
 
 @pytest.mark.parametrize("prec", PREC)
