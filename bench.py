@@ -60,7 +60,7 @@ def args_():
 # the translation units that hold device code, and every header: ncu
 # counters taken on other kernel code are not reported (the host-only
 # drivers rve.cu and batch.cu launch the same kernels)
-KERNEL_SOURCES = ("kernels_cp.cu", "kernels_spec.cu", "noalloc.cu")
+KERNEL_SOURCES = ("kernels_cp.cu", "kernels_spec.cu", "kernels_fft.cu", "noalloc.cu")
 
 
 def source_sha1():
@@ -141,11 +141,12 @@ def probe_dominant(FF, cfg, mat, opts, stream, prec):
     else:
         os.environ["FATIGUEFFT_PROF_SAMPLE"] = old
     drv = Driver(cfg)
-    for k in range(8):
+    p0, p1 = cfg.get("probe", (8, 14))
+    for k in range(p0):
         drv(r, k)
     r.profile(FF.KERNEL_FAMILIES)
     torch.cuda.nvtx.range_push(f"probe_{prec}")  # the window of the committed ncu launch list
-    for k in range(8, 14):
+    for k in range(p0, p1):
         drv(r, k)
     bd = r.profile_read(reset=True)
     torch.cuda.nvtx.range_pop()
@@ -391,26 +392,34 @@ def run_ours(a):
     # field read back to pinned host memory
     r = FF.RVE(n, I.VOXEL_MM, cfg["grain_ids"], cfg["euler"], mat, opts, prec="mixed",
                stream=stream)
-    drv = Driver(cfg)
+    drv0 = Driver(cfg)
     for k in range(a.warmup):
-        drv(r, k)
+        drv0(r, k)
+    ckpt = r.state_save()  # the window is run three times from here (median)
     mixed_ctl = cfg["stress_mask"] is not None
     host_in = torch.empty((a.steps, 10), dtype=torch.float64).pin_memory()
     for i, k in enumerate(range(a.warmup, a.warmup + a.steps)):
         host_in[i, :9] = torch.from_numpy(prog[k][0])
         host_in[i, 9] = prog[k][1]
     host_out = torch.empty(N, dtype=torch.float64).pin_memory()
-    barrier()
-    t0 = time.perf_counter()
-    for i in range(a.steps):
-        row = host_in[i].numpy()
-        if mixed_ctl:  # the guess of the stress-controlled components is the last solved F
-            drv(r, a.warmup + i)
-        else:
-            r.run_increment(row[:9], float(row[9]))
-        FF.load().fields_out(r._h, FF.FIELDS["phi"][0], host_out.data_ptr(), host_out.nbytes, 0)
-    barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_runs = []
+    for _ in range(3):
+        r.state_load(ckpt)
+        drv = Driver(cfg)
+        drv.F = drv0.F
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(a.steps):
+            row = host_in[i].numpy()
+            if mixed_ctl:  # the guess of the stress-controlled components is the last solved F
+                drv(r, a.warmup + i)
+            else:
+                r.run_increment(row[:9], float(row[9]))
+            FF.load().fields_out(r._h, FF.FIELDS["phi"][0], host_out.data_ptr(),
+                                 host_out.nbytes, 0)
+        barrier()
+        e2e_runs.append(max_over_ranks(time.perf_counter() - t0))
+    e2e_s = statistics.median(e2e_runs)
     r.close()
 
     if rank != 0:
@@ -462,7 +471,10 @@ def run_ours(a):
         "mixed_vs_fp64_rel_l2": errs,
         "e2e": {"value": round(ws * N * a.steps / e2e_s, 1), "unit": "voxel-increments/s",
                 "h2d_bytes_per_step": 80 + (72 + 36 if mixed_ctl else 0),
-                "d2h_bytes_per_step": 8 * N},
+                "d2h_bytes_per_step": 8 * N,
+                "timing": "wall clock of the window through the public API, median of three "
+                          "runs from a checkpoint taken after the warm-up",
+                "runs_s": [round(x, 4) for x in e2e_runs]},
         "gpu_launches": int(mx["launches"]),
         "roofline": roof,
         "clocks": mx["clocks"],
@@ -471,17 +483,19 @@ def run_ours(a):
                            "staggered": sum(s["stag_it"] for s in results[p]["stats"]),
                            "phase_field": sum(s["pf_it_total"] for s in results[p]["stats"])}
                        for p in results},
-        "kernel_ms_probe_increments_9_14": {
+        "kernel_ms_probe": {
             p: {k: round(v[0], 3) for k, v in results[p]["breakdown"].items() if v[1]}
             for p in results},
-        "kernel_launches_probe_increments_9_14": {
+        "kernel_launches_probe": {
             p: {k: int(v[1]) for k, v in results[p]["breakdown"].items() if v[1]}
             for p in results},
-        "kernel_gbs_probe_increments_9_14": {
+        "kernel_gbs_probe": {
             p: {k: round(v[2] / v[0] / 1e6, 1)
                 for k, v in results[p]["breakdown"].items() if v[2] > 0 and v[0] > 0}
             for p in results},
     }
+    p0, p1 = cfg.get("probe", (8, 14))
+    line["probe_increments"] = [p0 + 1, p1]
     if a.config == CONFIG_NAME and not a.no_damage_window:
         line["damage_window"] = damage_window(FF, a, stream, flush)
     if ws == 1 and not a.no_cpu_baseline:

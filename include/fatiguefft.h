@@ -73,7 +73,9 @@ typedef struct {
 } fft_material;
 
 /* Solver controls.  Tolerances (Sec. 3.1-3.2): tol_stag on the Algorithm 1
- * ratios, tol_newton on ||grad du||inf / ||F - F_t||inf, tol_lin relative
+ * ratios (each change of an iteration relative to the change over the
+ * increment, the latter floored at 1e-12, and for the phase field at 100
+ * machine epsilons of the bulk type), tol_newton on ||grad du||inf / ||F - F_t||inf, tol_lin relative
  * GMRES residual, tol_pf relative phase-field CG residual, tol_local the
  * local slip-law residual (MPa).  The Newton update is damped (an
  * extension; the paper takes full steps): from the 4th iteration, an update

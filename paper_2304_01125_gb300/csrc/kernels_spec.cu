@@ -334,7 +334,7 @@ __device__ __forceinline__ bool hs_partner(const SGrid& g, size_t e64, size_t& p
 // k and -k coincide, have zero multipliers).  Its entries are loaded with
 // the entry's own (off the planes p = e, a cache hit), so no lane waits for
 // a second round of loads.
-template <typename R, bool IL = false>
+template <typename R, bool IL = false, bool WIL = false>
 __device__ __forceinline__ void div3_real(const typename Tr<R>::Cx* T, const SGrid& g, size_t e,
                                           const R* xd, R sign, typename Tr<R>::Cx* out) {
     typedef typename Tr<R>::Cx Cx;
@@ -347,7 +347,7 @@ __device__ __forceinline__ void div3_real(const typename Tr<R>::Cx* T, const SGr
         te[q] = T[fld_at<IL>(g, e, q)];
         tp[q] = T[fld_at<IL>(g, p, q)];
     }
-    if (g.willot) {
+    if (WIL) {
         // divergence symbols S_j = -conj(D_j) (the adjoint of the rotated
         // gradient); the partner's are conj(S_j)
         Cx D[3];
@@ -404,7 +404,7 @@ __device__ __forceinline__ void div3_real(const typename Tr<R>::Cx* T, const SGr
 // b_i = sum_j F{gP}_ij i xi_j (Eq. momentum / newton right-hand side, sign
 // flipped), projected onto real fields.  out[0] = ||b||^2, out[1] = the
 // round-off scale of b, sum_ij |F{gP}_ij xi_j|^2 (Hermitian-weighted).
-template <typename R>
+template <typename R, bool WIL>
 __global__ void k_residual(const typename Tr<R>::Cx* Ph, SGrid g, typename Tr<R>::Cx* b, Red red) {
     typedef typename Tr<R>::Cx Cx;
     const size_t Nh = g.Nh;
@@ -413,10 +413,10 @@ __global__ void k_residual(const typename Tr<R>::Cx* Ph, SGrid g, typename Tr<R>
         R xi[3], xd[3], w;
         hs_freq<R>(g, e, xi, xd, w);
         Cx s[3];
-        div3_real<R>(Ph, g, e, xd, R(1), s);
+        div3_real<R, false, WIL>(Ph, g, e, xd, R(1), s);
 #pragma unroll
         R d2[3] = {xd[0] * xd[0], xd[1] * xd[1], xd[2] * xd[2]};
-        if (g.willot) {
+        if (WIL) {
             Cx D[3];
             willot_D<R>(g, e, D);
 #pragma unroll
@@ -438,8 +438,11 @@ __global__ void k_residual(const typename Tr<R>::Cx* Ph, SGrid g, typename Tr<R>
 }
 template <typename R>
 void residual(const void* Ph, const SGrid& g, void* b, const Red& red, cudaStream_t s) {
-    k_residual<R><<<kRedBlocks, kThreads, 0, s>>>((const typename Tr<R>::Cx*)Ph, g,
-                                                  (typename Tr<R>::Cx*)b, red);
+    typedef typename Tr<R>::Cx Cx;
+    if (g.willot)
+        k_residual<R, true><<<kRedBlocks, kThreads, 0, s>>>((const Cx*)Ph, g, (Cx*)b, red);
+    else
+        k_residual<R, false><<<kRedBlocks, kThreads, 0, s>>>((const Cx*)Ph, g, (Cx*)b, red);
 }
 
 // -------------------------------------------------------------------- GMRES
@@ -580,11 +583,11 @@ __device__ __forceinline__ void green_apply_w(const R* Ks, const typename Tr<R>:
 
 // z = M v with the Green preconditioner of the grid's derivative scheme;
 // D receives Willot's symbols when that scheme is selected.
-template <typename R>
+template <typename R, bool WIL>
 __device__ __forceinline__ void green_any(const SGrid& g, size_t e, const R* Ks, const R* xd,
                                           const typename Tr<R>::Cx* v, typename Tr<R>::Cx* z,
                                           typename Tr<R>::Cx* D) {
-    if (g.willot) {
+    if (WIL) {
         willot_D<R>(g, e, D);
         green_apply_w<R>(Ks, D, v, z);
     } else {
@@ -592,16 +595,15 @@ __device__ __forceinline__ void green_any(const SGrid& g, size_t e, const R* Ks,
     }
 }
 // gradient entry z_i d_j: d_j = i xi_j (spectral) or Willot's D_j
-template <typename R>
-__device__ __forceinline__ typename Tr<R>::Cx grad_sym(const SGrid& g, typename Tr<R>::Cx z,
-                                                       const R* xd,
+template <typename R, bool WIL>
+__device__ __forceinline__ typename Tr<R>::Cx grad_sym(typename Tr<R>::Cx z, const R* xd,
                                                        const typename Tr<R>::Cx* D, int j) {
-    return g.willot ? cmul(z, D[j]) : cmul_i(z, xd[j]);
+    return WIL ? cmul(z, D[j]) : cmul_i(z, xd[j]);
 }
 
 // v = scale * vin (optionally stored to vout); z = M(xi) v when use_pre,
 // else z = v; G_ij = z_i i xi_j, the 9-component spectrum of grad z.
-template <typename R, bool IL>
+template <typename R, bool IL, bool WIL>
 __global__ void __launch_bounds__(kThreads, 3) k_precond_grad(const typename Tr<R>::Cx* vin,
                                                               R scale, typename Tr<R>::Cx* vout,
                                                               const double* Kbar, SGrid g,
@@ -624,9 +626,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_precond_grad(const typename Tr<
         }
         Cx D[3];
         if (use_pre) {
-            green_any<R>(g, e, Ks, xd, v, z, D);
+            green_any<R, WIL>(g, e, Ks, xd, v, z, D);
         } else {
-            if (g.willot) willot_D<R>(g, e, D);
+            if (WIL) willot_D<R>(g, e, D);
 #pragma unroll
             for (int i = 0; i < 3; ++i) z[i] = v[i];
         }
@@ -634,7 +636,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_precond_grad(const typename Tr<
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = 0; j < 3; ++j)
-                G[fld_at<IL>(g, e, 3 * i + j)] = grad_sym<R>(g, z[i], xd, D, j);
+                G[fld_at<IL>(g, e, 3 * i + j)] = grad_sym<R, WIL>(z[i], xd, D, j);
     }
 }
 template <typename R>
@@ -642,10 +644,13 @@ void precond_grad(const void* vin, double scale, void* vout, const double* Kbar,
                   void* G, int use_pre, cudaStream_t s, int il) {
     typedef typename Tr<R>::Cx Cx;
     if (il)
-        k_precond_grad<R, true><<<grid_for(g.Nh), kThreads, 0, s>>>(
+        k_precond_grad<R, true, false><<<grid_for(g.Nh), kThreads, 0, s>>>(
+            (const Cx*)vin, (R)scale, (Cx*)vout, Kbar, g, (Cx*)G, use_pre);
+    else if (g.willot)
+        k_precond_grad<R, false, true><<<grid_for(g.Nh), kThreads, 0, s>>>(
             (const Cx*)vin, (R)scale, (Cx*)vout, Kbar, g, (Cx*)G, use_pre);
     else
-        k_precond_grad<R, false><<<grid_for(g.Nh), kThreads, 0, s>>>(
+        k_precond_grad<R, false, false><<<grid_for(g.Nh), kThreads, 0, s>>>(
             (const Cx*)vin, (R)scale, (Cx*)vout, Kbar, g, (Cx*)G, use_pre);
 }
 
@@ -734,7 +739,7 @@ void tangent_apply(void* G, const void* K, const void* phi, double kres, size_t 
 
 // w = -div(T) = -sum_j i xi_j T_ij (the sign that makes the operator
 // positive), projected onto real fields.
-template <typename R>
+template <typename R, bool WIL>
 __global__ void k_contract(const typename Tr<R>::Cx* T, SGrid g, typename Tr<R>::Cx* w) {
     typedef typename Tr<R>::Cx Cx;
     const size_t Nh = g.Nh;
@@ -742,7 +747,7 @@ __global__ void k_contract(const typename Tr<R>::Cx* T, SGrid g, typename Tr<R>:
         R xi[3], xd[3], wt;
         hs_freq<R>(g, e, xi, xd, wt);
         Cx a[3];
-        div3_real<R>(T, g, e, xd, R(-1), a);
+        div3_real<R, false, WIL>(T, g, e, xd, R(-1), a);
 #pragma unroll
         for (int c = 0; c < 3; ++c) w[c * Nh + e] = a[c];
     }
@@ -750,7 +755,10 @@ __global__ void k_contract(const typename Tr<R>::Cx* T, SGrid g, typename Tr<R>:
 template <typename R>
 void contract(const void* T, const SGrid& g, void* w, cudaStream_t s) {
     typedef typename Tr<R>::Cx Cx;
-    k_contract<R><<<grid_for(g.Nh), kThreads, 0, s>>>((const Cx*)T, g, (Cx*)w);
+    if (g.willot)
+        k_contract<R, true><<<grid_for(g.Nh), kThreads, 0, s>>>((const Cx*)T, g, (Cx*)w);
+    else
+        k_contract<R, false><<<grid_for(g.Nh), kThreads, 0, s>>>((const Cx*)T, g, (Cx*)w);
 }
 
 // Coefficients of DCGS2 step k from the dots d (layout above) and
@@ -854,7 +862,7 @@ __device__ __forceinline__ void dots_finish(const A (&acc)[3 + 2 * NQ], int k, c
 // A is the per-thread accumulator type: the bulk type R by default, or FP64
 // (products and sums, FATIGUEFFT_DOT64=1) to measure what the FP32 partial
 // sums of the mixed path cost in accuracy.
-template <typename R, int NQ, bool IL, typename A>
+template <typename R, int NQ, bool IL, typename A, bool WIL>
 __global__ void __launch_bounds__(kThreads, 2) k_contract_dots(
     const typename Tr<R>::Cx* T, SGrid g, typename Tr<R>::Cx* w, const typename Tr<R>::Cx* c,
     const typename Tr<R>::Cx* V, size_t vstride, int k, Red red, double* Hd, double* Hp,
@@ -871,7 +879,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_contract_dots(
         Cx zc[3], cv[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) cv[q] = c[q * Nh + e];
-        div3_real<R, IL>(T, g, e, xd, R(-1), zc);
+        div3_real<R, IL, WIL>(T, g, e, xd, R(-1), zc);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             w[q * Nh + e] = zc[q];
@@ -916,13 +924,16 @@ void contract_dots(const void* T, const SGrid& g, void* w, const void* c, const 
 #define CDOTS(NQ)                                                                             \
     do {                                                                                      \
         if (il)                                                                               \
-            k_contract_dots<R, NQ, true, R><<<kRedBlocks, kThreads, 0, s>>>(                  \
+            k_contract_dots<R, NQ, true, R, false><<<kRedBlocks, kThreads, 0, s>>>(           \
+                TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err);                 \
+        else if (g.willot)                                                                    \
+            k_contract_dots<R, NQ, false, R, true><<<kRedBlocks, kThreads, 0, s>>>(           \
                 TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err);                 \
         else if (dot64)                                                                       \
-            k_contract_dots<R, NQ, false, double><<<kRedBlocks, kThreads, 0, s>>>(            \
+            k_contract_dots<R, NQ, false, double, false><<<kRedBlocks, kThreads, 0, s>>>(     \
                 TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err);                 \
         else                                                                                  \
-            k_contract_dots<R, NQ, false, R><<<kRedBlocks, kThreads, 0, s>>>(                 \
+            k_contract_dots<R, NQ, false, R, false><<<kRedBlocks, kThreads, 0, s>>>(          \
                 TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err);                 \
     } while (0)
     if (k <= 0)
@@ -970,7 +981,7 @@ __device__ __forceinline__ void bulk_drain(uint64_t* full, int issued) {
     }
 }
 
-template <typename R, bool IL>
+template <typename R, bool IL, bool WIL>
 __global__ void __launch_bounds__(kUpdT) k_dcgs_update_bulk(
     typename Tr<R>::Cx* V, size_t vstride, int k, const typename Tr<R>::Cx* z,
     const double* coef, const double* Kbar, SGrid g, typename Tr<R>::Cx* G, int tpc, Red red,
@@ -1086,12 +1097,12 @@ __global__ void __launch_bounds__(kUpdT) k_dcgs_update_bulk(
             acc[0] += wt * nn;
             if (G) {
                 Cx zz[3], D[3];
-                green_any<R>(g, e, Ks, xd, nx, zz, D);
+                green_any<R, WIL>(g, e, Ks, xd, nx, zz, D);
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
 #pragma unroll
                     for (int j = 0; j < 3; ++j)
-                        G[fld_at<IL>(g, e, 3 * i + j)] = grad_sym<R>(g, zz[i], xd, D, j);
+                        G[fld_at<IL>(g, e, 3 * i + j)] = grad_sym<R, WIL>(zz[i], xd, D, j);
             }
         }
     }
@@ -1114,12 +1125,14 @@ int dcgs_bulk_setup(BulkCfg& bc) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int su = (int)upd_bulk_smem<R>();
     int nu = 0;
-    if (cudaFuncSetAttribute(k_dcgs_update_bulk<R, false>,
+    if (cudaFuncSetAttribute(k_dcgs_update_bulk<R, false, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, su) != cudaSuccess ||
-        cudaFuncSetAttribute(k_dcgs_update_bulk<R, true>,
+        cudaFuncSetAttribute(k_dcgs_update_bulk<R, true, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, su) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nu, k_dcgs_update_bulk<R, false>, kUpdT,
-                                                      su) != cudaSuccess)
+        cudaFuncSetAttribute(k_dcgs_update_bulk<R, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, su) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nu, k_dcgs_update_bulk<R, false, false>,
+                                                      kUpdT, su) != cudaSuccess)
         nu = 0;
     cudaGetLastError();
     // the reduction buffers hold kRedSlots x kRedBlocks partials
@@ -1144,7 +1157,7 @@ static inline void tile_split(int ntiles, int maxb, int& tpc, int& nb) {
 //   c_{k+1} = z / nu - Q_k e - c_k dd_k / nu     -> slot k + 1
 //   G = (M c_{k+1}) (x) i xi                     -> the next step's gradient
 // and out[0] = |c_{k+1}|^2.
-template <typename R, bool IL>
+template <typename R, bool IL, bool WIL>
 __global__ void __launch_bounds__(kThreads, 2) k_dcgs_update(typename Tr<R>::Cx* V,
                                                              size_t vstride, int k,
                                                              const typename Tr<R>::Cx* z,
@@ -1204,12 +1217,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_dcgs_update(typename Tr<R>::Cx*
         acc[0] += wt * nn;
         if (G) {
             Cx zz[3], D[3];
-            green_any<R>(g, e, Ks, xd, nx, zz, D);
+            green_any<R, WIL>(g, e, Ks, xd, nx, zz, D);
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
-                    G[fld_at<IL>(g, e, 3 * i + j)] = grad_sym<R>(g, zz[i], xd, D, j);
+                    G[fld_at<IL>(g, e, 3 * i + j)] = grad_sym<R, WIL>(zz[i], xd, D, j);
         }
     }
     block_partials<1, kThreads>(acc, 1, 0u, red.part);
@@ -1234,23 +1247,29 @@ void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* co
         cfg.attrs = at;
         cfg.numAttrs = 1;
         if (il)
-            cudaLaunchKernelEx(&cfg, k_dcgs_update_bulk<R, true>, (Cx*)V, vstride, k,
+            cudaLaunchKernelEx(&cfg, k_dcgs_update_bulk<R, true, false>, (Cx*)V, vstride, k,
+                               (const Cx*)z, coef, Kbar, g, (Cx*)G, tpc, red, bc->err);
+        else if (g.willot)
+            cudaLaunchKernelEx(&cfg, k_dcgs_update_bulk<R, false, true>, (Cx*)V, vstride, k,
                                (const Cx*)z, coef, Kbar, g, (Cx*)G, tpc, red, bc->err);
         else
-            cudaLaunchKernelEx(&cfg, k_dcgs_update_bulk<R, false>, (Cx*)V, vstride, k,
+            cudaLaunchKernelEx(&cfg, k_dcgs_update_bulk<R, false, false>, (Cx*)V, vstride, k,
                                (const Cx*)z, coef, Kbar, g, (Cx*)G, tpc, red, bc->err);
         return;
     }
     if (il)
-        k_dcgs_update<R, true><<<grid_for(g.Nh), kThreads, 0, s>>>(
+        k_dcgs_update<R, true, false><<<grid_for(g.Nh), kThreads, 0, s>>>(
+            (Cx*)V, vstride, k, (const Cx*)z, coef, Kbar, g, (Cx*)G, red);
+    else if (g.willot)
+        k_dcgs_update<R, false, true><<<grid_for(g.Nh), kThreads, 0, s>>>(
             (Cx*)V, vstride, k, (const Cx*)z, coef, Kbar, g, (Cx*)G, red);
     else
-        k_dcgs_update<R, false><<<grid_for(g.Nh), kThreads, 0, s>>>(
+        k_dcgs_update<R, false, false><<<grid_for(g.Nh), kThreads, 0, s>>>(
             (Cx*)V, vstride, k, (const Cx*)z, coef, Kbar, g, (Cx*)G, red);
 }
 
 // x += M (sum_i y_i V_i)  (right-preconditioned GMRES update)
-template <typename R>
+template <typename R, bool WIL>
 __global__ void k_xupdate(typename Tr<R>::Cx* x, const typename Tr<R>::Cx* V, size_t vstride,
                           int k, const double* y, const double* Kbar, SGrid g) {
     typedef typename Tr<R>::Cx Cx;
@@ -1274,7 +1293,7 @@ __global__ void k_xupdate(typename Tr<R>::Cx* x, const typename Tr<R>::Cx* V, si
             }
         }
         Cx D[3];
-        green_any<R>(g, e, Ks, xd, c, z, D);
+        green_any<R, WIL>(g, e, Ks, xd, c, z, D);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             Cx xv = x[i * Nh + e];
@@ -1288,8 +1307,12 @@ template <typename R>
 void xupdate(void* x, const void* V, size_t vstride, int k, const double* y, const double* Kbar,
              const SGrid& g, cudaStream_t s) {
     typedef typename Tr<R>::Cx Cx;
-    k_xupdate<R><<<grid_for(g.Nh), kThreads, 0, s>>>((Cx*)x, (const Cx*)V, vstride, k, y, Kbar,
-                                                     g);
+    if (g.willot)
+        k_xupdate<R, true><<<grid_for(g.Nh), kThreads, 0, s>>>((Cx*)x, (const Cx*)V, vstride, k,
+                                                               y, Kbar, g);
+    else
+        k_xupdate<R, false><<<grid_for(g.Nh), kThreads, 0, s>>>((Cx*)x, (const Cx*)V, vstride, k,
+                                                                y, Kbar, g);
 }
 
 // out = alpha a + beta b (complex vectors of n3 entries; b may be null)

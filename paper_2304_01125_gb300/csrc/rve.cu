@@ -1090,11 +1090,18 @@ struct Impl {
         const double dphi = o4[0], dphit = o4[1];
         r->phi_changed = o4[2] > 0;
         const double tol = r->opt.tol_stag;
-        r->converged = dF <= tol * std::max(dFt, 1e-12) && dphi <= tol * std::max(dphit, 1e-12);
+        // the phase-field ratio of Algorithm 1 is 0/0 when phi does not
+        // change over the increment; its denominator is kept above the
+        // resolution of phi in the bulk type (100 eps: 1.2e-5 in FP32, the
+        // 1e-12 floor in FP64), below which the iterations' changes are
+        // round-off of the phase-field solve
+        const double phi_floor = std::max(1e-12, 100.0 * Tr<R>::eps);
+        r->converged =
+            dF <= tol * std::max(dFt, 1e-12) && dphi <= tol * std::max(dphit, phi_floor);
         for (int c = 0; c < 9; ++c) r->Pbar_cur[c] = r->hred[2 + c];
         if (st) {
             st->res_F = dF / std::max(dFt, 1e-12);
-            st->res_phi = dphi / std::max(dphit, 1e-12);
+            st->res_phi = dphi / std::max(dphit, phi_floor);
             st->converged = r->converged;
             for (int c = 0; c < 9; ++c) st->Pbar[c] = r->hred[2 + c];
             st->cracked = (long)o4[3];
