@@ -743,9 +743,16 @@ struct Impl {
             first = false;
             std::fill(Hm.begin(), Hm.end(), 0.0);
             int kcols = 0;
+            // residual estimates of the last two processed steps: when the
+            // next one is predicted to converge (geometric extrapolation),
+            // the following step is enqueued only after it has been read,
+            // instead of ahead of it (it would be discarded)
+            double res1 = -1.0, res2 = -1.0;
             for (int j = 0;; ++j) {
                 const bool enq = j < m && lin + j < r->opt.max_lin;
-                if (enq) TRY(enqueue_step(r, j, src, 1.0 / beta));
+                const bool defer = enq && j >= 2 && res2 > 0.0 && res1 > 0.0 &&
+                                   res1 * (res1 / res2) <= target;
+                if (enq && !defer) TRY(enqueue_step(r, j, src, 1.0 / beta));
                 if (j == 0) {
                     if (!enq) break;
                     continue;
@@ -787,10 +794,13 @@ struct Impl {
                     break;
                 }
                 if (!enq) break;
+                if (defer) TRY(enqueue_step(r, j, src, 1.0 / beta));
+                res2 = res1;
+                res1 = res;
             }
             const int k = kcols;
             hess_lsq(Hm, m, k, beta, y.data());
-            CK(r, cudaStreamSynchronize(r->st));  // the discarded look-ahead step, hy reuse
+            CK(r, cudaStreamSynchronize(r->st));  // a discarded look-ahead step, hy reuse
             prof_collect(r);
             if (k > 0) {
                 std::memcpy(r->hy, y.data(), k * sizeof(double));
