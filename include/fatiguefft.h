@@ -114,6 +114,16 @@ typedef struct {
      * and the phase-field Laplacian stay spectral.  Other values:
      * FFT_ERR_ARG at init_rve. */
     int derivative;
+    /* Kernel variants of the Arnoldi step (results agree to the Krylov
+     * tolerance; speed differs by grid size): bit 0 = the fused x pass (the
+     * inverse real transform along x of the 9 gradient components, the
+     * tangent apply and the forward real transform in one kernel, between
+     * batched 2-D transforms over (z, y); used where n0 is a power of two
+     * in [8, 512]), bit 1 = the register-streaming update pass instead of
+     * the pipelined bulk-copy one.  0 is the default; values outside 0..3:
+     * FFT_ERR_ARG.  The environment variables FATIGUEFFT_FUSED and
+     * FATIGUEFFT_BULK (0 or 1) override the respective bit. */
+    int kernel_variant;
 } fft_options;
 
 /* Per-increment statistics (accumulated since apply_increment). */

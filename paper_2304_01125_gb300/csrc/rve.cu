@@ -1428,6 +1428,7 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
         return FFT_ERR_ARG;
     if (opt->max_cutbacks < 0 || opt->max_cutbacks > 10) return FFT_ERR_ARG;
     if (opt->derivative != 0 && opt->derivative != 1) return FFT_ERR_ARG;
+    if (opt->kernel_variant < 0 || opt->kernel_variant > 3) return FFT_ERR_ARG;
     fft_rve_s* r = new fft_rve_s();
     r->prec = opt->prec;
     r->esz = opt->prec == FFT_PREC_FP64 ? 8 : 4;
@@ -1574,20 +1575,23 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
     cudaMemsetAsync(r->counter, 0, sizeof(unsigned), r->st);
     cudaMemsetAsync(r->bulk.err, 0, sizeof(int), r->st);
     {
-        // FATIGUEFFT_BULK=0 keeps the register-streaming Arnoldi kernels
+        // the register-streaming Arnoldi update pass: kernel_variant bit 1,
+        // or FATIGUEFFT_BULK=0 (FATIGUEFFT_BULK=1 forces the pipelined one)
         const char* bv = std::getenv("FATIGUEFFT_BULK");
-        const bool want = !(bv && bv[0] == '0');
+        const bool want = bv ? bv[0] != '0' : !(opt->kernel_variant & 2);
         r->use_bulk = want && (r->prec == FFT_PREC_FP64 ? dcgs_bulk_setup<double>(r->bulk)
                                                         : dcgs_bulk_setup<float>(r->bulk));
     }
     {
-        // FATIGUEFFT_FUSED=1 selects the fused x pass in the Arnoldi step
-        // (measured slower than the library 3-D transforms with the separate
-        // tangent apply at 64^3: the strided batched 2-D transforms cost more
-        // than the transform passes they replace); grids whose n0 is not a
-        // power of two (or with n1 = n2 = 1) always use the library path
+        // the fused x pass in the Arnoldi step: kernel_variant bit 0, or
+        // FATIGUEFFT_FUSED=1 (FATIGUEFFT_FUSED=0 forbids it); measured slower
+        // than the library 3-D transforms with the separate tangent apply at
+        // 64^3 (the strided batched 2-D transforms cost more than the
+        // transform passes they replace).  Grids whose n0 is not a power of
+        // two (or with n1 = n2 = 1) always use the library path
         const char* fv = std::getenv("FATIGUEFFT_FUSED");
-        const bool want = (fv && fv[0] == '1') && (g.n1 > 1 || g.n2 > 1);
+        const bool want = (fv ? fv[0] == '1' : (opt->kernel_variant & 1) != 0) &&
+                          (g.n1 > 1 || g.n2 > 1);
         const bool f64 = r->prec == FFT_PREC_FP64;
         if (want && (f64 ? fused_x_plan<double>(r->fx, g) : fused_x_plan<float>(r->fx, g))) {
             void* tw = nullptr;

@@ -52,7 +52,7 @@ class Options(C.Structure):
                 ("max_stag", C.c_int), ("max_newton", C.c_int), ("max_lin", C.c_int),
                 ("max_pf", C.c_int), ("max_local", C.c_int), ("restart", C.c_int),
                 ("prec", C.c_int), ("cuda_stream", C.c_void_p), ("max_cutbacks", C.c_int),
-                ("derivative", C.c_int)]
+                ("derivative", C.c_int), ("kernel_variant", C.c_int)]
 
 DERIVATIVES = {"spectral": 0, "willot": 1}
 
@@ -171,6 +171,7 @@ def _options(opts, prec, stream):
     o.cuda_stream = stream or None
     o.max_cutbacks = int(opts.get("max_cutbacks", 0))
     o.derivative = DERIVATIVES[d]
+    o.kernel_variant = int(opts.get("kernel_variant", 0))
     return o
 
 

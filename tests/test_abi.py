@@ -95,3 +95,14 @@ def test_derivative_scheme_option():
                        None).derivative == 1
     with pytest.raises(ValueError):
         FF._options(I.solver_options("paper", derivative="central"), "mixed", None)
+
+
+def test_kernel_variant_option():
+    """The kernel-variant bits reach the C ABI unchanged; the default is 0
+    (bulk-copy update pass, unfused x pass)."""
+    from paper_2304_01125_gb300 import fatiguefft as FF
+    from paper_2304_01125_gb300 import inputs as I
+    assert FF._options(I.solver_options("paper"), "mixed", None).kernel_variant == 0
+    for v in range(4):
+        assert FF._options(I.solver_options("paper", kernel_variant=v), "fp64",
+                           None).kernel_variant == v

@@ -1,0 +1,40 @@
+"""Host logic of the kernel-variant autotuner: candidates per grid, the
+choice of the fastest measured variant, and the JSON cache (a stored choice
+is reused without measuring; another grid or precision is measured)."""
+import json
+
+from paper_2304_01125_gb300 import autotune as A
+
+
+def test_candidates_follow_the_fused_pass_support():
+    assert A.candidates((64, 64, 64)) == [0, 2, 1, 3]
+    assert A.candidates((48, 48, 48)) == [0, 2]      # n0 not a power of two
+    assert A.candidates((64, 1, 1)) == [0, 2]        # a line: no 2-D transforms
+    assert A.candidates((256, 256, 1)) == [0, 2, 1, 3]
+
+
+def test_best_variant_measures_once_and_caches(tmp_path):
+    path = str(tmp_path / "cache.json")
+    calls = []
+
+    def fake(n, prec, v):
+        calls.append((n, prec, v))
+        return {0: 1.0, 1: 0.7, 2: 1.2, 3: 0.9}[v]
+
+    assert A.best_variant((64, 64, 64), "mixed", "GPU", path=path, measure_fn=fake) == 1
+    assert len(calls) == 4
+    d = json.load(open(path))
+    e = d["GPU|64x64x64|mixed"]
+    assert e["kernel_variant"] == 1 and set(e["ms_per_gmres_iteration"]) == {"0", "1", "2", "3"}
+    # cached: no measurement
+    assert A.best_variant((64, 64, 64), "mixed", "GPU", path=path, measure_fn=fake) == 1
+    assert len(calls) == 4
+    # another precision and a grid without the fused pass are measured
+    assert A.best_variant((64, 64, 64), "fp64", "GPU", path=path, measure_fn=fake) == 1
+    assert A.best_variant((48, 48, 48), "mixed", "GPU", path=path, measure_fn=fake) == 0
+    assert len(calls) == 4 + 4 + 2
+    assert set(json.load(open(path))) == {"GPU|64x64x64|mixed", "GPU|64x64x64|fp64",
+                                          "GPU|48x48x48|mixed"}
+    # refresh re-measures
+    A.best_variant((64, 64, 64), "mixed", "GPU", path=path, measure_fn=fake, refresh=True)
+    assert len(calls) == 14
