@@ -309,7 +309,10 @@ const char* fft_last_error(fft_rve_t r);
  * cuda_stream (FFT_ERR_ARG otherwise); the caller keeps ownership of the
  * handles and must not use them from other threads while the batch runs.
  * n_threads host threads (<= 0: the hardware concurrency; at most n) drive
- * the handles' increments concurrently, largest grid first.
+ * the handles' increments concurrently, largest grid first.  While grouped,
+ * a handle's host waits poll its stream and yield the core between polls
+ * (instead of spinning), so that more threads than host cores can drive
+ * handles; batch_destroy restores the spinning waits.
  * batch_run_increment = run_increment on every handle: Fbar 9n doubles
  * (row-major per handle), dt n doubles, stats n entries (may be NULL),
  * status n ints (may be NULL) receive each handle's own result; returns
@@ -319,8 +322,35 @@ const char* fft_last_error(fft_rve_t r);
  * previous one to finish).
  * batch_run_increment_mixed = run_increment_mixed on every handle, with the
  * same layouts plus Pbar 9n doubles (may be NULL: zero targets) and mask 9n
- * int32 (per handle as in run_increment_mixed; NULL: FFT_ERR_ARG). */
+ * int32 (per handle as in run_increment_mixed; NULL: FFT_ERR_ARG).
+ *
+ * Lockstep classes: batch_create groups the handles of one size class (same
+ * device, precision, grid and fft_options; the unfused Arnoldi step, CUDA
+ * graphs on) into classes of up to 64 members.  Under strain control
+ * (batch_run_increment) a class's increments run together: the Newton and
+ * GMRES iterations in lockstep over the members still iterating, each Krylov
+ * column of the whole class one CUDA graph launch with one batched library
+ * transform per direction over the class's 9 x members fields; the damage
+ * updates and the cut-backs of a member whose increment did not converge run
+ * per member.  Each member's arithmetic is that of its own run_increment.
+ * The class holds the members' Arnoldi-step scratch in one arena while the
+ * batch exists (the handles stay usable on their own, from the thread that
+ * owns the batch, between batch calls).  Mixed control runs every handle on
+ * its own.  batch_create_ex with flags = 0 forms no classes (flags bit 0 =
+ * classes; other bits: FFT_ERR_ARG); batch_create = batch_create_ex with
+ * flags 1.  batch_classes returns the number of classes and, per class,
+ * its member count, the column graphs launched so far and, while timing is
+ * on, the device milliseconds of those launches (CUDA events on the class's
+ * stream) and their algorithmic bytes (the two 9-field transforms, tangent
+ * apply, contraction with the dot pass and update of every member); timing
+ * = 1 or 0 switches the timing on or off and zeroes the sums after reading
+ * them, -1 leaves both (every array may be NULL; room for batch_size
+ * entries suffices). */
 fft_status batch_create(fft_batch_t* out, fft_rve_t const* rves, int n, int n_threads);
+fft_status batch_create_ex(fft_batch_t* out, fft_rve_t const* rves, int n, int n_threads,
+                           int flags);
+int batch_classes(fft_batch_t b, int timing, int* sizes, long long* graph_launches,
+                  double* graph_ms, double* graph_bytes);
 fft_status batch_run_increment(fft_batch_t b, const double* Fbar, const double* dt,
                                fft_stats* stats, int* status);
 fft_status batch_run_increment_mixed(fft_batch_t b, const double* Fbar, const double* Pbar,

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUTDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUTDIR, "libfatiguefft.so")
-SOURCES = ["kernels_cp.cu", "kernels_spec.cu", "kernels_fft.cu", "rve.cu", "noalloc.cu",
+SOURCES = ["kernels_cp.cu", "kernels_spec.cu", "kernels_fft.cu", "rve.cu", "gang.cu", "noalloc.cu",
            "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

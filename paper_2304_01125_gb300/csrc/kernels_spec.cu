@@ -664,8 +664,9 @@ template <> struct V2<float> { typedef float2 T; };
 template <> struct V2<double> { typedef double2 T; };
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_tangent_apply(R* G, const R* K, const R* phi, R kres,
-                                                            R invN, size_t N) {
+                                                            R invN, size_t N, const int* act) {
     typedef typename V2<R>::T T2;
+    if (act && *act == 0) return;  // a lockstep class member that has left the loop
     if (N & 1) {
         GRID_STRIDE(v, N) {
             R gz[9];
@@ -711,9 +712,9 @@ __global__ void __launch_bounds__(kThreads) k_tangent_apply(R* G, const R* K, co
 }
 template <typename R>
 void tangent_apply(void* G, const void* K, const void* phi, double kres, size_t N,
-                   cudaStream_t s) {
+                   cudaStream_t s, const int* act) {
     k_tangent_apply<R><<<grid_for((N & 1) ? N : N / 2), kThreads, 0, s>>>(
-        (R*)G, (const R*)K, (const R*)phi, (R)kres, (R)(1.0 / (double)N), N);
+        (R*)G, (const R*)K, (const R*)phi, (R)kres, (R)(1.0 / (double)N), N, act);
 }
 
 // ------------------------------------------------------ Arnoldi step kernels
@@ -866,9 +867,10 @@ template <typename R, int NQ, bool IL, typename A, bool WIL>
 __global__ void __launch_bounds__(kThreads, 2) k_contract_dots(
     const typename Tr<R>::Cx* T, SGrid g, typename Tr<R>::Cx* w, const typename Tr<R>::Cx* c,
     const typename Tr<R>::Cx* V, size_t vstride, int k, Red red, double* Hd, double* Hp,
-    double* slot, double* coef, const int* err) {
+    double* slot, double* coef, const int* err, const int* act) {
     typedef typename Tr<R>::Cx Cx;
     constexpr int G = NQ < 8 ? NQ : 8;
+    if (act && *act == 0) return;
     A acc[3 + 2 * NQ];
 #pragma unroll
     for (int v = 0; v < 3 + 2 * NQ; ++v) acc[v] = 0;
@@ -916,7 +918,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_contract_dots(
 template <typename R>
 void contract_dots(const void* T, const SGrid& g, void* w, const void* c, const void* V,
                    size_t vstride, int k, const Red& red, double* Hd, double* Hp, double* slot,
-                   double* coef, const BulkCfg* bc, cudaStream_t s, int il, int dot64) {
+                   double* coef, const BulkCfg* bc, cudaStream_t s, int il, int dot64,
+                   const int* act) {
     typedef typename Tr<R>::Cx Cx;
     const Cx *TT = (const Cx*)T, *cc = (const Cx*)c, *VV = (const Cx*)V;
     Cx* ww = (Cx*)w;
@@ -925,16 +928,16 @@ void contract_dots(const void* T, const SGrid& g, void* w, const void* c, const 
     do {                                                                                      \
         if (il)                                                                               \
             k_contract_dots<R, NQ, true, R, false><<<kRedBlocks, kThreads, 0, s>>>(           \
-                TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err);                 \
+                TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err, act);            \
         else if (g.willot)                                                                    \
             k_contract_dots<R, NQ, false, R, true><<<kRedBlocks, kThreads, 0, s>>>(           \
-                TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err);                 \
+                TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err, act);            \
         else if (dot64)                                                                       \
             k_contract_dots<R, NQ, false, double, false><<<kRedBlocks, kThreads, 0, s>>>(     \
-                TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err);                 \
+                TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err, act);            \
         else                                                                                  \
             k_contract_dots<R, NQ, false, R, false><<<kRedBlocks, kThreads, 0, s>>>(          \
-                TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err);                 \
+                TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err, act);            \
     } while (0)
     if (k <= 0)
         CDOTS(0);
@@ -985,8 +988,9 @@ template <typename R, bool IL, bool WIL>
 __global__ void __launch_bounds__(kUpdT) k_dcgs_update_bulk(
     typename Tr<R>::Cx* V, size_t vstride, int k, const typename Tr<R>::Cx* z,
     const double* coef, const double* Kbar, SGrid g, typename Tr<R>::Cx* G, int tpc, Red red,
-    int* err) {
+    int* err, const int* act) {
     typedef typename Tr<R>::Cx Cx;
+    if (act && *act == 0) return;
     extern __shared__ __align__(128) unsigned char dyn[];
     Cx* buf = reinterpret_cast<Cx*>(dyn);  // [kBulkS][3][kUpdT]
     __shared__ __align__(8) uint64_t full[kBulkS];
@@ -1163,8 +1167,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_dcgs_update(typename Tr<R>::Cx*
                                                              const typename Tr<R>::Cx* z,
                                                              const double* coef,
                                                              const double* Kbar, SGrid g,
-                                                             typename Tr<R>::Cx* G, Red red) {
+                                                             typename Tr<R>::Cx* G, Red red,
+                                                             const int* act) {
     typedef typename Tr<R>::Cx Cx;
+    if (act && *act == 0) return;
     __shared__ R s_a[kMaxKrylov], s_e[kMaxKrylov];
     __shared__ R Ks[81];
     for (int q = threadIdx.x; q < 81; q += blockDim.x) Ks[q] = (R)Kbar[q];
@@ -1231,7 +1237,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dcgs_update(typename Tr<R>::Cx*
 template <typename R>
 void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* coef,
                  const double* Kbar, const SGrid& g, void* G, const Red& red, const BulkCfg* bc,
-                 cudaStream_t s, int il) {
+                 cudaStream_t s, int il, const int* act) {
     typedef typename Tr<R>::Cx Cx;
     if (bc && bulk_aligned<R>(g)) {
         int tpc, nb;
@@ -1248,24 +1254,24 @@ void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* co
         cfg.numAttrs = 1;
         if (il)
             cudaLaunchKernelEx(&cfg, k_dcgs_update_bulk<R, true, false>, (Cx*)V, vstride, k,
-                               (const Cx*)z, coef, Kbar, g, (Cx*)G, tpc, red, bc->err);
+                               (const Cx*)z, coef, Kbar, g, (Cx*)G, tpc, red, bc->err, act);
         else if (g.willot)
             cudaLaunchKernelEx(&cfg, k_dcgs_update_bulk<R, false, true>, (Cx*)V, vstride, k,
-                               (const Cx*)z, coef, Kbar, g, (Cx*)G, tpc, red, bc->err);
+                               (const Cx*)z, coef, Kbar, g, (Cx*)G, tpc, red, bc->err, act);
         else
             cudaLaunchKernelEx(&cfg, k_dcgs_update_bulk<R, false, false>, (Cx*)V, vstride, k,
-                               (const Cx*)z, coef, Kbar, g, (Cx*)G, tpc, red, bc->err);
+                               (const Cx*)z, coef, Kbar, g, (Cx*)G, tpc, red, bc->err, act);
         return;
     }
     if (il)
         k_dcgs_update<R, true, false><<<grid_for(g.Nh), kThreads, 0, s>>>(
-            (Cx*)V, vstride, k, (const Cx*)z, coef, Kbar, g, (Cx*)G, red);
+            (Cx*)V, vstride, k, (const Cx*)z, coef, Kbar, g, (Cx*)G, red, act);
     else if (g.willot)
         k_dcgs_update<R, false, true><<<grid_for(g.Nh), kThreads, 0, s>>>(
-            (Cx*)V, vstride, k, (const Cx*)z, coef, Kbar, g, (Cx*)G, red);
+            (Cx*)V, vstride, k, (const Cx*)z, coef, Kbar, g, (Cx*)G, red, act);
     else
         k_dcgs_update<R, false, false><<<grid_for(g.Nh), kThreads, 0, s>>>(
-            (Cx*)V, vstride, k, (const Cx*)z, coef, Kbar, g, (Cx*)G, red);
+            (Cx*)V, vstride, k, (const Cx*)z, coef, Kbar, g, (Cx*)G, red, act);
 }
 
 // x += M (sum_i y_i V_i)  (right-preconditioned GMRES update)
@@ -1694,15 +1700,15 @@ int selftest_bounded_wait(unsigned limit) {
     template void precond_grad<R>(const void*, double, void*, const double*, const SGrid&,      \
                                   void*, int, cudaStream_t, int);                               \
     template void tangent_apply<R>(void*, const void*, const void*, double, size_t,             \
-                                   cudaStream_t);                                               \
+                                   cudaStream_t, const int*);                                   \
     template void contract<R>(const void*, const SGrid&, void*, cudaStream_t);                  \
     template void dcgs_update<R>(void*, size_t, int, const void*, const double*,                \
                                  const double*, const SGrid&, void*, const Red&,                \
-                                 const BulkCfg*, cudaStream_t, int);                            \
+                                 const BulkCfg*, cudaStream_t, int, const int*);                \
     template int dcgs_bulk_setup<R>(BulkCfg&);                                                  \
     template void contract_dots<R>(const void*, const SGrid&, void*, const void*, const void*,  \
                                    size_t, int, const Red&, double*, double*, double*, double*, \
-                                   const BulkCfg*, cudaStream_t, int, int);                     \
+                                   const BulkCfg*, cudaStream_t, int, int, const int*);         \
     template void norm2<R>(const void*, const SGrid&, const Red&, cudaStream_t);                \
     template void xupdate<R>(void*, const void*, size_t, int, const double*, const double*,     \
                              const SGrid&, cudaStream_t);                                       \

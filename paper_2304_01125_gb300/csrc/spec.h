@@ -38,7 +38,9 @@ template <typename R> void degrade(const void* P, const void* phi, double kres, 
 template <typename R> void residual(const void* Ph, const SGrid& g, void* b, const Red& red, cudaStream_t s);
 // il = 1 writes G in the interleaved layout of the fused x pass
 template <typename R> void precond_grad(const void* vin, double scale, void* vout, const double* Kbar, const SGrid& g, void* G, int use_pre, cudaStream_t s, int il = 0);
-template <typename R> void tangent_apply(void* G, const void* K, const void* phi, double kres, size_t N, cudaStream_t s);
+// act (nullable): a device flag; 0 makes the Arnoldi step kernels below return
+// at once (a lockstep class member that has left the iteration)
+template <typename R> void tangent_apply(void* G, const void* K, const void* phi, double kres, size_t N, cudaStream_t s, const int* act = nullptr);
 template <typename R> void contract(const void* T, const SGrid& g, void* w, cudaStream_t s);
 // Arnoldi step kernels (DCGS2, see kernels_spec.cu).  Hessenberg columns on
 // the device are kHcol doubles apart; the host slot holds the final column
@@ -67,8 +69,8 @@ int selftest_bounded_wait(unsigned limit);
 // fused x pass
 // dot64 = 1: per-thread products and partial sums in FP64 (default: the
 // bulk type, FP64 from the block combine on)
-template <typename R> void contract_dots(const void* T, const SGrid& g, void* w, const void* c, const void* V, size_t vstride, int k, const Red& red, double* Hd, double* Hp, double* slot, double* coef, const BulkCfg* bc, cudaStream_t s, int il = 0, int dot64 = 0);
-template <typename R> void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* coef, const double* Kbar, const SGrid& g, void* G, const Red& red, const BulkCfg* bc, cudaStream_t s, int il = 0);
+template <typename R> void contract_dots(const void* T, const SGrid& g, void* w, const void* c, const void* V, size_t vstride, int k, const Red& red, double* Hd, double* Hp, double* slot, double* coef, const BulkCfg* bc, cudaStream_t s, int il = 0, int dot64 = 0, const int* act = nullptr);
+template <typename R> void dcgs_update(void* V, size_t vstride, int k, const void* z, const double* coef, const double* Kbar, const SGrid& g, void* G, const Red& red, const BulkCfg* bc, cudaStream_t s, int il = 0, const int* act = nullptr);
 template <typename R> void norm2(const void* v, const SGrid& g, const Red& red, cudaStream_t s);
 
 // Fused x pass of the Arnoldi step (kernels_fft.cu): inverse real

@@ -30,7 +30,8 @@ SYMBOLS = ["init_rve", "apply_increment", "solve_equilibrium", "update_damage",
            "rve_kernel_launches", "rve_profile", "rve_profile_read",
            "degraded_average_noalloc", "batch_create", "batch_run_increment", "batch_size",
            "batch_destroy", "fft_selftest_bounded_wait", "apply_increment_mixed",
-           "run_increment_mixed", "state_save", "state_load", "batch_run_increment_mixed"]
+           "run_increment_mixed", "state_save", "state_load", "batch_run_increment_mixed",
+           "batch_create_ex", "batch_classes"]
 KERNEL_FAMILIES = ["constitutive", "tangent_apply", "precond_grad", "contract", "gmres_dot",
                    "gs_update", "gmres_xupdate", "kbar", "residual", "f_update", "phase_field",
                    "gnd", "cufft_9field", "cufft_scalar", "reductions", "other"]
@@ -121,6 +122,11 @@ def load(path=LIB_PATH):
     L.batch_run_increment_mixed.argtypes = [vp, dp, dp, C.POINTER(C.c_int32), dp,
                                             C.POINTER(Stats), C.POINTER(C.c_int)]
     L.batch_run_increment_mixed.restype = C.c_int
+    L.batch_create_ex.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int, C.c_int, C.c_int]
+    L.batch_create_ex.restype = C.c_int
+    L.batch_classes.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
+                                dp, dp]
+    L.batch_classes.restype = C.c_int
     L.batch_size.argtypes = [vp]
     L.batch_size.restype = C.c_int
     L.batch_destroy.argtypes = [vp]
@@ -342,16 +348,33 @@ class Batch:
     """Many independent RVE handles advanced together (batch_run_increment):
     each handle needs its own stream; a native thread pool of ``threads``
     host threads (None: the hardware concurrency) drives them concurrently.
-    The handles stay owned by the caller."""
+    With ``classes`` (default), handles of one size class (grid, precision,
+    options) run in lockstep under strain control, each Krylov column of a
+    class one graph launch (batch_create_ex).  The handles stay owned by the
+    caller."""
 
-    def __init__(self, rves, threads=None):
+    def __init__(self, rves, threads=None, classes=True):
         self.rves = list(rves)
         arr = (C.c_void_p * len(self.rves))(*[r._h for r in self.rves])
         h = C.c_void_p()
-        s = load().batch_create(C.byref(h), arr, len(self.rves), int(threads or 0))
+        s = load().batch_create_ex(C.byref(h), arr, len(self.rves), int(threads or 0),
+                                   1 if classes else 0)
         if s != FFT_OK:
             raise FFTError("batch_create", s, "distinct handles, each with its own stream")
         self._h = h
+
+    def classes(self, timing=None):
+        """[(members, column graphs launched, graph ms, algorithmic bytes)]
+        per lockstep class; timing True/False switches the event timing of
+        the column graphs on/off (the sums are read, then zeroed)."""
+        n = len(self.rves)
+        sz = (C.c_int * n)()
+        gl = (C.c_longlong * n)()
+        ms = (C.c_double * n)()
+        by = (C.c_double * n)()
+        t = -1 if timing is None else int(bool(timing))
+        k = load().batch_classes(self._h, t, sz, gl, ms, by)
+        return [(int(sz[i]), int(gl[i]), float(ms[i]), float(by[i])) for i in range(k)]
 
     def run_increment(self, Fbars, dts, check=True, Pbars=None, stress_masks=None):
         """Fbars: (n, 9) absolute macroscopic F per handle; dts: (n,).  With

@@ -238,3 +238,135 @@ def test_bounded_wait_gives_up_on_a_barrier_nothing_completes():
     s, _ = r.run_increment(*I.uniaxial_cycle_program(0.004, 8, 1)[0])
     assert s == FF.FFT_OK
     r.close()
+
+
+# ------------------------------------------------------------ lockstep classes
+def _same_as_alone(batch_rves, make, prog, fields=("F", "P", "Fp", "gamma")):
+    """Each batch handle against a fresh handle run alone through prog:
+    the same status, iteration counts and field bits."""
+    out = []
+    for i, br in enumerate(batch_rves):
+        r = make(i)
+        sts = []
+        for Fb, dt in prog:
+            s, st = r.run_increment(Fb, dt, check=False)
+            sts.append((s, st["newton_it"], st["lin_it_total"], st["stag_it"],
+                        st["pf_it_total"], st["cutbacks"]))
+        out.append(sts)
+        for f in fields:
+            assert np.array_equal(r.field(f), br.field(f)), (i, f)
+        r.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_lockstep_class_matches_single_runs(prec):
+    """Four handles of one grid form a lockstep class (one graph launch per
+    Krylov column for all four, one batched transform per direction), a
+    fifth of another grid runs on its own: every handle's iteration counts
+    and fields are those of the handle run alone, bit for bit."""
+    prog = I.uniaxial_cycle_program(0.006, 24, 1)[:4]
+    grids = [(12, 10, 8)] * 4 + [(8, 8, 8)]
+    make = lambda i: _make(grids[i], 70 + i, prec)  # noqa: E731
+    rves = [make(i) for i in range(len(grids))]
+    b = FF.Batch(rves, threads=2)
+    got = [[] for _ in rves]
+    for Fb, dt in prog:
+        s, per, stats = b.run_increment([Fb] * len(rves), [dt] * len(rves))
+        assert s == FF.FFT_OK
+        for i, st in enumerate(stats):
+            got[i].append((per[i], st["newton_it"], st["lin_it_total"], st["stag_it"],
+                           st["pf_it_total"], st["cutbacks"]))
+    cls = b.classes()
+    assert len(cls) == 1 and cls[0][0] == 4 and cls[0][1] > 0, cls
+    b.close()
+    assert sum(x[2] for x in got[0]) > 0
+    assert _same_as_alone(rves, make, prog) == got
+    for r in rves:
+        r.close()
+
+
+def test_lockstep_class_without_classes_flag():
+    """classes=False forms no class: the same handles run one by one."""
+    grids = [(8, 8, 8)] * 3
+    rves = [_make(n, 80 + i, "mixed") for i, n in enumerate(grids)]
+    b = FF.Batch(rves, classes=False)
+    assert b.classes() == []
+    Fb, dt = I.uniaxial_cycle_program(0.004, 8, 1)[0]
+    s, per, _ = b.run_increment([Fb] * 3, [dt] * 3)
+    assert s == FF.FFT_OK
+    b.close()
+    for r in rves:
+        r.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_lockstep_class_through_crack_growth(prec):
+    """Three 12^3 polycrystals (the damaged-regime workload of the damage
+    parity test, three seeds) as one lockstep class through damage
+    nucleation and unstable growth (30 increments, up to tens of staggered
+    iterations per increment, members leaving the staggered loop at
+    different iterations): statuses, iteration counts (Newton, GMRES,
+    staggered, phase-field) and the damage and stress fields equal those of
+    each handle run alone."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "make_damage12", os.path.join(os.path.dirname(__file__), "golden", "make_damage12.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    import torch
+    _, _, mat, prog, opts = mod.setup()
+
+    def make(i):
+        gid, eul = I.voronoi(mod.N_GRID, 4, 31 + i)
+        return FF.RVE(mod.N_GRID, H, gid, eul, mat, opts, prec=prec, stream=torch.cuda.Stream())
+
+    rves = [make(i) for i in range(3)]
+    b = FF.Batch(rves, threads=1)
+    got = [[] for _ in rves]
+    for Fb, dt in prog:
+        s, per, stats = b.run_increment([Fb] * 3, [dt] * 3, check=False)
+        for i, st in enumerate(stats):
+            got[i].append((per[i], st["newton_it"], st["lin_it_total"], st["stag_it"],
+                           st["pf_it_total"], st["cutbacks"]))
+    assert b.classes()[0][0] == 3
+    b.close()
+    assert max(x[4] for x in got[0]) > 0  # the phase field was solved
+    assert _same_as_alone(rves, make, prog, fields=("phi", "P", "F")) == got
+    for r in rves:
+        r.close()
+
+
+def test_lockstep_class_cuts_back_a_member():
+    """Two 96^3 batched-workload RVEs as a class through the first 0.6 %
+    peak, where one needs a cut-back (max_lin 300): that member is cut back
+    on its own after the lockstep attempt, and both end as when run alone."""
+    import torch
+    c = I.CONFIGS["batch32"]
+    cfgs = I.batch_configs(seed=c["seed"], count=c["count"], sizes=c["sizes"],
+                           grains=c["grains"])
+    prog = I.uniaxial_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"])[:8]
+    pick = [26] + [i for i, x in enumerate(cfgs) if x["n"] == cfgs[26]["n"] and i != 26][:1]
+    opts = I.solver_options("paper", max_lin=300, max_cutbacks=4)
+    mat = I.material("baseline")
+
+    def make(i):
+        x = cfgs[pick[i]]
+        return FF.RVE(x["n"], H, x["grain_ids"], x["euler"], mat, opts, prec="mixed",
+                      stream=torch.cuda.Stream())
+
+    rves = [make(i) for i in range(2)]
+    b = FF.Batch(rves)
+    got = [[] for _ in rves]
+    for Fb, dt in prog:
+        s, per, stats = b.run_increment([Fb] * 2, [dt] * 2)
+        for i, st in enumerate(stats):
+            got[i].append((per[i], st["newton_it"], st["lin_it_total"], st["stag_it"],
+                           st["pf_it_total"], st["cutbacks"]))
+    assert b.classes()[0][0] == 2
+    b.close()
+    assert sum(x[5] for x in got[0]) >= 1  # the cut-back happened
+    assert _same_as_alone(rves, make, prog) == got
+    for r in rves:
+        r.close()

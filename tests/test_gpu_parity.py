@@ -7,6 +7,7 @@ Tolerances (relative L2 over each field unless noted):
   * mixed path (FP32 bulk, FP64 reductions): 1e-4 per field, the stress and
     damage bound the method is held to.
 """
+import json
 import os
 
 import numpy as np
@@ -849,3 +850,46 @@ def test_checkpoint_resume_is_bitwise(prec):
         e.state_load(ck)
     for r in (a, b, c, d, e):
         r.close()
+
+
+def test_kernel_variant_option_and_autotuner(monkeypatch, tmp_path):
+    """The kernel_variant solver option selects the Arnoldi step's kernels
+    (bit 0: the fused x pass, seen in the tangent family's bytes per
+    launch); all four variants give the same fields to the Krylov
+    tolerance.  The autotuner times the candidates on the grid, returns one
+    of them and caches the choice."""
+    from paper_2304_01125_gb300 import autotune as A
+    monkeypatch.delenv("FATIGUEFFT_FUSED", raising=False)
+    monkeypatch.delenv("FATIGUEFFT_BULK", raising=False)
+    n = (16, 16, 16)
+    gid, eul = I.voronoi(n, 3, 29)
+    mat = dict(MAT, tau_c0=250.0)
+    prog = I.uniaxial_cycle_program(0.006, 24, 1)[:4]
+    N = int(np.prod(n))
+    Nh = (n[0] // 2 + 1) * n[1] * n[2]
+    per_launch = {1: Nh * 2 * 4 * 18 + N * 4 * 82, 0: N * 4 * 100}
+    fields = {}
+    for v in range(4):
+        r = FF.RVE(n, H, gid, eul, mat, opts_for("mixed", kernel_variant=v), prec="mixed",
+                   stream=stream())
+        r.profile(["tangent_apply"])
+        for Fb, dt in prog:
+            r.run_increment(Fb, dt)
+        ms, cnt, by = r.profile_read()["tangent_apply"]
+        assert cnt > 0 and abs(by / cnt - per_launch[v & 1]) < 1e-6 * per_launch[v & 1], v
+        fields[v] = {f: r.field(f) for f in ("P", "Fp")}
+        r.close()
+    eye = np.eye(3).reshape(9, 1)
+    for v in (1, 2, 3):
+        for f in fields[0]:
+            a, b = fields[v][f], fields[0][f]
+            if f == "Fp":
+                a, b = a - eye, b - eye
+            assert rel(a, b, floor=FLOOR[f] * np.sqrt(b.size)) < 1e-4, (v, f)
+    path = str(tmp_path / "tune.json")
+    best = A.best_variant(n, "mixed", path=path)
+    assert best in A.candidates(n)
+    with open(path) as fh:
+        entry = next(iter(json.load(fh).values()))
+    assert entry["kernel_variant"] == best
+    assert all(t > 0 for t in entry["ms_per_gmres_iteration"].values())
