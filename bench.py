@@ -52,10 +52,14 @@ def args_():
     p.add_argument("--tol", default="paper", choices=["paper", "parity32", "parity64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-damage-window", action="store_true")
+    p.add_argument("--no-batch-window", action="store_true",
+                   help="default config: skip the short batched-workload figure")
     p.add_argument("--batch-threads", type=int, default=None,
                    help="--config batch32: host threads driving the handles")
     p.add_argument("--no-classes", action="store_true",
                    help="--config batch32: no lockstep classes (every handle on its own)")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="--config batch32: default kernel variants (no per-size autotuning)")
     p.add_argument("--verbose", action="store_true")
     p.add_argument("--ref-budget-s", type=float, default=150.0,
                    help="--impl reference: stop timing the oracle after this many seconds")
@@ -488,7 +492,10 @@ def run_ours(a):
         "iterations": {p: {"newton": sum(s["newton_it"] for s in results[p]["stats"]),
                            "gmres": sum(s["lin_it_total"] for s in results[p]["stats"]),
                            "staggered": sum(s["stag_it"] for s in results[p]["stats"]),
-                           "phase_field": sum(s["pf_it_total"] for s in results[p]["stats"])}
+                           "phase_field": sum(s["pf_it_total"] for s in results[p]["stats"]),
+                           "voxel_gmres_per_s": round(
+                               N * sum(s["lin_it_total"] for s in results[p]["stats"]) /
+                               (results[p]["total_ms"] / 1e3), 1)}
                        for p in results},
         "kernel_ms_probe": {
             p: {k: round(v[0], 3) for k, v in results[p]["breakdown"].items() if v[1]}
@@ -505,12 +512,24 @@ def run_ours(a):
     line["probe_increments"] = [p0 + 1, p1]
     if a.config == CONFIG_NAME and not a.no_damage_window:
         line["damage_window"] = damage_window(FF, a, stream, flush)
+    if a.config == CONFIG_NAME and ws == 1 and not a.no_batch_window:
+        # the batched workload (32 RVEs of 32^3-96^3 in lockstep size
+        # classes), three increments after three warm-up ones
+        import copy
+        b = copy.copy(a)
+        b.steps, b.warmup = 3, 3
+        bl = run_batch(b, short=True)
+        line["batch_window"] = {k: bl[k] for k in ("value", "unit", "ms_per_step", "steps",
+                                                   "warmup", "roofline", "iterations",
+                                                   "kernel_variants")}
+        line["batch_window"]["workload"] = bl["config"]["workload"]
+        line["batch_window"]["parallelism"] = bl["config"]["parallelism"]
     if ws == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, mat, opts, a)
     return line
 
 
-def run_batch(a):
+def run_batch(a, short=False):
     """The batched workload: 32 polycrystals with grids from {32,48,64,96}^3
     and 20-150 grains, advanced together (batch_run_increment, one stream
     per RVE), mixed precision.  A step is one load increment of every RVE."""
@@ -532,12 +551,20 @@ def run_batch(a):
     # a few of these RVEs stall at the load peaks with the full-step tangent:
     # increments are cut back (halved) on non-convergence, detected early
     opts = I.solver_options(a.tol, max_lin=300, max_cutbacks=4)
+    # the Arnoldi step's kernel variant per grid size, timed on this GPU
+    # (autotune.py; the unfused variants, which a lockstep class runs)
+    variants = {}
+    if not a.no_autotune:
+        from paper_2304_01125_gb300 import autotune as AT
+        for n in sorted({tuple(x["n"]) for x in cfgs}):
+            variants[n] = AT.best_variant(n, "mixed", fused=a.no_classes)
     nvox = [int(np.prod(x["n"])) for x in cfgs]
     Ntot = sum(nvox)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
     def make():
-        rv = [FF.RVE(x["n"], I.VOXEL_MM, x["grain_ids"], x["euler"], mat, opts, prec="mixed",
+        rv = [FF.RVE(x["n"], I.VOXEL_MM, x["grain_ids"], x["euler"], mat,
+                     dict(opts, kernel_variant=variants.get(tuple(x["n"]), 0)), prec="mixed",
                      stream=torch.cuda.Stream(device=dev)) for x in cfgs]
         return rv, FF.Batch(rv, threads=a.batch_threads, classes=not a.no_classes)
 
@@ -554,7 +581,7 @@ def run_batch(a):
     clk = Clocks(local)
     clk.start()
     l0 = sum(r.kernel_launches for r in rves)
-    ms, its, cuts = [], 0, 0
+    ms, its, vits, cuts = [], 0, 0, 0
     for k in range(a.warmup, a.warmup + a.steps):
         flush.fill_(float(k))
         e0 = torch.cuda.Event(enable_timing=True)
@@ -565,6 +592,7 @@ def run_batch(a):
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
         its += sum(x["lin_it_total"] for x in st)
+        vits += sum(nv * x["lin_it_total"] for nv, x in zip(nvox, st))
         cuts += sum(x["cutbacks"] for x in st)
     clocks = clk.stop()
     launches = sum(r.kernel_launches for r in rves) - l0
@@ -608,8 +636,24 @@ def run_batch(a):
                 "timing": "CUDA events on each RVE's stream while the other RVEs' kernels run "
                           "concurrently: a launch's interval includes time shared with them, so "
                           "this is a lower bound on the kernel's own bandwidth"}
-    # end to end: fresh handles, inputs from pinned host memory, every RVE's
-    # damage field read back each step
+    if short:
+        e2e_s = serial_s = None
+    else:
+        e2e_s, serial_s = batch_e2e_and_serial(a, make, step, nvox, prog)
+    sizes = {}
+    for x in cfgs:
+        sizes[x["n"][0]] = sizes.get(x["n"][0], 0) + 1
+    return batch_line(a, ws, rank, cfgs, sizes, Ntot, ms, value, e2e_s, serial_s, launches, roof,
+                      clocks, its, cuts, cls, variants, vits)
+
+
+def batch_e2e_and_serial(a, make, step, nvox, prog):
+    """End to end (fresh handles, inputs from pinned host memory, every RVE's
+    damage field read back each step) and the handles run one after
+    another: wall seconds of the same increments."""
+    import torch
+
+    from paper_2304_01125_gb300 import fatiguefft as FF
     rves, b = make()
     for k in range(a.warmup):
         step(b, k)
@@ -640,9 +684,11 @@ def run_batch(a):
     b.close()
     for r in rves:
         r.close()
-    sizes = {}
-    for x in cfgs:
-        sizes[x["n"][0]] = sizes.get(x["n"][0], 0) + 1
+    return e2e_s, serial_s
+
+
+def batch_line(a, ws, rank, cfgs, sizes, Ntot, ms, value, e2e_s, serial_s, launches, roof, clocks,
+               its, cuts, cls, variants, vits):
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "voxel-increments/s",
         "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
@@ -662,13 +708,21 @@ def run_batch(a):
                                    + ", ".join(f"{c[0]} members" for c in cls)
                                    + " (one graph launch per Krylov column per class, batched "
                                      "9-field transforms); one stream per RVE otherwise")},
-        "e2e": {"value": round(Ntot * a.steps / e2e_s, 1), "unit": "voxel-increments/s",
-                "h2d_bytes_per_step": 80 * len(cfgs), "d2h_bytes_per_step": 8 * Ntot},
+        "e2e": None if e2e_s is None else {
+            "value": round(Ntot * a.steps / e2e_s, 1), "unit": "voxel-increments/s",
+            "h2d_bytes_per_step": 80 * len(cfgs), "d2h_bytes_per_step": 8 * Ntot},
         "gpu_launches": int(launches), "roofline": roof, "clocks": clocks,
-        "iterations": {"gmres": its, "cutbacks": cuts},
-        "serial": {"value": round(Ntot * a.steps / serial_s, 1), "unit": "voxel-increments/s",
-                   "note": "the same increments, one handle after another (wall clock)"},
+        "iterations": {"gmres": its, "cutbacks": cuts,
+                       "voxel_gmres_per_s": round(vits / (sum(ms) / 1e3), 1),
+                       "note": "voxel_gmres_per_s: sum over RVEs of voxels x GMRES iterations "
+                               "per second of the timed steps (Krylov throughput independent "
+                               "of how many iterations the increments need)"},
+        "serial": None if serial_s is None else {
+            "value": round(Ntot * a.steps / serial_s, 1), "unit": "voxel-increments/s",
+            "note": "the same increments, one handle after another (wall clock)"},
         "host_threads": a.batch_threads or "hardware concurrency",
+        "kernel_variants": ({f"{n[0]}^3": v for n, v in sorted(variants.items())}
+                            or "default (bulk-copy update pass, unfused)"),
     }
     return line if rank == 0 else None
 

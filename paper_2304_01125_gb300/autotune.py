@@ -29,11 +29,12 @@ def cache_path():
                                                      "fatiguefft", "autotune.json")
 
 
-def candidates(n):
+def candidates(n, fused=True):
     """Variant values worth timing on grid n: the fused x pass only where the
-    library can use it (n0 a power of two in [8, 512], not a line)."""
+    library can use it (n0 a power of two in [8, 512], not a line) and when
+    allowed (a lockstep batch class runs the unfused step)."""
     n0 = int(n[0])
-    fused_ok = 8 <= n0 <= 512 and (n0 & (n0 - 1)) == 0 and (n[1] > 1 or n[2] > 1)
+    fused_ok = fused and 8 <= n0 <= 512 and (n0 & (n0 - 1)) == 0 and (n[1] > 1 or n[2] > 1)
     return [0, 2] + ([1, 3] if fused_ok else [])
 
 
@@ -83,21 +84,22 @@ def _store(path, data):
 
 
 def best_variant(n, prec, device_name=None, stream=None, path=None, refresh=False,
-                 measure_fn=None):
-    """The fastest kernel variant for grid n and precision prec on this GPU:
-    from the cache, else measured (measure_fn(n, prec, variant) -> ms per
-    GMRES iteration; the GPU measurement by default) and stored."""
+                 measure_fn=None, fused=True):
+    """The fastest kernel variant for grid n and precision prec on this GPU
+    (fused=False: among the unfused ones): from the cache, else measured
+    (measure_fn(n, prec, variant) -> ms per GMRES iteration; the GPU
+    measurement by default) and stored."""
     n = tuple(int(x) for x in n)
     if device_name is None:
         import torch
         device_name = torch.cuda.get_device_name()
     path = path or cache_path()
-    key = f"{device_name}|{n[0]}x{n[1]}x{n[2]}|{prec}"
+    key = f"{device_name}|{n[0]}x{n[1]}x{n[2]}|{prec}" + ("" if fused else "|unfused")
     data = _load(path)
     if key in data and not refresh:
         return int(data[key]["kernel_variant"])
     fn = measure_fn or (lambda nn, pp, v: measure(nn, pp, v, stream=stream))
-    times = {v: float(fn(n, prec, v)) for v in candidates(n)}
+    times = {v: float(fn(n, prec, v)) for v in candidates(n, fused)}
     best = min(times, key=lambda v: (times[v], v))
     data = _load(path)  # another process may have written meanwhile
     data[key] = {"kernel_variant": best,

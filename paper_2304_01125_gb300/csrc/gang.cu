@@ -659,14 +659,23 @@ static void gang_release(GangBase* g) {
 // ------------------------------------------------------------ class entry points
 // (internal to the library; the batch driver forms the classes)
 
+// the solver options that the lockstep loops share (all but the stream)
+static bool same_options(const fft_options& a, const fft_options& b) {
+    return a.tol_stag == b.tol_stag && a.tol_newton == b.tol_newton && a.tol_lin == b.tol_lin &&
+           a.tol_pf == b.tol_pf && a.tol_local == b.tol_local && a.max_stag == b.max_stag &&
+           a.max_newton == b.max_newton && a.max_lin == b.max_lin && a.max_pf == b.max_pf &&
+           a.max_local == b.max_local && a.restart == b.restart && a.prec == b.prec &&
+           a.max_cutbacks == b.max_cutbacks && a.derivative == b.derivative &&
+           a.kernel_variant == b.kernel_variant;
+}
+
 // 1 when b can run in lockstep with a: same device, precision, grid, solver
-// options; the unfused Arnoldi step with graphs; not yet a class member.
+// options (but the stream); the unfused Arnoldi step with graphs.
 int fatfft_gang_compatible(fft_rve_t a, fft_rve_t b) {
     if (!a || !b) return 0;
     return a->dev == b->dev && a->prec == b->prec && a->g.n0 == b->g.n0 &&
-           a->g.n1 == b->g.n1 && a->g.n2 == b->g.n2 &&
-           std::memcmp(&a->opt, &b->opt, sizeof(fft_options)) == 0 && !a->use_fused &&
-           !b->use_fused && a->graphs && b->graphs && a->st && b->st;
+           a->g.n1 == b->g.n1 && a->g.n2 == b->g.n2 && same_options(a->opt, b->opt) &&
+           !a->use_fused && !b->use_fused && a->graphs && b->graphs && a->st && b->st;
 }
 
 fft_status fatfft_gang_create(fft_rve_t const* members, int n, void** out) {

@@ -38,3 +38,18 @@ def test_best_variant_measures_once_and_caches(tmp_path):
     # refresh re-measures
     A.best_variant((64, 64, 64), "mixed", "GPU", path=path, measure_fn=fake, refresh=True)
     assert len(calls) == 14
+
+
+def test_unfused_choice_is_cached_apart(tmp_path):
+    path = str(tmp_path / "c.json")
+    seen = []
+
+    def fake(n, prec, v):
+        seen.append(v)
+        return {0: 1.0, 1: 0.5, 2: 0.9, 3: 0.6}[v]
+
+    assert A.best_variant((64, 64, 64), "mixed", "GPU", path=path, measure_fn=fake) == 1
+    assert A.best_variant((64, 64, 64), "mixed", "GPU", path=path, measure_fn=fake,
+                          fused=False) == 2
+    assert sorted(seen) == [0, 0, 1, 2, 2, 3]
+    assert A.candidates((64, 64, 64), fused=False) == [0, 2]
