@@ -58,6 +58,9 @@ def args_():
                    help="--config batch32: host threads driving the handles")
     p.add_argument("--no-classes", action="store_true",
                    help="--config batch32: no lockstep classes (every handle on its own)")
+    p.add_argument("--classes-all", action="store_true",
+                   help="--config batch32: lockstep classes at every grid size (default: up "
+                        "to 64^3)")
     p.add_argument("--no-autotune", action="store_true",
                    help="--config batch32: default kernel variants (no per-size autotuning)")
     p.add_argument("--verbose", action="store_true")
@@ -566,7 +569,8 @@ def run_batch(a, short=False):
         rv = [FF.RVE(x["n"], I.VOXEL_MM, x["grain_ids"], x["euler"], mat,
                      dict(opts, kernel_variant=variants.get(tuple(x["n"]), 0)), prec="mixed",
                      stream=torch.cuda.Stream(device=dev)) for x in cfgs]
-        return rv, FF.Batch(rv, threads=a.batch_threads, classes=not a.no_classes)
+        return rv, FF.Batch(rv, threads=a.batch_threads,
+                            classes=False if a.no_classes else ("all" if a.classes_all else True))
 
     def step(b, k):
         return b.run_increment([prog[k][0]] * len(cfgs), [prog[k][1]] * len(cfgs))

@@ -37,6 +37,13 @@ void fatfft_gang_destroy(void* g);
 
 namespace {
 constexpr int kClassMax = 64;  // members of one lockstep class
+// Classes form by default only for grids of at most 64^3 voxels: there a
+// GMRES step is mostly launch and synchronisation latency (about 0.09 ms
+// per step from 16^3 to 32^3, 0.18 ms at 64^3 on GB300), which one graph
+// launch for the class amortises; on larger grids a step is bandwidth-bound
+// and lockstep only adds the wait for the slowest member (flags bit 1 forms
+// classes at any size).
+constexpr size_t kClassMaxVoxels = 64 * 64 * 64;
 // a unit of work for one pool thread: a lockstep class or a single handle
 struct Unit {
     std::vector<int> idx;  // batch indices
@@ -126,7 +133,7 @@ extern "C" {
 
 fft_status batch_create_ex(fft_batch_t* out, fft_rve_t const* rves, int n, int n_threads,
                            int flags) {
-    if (!out || !rves || n < 1 || (flags & ~1)) return FFT_ERR_ARG;
+    if (!out || !rves || n < 1 || (flags & ~3)) return FFT_ERR_ARG;
     *out = nullptr;
     std::set<fft_rve_t> seen;
     std::set<void*> streams;
@@ -155,7 +162,8 @@ fft_status batch_create_ex(fft_batch_t* out, fft_rve_t const* rves, int n, int n
         Unit u;
         u.idx.push_back(a);
         taken[a] = 1;
-        if (flags & 1)
+        const bool sized = (flags & 2) || fatfft_rve_voxels(rves[a]) <= kClassMaxVoxels;
+        if ((flags & 3) && sized)
             for (int c : b->order)
                 if (!taken[c] && (int)u.idx.size() < kClassMax &&
                     fatfft_gang_compatible(rves[a], rves[c])) {

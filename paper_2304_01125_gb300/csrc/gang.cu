@@ -271,14 +271,22 @@ struct Gang {
                 if (alive(i)) cur.push_back(i);
             C.swap(cur);
             if (C.empty()) break;
+            // Sparse mode: once fewer than half the members iterate, the
+            // batched transforms would mostly transform idle members, so the
+            // rest of the cycle runs each member's own step graph (the
+            // single-handle driver's, on its stream and its arena slot).
+            bool sparse = 2 * (int)C.size() < B;
+            std::vector<char> col_sparse(mres + 1, 0);
             // first column of the cycle: V_0 = src / beta and its gradient
             // spectrum, per member, before the class stream's column graphs
+            // (in sparse mode enqueue_step forms it)
             for (int i : C) {
                 fft_rve_s* r = g->m[i];
                 std::fill(Hm[i].begin(), Hm[i].end(), 0.0);
                 kcols[i] = 0;
                 res1[i] = res2[i] = -1.0;
                 in_cycle[i] = 1;
+                if (sparse) continue;
                 precond_grad<R>(src[i], 1.0 / beta[i], r->V, r->Kbar, r->g, r->cb9, 1, r->st, 0);
                 r->launches += 1;
                 if (cudaEventRecord(g->ev_m[i], r->st) != cudaSuccess ||
@@ -301,6 +309,26 @@ struct Gang {
                 return false;
             };
             if (gs != FFT_OK) r0->err = "class stream memset failed";
+            // column j for the members still in the cycle
+            auto launch = [&](int j) -> fft_status {
+                int na = 0;
+                for (int i : C) na += in_cycle[i] ? 1 : 0;
+                if (!sparse && j >= 1 && 2 * na < B) {
+                    // switch: the members' streams follow the class stream
+                    sparse = true;
+                    CK(r0, cudaEventRecord(g->ev_a, g->st));
+                    for (int i : C)
+                        if (in_cycle[i]) CK(g->m[i], cudaStreamWaitEvent(g->m[i]->st, g->ev_a, 0));
+                }
+                col_sparse[j] = sparse;
+                if (!sparse) return launch_col(g, j);
+                for (int i : C)
+                    if (in_cycle[i]) {
+                        const fft_status s1 = I::enqueue_step(g->m[i], j, src[i], 1.0 / beta[i]);
+                        if (s1 != FFT_OK) fail(i, s1);
+                    }
+                return FFT_OK;
+            };
             for (int j = 0; gs == FFT_OK; ++j) {
                 const bool enq = j < mres && lin + j < max_lin;
                 // defer the look-ahead step when every member still in the
@@ -311,7 +339,7 @@ struct Gang {
                                          res1[i] * (res1[i] / res2[i]) <= target[i]))
                         defer = false;
                 if (enq && !defer) {
-                    gs = launch_col(g, j);
+                    gs = launch(j);
                     if (gs != FFT_OK) break;
                 }
                 if (j == 0) {
@@ -320,15 +348,22 @@ struct Gang {
                 }
                 const int k = j - 1;
                 for (int i : C) was_in[i] = in_cycle[i];
-                const cudaError_t we = gang_wait(g, g->slot_ev[k % 2]);
-                if (we != cudaSuccess) {
-                    r0->err = std::string("class stream: ") + cudaGetErrorString(we);
-                    gs = FFT_ERR_CUDA;
-                    break;
+                if (!col_sparse[k]) {
+                    const cudaError_t we = gang_wait(g, g->slot_ev[k % 2]);
+                    if (we != cudaSuccess) {
+                        r0->err = std::string("class stream: ") + cudaGetErrorString(we);
+                        gs = FFT_ERR_CUDA;
+                        break;
+                    }
                 }
                 for (int i : C) {
                     if (!in_cycle[i]) continue;
                     fft_rve_s* r = g->m[i];
+                    if (col_sparse[k] && host_wait(r, r->slot_ev[k % 2]) != cudaSuccess) {
+                        r->err = "stream synchronisation in the Arnoldi step failed";
+                        fail(i, FFT_ERR_CUDA);
+                        continue;
+                    }
                     const double* slot = r->hslot + (size_t)(k % 2) * kSlot;
                     if (slot[kSlotErr] != 0.0) {
                         r->err = "a bulk-copy wait in the Arnoldi step timed out";
@@ -383,13 +418,19 @@ struct Gang {
                 ++lin;
                 if (!any_in_cycle() || !enq) break;
                 if (defer) {
-                    gs = launch_col(g, j);
+                    gs = launch(j);
                     if (gs != FFT_OK) break;
                 }
             }
-            // the class stream idle (a discarded look-ahead step), then the
-            // solution update of every member of the cycle
+            // the class stream and the members' streams idle (a discarded
+            // look-ahead step), then the solution update of every member
             if (gs == FFT_OK) gs = wait_stream(g);
+            if (sparse)
+                for (int i : C)
+                    if (st[i] == FFT_OK && host_wait(g->m[i]) != cudaSuccess) {
+                        g->m[i]->err = "stream synchronisation after the Arnoldi steps failed";
+                        st[i] = FFT_ERR_CUDA;
+                    }
             if (gs != FFT_OK) {
                 for (int i : C)
                     if (st[i] == FFT_OK) {
@@ -613,15 +654,23 @@ struct Gang {
             g->m[i]->err = b;
             st[i] = FFT_ERR_NOT_CONVERGED;
         }
+        // cut-backs: each failed member on its own host thread (the members'
+        // streams and state are independent; the cut-backs diverge)
+        std::vector<std::thread> cut;
         for (int i = 0; i < B; ++i) {
             fft_rve_s* r = g->m[i];
-            if (st[i] == FFT_ERR_NOT_CONVERGED && r->opt.max_cutbacks > 0) {
-                if (r->verbose)
-                    std::fprintf(stderr, "  class member %d not converged: cutting back\n", i);
-                st[i] = I::run_halves(r, Fbar[i], nullptr, nullptr, dt[i], stats[i], 1);
-            }
-            if (st[i] == FFT_OK && host_wait(r) != cudaSuccess) st[i] = FFT_ERR_CUDA;
+            if (st[i] != FFT_ERR_NOT_CONVERGED || r->opt.max_cutbacks <= 0) continue;
+            if (r->verbose)
+                std::fprintf(stderr, "  class member %d not converged: cutting back\n", i);
+            cut.emplace_back([=] {
+                st[i] = cudaSetDevice(r->dev) != cudaSuccess
+                            ? FFT_ERR_CUDA
+                            : I::run_halves(r, Fbar[i], nullptr, nullptr, dt[i], stats[i], 1);
+            });
         }
+        for (auto& t : cut) t.join();
+        for (int i = 0; i < B; ++i)
+            if (st[i] == FFT_OK && host_wait(g->m[i]) != cudaSuccess) st[i] = FFT_ERR_CUDA;
     }
 };
 

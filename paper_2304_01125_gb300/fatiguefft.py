@@ -348,17 +348,18 @@ class Batch:
     """Many independent RVE handles advanced together (batch_run_increment):
     each handle needs its own stream; a native thread pool of ``threads``
     host threads (None: the hardware concurrency) drives them concurrently.
-    With ``classes`` (default), handles of one size class (grid, precision,
-    options) run in lockstep under strain control, each Krylov column of a
-    class one graph launch (batch_create_ex).  The handles stay owned by the
-    caller."""
+    With ``classes`` (default True), handles of one size class (grid,
+    precision, options) of at most 64^3 voxels run in lockstep under strain
+    control, each Krylov column of a class one graph launch
+    (batch_create_ex); ``classes="all"`` forms classes at any grid size,
+    False none.  The handles stay owned by the caller."""
 
     def __init__(self, rves, threads=None, classes=True):
         self.rves = list(rves)
         arr = (C.c_void_p * len(self.rves))(*[r._h for r in self.rves])
         h = C.c_void_p()
-        s = load().batch_create_ex(C.byref(h), arr, len(self.rves), int(threads or 0),
-                                   1 if classes else 0)
+        flags = 3 if classes == "all" else (1 if classes else 0)
+        s = load().batch_create_ex(C.byref(h), arr, len(self.rves), int(threads or 0), flags)
         if s != FFT_OK:
             raise FFTError("batch_create", s, "distinct handles, each with its own stream")
         self._h = h

@@ -357,7 +357,7 @@ def test_lockstep_class_cuts_back_a_member():
                       stream=torch.cuda.Stream())
 
     rves = [make(i) for i in range(2)]
-    b = FF.Batch(rves)
+    b = FF.Batch(rves, classes="all")
     got = [[] for _ in rves]
     for Fb, dt in prog:
         s, per, stats = b.run_increment([Fb] * 2, [dt] * 2)
