@@ -17,12 +17,88 @@
 // arithmetic is that of the single-handle driver step for step; only the
 // order in which the host reads the results differs.  The staggered loop's
 // damage updates run per member; a member whose increment does not converge
-// is cut back on its own, by the single-handle driver.
+// is cut back on its own, by the single-handle driver.  The per-member host
+// work (enqueueing a member's stages, waiting for and reading its results)
+// is spread over a few helper threads of the class.
+#include <atomic>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
+
 #include "rve_impl.cuh"
 
 namespace {
 
 constexpr int kGangMax = 64;
+constexpr int kGangHelpers = 7;  // host threads besides the caller per class
+
+// Fork-join helper threads of a class: run(n, f) calls f(0) .. f(n-1), the
+// items taken in order by the caller and the helpers, and returns when all
+// are done.  The members' per-member host work (enqueueing their stages,
+// waiting for and reading their results) is independent from member to
+// member, so that one host thread does not serialise it for the class.
+struct ParFor {
+    std::vector<std::thread> th;
+    std::mutex m;
+    std::condition_variable cv, cv_done;
+    std::function<void(int)> fn;
+    std::atomic<int> next{0};
+    int n = 0, busy = 0;
+    long long gen = 0;
+    bool quit = false;
+
+    void start(int helpers, int dev) {
+        for (int t = 0; t < helpers; ++t)
+            th.emplace_back([this, dev] {
+                cudaSetDevice(dev);
+                long long seen = 0;
+                std::unique_lock<std::mutex> lk(m);
+                for (;;) {
+                    cv.wait(lk, [&] { return quit || gen != seen; });
+                    if (quit) return;
+                    seen = gen;
+                    lk.unlock();
+                    work();
+                    lk.lock();
+                    if (--busy == 0) cv_done.notify_all();
+                }
+            });
+    }
+    void work() {
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= n) return;
+            fn(i);
+        }
+    }
+    void run(int count, const std::function<void(int)>& f) {
+        if (th.empty() || count <= 1) {
+            for (int i = 0; i < count; ++i) f(i);
+            return;
+        }
+        {
+            std::lock_guard<std::mutex> lk(m);
+            fn = f;
+            n = count;
+            next = 0;
+            busy = (int)th.size();
+            ++gen;
+        }
+        cv.notify_all();
+        work();
+        std::unique_lock<std::mutex> lk(m);
+        cv_done.wait(lk, [&] { return busy == 0; });
+    }
+    void stop() {
+        {
+            std::lock_guard<std::mutex> lk(m);
+            quit = true;
+        }
+        cv.notify_all();
+        for (auto& t : th) t.join();
+        th.clear();
+    }
+};
 
 struct GangBase {
     std::vector<fft_rve_s*> m;
@@ -36,6 +112,12 @@ struct GangBase {
     // stream, in order with the column graphs
     int* act = nullptr;
     std::vector<void*> rb9_own, cb9_own;  // the members' own scratch, restored at destroy
+    // the members' reduction buffers (kRedSlots doubles each) in one arena,
+    // so that one strided copy per column brings every member's step
+    // coefficients to the host (hslots: 2 x B x kSlot, pinned)
+    double* red = nullptr;
+    std::vector<double*> red_own;
+    double* hslots = nullptr;
     cudaGraphExec_t col[kMaxKrylov] = {};
     cudaEvent_t ev_a = nullptr, slot_ev[2] = {nullptr, nullptr}, done_ev = nullptr;
     std::vector<cudaEvent_t> ev_m;  // per member: fork/join of the column graphs
@@ -46,8 +128,15 @@ struct GangBase {
     std::vector<cudaEvent_t> tpool;
     std::vector<std::pair<std::pair<cudaEvent_t, cudaEvent_t>, double>> tpend;
     double graph_ms = 0.0, graph_bytes = 0.0;
+    ParFor pool;
     std::string err;
 };
+
+// f(i) for every member index in idx, spread over the class's host threads
+static void for_members(GangBase* g, const std::vector<int>& idx,
+                        const std::function<void(int)>& f) {
+    g->pool.run((int)idx.size(), [&](int t) { f(idx[t]); });
+}
 
 // one host wait on the class stream (polling: the batch's threads may
 // outnumber the host cores)
@@ -121,13 +210,15 @@ struct Gang {
                              r->dot64 ? 1 : 0, g->act + i);
             dcgs_update<R>(V, vs, k, r->w, coef, r->Kbar, r->g, r->cb9,
                            red_at(r, dslot + kSlotNorm), bc, r->st, 0, g->act + i);
-            ok = ok && cudaMemcpyAsync(r->hslot + (size_t)(k % 2) * kSlot, dslot,
-                                       kSlotLen * sizeof(double), cudaMemcpyDeviceToHost,
-                                       r->st) == cudaSuccess;
             ok = ok && cudaEventRecord(g->ev_m[i], r->st) == cudaSuccess;
         }
         for (int i = 0; ok && i < g->B; ++i)
             ok = cudaStreamWaitEvent(g->st, g->ev_m[i], 0) == cudaSuccess;
+        // every member's step coefficients in one copy
+        ok = ok && cudaMemcpy2DAsync(g->hslots + (size_t)(k % 2) * g->B * kSlot,
+                                     kSlot * sizeof(double), g->red + kDslot,
+                                     kRedSlots * sizeof(double), kSlotLen * sizeof(double),
+                                     g->B, cudaMemcpyDeviceToHost, g->st) == cudaSuccess;
         cudaGraph_t gr = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(g->st, &gr);
         cudaError_t ie = ce;
@@ -231,41 +322,35 @@ struct Gang {
             C.swap(cur);
             if (C.empty()) break;
             // restart residuals r = b - A M x of the members past their first cycle
-            for (int i : C) {
-                if (first[i]) continue;
+            for_members(g, C, [&](int i) {
                 fft_rve_s* r = g->m[i];
+                if (st[i] != FFT_OK) return;
+                if (first[i]) {
+                    beta[i] = bn[i];
+                    src[i] = r->b;
+                    first[i] = 0;
+                    return;
+                }
                 fft_status s = I::apply_op(r, r->x, 1.0, nullptr, 0, r->w, 0);
                 if (s == FFT_OK) {
                     axpby<R>(r->w, r->b, r->w, 1.0, -1.0, n3, r->st);
                     norm2<R>(r->w, r->g, red_at(r, r->red), r->st);
                     r->launches += 2;
-                    s = I::fetch_enq(r, 1);
+                    s = I::fetch(r, 1);
                 }
-                if (s != FFT_OK) st[i] = s;
-            }
-            for (int i : C) {
-                fft_rve_s* r = g->m[i];
-                if (st[i] != FFT_OK) continue;
-                if (first[i]) {
-                    beta[i] = bn[i];
-                    src[i] = r->b;
-                    first[i] = 0;
-                    continue;
-                }
-                const fft_status s = I::fetch_get(r, 1);
                 if (s != FFT_OK) {
                     st[i] = s;
-                    continue;
+                    return;
                 }
                 beta[i] = std::sqrt(r->hred[0]);
                 if (r->verbose)
                     std::fprintf(stderr, "  gmres restart: true |r|/|b| %.3e\n", beta[i] / bn[i]);
                 if (beta[i] <= target[i]) {
                     ok[i] = 1;
-                    continue;
+                    return;
                 }
                 src[i] = r->w;
-            }
+            });
             cur.clear();
             for (int i : C)
                 if (alive(i)) cur.push_back(i);
@@ -364,7 +449,9 @@ struct Gang {
                         fail(i, FFT_ERR_CUDA);
                         continue;
                     }
-                    const double* slot = r->hslot + (size_t)(k % 2) * kSlot;
+                    const double* slot =
+                        col_sparse[k] ? r->hslot + (size_t)(k % 2) * kSlot
+                                      : g->hslots + ((size_t)(k % 2) * B + i) * kSlot;
                     if (slot[kSlotErr] != 0.0) {
                         r->err = "a bulk-copy wait in the Arnoldi step timed out";
                         fail(i, FFT_ERR_CUDA);
@@ -439,9 +526,9 @@ struct Gang {
                     }
                 break;
             }
-            for (int i : C) {
+            for_members(g, C, [&](int i) {
                 in_cycle[i] = 0;
-                if (st[i] != FFT_OK) continue;
+                if (st[i] != FFT_OK) return;
                 fft_rve_s* r = g->m[i];
                 const int k = kcols[i];
                 I::hess_lsq(Hm[i], mres, k, beta[i], y[i].data());
@@ -451,19 +538,18 @@ struct Gang {
                                         r->st) != cudaSuccess) {
                         r->err = "GMRES coefficient upload failed";
                         st[i] = FFT_ERR_CUDA;
-                        continue;
+                        return;
                     }
                     cudaEvent_t e = prof_begin(r, KF_XUPD);
                     xupdate<R>(r->x, r->V, vs, k, r->dy, r->Kbar, r->g, r->st);
                     prof_end(r, KF_XUPD, e, (double)Nh * 2 * es * 3 * (k + 2));
                     r->launches += 1;
                 }
-            }
-            for (int i : C)
-                if (st[i] == FFT_OK && host_wait(g->m[i]) != cudaSuccess) {
-                    g->m[i]->err = "stream synchronisation after the GMRES update failed";
+                if (host_wait(r) != cudaSuccess) {
+                    r->err = "stream synchronisation after the GMRES update failed";
                     st[i] = FFT_ERR_CUDA;
                 }
+            });
             lin = 0;
             for (int i : C)
                 if (alive(i)) lin = std::max(lin, lin_i[i]);
@@ -499,10 +585,11 @@ struct Gang {
         const int B = g->B;
         std::vector<double> alpha(B, 1.0), prev(B, 0.0), bn(B), pn(B);
         std::vector<int> its(B, 0);
-        std::vector<char> cp_pending(B, 0);
+        std::vector<char> cp_pending(B, 0), go(B, 0);
         const int max_newton = g->m[0]->opt.max_newton;
         for (int it = 0; it < max_newton && !E.empty(); ++it) {
-            for (int i : E) {
+            // residual of every member (Impl::newton_solve's opening), enqueued
+            for_members(g, E, [&](int i) {
                 fft_rve_s* r = g->m[i];
                 const size_t N = r->g.N;
                 fft_status s = FFT_OK;
@@ -529,29 +616,34 @@ struct Gang {
                     s = I::fetch_enq(r, 2);
                 }
                 st[i] = s;
-            }
-            std::vector<int> L;
-            for (int i : E) {
+            });
+            // ... and read
+            for_members(g, E, [&](int i) {
                 fft_rve_s* r = g->m[i];
-                if (st[i] != FFT_OK) continue;
+                go[i] = 0;
+                if (st[i] != FFT_OK) return;
                 if (cp_pending[i]) {
                     int nf = 0;
                     st[i] = I::cp_get(r, &nf);
-                    if (st[i] != FFT_OK) continue;
+                    if (st[i] != FFT_OK) return;
                     if (stats[i]) stats[i]->local_fail += nf;
                 }
                 st[i] = I::fetch_get(r, 2);
-                if (st[i] != FFT_OK) continue;
+                if (st[i] != FFT_OK) return;
                 bn[i] = std::sqrt(r->hred[0]);
                 pn[i] = std::sqrt(r->hred[1]);
-                L.push_back(i);
-            }
+                go[i] = 1;
+            });
+            std::vector<int> L;
+            for (int i : E)
+                if (go[i]) L.push_back(i);
             gmres(g, L, bn.data(), pn.data(), its.data(), st);
-            std::vector<int> U;
-            for (int i : L) {
+            // the Newton update F += alpha grad(M x) of every member
+            for_members(g, L, [&](int i) {
                 fft_rve_s* r = g->m[i];
+                go[i] = 0;
                 if (stats[i]) stats[i]->lin_it_total += its[i];
-                if (st[i] != FFT_OK) continue;
+                if (st[i] != FFT_OK) return;
                 const size_t N = r->g.N;
                 cudaEvent_t e = prof_begin(r, KF_PRECOND);
                 precond_grad<R>(r->x, alpha[i], nullptr, r->Kbar, r->g, r->cb9, 0, r->st);
@@ -565,27 +657,27 @@ struct Gang {
                     s = I::fetch_enq(r, 2);
                 }
                 st[i] = s;
-                if (s == FFT_OK) U.push_back(i);
-            }
-            std::vector<int> next;
-            for (int i : U) {
-                fft_rve_s* r = g->m[i];
+                if (s != FFT_OK) return;
+                // the convergence test and the damping of Impl::newton_solve
                 st[i] = I::fetch_get(r, 2);
-                if (st[i] != FFT_OK) continue;
+                if (st[i] != FFT_OK) return;
                 r->cp_valid = false;
                 const double gmax = r->hred[0] / alpha[i], dFt = std::max(r->hred[1], 1e-30);
                 const double ratio = gmax / dFt;
                 if (r->verbose)
                     std::fprintf(stderr, "newton %d (class member %d) |b| %.3e lin %d ratio %.3e\n",
                                  it, i, bn[i], its[i], ratio);
-                if (ratio < r->opt.tol_newton) continue;  // converged
+                if (ratio < r->opt.tol_newton) return;  // converged
                 if (it + 1 >= I::kDampFrom && ratio >= prev[i])
                     alpha[i] = std::max(0.5 * alpha[i], 1.0 / 16);
                 else if (ratio < 0.5 * prev[i])
                     alpha[i] = std::min(2.0 * alpha[i], 1.0);
                 prev[i] = ratio;
-                next.push_back(i);
-            }
+                go[i] = 1;
+            });
+            std::vector<int> next;
+            for (int i : L)
+                if (go[i]) next.push_back(i);
             E.swap(next);
         }
         for (int i : E) {
@@ -602,12 +694,15 @@ struct Gang {
     static void run_increment(GangBase* g, const double* const* Fbar, const double* dt,
                               fft_stats** stats, fft_status* st) {
         const int B = g->B;
-        std::vector<int> A;
-        for (int i = 0; i < B; ++i) {
+        std::vector<int> all(B), A;
+        for (int i = 0; i < B; ++i) all[i] = i;
+        for_members(g, all, [&](int i) {
             if (stats[i]) std::memset(stats[i], 0, sizeof(fft_stats));
             st[i] = I::apply_increment(g->m[i], Fbar[i], dt[i]);
+        });
+        for (int i = 0; i < B; ++i)
             if (st[i] == FFT_OK) A.push_back(i);
-        }
+        std::vector<char> more(B, 0);
         const int max_stag = g->m[0]->opt.max_stag;
         for (int it = 0; it < max_stag && !A.empty(); ++it) {
             std::vector<int> E;
@@ -635,17 +730,22 @@ struct Gang {
                 E.push_back(i);
             }
             newton(g, E, stats, st);
-            std::vector<int> next;
-            for (int i : A) {
-                if (st[i] != FFT_OK) continue;
+            // the damage update of every member, each with its own host
+            // round trips (phase-field CG, staggered test), side by side
+            for_members(g, A, [&](int i) {
+                more[i] = 0;
+                if (st[i] != FFT_OK) return;
                 fft_rve_s* r = g->m[i];
                 st[i] = I::update_damage(r, stats[i]);
-                if (st[i] != FFT_OK) continue;
+                if (st[i] != FFT_OK) return;
                 if (r->converged)
                     st[i] = I::commit(r);
                 else
-                    next.push_back(i);
-            }
+                    more[i] = 1;
+            });
+            std::vector<int> next;
+            for (int i : A)
+                if (more[i]) next.push_back(i);
             A.swap(next);
         }
         for (int i : A) {
@@ -675,6 +775,7 @@ struct Gang {
 };
 
 static void gang_release(GangBase* g) {
+    g->pool.stop();
     for (auto& e : g->col)
         if (e) {
             cudaGraphExecDestroy(e);
@@ -685,6 +786,7 @@ static void gang_release(GangBase* g) {
         drop_graphs(r);  // the members' own step graphs used the arena
         r->rb9 = g->rb9_own[i];
         r->cb9 = g->cb9_own[i];
+        if (i < g->red_own.size()) r->red = g->red_own[i];
         r->poll = false;
     }
     if (g->plans) {
@@ -692,6 +794,8 @@ static void gang_release(GangBase* g) {
         cufftDestroy(g->c2r);
     }
     if (g->rb9) cudaFree(g->rb9);
+    if (g->red) cudaFree(g->red);
+    if (g->hslots) cudaFreeHost(g->hslots);
     if (g->act) cudaFree(g->act);
     if (g->cb9) cudaFree(g->cb9);
     for (cudaEvent_t e : g->ev_m)
@@ -756,7 +860,9 @@ fft_status fatfft_gang_create(fft_rve_t const* members, int n, void** out) {
         return bad(FFT_ERR_CUDA);
     if (cudaMalloc(&g->rb9, (size_t)n * 9 * N * es) != cudaSuccess ||
         cudaMalloc(&g->cb9, (size_t)n * 9 * Nh * 2 * es) != cudaSuccess ||
-        cudaMalloc((void**)&g->act, (size_t)n * sizeof(int)) != cudaSuccess)
+        cudaMalloc((void**)&g->act, (size_t)n * sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&g->red, (size_t)n * kRedSlots * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&g->hslots, (size_t)2 * n * kSlot * sizeof(double)) != cudaSuccess)
         return bad(FFT_ERR_OOM);
     // the member plans' layout, batched over the class: 9 n fields
     int dims3[3] = {r0->g.n2, r0->g.n1, r0->g.n0};
@@ -785,8 +891,15 @@ fft_status fatfft_gang_create(fft_rve_t const* members, int n, void** out) {
         g->cb9_own.push_back(r->cb9);
         r->rb9 = (char*)g->rb9 + (size_t)i * 9 * N * es;
         r->cb9 = (char*)g->cb9 + (size_t)i * 9 * Nh * 2 * es;
+        double* red_i = g->red + (size_t)i * kRedSlots;
+        if (cudaMemcpy(red_i, r->red, kRedSlots * sizeof(double), cudaMemcpyDeviceToDevice) !=
+            cudaSuccess)
+            return bad(FFT_ERR_CUDA);
+        g->red_own.push_back(r->red);
+        r->red = red_i;
         r->poll = true;
     }
+    g->pool.start(std::min(kGangHelpers, n - 1), r0->dev);
     *out = g;
     return FFT_OK;
 }

@@ -13,9 +13,13 @@
 // multipliers i xi_i are zero on the Nyquist frequency of an even axis; the
 // Laplacian keeps -|xi|^2 there.
 //
-// Every reduction kernel runs kRedBlocks blocks; each block writes one FP64
-// partial per value and the last block to finish combines them in a fixed
-// order (deterministic results, no separate finalisation launch).
+// Every reduction kernel runs a grid fixed by the problem size (kRedBlocks
+// blocks; the dot pass of the Arnoldi step fewer on small grids); each
+// block writes one FP64 partial per value and the last block to finish
+// combines them in a fixed order (deterministic results, no separate
+// finalisation launch).
+#include <algorithm>
+
 #include "bulk.cuh"
 #include "common.cuh"
 #include "spec.h"
@@ -924,19 +928,24 @@ void contract_dots(const void* T, const SGrid& g, void* w, const void* c, const 
     const Cx *TT = (const Cx*)T, *cc = (const Cx*)c, *VV = (const Cx*)V;
     Cx* ww = (Cx*)w;
     const int* err = bc ? bc->err : nullptr;
+    // one frequency per thread up to the fixed reduction grid: small grids
+    // (below about 44^3) launch fewer blocks, so that the dot passes of
+    // several handles run side by side instead of each filling the GPU
+    const int nb = (int)std::min<size_t>((size_t)kRedBlocks,
+                                         std::max<size_t>(1, (g.Nh + kThreads - 1) / kThreads));
 #define CDOTS(NQ)                                                                             \
     do {                                                                                      \
         if (il)                                                                               \
-            k_contract_dots<R, NQ, true, R, false><<<kRedBlocks, kThreads, 0, s>>>(           \
+            k_contract_dots<R, NQ, true, R, false><<<nb, kThreads, 0, s>>>(                  \
                 TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err, act);            \
         else if (g.willot)                                                                    \
-            k_contract_dots<R, NQ, false, R, true><<<kRedBlocks, kThreads, 0, s>>>(           \
+            k_contract_dots<R, NQ, false, R, true><<<nb, kThreads, 0, s>>>(                  \
                 TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err, act);            \
         else if (dot64)                                                                       \
-            k_contract_dots<R, NQ, false, double, false><<<kRedBlocks, kThreads, 0, s>>>(     \
+            k_contract_dots<R, NQ, false, double, false><<<nb, kThreads, 0, s>>>(            \
                 TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err, act);            \
         else                                                                                  \
-            k_contract_dots<R, NQ, false, R, false><<<kRedBlocks, kThreads, 0, s>>>(          \
+            k_contract_dots<R, NQ, false, R, false><<<nb, kThreads, 0, s>>>(                 \
                 TT, g, ww, cc, VV, vstride, k, red, Hd, Hp, slot, coef, err, act);            \
     } while (0)
     if (k <= 0)
