@@ -60,7 +60,7 @@ def args_():
                    help="--config batch32: no lockstep classes (every handle on its own)")
     p.add_argument("--classes-all", action="store_true",
                    help="--config batch32: lockstep classes at every grid size (default: up "
-                        "to 64^3)")
+                        "to 2^16 voxels)")
     p.add_argument("--no-autotune", action="store_true",
                    help="--config batch32: default kernel variants (no per-size autotuning)")
     p.add_argument("--verbose", action="store_true")
@@ -516,11 +516,11 @@ def run_ours(a):
     if a.config == CONFIG_NAME and not a.no_damage_window:
         line["damage_window"] = damage_window(FF, a, stream, flush)
     if a.config == CONFIG_NAME and ws == 1 and not a.no_batch_window:
-        # the batched workload (32 RVEs of 32^3-96^3 in lockstep size
-        # classes), three increments after three warm-up ones
+        # the batched workload (32 RVEs of 32^3-96^3, the smallest grids in a
+        # lockstep size class): increments 4-13, as `--config batch32`
         import copy
         b = copy.copy(a)
-        b.steps, b.warmup = 3, 3
+        b.steps, b.warmup = 10, 3
         bl = run_batch(b, short=True)
         line["batch_window"] = {k: bl[k] for k in ("value", "unit", "ms_per_step", "steps",
                                                    "warmup", "roofline", "iterations",

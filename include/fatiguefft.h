@@ -326,8 +326,8 @@ const char* fft_last_error(fft_rve_t r);
  *
  * Lockstep classes: batch_create groups the handles of one size class (same
  * device, precision, grid and fft_options; the unfused Arnoldi step, CUDA
- * graphs on; by default grids of at most 64^3 voxels, where a GMRES step is
- * latency-bound) into classes of up to 64 members.  Under strain control
+ * graphs on; by default grids of at most 2^16 voxels, e.g. 40^3, where a
+ * GMRES step is latency-bound) into classes of up to 64 members.  Under strain control
  * (batch_run_increment) a class's increments run together: the Newton and
  * GMRES iterations in lockstep over the members still iterating, each Krylov
  * column of the whole class one CUDA graph launch with one batched library
@@ -337,7 +337,7 @@ const char* fft_last_error(fft_rve_t r);
  * The class holds the members' Arnoldi-step scratch in one arena while the
  * batch exists (the handles stay usable on their own, from the thread that
  * owns the batch, between batch calls).  Mixed control runs every handle on
- * its own.  batch_create_ex flags: bit 0 = classes of grids up to 64^3
+ * its own.  batch_create_ex flags: bit 0 = classes of grids up to 2^16
  * voxels, bit 1 = classes at any grid size, 0 = no classes (other bits:
  * FFT_ERR_ARG); batch_create = batch_create_ex with flags 1.  batch_classes returns the number of classes and, per class,
  * its member count, the column graphs launched so far and, while timing is

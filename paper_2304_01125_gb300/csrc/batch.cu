@@ -37,13 +37,16 @@ void fatfft_gang_destroy(void* g);
 
 namespace {
 constexpr int kClassMax = 64;  // members of one lockstep class
-// Classes form by default only for grids of at most 64^3 voxels: there a
-// GMRES step is mostly launch and synchronisation latency (about 0.09 ms
-// per step from 16^3 to 32^3, 0.18 ms at 64^3 on GB300), which one graph
-// launch for the class amortises; on larger grids a step is bandwidth-bound
-// and lockstep only adds the wait for the slowest member (flags bit 1 forms
-// classes at any size).
-constexpr size_t kClassMaxVoxels = 64 * 64 * 64;
+// Classes form by default only for grids of at most 2^16 voxels (40^3):
+// there a GMRES step is mostly launch and synchronisation latency (about
+// 0.09 ms per step from 16^3 to 32^3 on GB300), which one graph launch for
+// the class amortises (32 RVEs of 32^3: 43.1 M against 40.0 M
+// voxel-increments/s on their own streams; of 16^3: 12.2 M against 10.0 M);
+// from 48^3 on a step is increasingly bandwidth-bound and lockstep gains
+// nothing over concurrent streams (16 of 48^3: 43.0 M against 43.7 M), it
+// only adds the wait for the slowest member.  Flags bit 1 forms classes at
+// any size.
+constexpr size_t kClassMaxVoxels = 1 << 16;
 // a unit of work for one pool thread: a lockstep class or a single handle
 struct Unit {
     std::vector<int> idx;  // batch indices

@@ -349,7 +349,7 @@ class Batch:
     each handle needs its own stream; a native thread pool of ``threads``
     host threads (None: the hardware concurrency) drives them concurrently.
     With ``classes`` (default True), handles of one size class (grid,
-    precision, options) of at most 64^3 voxels run in lockstep under strain
+    precision, options) of at most 2^16 voxels run in lockstep under strain
     control, each Krylov column of a class one graph launch
     (batch_create_ex); ``classes="all"`` forms classes at any grid size,
     False none.  The handles stay owned by the caller."""
