@@ -280,6 +280,64 @@ def test_local_solve_robust_on_extreme_states():
                 assert abs(over - inv) < 1e-8
 
 
+def test_local_solve_matches_an_independent_solver():
+    """Sec. 2.1, Eqs. flowrule and the multiplicative split: the local slip
+    problem restated here from the paper (F_p^-1 = F_pn^-1 (I - sum dg s(x)n),
+    F_e = F F_p^-1 in the lattice frame, S = C : (F_e^T F_e - I)/2 through the
+    Voigt matrix, tau = S : s(x)n, |tau| - tau_c = sT asinh(|dg| / (dt g0))
+    on slipping systems, |tau| <= tau_c on the others) and solved by another
+    method -- continuation in the time step from a nearly elastic 1e-4 dt up
+    to dt, each stage by the library's Powell hybrid root finder on all 12
+    systems at once (no active set, no line search) -- gives the oracle's
+    slips on generic multi-slip states (2 to 8 systems slipping) to 1e-10;
+    the oracle's stress and plastic deformation follow from its slips by
+    the same restated equations."""
+    so = pytest.importorskip("scipy.optimize")
+    mat = dict(MAT, tau_c0=150.0)
+    s, n = O.fcc_systems()
+    kT = mat["k_B"] * mat["T"]
+    g0 = mat["rho_m"] * mat["b"] ** 2 * mat["nu_D"] * np.exp(-mat["dF"] / kT)
+    sT = kT / (mat["dV"] * 1e-3)
+    rng = np.random.default_rng(5)
+    nact = set()
+    for _ in range(16):
+        Q = O.euler_to_Q(I.random_orientations(rng, 1)[0])
+        e = 0.004 * (1 + rng.random())
+        F = np.diag([1 - 0.3 * e, 1 + e, 1 - 0.3 * e]) + 0.0005 * rng.standard_normal((3, 3))
+        FpL = np.eye(3) + 0.002 * rng.standard_normal((3, 3))
+        dt = float(rng.choice([0.1, 1.0, 10.0]))
+        r = O.cp_point(mat, Q, F, FpL, mat["rho_ssd0"], 1e5, dt, tol_local=1e-9, tangent=False)
+        assert r["fail"] == 0
+        tc = mat["tau_c0"] + mat["mu"] * mat["b"] * np.sqrt(mat["rho_ssd0"] + 1e5)
+        assert abs(r["tau_c"] - tc) < 1e-12 * tc
+        FL = Q.T @ F @ Q
+        A = np.linalg.inv(FpL)
+
+        def state(dg):
+            Fpi = A @ (np.eye(3) - sum(dg[a] * np.outer(s[a], n[a]) for a in range(12)))
+            Fe = FL @ Fpi
+            S = cubic_apply_np(mat, 0.5 * (Fe.T @ Fe - np.eye(3)))
+            return np.array([s[a] @ S @ n[a] for a in range(12)]), Fe, S, Fpi
+
+        def res(dg, d):
+            tau = state(dg)[0]
+            return sT * np.arcsinh(dg / (d * g0)) - np.sign(tau) * np.maximum(np.abs(tau) - tc, 0)
+
+        x = np.zeros(12)
+        for d in np.geomspace(dt * 1e-4, dt, 41):
+            x = so.root(lambda z: res(z, d), x, method="hybr", options=dict(xtol=1e-15)).x
+        assert np.abs(res(x, dt)).max() < 1e-9  # MPa: a root of the restated problem
+        ref = np.abs(x).max()
+        assert ref > 0 and np.abs(r["dgamma"] - x).max() < 1e-10 * ref
+        nact.add(int(np.sum(r["dgamma"] != 0)))
+        tau, Fe, S, Fpi = state(r["dgamma"])
+        assert np.abs(tau - r["tau"]).max() < 1e-9 * np.abs(tau).max()
+        P = Q @ (Fe @ S @ Fpi.T) @ Q.T
+        assert np.abs(P - r["P"]).max() < 1e-10 * np.abs(P).max()
+        assert np.abs(np.linalg.inv(Fpi) - r["Fp_L"]).max() < 1e-12
+    assert min(nact) <= 3 and max(nact) >= 6
+
+
 # ----------------------------------------------------------------- P13
 def test_eigen_split_degenerate_and_rotated():
     """Eq. decMiehe: eps+ from the eigen-decomposition of 1/2 ln(Fe Fe^T),
