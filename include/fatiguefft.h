@@ -334,9 +334,10 @@ const char* fft_last_error(fft_rve_t r);
  * transform per direction over the class's 9 x members fields; the damage
  * updates and the cut-backs of a member whose increment did not converge run
  * per member.  Each member's arithmetic is that of its own run_increment.
- * The class holds the members' Arnoldi-step scratch in one arena while the
- * batch exists (the handles stay usable on their own, from the thread that
- * owns the batch, between batch calls).  Mixed control runs every handle on
+ * The class holds the members' Arnoldi-step scratch and reduction buffers
+ * in arenas while the batch exists (the handles stay usable on their own,
+ * from the thread that owns the batch, between batch calls); destroy the
+ * batch before any of its handles.  Mixed control runs every handle on
  * its own.  batch_create_ex flags: bit 0 = classes of grids up to 2^16
  * voxels, bit 1 = classes at any grid size, 0 = no classes (other bits:
  * FFT_ERR_ARG); batch_create = batch_create_ex with flags 1.  batch_classes returns the number of classes and, per class,

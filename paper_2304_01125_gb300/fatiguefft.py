@@ -7,6 +7,7 @@ PyTorch, when given, supplies the CUDA stream and device buffers.
 """
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -189,6 +190,7 @@ class RVE:
                  elastic_only=None, stream=None):
         L = load()
         self.n = tuple(int(x) for x in n)
+        self._batches = weakref.WeakSet()  # live batches holding this handle
         self.N = int(np.prod(self.n))
         if stream is not None and hasattr(stream, "cuda_stream"):
             stream = stream.cuda_stream
@@ -221,6 +223,10 @@ class RVE:
 
     def close(self):
         if getattr(self, "_h", None):
+            # a batch holding the handle is destroyed first (a lockstep class
+            # keeps part of the handle's buffers in its arenas)
+            for b in list(getattr(self, "_batches", ())):
+                b.close()
             load().rve_destroy(self._h)
             self._h = None
 
@@ -363,6 +369,8 @@ class Batch:
         if s != FFT_OK:
             raise FFTError("batch_create", s, "distinct handles, each with its own stream")
         self._h = h
+        for r in self.rves:
+            r._batches.add(self)
 
     def classes(self, timing=None):
         """[(members, column graphs launched, graph ms, algorithmic bytes)]

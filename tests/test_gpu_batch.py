@@ -370,3 +370,22 @@ def test_lockstep_class_cuts_back_a_member():
     assert _same_as_alone(rves, make, prog) == got
     for r in rves:
         r.close()
+
+
+def test_closing_a_class_member_closes_its_batch_first():
+    """A lockstep class keeps part of its members' buffers in its arenas:
+    closing a member handle closes the batch first (the binding keeps that
+    order), after which the other members run on their own."""
+    grids = [(8, 8, 8)] * 3
+    rves = [_make(n, 90 + i, "mixed") for i, n in enumerate(grids)]
+    b = FF.Batch(rves)
+    assert b.classes()[0][0] == 3
+    Fb, dt = I.uniaxial_cycle_program(0.004, 8, 1)[0]
+    s, _, _ = b.run_increment([Fb] * 3, [dt] * 3)
+    assert s == FF.FFT_OK
+    rves[0].close()
+    assert b._h is None
+    for r in rves[1:]:
+        s, st = r.run_increment(*I.uniaxial_cycle_program(0.004, 8, 1)[1])
+        assert s == FF.FFT_OK and st["lin_it_total"] >= 0
+        r.close()
