@@ -308,6 +308,20 @@ def test_mixed_control_uniaxial_stress(prec):
     assert np.abs(o.field("Fp") - np.eye(3).reshape(9, 1)).max() > 1e-6  # plastic by the end
 
 
+@pytest.mark.parametrize("prec", PREC)
+def test_paper_loading_into_plasticity(prec):
+    """The paper's own loading (Sec. 4: R = 0 to 2 %, uniaxial stress with
+    free lateral faces) on the 50-grain polycrystal of the 2 % workload cut
+    to 8^3: eight increments to 0.8 % strain, past yield (from the fourth
+    on, GMRES needs 3-8 times its elastic iteration count), against the
+    oracle under the same mixed control."""
+    cfg = I.build_config("poly64_r0", n_override=(8, 8, 8))
+    o, Fo = _mixed_parity(prec, cfg["n"], cfg["grain_ids"], cfg["euler"], MAT,
+                          cfg["program"][:8], cfg["stress_mask"])
+    assert Fo[4] > 1.0075 and Fo[0] < 1.0 and Fo[8] < 1.0
+    assert np.abs(o.field("Fp") - np.eye(3).reshape(9, 1)).max() > 1e-4  # plastic
+
+
 GENERIC = (0.3, 0.9, 1.7)  # Bunge angles with no symmetric multi-slip along y
 
 
