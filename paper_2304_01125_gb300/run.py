@@ -58,6 +58,27 @@ def drive(rve, cfg, increments, emit, phi_max=False):
     return done
 
 
+def option_overrides(tol, pairs):
+    """Solver options from KEY=VALUE strings: the numeric options of the
+    preset (typed as the preset's), `kernel_variant` (int) and `derivative`
+    (spectral | willot); ValueError for anything else."""
+    base = I.solver_options(tol)
+    out = {}
+    for kv in pairs:
+        k, v = kv.split("=", 1)
+        if k == "derivative":
+            if v not in ("spectral", "willot"):
+                raise ValueError(f"derivative must be spectral or willot, not {v}")
+            out[k] = v
+        elif k == "kernel_variant":
+            out[k] = int(v)
+        elif k in base:
+            out[k] = type(base[k])(float(v))
+        else:
+            raise ValueError(f"unknown solver option {k}")
+    return out
+
+
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     p.add_argument("--config", default="poly64", choices=sorted(I.CONFIGS))
@@ -83,9 +104,10 @@ def main(argv=None):
     over = dict(cfg.get("options", {}))
     if a.max_cutbacks is not None:
         over["max_cutbacks"] = a.max_cutbacks
-    for kv in a.opt:
-        k, v = kv.split("=", 1)
-        over[k] = type(I.solver_options(a.tol)[k])(float(v))
+    try:
+        over.update(option_overrides(a.tol, a.opt))
+    except ValueError as e:
+        p.error(str(e))
     opts = I.solver_options(a.tol, **over)
     mat = I.material("baseline", **cfg.get("material", {}))
     for kv in a.mat:

@@ -49,3 +49,14 @@ def test_stops_at_the_first_failure():
     done = run.drive(FakeRVE(fail_at=1), cfg, 5, recs.append)
     assert done == 1 and len(recs) == 2 and recs[-1]["status"] == -5
     assert "phi_max" not in recs[0]
+
+
+def test_option_overrides():
+    o = run.option_overrides("paper", ["max_lin=5000", "tol_lin=1e-6", "derivative=willot",
+                                       "kernel_variant=2"])
+    assert o == {"max_lin": 5000, "tol_lin": 1e-6, "derivative": "willot", "kernel_variant": 2}
+    assert isinstance(o["max_lin"], int)
+    import pytest
+    for bad in (["derivative=central"], ["no_such=1"]):
+        with pytest.raises(ValueError):
+            run.option_overrides("paper", bad)
