@@ -88,15 +88,17 @@ def source_sha1():
     return h.hexdigest()
 
 
-def ncu_traffic(family):
+def ncu_traffic(family, workload):
     """DRAM bytes per launch of the family's kernel from the committed ncu
-    summary, or None when absent or taken on other kernel sources."""
+    summary, or None when absent, taken on other kernel sources or on
+    another workload (traffic per launch depends on the grid, and on what
+    stays in L2)."""
     try:
         d = json.load(open(TRAFFIC_FILE))
     except (OSError, ValueError):
         return None
     e = d.get(family)
-    if not e or e.get("source_sha1") != source_sha1():
+    if not e or e.get("source_sha1") != source_sha1() or d.get("_workload") != workload:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -448,7 +450,7 @@ def run_ours(a):
         avg_s = mx["dom_ms"] / mx["dom_count"] / 1e3
         bytes_per_launch = mx["dom_bytes"] / mx["dom_count"]
         achieved = bytes_per_launch / avg_s / 1e9
-        traffic = ncu_traffic(dom)
+        traffic = ncu_traffic(dom, a.config)
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4),
                 "traffic": int(traffic) if traffic is not None else None,
