@@ -30,10 +30,11 @@ STAT_KEYS = ("stag_it", "newton_it", "lin_it_total", "pf_it_total", "local_fail"
              "mixed_it", "cracked", "converged")
 
 
-def drive(rve, cfg, increments, emit, phi_max=False):
+def drive(rve, cfg, increments, emit, phi_max=False, after=None):
     """Run increments [0, increments) of cfg's program on rve (anything with
     the RVE's run_increment and field methods), calling emit(record) after
-    each; returns the number of converged increments."""
+    each and after(k) after each converged one; returns the number of
+    converged increments."""
     F = None
     done = 0
     for k in range(min(increments, len(cfg["program"]))):
@@ -53,6 +54,8 @@ def drive(rve, cfg, increments, emit, phi_max=False):
         if s != 0:
             break
         done += 1
+        if after is not None:
+            after(k)
         if kw:
             F = np.array(st["Fbar"])
     return done
@@ -91,6 +94,8 @@ def main(argv=None):
     p.add_argument("--out", default="-", help="JSON lines file (- for stdout)")
     p.add_argument("--checkpoint", default=None, help="write state_save here at the end")
     p.add_argument("--fields-out", default=None, help="write phi and Wcrit (.npz) at the end")
+    p.add_argument("--fields-every", type=int, default=0,
+                   help="with --fields-out: also rewrite it after every K converged increments")
     p.add_argument("--mat", action="append", default=[], help="material override KEY=VALUE")
     p.add_argument("--opt", action="append", default=[], help="solver option override KEY=VALUE")
     a = p.parse_args(argv)
@@ -119,16 +124,24 @@ def main(argv=None):
                  opts, prec=a.prec, stream=torch.cuda.Stream(), phi0=cfg["phi0"],
                  elastic_only=cfg["elastic_only"])
     out = sys.stdout if a.out == "-" else open(a.out, "w")
+
+    def save_fields(k):
+        np.savez_compressed(a.fields_out, phi=rve.field("phi").astype(np.float32),
+                            Wcrit=rve.field("Wcrit").astype(np.float32), increment=k)
+
+    def after(k):
+        if a.fields_out and a.fields_every > 0 and (k + 1) % a.fields_every == 0:
+            save_fields(k)
+
     try:
         done = drive(rve, cfg, a.increments,
                      lambda rec: (out.write(json.dumps(rec) + "\n"), out.flush()),
-                     phi_max=a.phi_max)
+                     phi_max=a.phi_max, after=after)
         if a.checkpoint:
             with open(a.checkpoint, "wb") as f:
                 f.write(rve.state_save())
         if a.fields_out:
-            np.savez_compressed(a.fields_out, phi=rve.field("phi").astype(np.float32),
-                                Wcrit=rve.field("Wcrit").astype(np.float32))
+            save_fields(done - 1)
     finally:
         if out is not sys.stdout:
             out.close()
