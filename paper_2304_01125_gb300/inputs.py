@@ -385,7 +385,7 @@ CONFIGS = {
 }
 
 
-def build_config(name, n_override=None):
+def build_config(name, n_override=None, cycles=None):
     """Grain ids, Euler angles, phi0, elastic mask and loading for one config.
 
     ``sx16``'s pre-crack is the plane y = 8, x = 6..9, all z (a 4 x 16 plane
@@ -394,7 +394,7 @@ def build_config(name, n_override=None):
     c = CONFIGS[name]
     n = tuple(n_override) if n_override else c["n"]
     if "plate" in c:
-        return _plate_config(c, n)
+        return _plate_config(c, n, cycles)
     if c["grains"] == 1:
         gid, eul = single_crystal(n)
     elif "sigma" in c:
@@ -406,10 +406,11 @@ def build_config(name, n_override=None):
         s = n[0] / 16.0
         x0, x1 = int(round(6 * s)), int(round(10 * s)) - 1
         phi0, mask = precrack_plane(n, (x0, x1), n[1] // 2)
+    ncyc = int(cycles) if cycles else c["cycles"]
     if c.get("ratio", -1) == 0:
-        prog = pulsating_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"])
+        prog = pulsating_cycle_program(c["amplitude"], c["inc_per_cycle"], ncyc)
     else:
-        prog = uniaxial_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"])
+        prog = uniaxial_cycle_program(c["amplitude"], c["inc_per_cycle"], ncyc)
     out = dict(n=n, h=VOXEL_MM, grain_ids=gid, euler=eul, phi0=phi0, elastic_only=mask,
                program=prog, stress_mask=None, Pbar=None, material=dict(c.get("material", {})),
                options=dict(c.get("options", {})))
@@ -421,7 +422,7 @@ def build_config(name, n_override=None):
     return out
 
 
-def _plate_config(c, n):
+def _plate_config(c, n, cycles=None):
     """Plates of Sec. 4 (2-D, one voxel thick): single crystal with a central
     soft pre-crack (length scaled with n0), periodic bicrystal, polycrystal
     with log-normal grain sizes (Sec. 4.3), notched
@@ -446,9 +447,11 @@ def _plate_config(c, n):
         phi0, mask = edge_notch(n, max(1, c["notch"] * n[1] // 128), 2, b, phi0, mask)
         axis = 0
     if c.get("ratio", -1) == 0:
-        prog = pulsating_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"], axis)
+        prog = pulsating_cycle_program(c["amplitude"], c["inc_per_cycle"],
+                                       int(cycles) if cycles else c["cycles"], axis)
     else:
-        prog = uniaxial_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"], axis)
+        prog = uniaxial_cycle_program(c["amplitude"], c["inc_per_cycle"],
+                                      int(cycles) if cycles else c["cycles"], axis)
     return dict(n=n, h=VOXEL_MM, grain_ids=gid, euler=eul, phi0=phi0, elastic_only=mask,
                 program=prog, stress_mask=uniaxial_stress_mask(axis), Pbar=np.zeros(9),
                 material={}, options={})

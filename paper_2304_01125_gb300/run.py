@@ -93,9 +93,11 @@ def main(argv=None):
     p.add_argument("--phi-max", action="store_true")
     p.add_argument("--out", default="-", help="JSON lines file (- for stdout)")
     p.add_argument("--checkpoint", default=None, help="write state_save here at the end")
+    p.add_argument("--cycles", type=int, default=None, help="loading cycles (default: the config's)")
     p.add_argument("--fields-out", default=None, help="write phi and Wcrit (.npz) at the end")
     p.add_argument("--fields-every", type=int, default=0,
-                   help="with --fields-out: also rewrite it after every K converged increments")
+                   help="with --fields-out: also write <stem>_<increment>.npz after every K "
+                        "converged increments")
     p.add_argument("--mat", action="append", default=[], help="material override KEY=VALUE")
     p.add_argument("--opt", action="append", default=[], help="solver option override KEY=VALUE")
     a = p.parse_args(argv)
@@ -105,7 +107,7 @@ def main(argv=None):
     from . import fatiguefft as FF
 
     n = tuple(int(x) for x in a.n.split(",")) if a.n else None
-    cfg = I.build_config(a.config, n_override=n)
+    cfg = I.build_config(a.config, n_override=n, cycles=a.cycles)
     over = dict(cfg.get("options", {}))
     if a.max_cutbacks is not None:
         over["max_cutbacks"] = a.max_cutbacks
@@ -125,13 +127,14 @@ def main(argv=None):
                  elastic_only=cfg["elastic_only"])
     out = sys.stdout if a.out == "-" else open(a.out, "w")
 
-    def save_fields(k):
-        np.savez_compressed(a.fields_out, phi=rve.field("phi").astype(np.float32),
+    def save_fields(k, path):
+        np.savez_compressed(path, phi=rve.field("phi").astype(np.float32),
                             Wcrit=rve.field("Wcrit").astype(np.float32), increment=k)
 
     def after(k):
         if a.fields_out and a.fields_every > 0 and (k + 1) % a.fields_every == 0:
-            save_fields(k)
+            stem = a.fields_out[:-4] if a.fields_out.endswith(".npz") else a.fields_out
+            save_fields(k, f"{stem}_{k + 1:05d}.npz")
 
     try:
         done = drive(rve, cfg, a.increments,
@@ -141,7 +144,7 @@ def main(argv=None):
             with open(a.checkpoint, "wb") as f:
                 f.write(rve.state_save())
         if a.fields_out:
-            save_fields(done - 1)
+            save_fields(done - 1, a.fields_out)
     finally:
         if out is not sys.stdout:
             out.close()
