@@ -150,3 +150,18 @@ def test_lognormal_configs():
     assert np.array_equal(c["stress_mask"], I.uniaxial_stress_mask(1))
     eps = np.array([F[4] - 1.0 for F, _ in c["program"]])
     assert abs(eps.max() - 0.02) < 1e-15 and eps.min() >= 0.0
+
+
+def test_cycle_override_extends_the_loading():
+    """build_config(cycles=...) repeats the configuration's cycle: the same
+    increments, more of them (plates too)."""
+    import numpy as np
+    from paper_2304_01125_gb300 import inputs as I
+    for name, n in (("poly128_damage", (8, 8, 8)), ("plate256_sx100", (8, 8, 1))):
+        base = I.build_config(name, n)
+        c = I.CONFIGS[name]
+        more = I.build_config(name, n, cycles=c["cycles"] + 2)
+        per = c["inc_per_cycle"]
+        assert len(more["program"]) == len(base["program"]) + 2 * per
+        for (Fa, da), (Fb, db) in zip(base["program"], more["program"]):
+            assert np.array_equal(Fa, Fb) and da == db
