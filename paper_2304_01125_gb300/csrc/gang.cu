@@ -11,9 +11,11 @@
 // forward transform, then per member the contraction with its dot pass, the
 // Gram-Schmidt update and the copy of its step coefficients to the host.
 // The Newton and GMRES loops run in lockstep over the members still
-// iterating (a member that has converged leaves the loop; its branch of the
-// remaining steps of the cycle computes columns that are discarded, as the
-// look-ahead step of the single-handle driver is).  The per-member
+// iterating: a member that has converged leaves the loop, and a device flag
+// makes its step kernels in the remaining columns of the cycle return at
+// once; once fewer than half the members iterate, the rest of the cycle runs
+// their own step graphs instead (the batched transforms would mostly
+// transform idle members).  The per-member
 // arithmetic is that of the single-handle driver step for step; only the
 // order in which the host reads the results differs.  The staggered loop's
 // damage updates run per member; a member whose increment does not converge
