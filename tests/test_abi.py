@@ -71,6 +71,9 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu():
     assert L.batch_create(C.byref(b), arr, 1, 1) == FF.FFT_ERR_ARG
     assert L.batch_create(C.byref(b), arr, 0, 1) == FF.FFT_ERR_ARG
     assert L.batch_size(None) == 0
+    assert L.batch_create_ex(C.byref(b), arr, 1, 1, 4) == FF.FFT_ERR_ARG  # unknown flag
+    assert L.batch_create_ex(C.byref(b), None, 2, 1, 1) == FF.FFT_ERR_ARG
+    assert L.batch_classes(None, -1, None, None, None, None) == 0
     one = (C.c_double * 9)(*np.eye(3).reshape(9))
     assert L.batch_run_increment_mixed(None, one, None, None, one, None, None) == FF.FFT_ERR_ARG
     F9 = (C.c_double * 9)(*np.eye(3).reshape(9))
