@@ -340,7 +340,7 @@ CONFIGS = {
     "poly64": dict(n=(64, 64, 64), grains=50, amplitude=0.006, inc_per_cycle=40, cycles=3,
                    precrack=False, seed=1002),
     "poly128": dict(n=(128, 128, 128), grains=200, amplitude=0.007, inc_per_cycle=40,
-                    cycles=10, precrack=False, seed=1003),
+                    cycles=10, precrack=False, seed=1003, probe=(3, 6)),
     "batch32": dict(sizes=(32, 48, 64, 96), count=32, grains=(20, 150), amplitude=0.006,
                     inc_per_cycle=30, cycles=2, seed=2000),
     "poly64_r0": dict(n=(64, 64, 64), grains=50, amplitude=0.02, inc_per_cycle=40, cycles=2,
