@@ -97,8 +97,8 @@ def ncu_traffic(family, workload):
         d = json.load(open(TRAFFIC_FILE))
     except (OSError, ValueError):
         return None
-    e = d.get(family)
-    if not e or e.get("source_sha1") != source_sha1() or d.get("_workload") != workload:
+    e = d.get(workload, {}).get(family)
+    if not e or e.get("source_sha1") != source_sha1():
         return None
     return e.get("dram_bytes_per_launch")
 
