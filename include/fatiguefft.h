@@ -327,20 +327,21 @@ const char* fft_last_error(fft_rve_t r);
  * Lockstep classes: batch_create groups the handles of one size class (same
  * device, precision, grid and fft_options; the unfused Arnoldi step, CUDA
  * graphs on; by default grids of at most 2^16 voxels, e.g. 40^3, where a
- * GMRES step is latency-bound) into classes of up to 64 members.  Under strain control
- * (batch_run_increment) a class's increments run together: the Newton and
- * GMRES iterations in lockstep over the members still iterating, each Krylov
- * column of the whole class one CUDA graph launch with one batched library
- * transform per direction over the class's 9 x members fields; the damage
- * updates and the cut-backs of a member whose increment did not converge run
- * per member.  Each member's arithmetic is that of its own run_increment.
+ * GMRES step is latency-bound) into classes of up to 64 members.  A class's
+ * increments (batch_run_increment, batch_run_increment_mixed) run together:
+ * the Newton, mixed-control and GMRES iterations in lockstep over the
+ * members still iterating, each Krylov column of the whole class one CUDA
+ * graph launch with one batched library transform per direction over the
+ * class's 9 x members fields; the damage updates and the cut-backs of a
+ * member whose increment did not converge run per member.  Each member's
+ * arithmetic is that of its own run_increment(_mixed).
  * The class holds the members' Arnoldi-step scratch and reduction buffers
  * in arenas while the batch exists (the handles stay usable on their own,
  * from the thread that owns the batch, between batch calls); destroy the
- * batch before any of its handles.  Mixed control runs every handle on
- * its own.  batch_create_ex flags: bit 0 = classes of grids up to 2^16
- * voxels, bit 1 = classes at any grid size, 0 = no classes (other bits:
- * FFT_ERR_ARG); batch_create = batch_create_ex with flags 1.  batch_classes returns the number of classes and, per class,
+ * batch before any of its handles.  batch_create_ex flags: bit 0 = classes
+ * of grids up to 2^16 voxels, bit 1 = classes at any grid size, 0 = no
+ * classes (other bits: FFT_ERR_ARG); batch_create = batch_create_ex with
+ * flags 1.  batch_classes returns the number of classes and, per class,
  * its member count, the column graphs launched so far and, while timing is
  * on, the device milliseconds of those launches (CUDA events on the class's
  * stream) and their algorithmic bytes (the two 9-field transforms, tangent

@@ -2,7 +2,7 @@
 //
 // Each handle keeps its own stream and device buffers.  Handles of one size
 // class (same grid, precision and solver options) form a lockstep class
-// (gang.cu): under strain control their increments run together, every
+// (gang.cu): under strain or mixed control their increments run together, every
 // Krylov column of the whole class one graph launch with one batched
 // transform per direction.  A pool of host threads (native, persistent
 // across increments) drives the classes and the remaining single handles
@@ -29,8 +29,9 @@ size_t fatfft_rve_voxels(fft_rve_t r);
 void fatfft_rve_set_poll(fft_rve_t r, bool on);
 int fatfft_gang_compatible(fft_rve_t a, fft_rve_t b);
 fft_status fatfft_gang_create(fft_rve_t const* members, int n, void** out);
-fft_status fatfft_gang_run(void* g, const double* const* Fbar, const double* dt,
-                           fft_stats** stats, int* status);
+fft_status fatfft_gang_run(void* g, const double* const* Fbar, const double* const* Pstar,
+                           const int32_t* const* mask, const double* dt, fft_stats** stats,
+                           int* status);
 long long fatfft_gang_graph_launches(void* g);
 void fatfft_gang_timing(void* g, int on, double* ms, double* bytes);
 void fatfft_gang_destroy(void* g);
@@ -75,8 +76,7 @@ struct fft_batch_s {
     long long gen = 0;
     bool quit = false;
 
-    // the units of the current call: the classes (strain control) or every
-    // handle alone (mixed control)
+    // the units of a call: the classes and the single handles
     bool use_units = false;
     int njobs() const { return use_units ? (int)units.size() : (int)rves.size(); }
 
@@ -97,17 +97,21 @@ struct fft_batch_s {
             return;
         }
         const size_t n = u.idx.size();
-        std::vector<const double*> F(n);
+        std::vector<const double*> F(n), P(n);
+        std::vector<const int32_t*> M(n);
         std::vector<double> d(n);
         std::vector<fft_stats*> sp(n);
         std::vector<int> st(n, (int)FFT_ERR_CUDA);
         for (size_t k = 0; k < n; ++k) {
             const int i = u.idx[k];
             F[k] = Fbar + 9 * (size_t)i;
+            P[k] = Pbar ? Pbar + 9 * (size_t)i : nullptr;
+            M[k] = mask ? mask + 9 * (size_t)i : nullptr;
             d[k] = dt[i];
             sp[k] = stats ? stats + i : nullptr;
         }
-        fatfft_gang_run(u.gang, F.data(), d.data(), sp.data(), st.data());
+        fatfft_gang_run(u.gang, F.data(), mask ? P.data() : nullptr, mask ? M.data() : nullptr,
+                        d.data(), sp.data(), st.data());
         for (size_t k = 0; k < n; ++k) status[u.idx[k]] = st[k];
     }
 
@@ -220,7 +224,7 @@ static fft_status run_job(fft_batch_t b, const double* Fbar, const double* Pbar,
         b->status = st.data();
         b->next = 0;
         b->done = 0;
-        b->use_units = mask == nullptr;
+        b->use_units = true;
         ++b->gen;
         b->cv_work.notify_all();
         b->cv_done.wait(lk, [&] { return b->done == b->njobs(); });

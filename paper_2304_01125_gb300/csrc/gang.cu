@@ -690,17 +690,21 @@ struct Gang {
         }
     }
 
-    // One load increment under strain control for every member (run_increment
-    // of the single-handle driver): the staggered loop in lockstep, then
-    // cut-backs of the members that did not converge, one by one.
-    static void run_increment(GangBase* g, const double* const* Fbar, const double* dt,
-                              fft_stats** stats, fft_status* st) {
+    // One load increment for every member (run_increment of the
+    // single-handle driver, under strain or mixed control): the staggered
+    // loop in lockstep, then cut-backs of the members that did not converge,
+    // each on its own host thread.
+    static void run_increment(GangBase* g, const double* const* Fbar, const double* const* Pstar,
+                              const int32_t* const* mask, const double* dt, fft_stats** stats,
+                              fft_status* st) {
         const int B = g->B;
         std::vector<int> all(B), A;
         for (int i = 0; i < B; ++i) all[i] = i;
         for_members(g, all, [&](int i) {
             if (stats[i]) std::memset(stats[i], 0, sizeof(fft_stats));
-            st[i] = I::apply_increment(g->m[i], Fbar[i], dt[i]);
+            st[i] = mask ? I::apply_increment_mixed(g->m[i], Fbar[i], Pstar ? Pstar[i] : nullptr,
+                                                    mask[i], dt[i])
+                         : I::apply_increment(g->m[i], Fbar[i], dt[i]);
         });
         for (int i = 0; i < B; ++i)
             if (st[i] == FFT_OK) A.push_back(i);
@@ -731,7 +735,23 @@ struct Gang {
                 }
                 E.push_back(i);
             }
-            newton(g, E, stats, st);
+            // Newton, then under mixed control the outer rounds of
+            // Impl::mixed_step, until every member's stress targets hold
+            for (int outer = 0; !E.empty(); ++outer) {
+                newton(g, E, stats, st);
+                for_members(g, E, [&](int i) {
+                    more[i] = 0;
+                    fft_rve_s* r = g->m[i];
+                    if (st[i] != FFT_OK || !r->mixed) return;
+                    bool done = false;
+                    st[i] = I::mixed_step(r, stats[i], outer, &done);
+                    more[i] = st[i] == FFT_OK && !done;
+                });
+                std::vector<int> again;
+                for (int i : E)
+                    if (more[i]) again.push_back(i);
+                E.swap(again);
+            }
             // the damage update of every member, each with its own host
             // round trips (phase-field CG, staggered test), side by side
             for_members(g, A, [&](int i) {
@@ -767,7 +787,8 @@ struct Gang {
             cut.emplace_back([=] {
                 st[i] = cudaSetDevice(r->dev) != cudaSuccess
                             ? FFT_ERR_CUDA
-                            : I::run_halves(r, Fbar[i], nullptr, nullptr, dt[i], stats[i], 1);
+                            : I::run_halves(r, Fbar[i], Pstar && mask ? Pstar[i] : nullptr,
+                                            mask ? mask[i] : nullptr, dt[i], stats[i], 1);
             });
         }
         for (auto& t : cut) t.join();
@@ -906,18 +927,21 @@ fft_status fatfft_gang_create(fft_rve_t const* members, int n, void** out) {
     return FFT_OK;
 }
 
-// One increment under strain control for every member: Fbar[i] (9 doubles)
-// and dt[i] of member i, stats[i] nullable, status[i] per member.
-fft_status fatfft_gang_run(void* gp, const double* const* Fbar, const double* dt,
-                           fft_stats** stats, int* status) {
+// One increment for every member: Fbar[i] (9 doubles) and dt[i] of member
+// i; with mask (nullable: strain control) the mixed control of
+// run_increment_mixed, mask[i] (9 flags) and Pstar[i] (nullable arrays);
+// stats[i] nullable, status[i] per member.
+fft_status fatfft_gang_run(void* gp, const double* const* Fbar, const double* const* Pstar,
+                           const int32_t* const* mask, const double* dt, fft_stats** stats,
+                           int* status) {
     GangBase* g = (GangBase*)gp;
     if (!g) return FFT_ERR_ARG;
     if (cudaSetDevice(g->m[0]->dev) != cudaSuccess) return FFT_ERR_CUDA;
     std::vector<fft_status> st(g->B, FFT_OK);
     if (g->m[0]->prec == FFT_PREC_FP64)
-        Gang<double>::run_increment(g, Fbar, dt, stats, st.data());
+        Gang<double>::run_increment(g, Fbar, Pstar, mask, dt, stats, st.data());
     else
-        Gang<float>::run_increment(g, Fbar, dt, stats, st.data());
+        Gang<float>::run_increment(g, Fbar, Pstar, mask, dt, stats, st.data());
     fft_status worst = FFT_OK;
     for (int i = 0; i < g->B; ++i) {
         status[i] = (int)st[i];

@@ -389,3 +389,46 @@ def test_closing_a_class_member_closes_its_batch_first():
         s, st = r.run_increment(*I.uniaxial_cycle_program(0.004, 8, 1)[1])
         assert s == FF.FFT_OK and st["lin_it_total"] >= 0
         r.close()
+
+
+@pytest.mark.parametrize("prec,grid", [("fp64", (10, 8, 6)), ("mixed", (10, 8, 6)),
+                                       ("mixed", (16, 16, 1))])
+def test_lockstep_class_under_mixed_control(prec, grid):
+    """batch_run_increment_mixed with the handles in one lockstep class (three
+    polycrystals of one grid under uniaxial stress, the lateral mean stresses
+    zero; a 16 x 16 x 1 grid is a set of plates under plane stress): the
+    outer mixed-control rounds run in lockstep too, and every handle's solved
+    F, statistics and fields equal those of the handle run alone with
+    run_increment_mixed."""
+    m = I.uniaxial_stress_mask(1)
+    prog = I.uniaxial_cycle_program(0.006, 24, 1)[:4]
+
+    def guesses(prev, Fb):
+        return [Fb.copy() if p is None else np.where(m == 1, p, Fb) for p in prev]
+
+    rves = [_make(grid, 100 + i, prec) for i in range(3)]
+    b = FF.Batch(rves, threads=2)
+    assert b.classes()[0][0] == 3
+    prev = [None] * 3
+    got = [[] for _ in rves]
+    for Fb, dt in prog:
+        s, per, stats = b.run_increment(guesses(prev, Fb), [dt] * 3, stress_masks=[m] * 3)
+        assert s == FF.FFT_OK and all(x["mixed_it"] >= 1 for x in stats)
+        prev = [np.array(x["Fbar"]) for x in stats]
+        for i, x in enumerate(stats):
+            got[i].append((x["newton_it"], x["lin_it_total"], x["mixed_it"], x["stag_it"]))
+    b.close()
+    for i in range(3):
+        r = _make(grid, 100 + i, prec)
+        p = None
+        mine = []
+        for Fb, dt in prog:
+            _, st = r.run_increment(guesses([p], Fb)[0], dt, Pbar=np.zeros(9), stress_mask=m)
+            p = np.array(st["Fbar"])
+            mine.append((st["newton_it"], st["lin_it_total"], st["mixed_it"], st["stag_it"]))
+        assert mine == got[i] and np.array_equal(p, prev[i])
+        for f in ("F", "P", "Fp", "gamma"):
+            assert np.array_equal(r.field(f), rves[i].field(f)), (i, f)
+        r.close()
+    for r in rves:
+        r.close()
