@@ -29,6 +29,12 @@
  *    increment nothing is committed; the handle still accepts fields_out,
  *    apply_increment (restarting from the committed state) and rve_destroy.
  *  - One handle must not be used from two threads at the same time.
+ *  - Environment variables read at init_rve (diagnostics and measurement;
+ *    the defaults are the tested configuration): FATIGUEFFT_VERBOSE (solver
+ *    traces on stderr), FATIGUEFFT_GRAPHS=0 (no per-column CUDA graphs),
+ *    FATIGUEFFT_DOT64=1 (FP64 per-thread sums in the Arnoldi dot pass),
+ *    FATIGUEFFT_FUSED / FATIGUEFFT_BULK (the kernel-variant bits, see
+ *    fft_options.kernel_variant), FATIGUEFFT_PROF_SAMPLE (see rve_profile).
  */
 #ifndef FATIGUEFFT_H
 #define FATIGUEFFT_H
