@@ -536,8 +536,10 @@ def run_ours(a):
 
 def run_batch(a, short=False):
     """The batched workload: 32 polycrystals with grids from {32,48,64,96}^3
-    and 20-150 grains, advanced together (batch_run_increment, one stream
-    per RVE), mixed precision.  A step is one load increment of every RVE."""
+    (`batch32`; `batch32x32`: 32 of 32^3) and 20-150 grains, advanced
+    together (batch_run_increment: lockstep size classes, other handles on
+    their own streams), mixed precision.  A step is one load increment of
+    every RVE."""
     import torch
 
     from paper_2304_01125_gb300 import build as B
@@ -547,7 +549,7 @@ def run_batch(a, short=False):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     B.build()
-    c = I.CONFIGS["batch32"]
+    c = I.CONFIGS[a.config if a.config.startswith("batch") else "batch32"]
     cfgs = I.batch_configs(seed=c["seed"], count=c["count"], sizes=c["sizes"],
                            grains=c["grains"])
     prog = I.uniaxial_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"])
@@ -701,7 +703,8 @@ def batch_line(a, ws, rank, cfgs, sizes, Ntot, ms, value, e2e_s, serial_s, launc
         "ms_per_step": round(sum(ms) / a.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded periodic Voronoi, uniform SO(3) orientations)",
-        "config": {"workload": f"batch32: {len(cfgs)} RVEs, grids "
+        "config": {"workload": f"{a.config if a.config.startswith('batch') else 'batch32'}: "
+                               f"{len(cfgs)} RVEs, grids "
                                + ", ".join(f"{k}^3 x{v}" for k, v in sorted(sizes.items()))
                                + f" ({Ntot} voxels), 20-150 grains, R=-1 uniaxial strain 0.6%, "
                                f"30 increments/cycle, increments {a.warmup + 1}-"
@@ -811,7 +814,7 @@ def main():
     a = args_()
     if a.impl == "reference":
         line = run_reference(a)
-    elif a.config == "batch32":
+    elif a.config in ("batch32", "batch32x32"):
         line = run_batch(a)
     else:
         line = run_ours(a)

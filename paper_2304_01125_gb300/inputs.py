@@ -343,6 +343,9 @@ CONFIGS = {
                     cycles=10, precrack=False, seed=1003, probe=(3, 6)),
     "batch32": dict(sizes=(32, 48, 64, 96), count=32, grains=(20, 150), amplitude=0.006,
                     inc_per_cycle=30, cycles=2, seed=2000),
+    # the same loading on 32 small cells of one size (one lockstep class)
+    "batch32x32": dict(sizes=(32,), count=32, grains=(20, 150), amplitude=0.006,
+                       inc_per_cycle=30, cycles=2, seed=3000),
     "poly64_r0": dict(n=(64, 64, 64), grains=50, amplitude=0.02, inc_per_cycle=40, cycles=2,
                       precrack=False, seed=1002, ratio=0, control="uniaxial_stress"),
     # 2-D plates (one voxel thick, plane stress through mixed control)

@@ -84,7 +84,8 @@ def option_overrides(tol, pairs):
 
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    p.add_argument("--config", default="poly64", choices=sorted(I.CONFIGS))
+    p.add_argument("--config", default="poly64",
+                   choices=sorted(k for k in I.CONFIGS if "sizes" not in I.CONFIGS[k]))
     p.add_argument("--increments", type=int, default=10)
     p.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--tol", default="paper", choices=["paper", "parity32", "parity64"])
