@@ -41,7 +41,7 @@ constexpr int kClassMax = 64;  // members of one lockstep class
 // Classes form by default only for grids of at most 2^16 voxels (40^3):
 // there a GMRES step is mostly launch and synchronisation latency (about
 // 0.09 ms per step from 16^3 to 32^3 on GB300), which one graph launch for
-// the class amortises (32 RVEs of 32^3: 43.1 M against 40.0 M
+// the class amortises (32 RVEs of 32^3: 49.1 M against 40.4 M
 // voxel-increments/s on their own streams; of 16^3: 12.2 M against 10.0 M);
 // from 48^3 on a step is increasingly bandwidth-bound and lockstep gains
 // nothing over concurrent streams (16 of 48^3: 43.0 M against 43.7 M), it
