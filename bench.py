@@ -529,6 +529,19 @@ def run_ours(a):
                                                    "kernel_variants")}
         line["batch_window"]["workload"] = bl["config"]["workload"]
         line["batch_window"]["parallelism"] = bl["config"]["parallelism"]
+        # 32 cells of 32^3 (one lockstep class) against the same cells on
+        # 32 streams: where the lockstep classes pay
+        small = {}
+        for cls in (True, False):
+            b2 = copy.copy(b)
+            b2.config, b2.no_classes, b2.classes_all = "batch32x32", not cls, False
+            sl = run_batch(b2, short=True)
+            small["classes" if cls else "streams"] = {
+                "value": sl["value"], "ms_per_step": sl["ms_per_step"],
+                "voxel_gmres_per_s": sl["iterations"]["voxel_gmres_per_s"]}
+        small["workload"] = sl["config"]["workload"]
+        small["unit"] = "voxel-increments/s"
+        line["batch_window_32x32"] = small
     if ws == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, mat, opts, a)
     return line
