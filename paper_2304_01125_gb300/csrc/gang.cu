@@ -32,6 +32,12 @@
 namespace {
 
 constexpr int kGangMax = 64;
+// Sparse mode (see the GMRES cycle) starts once kSparse x (members still
+// iterating) < members; 0 never starts it.
+#ifndef FATIGUEFFT_SPARSE_FACTOR
+#define FATIGUEFFT_SPARSE_FACTOR 2
+#endif
+constexpr int kSparse = FATIGUEFFT_SPARSE_FACTOR;
 constexpr int kGangHelpers = 7;  // host threads besides the caller per class
 
 // Fork-join helper threads of a class: run(n, f) calls f(0) .. f(n-1), the
@@ -362,7 +368,7 @@ struct Gang {
             // batched transforms would mostly transform idle members, so the
             // rest of the cycle runs each member's own step graph (the
             // single-handle driver's, on its stream and its arena slot).
-            bool sparse = 2 * (int)C.size() < B;
+            bool sparse = kSparse * (int)C.size() < B;
             std::vector<char> col_sparse(mres + 1, 0);
             // first column of the cycle: V_0 = src / beta and its gradient
             // spectrum, per member, before the class stream's column graphs
@@ -400,7 +406,7 @@ struct Gang {
             auto launch = [&](int j) -> fft_status {
                 int na = 0;
                 for (int i : C) na += in_cycle[i] ? 1 : 0;
-                if (!sparse && j >= 1 && 2 * na < B) {
+                if (!sparse && j >= 1 && kSparse * na < B) {
                     // switch: the members' streams follow the class stream
                     sparse = true;
                     CK(r0, cudaEventRecord(g->ev_a, g->st));
