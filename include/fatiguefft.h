@@ -342,9 +342,11 @@ const char* fft_last_error(fft_rve_t r);
  * member whose increment did not converge run per member.  Each member's
  * arithmetic is that of its own run_increment(_mixed).
  * The class holds the members' Arnoldi-step scratch and reduction buffers
- * in arenas while the batch exists (the handles stay usable on their own,
- * from the thread that owns the batch, between batch calls); destroy the
- * batch before any of its handles.  batch_create_ex flags: bit 0 = classes
+ * in arenas while the batch exists (18 real-field components per voxel, in
+ * the handle's precision, plus 2 KB per member; the members' own buffers
+ * stay allocated and are used again after batch_destroy).  The handles stay
+ * usable on their own, from the thread that owns the batch, between batch
+ * calls; destroy the batch before any of its handles.  batch_create_ex flags: bit 0 = classes
  * of grids up to 2^16 voxels, bit 1 = classes at any grid size, 0 = no
  * classes (other bits: FFT_ERR_ARG); batch_create = batch_create_ex with
  * flags 1.  batch_classes returns the number of classes and, per class,
