@@ -57,3 +57,24 @@ def test_workload_options_and_description():
     assert bench.workload_desc("poly64", strain).startswith(
         "poly64: 4x4x4 voxels, 50 grains, R=-1 uniaxial strain 0.6%")
     assert "R=0 uniaxial stress (mixed control) 2%" in bench.workload_desc("poly64_r0", mixed)
+
+
+def test_committed_traffic_applies_only_to_its_workload_and_sources(tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed ncu summary only for the
+    workload it was captured on and while the kernel sources hash to the
+    recorded value."""
+    import json
+    sha = bench.source_sha1()
+    f = tmp_path / "t.json"
+    f.write_text(json.dumps({"poly64": {"gmres_dot": {"dram_bytes_per_launch": 123,
+                                                      "source_sha1": sha}},
+                             "poly128": {"gmres_dot": {"dram_bytes_per_launch": 7,
+                                                       "source_sha1": "old"}}}))
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench.ncu_traffic("gmres_dot", "poly64") == 123
+    assert bench.ncu_traffic("gmres_dot", "poly256") is None  # other workload
+    assert bench.ncu_traffic("gmres_dot", "poly128") is None  # other kernel sources
+    assert bench.ncu_traffic("tangent_apply", "poly64") is None
+    # the committed summary itself matches the current sources for the 64^3 workload
+    monkeypatch.undo()
+    assert bench.ncu_traffic("gmres_dot", "poly64") is not None
