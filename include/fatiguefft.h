@@ -177,7 +177,11 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
 /* Start a load increment (Algorithm 1 data): commits the previous increment
  * if it converged, sets F_0 = F_t + (Fbar_target - Fbar_t) uniformly,
  * phi^0 = phi_t, the step dt (s), and computes rho_GND from the committed
- * F_p (Nye tensor, Eq. nyeindexfourier, with the F_p regularisation). */
+ * F_p (Nye tensor, Eq. nyeindexfourier, with the F_p regularisation).
+ * A non-finite target component or dt, or dt < 0: FFT_ERR_ARG before
+ * anything runs (the same for every call below that takes targets,
+ * including the batch calls).  A non-finite value that arises in the solve
+ * (from a state set with fields_in, say) stops it with FFT_ERR_NONFINITE. */
 fft_status apply_increment(fft_rve_t r, const double Fbar_target[9], double dt);
 
 /* One "solve Eq. momentum" line of Algorithm 1: Newton-Krylov at the current

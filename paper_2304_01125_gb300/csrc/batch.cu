@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <mutex>
@@ -210,8 +211,13 @@ static fft_status run_job(fft_batch_t b, const double* Fbar, const double* Pbar,
                           int* status) {
     if (!b || !Fbar || !dt) return FFT_ERR_ARG;
     const int n = (int)b->rves.size();
-    for (int i = 0; i < n; ++i)
-        if (!(dt[i] >= 0)) return FFT_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!(dt[i] >= 0) || !std::isfinite(dt[i])) return FFT_ERR_ARG;
+        for (int c = 0; c < 9; ++c)
+            if (!std::isfinite(Fbar[9 * (size_t)i + c]) ||
+                (Pbar && !std::isfinite(Pbar[9 * (size_t)i + c])))
+                return FFT_ERR_ARG;
+    }
     std::vector<int> st(n, (int)FFT_OK);
     std::lock_guard<std::mutex> serial(b->call);
     {

@@ -193,6 +193,15 @@ void ckpt_parts(fft_rve_s* r, CkptPart out[4]) {
 }
 }  // namespace
 
+// a macroscopic target (9 values; nullptr: none) is finite, and dt is
+// finite and non-negative
+static bool finite_targets(const double* a, const double* b, double dt) {
+    if (!(dt >= 0) || !std::isfinite(dt)) return false;
+    for (int c = 0; c < 9; ++c)
+        if ((a && !std::isfinite(a[c])) || (b && !std::isfinite(b[c]))) return false;
+    return true;
+}
+
 extern "C" {
 
 fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_ids, int n_grains,
@@ -446,19 +455,19 @@ fft_status init_rve(fft_rve_t* out, const fft_grid* grid, const int32_t* grain_i
 }
 
 fft_status apply_increment(fft_rve_t r, const double Fbar_target[9], double dt) {
-    if (!r || !Fbar_target || !(dt >= 0)) return FFT_ERR_ARG;
+    if (!r || !Fbar_target || !finite_targets(Fbar_target, nullptr, dt)) return FFT_ERR_ARG;
     return DISPATCH(r, apply_increment(r, Fbar_target, dt));
 }
 
 fft_status apply_increment_mixed(fft_rve_t r, const double Fbar[9], const double Pbar[9],
                                  const int32_t mask[9], double dt) {
-    if (!r || !Fbar || !mask || !(dt >= 0)) return FFT_ERR_ARG;
+    if (!r || !Fbar || !mask || !finite_targets(Fbar, Pbar, dt)) return FFT_ERR_ARG;
     return DISPATCH(r, apply_increment_mixed(r, Fbar, Pbar, mask, dt));
 }
 
 fft_status run_increment_mixed(fft_rve_t r, const double Fbar[9], const double Pbar[9],
                                const int32_t mask[9], double dt, fft_stats* st) {
-    if (!r || !Fbar || !mask || !(dt >= 0)) return FFT_ERR_ARG;
+    if (!r || !Fbar || !mask || !finite_targets(Fbar, Pbar, dt)) return FFT_ERR_ARG;
     if (st) std::memset(st, 0, sizeof(*st));
     fft_status s = DISPATCH(r, run_increment(r, Fbar, Pbar, mask, dt, st));
     if (s == FFT_OK && host_wait(r) != cudaSuccess) return FFT_ERR_CUDA;
@@ -483,7 +492,7 @@ fft_status commit_increment(fft_rve_t r) {
 }
 
 fft_status run_increment(fft_rve_t r, const double Fbar_target[9], double dt, fft_stats* st) {
-    if (!r || !Fbar_target || !(dt >= 0)) return FFT_ERR_ARG;
+    if (!r || !Fbar_target || !finite_targets(Fbar_target, nullptr, dt)) return FFT_ERR_ARG;
     if (st) std::memset(st, 0, sizeof(*st));
     fft_status s = DISPATCH(r, run_increment(r, Fbar_target, nullptr, nullptr, dt, st));
     if (s == FFT_OK && host_wait(r) != cudaSuccess) return FFT_ERR_CUDA;

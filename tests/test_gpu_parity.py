@@ -907,3 +907,43 @@ def test_kernel_variant_option_and_autotuner(monkeypatch, tmp_path):
         entry = next(iter(json.load(fh).values()))
     assert entry["kernel_variant"] == best
     assert all(t > 0 for t in entry["ms_per_gmres_iteration"].values())
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_non_finite_inputs_and_state(prec):
+    """A NaN in a macroscopic target or the step is refused at the boundary
+    (FFT_ERR_ARG, nothing runs); a NaN planted in the committed state with
+    fields_in stops the next increment with FFT_ERR_NONFINITE instead of
+    iterating on it; after the state is set right again the handle solves
+    the increment as a fresh handle does, bit for bit."""
+    n = (6, 6, 6)
+    gid, eul = I.voronoi(n, 3, 11)
+    prog = I.uniaxial_cycle_program(0.004, 8, 1)
+    r = FF.RVE(n, H, gid, eul, MAT, opts_for(prec), prec=prec, stream=stream())
+    ref = FF.RVE(n, H, gid, eul, MAT, opts_for(prec), prec=prec, stream=stream())
+    Fb, dt = prog[0]
+    bad = Fb.copy()
+    bad[4] = np.nan
+    s, _ = r.run_increment(bad, dt, check=False)
+    assert s == FF.FFT_ERR_ARG
+    s, _ = r.run_increment(Fb, float("inf"), check=False)
+    assert s == FF.FFT_ERR_ARG
+    s, _ = r.run_increment(Fb, dt, Pbar=np.full(9, np.nan), stress_mask=I.uniaxial_stress_mask(1),
+                           check=False)
+    assert s == FF.FFT_ERR_ARG
+    for x in (r, ref):
+        assert x.run_increment(Fb, dt)[0] == FF.FFT_OK
+    Ft = r.field("Ft")
+    poisoned = Ft.copy()
+    poisoned[4, 7] = np.nan
+    r.set_field("Ft", poisoned)
+    s, _ = r.run_increment(*prog[1], check=False)
+    assert s == FF.FFT_ERR_NONFINITE
+    assert "non-finite" in FF.load().fft_last_error(r._h).decode()
+    r.set_field("Ft", Ft)
+    for x in (r, ref):
+        assert x.run_increment(*prog[1])[0] == FF.FFT_OK
+    for f in ("F", "P", "Fp"):
+        assert np.array_equal(r.field(f), ref.field(f)), f
+    r.close()
+    ref.close()
