@@ -109,3 +109,18 @@ def test_kernel_variant_option():
     for v in range(4):
         assert FF._options(I.solver_options("paper", kernel_variant=v), "fp64",
                            None).kernel_variant == v
+
+
+def test_header_is_plain_c():
+    """The boundary header compiles as C99 (no C++ in the C ABI)."""
+    import os
+    import shutil
+    import subprocess
+    import pytest
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                       "fatiguefft.h")
+    subprocess.run([cc, "-fsyntax-only", "-std=c99", "-Wall", "-Werror", "-x", "c", hdr],
+                   check=True)
