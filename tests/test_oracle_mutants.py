@@ -11,7 +11,7 @@ import pytest
 
 import oracle as O
 from oracle import build as OB
-from test_oracle_pins import history_chain_check
+from test_oracle_pins import history_chain_check, local_solve_check
 
 MUTANTS = {
     # Eq. Gs / R10: the stored energy increment divides by the density after
@@ -28,8 +28,29 @@ MUTANTS = {
 }
 
 
+# mistakes in the local crystal-plasticity update (Sec. 2.1), against the
+# pin that restates it and solves it by another method
+MUTANTS_CP = {
+    # the implicit update F_p^-1 = F_pn^-1 (I - sum dgamma s (x) n) with the
+    # sign of the plastic increment flipped
+    "fp_update_sign": ("cp.cpp", "ev.M = sub(eye3(), dL);", "ev.M = add(eye3(), dL);"),
+    # Taylor hardening without the GND density
+    "hardening_without_gnd": ("cp.cpp", "std::sqrt(rho_ssd_n + rho_gnd)",
+                              "std::sqrt(rho_ssd_n)"),
+    # the elastic strain as the small-strain sym(F_e) - I instead of
+    # (F_e^T F_e - I) / 2
+    "small_strain_measure": ("cp.cpp",
+                             "const M3 Ee = scale(sub(mul(tr(ev.Fe), ev.Fe), eye3()), 0.5);\n"
+                             "    ev.S = cubic_apply(m, Ee);",
+                             "const M3 Ee = sub(scale(add(ev.Fe, tr(ev.Fe)), 0.5), eye3());\n"
+                             "    ev.S = cubic_apply(m, Ee);"),
+    # the thermal stress kT / dV with dV left in mm^3 (tau dV in N mm)
+    "thermal_stress_units": ("cp.cpp", "kT / (m.dV * 1e-3)", "kT / m.dV"),
+}
+
+
 def _build_mutant(tmp, name):
-    fname, old, new = MUTANTS[name]
+    fname, old, new = {**MUTANTS, **MUTANTS_CP}[name]
     src = os.path.join(tmp, "src")
     os.makedirs(src, exist_ok=True)
     for f in OB.SOURCES + ["oracle.h", "oracle_internal.hpp"]:
@@ -51,3 +72,11 @@ def test_history_pin_catches_mutant(name, tmp_path):
         with pytest.raises(AssertionError):
             history_chain_check()
     history_chain_check()  # the committed oracle still passes
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_CP))
+def test_local_solve_pin_catches_mutant(name, tmp_path):
+    path = _build_mutant(str(tmp_path), name)
+    with O.library(path):
+        with pytest.raises(AssertionError):
+            local_solve_check()

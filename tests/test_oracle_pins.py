@@ -281,6 +281,10 @@ def test_local_solve_robust_on_extreme_states():
 
 
 def test_local_solve_matches_an_independent_solver():
+    local_solve_check()
+
+
+def local_solve_check():
     """Sec. 2.1, Eqs. flowrule and the multiplicative split: the local slip
     problem restated here from the paper (F_p^-1 = F_pn^-1 (I - sum dg s(x)n),
     F_e = F F_p^-1 in the lattice frame, S = C : (F_e^T F_e - I)/2 through the
