@@ -11,6 +11,7 @@ import pytest
 
 import oracle as O
 from oracle import build as OB
+import test_oracle_pins as pins
 from test_oracle_pins import history_chain_check, local_solve_check
 
 MUTANTS = {
@@ -49,8 +50,28 @@ MUTANTS_CP = {
 }
 
 
+# mistakes in the phase-field solve (Eqs. strpf, phase), against its
+# closed-form pins (uniform source, exact discrete point source, 1-D profile)
+MUTANTS_PF = {
+    # the reaction term (1 + 2S) phi written as (1 + S) phi
+    "pf_reaction_factor": ("rve.cpp", "y[v] += (1.0 + 2.0 * S[v]) * x[v];",
+                           "y[v] += (1.0 + S[v]) * x[v];"),
+    # the right-hand side 2S written as S
+    "pf_source_factor": ("rve.cpp", "r[v] = 2.0 * S[v] - q[v];", "r[v] = S[v] - q[v];"),
+    # the length scale entering the operator unsquared
+    "pf_ell_unsquared": ("rve.cpp", "const double l2 = ell * ell;\n    std::vector<double> lap_w",
+                         "const double l2 = ell;\n    std::vector<double> lap_w"),
+}
+
+
+def phase_field_checks():
+    pins.test_phase_field_uniform_source()
+    pins.test_phase_field_point_source_exact()
+    pins.test_phase_field_1d_profile_exp()
+
+
 def _build_mutant(tmp, name):
-    fname, old, new = {**MUTANTS, **MUTANTS_CP}[name]
+    fname, old, new = {**MUTANTS, **MUTANTS_CP, **MUTANTS_PF}[name]
     src = os.path.join(tmp, "src")
     os.makedirs(src, exist_ok=True)
     for f in OB.SOURCES + ["oracle.h", "oracle_internal.hpp"]:
@@ -80,3 +101,11 @@ def test_local_solve_pin_catches_mutant(name, tmp_path):
     with O.library(path):
         with pytest.raises(AssertionError):
             local_solve_check()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_PF))
+def test_phase_field_pins_catch_mutant(name, tmp_path):
+    path = _build_mutant(str(tmp_path), name)
+    with O.library(path):
+        with pytest.raises(AssertionError):
+            phase_field_checks()
