@@ -64,6 +64,39 @@ MUTANTS_PF = {
 }
 
 
+# mistakes in the GND stage (Eqs. nye1, nyeindexfourier, the F_p
+# regularisation) and in the cubic elasticity (Sec. 2.1), against their pins
+MUTANTS_NYE = {
+    # the curl taken over the first index of F_p instead of the second
+    "nye_transposed_fp": ("rve.cpp", "* Fh[3 * i + l][v];", "* Fh[3 * l + i][v];"),
+    # the regularisation length entering unsquared
+    "nye_reg_unsquared": ("rve.cpp", "const double l2 = m.ell_Fp * m.ell_Fp;",
+                          "const double l2 = m.ell_Fp;"),
+    # the dislocation densities multiplied by b instead of divided
+    "gnd_times_burgers": ("rve.cpp", "x /= m.b;", "x *= m.b;"),
+}
+MUTANTS_EL = {
+    # tensor shear strains taken as engineering ones: sigma_12 = C44 e_12
+    "cubic_shear_half": ("cp.cpp", "S[1] = S[3] = 2.0 * m.C44 * 0.5 * (E[1] + E[3]);",
+                         "S[1] = S[3] = m.C44 * 0.5 * (E[1] + E[3]);"),
+    # C11 and C12 exchanged on the diagonal
+    "cubic_c11_c12": ("cp.cpp", "S[0] = (m.C11 - m.C12) * E[0] + m.C12 * tr_;",
+                      "S[0] = (m.C12 - m.C11) * E[0] + m.C11 * tr_;"),
+}
+
+
+def nye_checks():
+    pins.test_nye_of_compatible_field_vanishes()
+    pins.test_nye_single_slip_sinusoid()
+    pins.test_nye_constant_fp_and_regulariser()
+
+
+def elastic_checks():
+    pins.test_elastic_uniaxial_closed_form()
+    pins.test_elastic_simple_shear_closed_form()
+    pins.test_elastic_rotated_crystal_frame_covariance()
+
+
 def phase_field_checks():
     pins.test_phase_field_uniform_source()
     pins.test_phase_field_point_source_exact()
@@ -71,7 +104,8 @@ def phase_field_checks():
 
 
 def _build_mutant(tmp, name):
-    fname, old, new = {**MUTANTS, **MUTANTS_CP, **MUTANTS_PF}[name]
+    fname, old, new = {**MUTANTS, **MUTANTS_CP, **MUTANTS_PF, **MUTANTS_NYE,
+                       **MUTANTS_EL}[name]
     src = os.path.join(tmp, "src")
     os.makedirs(src, exist_ok=True)
     for f in OB.SOURCES + ["oracle.h", "oracle_internal.hpp"]:
@@ -109,3 +143,19 @@ def test_phase_field_pins_catch_mutant(name, tmp_path):
     with O.library(path):
         with pytest.raises(AssertionError):
             phase_field_checks()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_NYE))
+def test_gnd_pins_catch_mutant(name, tmp_path):
+    path = _build_mutant(str(tmp_path), name)
+    with O.library(path):
+        with pytest.raises(AssertionError):
+            nye_checks()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_EL))
+def test_elastic_pins_catch_mutant(name, tmp_path):
+    path = _build_mutant(str(tmp_path), name)
+    with O.library(path):
+        with pytest.raises(AssertionError):
+            elastic_checks()

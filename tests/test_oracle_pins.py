@@ -135,6 +135,23 @@ def test_elastic_uniaxial_closed_form():
         assert abs(r["We_plus"] - we) < 1e-12
 
 
+def test_elastic_simple_shear_closed_form():
+    """Sec. 2.1 with S = C:E and tensor (not engineering) shear strains: a
+    [100] crystal under F = I + g e1 (x) e2 below yield has E12 = E21 = g/2,
+    E22 = g^2/2, so S12 = 2 C44 E12 = C44 g, S22 = C11 g^2/2, S11 = S33 =
+    C12 g^2/2, and P = F S."""
+    g = 2e-3
+    F = np.eye(3)
+    F[0, 1] = g
+    r = O.cp_point(MAT, np.eye(3), F, np.eye(3), MAT["rho_ssd0"], 0.0, 1.0)
+    assert r["fail"] == 0 and np.all(r["dgamma"] == 0)
+    E22 = g * g / 2
+    S = np.array([[MAT["C12"] * E22, MAT["C44"] * g, 0.0],
+                  [MAT["C44"] * g, MAT["C11"] * E22, 0.0],
+                  [0.0, 0.0, MAT["C12"] * E22]])
+    assert np.abs(r["P"] - F @ S).max() < 1e-9
+
+
 def test_elastic_rotated_crystal_frame_covariance():
     """Sec. 2.1: rotating the crystal and the loading together leaves the
     response unchanged (P rotates with Q)."""
@@ -531,6 +548,11 @@ def test_nye_single_slip_sinusoid():
     assert np.abs(A @ rvec - Lam / MAT["b"]).max() < 1e-9 * np.abs(Lam / MAT["b"]).max()
     gradn = np.linalg.norm(dg, axis=0) * reg / MAT["b"]
     assert np.all(rho <= gradn * (1 + 1e-9) + 1e-6)
+    # the minimum-norm densities: Ap is the Moore-Penrose inverse of the
+    # basis (NumPy's), and rho_GND is their norm per voxel
+    assert np.abs(Ap - np.linalg.pinv(A)).max() < 1e-10 * np.abs(Ap).max()
+    want_rho = np.linalg.norm(np.linalg.pinv(A) @ Lam, axis=0) / MAT["b"]
+    assert np.abs(rho - want_rho).max() < 1e-9 * want_rho.max()
 
 
 def test_nye_constant_fp_and_regulariser():
