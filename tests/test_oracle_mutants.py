@@ -12,7 +12,7 @@ import pytest
 import oracle as O
 from oracle import build as OB
 import test_oracle_pins as pins
-from test_oracle_pins import history_chain_check, local_solve_check
+from test_oracle_pins import history_chain_check, local_solve_check, staggered_fixed_point_check
 
 MUTANTS = {
     # Eq. Gs / R10: the stored energy increment divides by the density after
@@ -85,6 +85,12 @@ MUTANTS_EL = {
 }
 
 
+# Algorithm 1: the staggered loop stopped after its first pass
+MUTANTS_ALG1 = {
+    "stag_single_pass": ("rve.cpp", "r->converged = cF && cP;", "r->converged = true;"),
+}
+
+
 def nye_checks():
     pins.test_nye_of_compatible_field_vanishes()
     pins.test_nye_single_slip_sinusoid()
@@ -105,7 +111,7 @@ def phase_field_checks():
 
 def _build_mutant(tmp, name):
     fname, old, new = {**MUTANTS, **MUTANTS_CP, **MUTANTS_PF, **MUTANTS_NYE,
-                       **MUTANTS_EL}[name]
+                       **MUTANTS_EL, **MUTANTS_ALG1}[name]
     src = os.path.join(tmp, "src")
     os.makedirs(src, exist_ok=True)
     for f in OB.SOURCES + ["oracle.h", "oracle_internal.hpp"]:
@@ -159,3 +165,11 @@ def test_elastic_pins_catch_mutant(name, tmp_path):
     with O.library(path):
         with pytest.raises(AssertionError):
             elastic_checks()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_ALG1))
+def test_fixed_point_pin_catches_mutant(name, tmp_path):
+    path = _build_mutant(str(tmp_path), name)
+    with O.library(path):
+        with pytest.raises(AssertionError):
+            staggered_fixed_point_check()

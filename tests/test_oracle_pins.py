@@ -1056,6 +1056,52 @@ def test_history_and_driving_force_chain():
     history_chain_check()
 
 
+def _spectral_freqs(n, h):
+    """Angular frequencies per axis, shaped for (n2, n1, n0) arrays."""
+    ks = [2 * np.pi * np.fft.fftfreq(n[d], d=1.0 / n[d]) / (n[d] * h) for d in range(3)]
+    return ks[0][None, None, :], ks[1][None, :, None], ks[2][:, None, None]
+
+
+def staggered_fixed_point_check():
+    """Algorithm 1 converged, at an increment where the crack grows over 13
+    staggered iterations (6^3 three-grain polycrystal, damage parameters of
+    the damage tests, tight tolerances): the degraded stress g(phi) P is in
+    equilibrium (Eq. momentum: i xi_j F{g P}_ij = 0, the derivative zero on
+    the Nyquist frequency of an even axis) and phi solves Eq. phase for the
+    final drive, (1 + 2S) phi - ell^2 lap(phi) = 2S, wherever it lies above
+    phi_t -- both residuals computed here with NumPy's FFT."""
+    n = (6, 6, 6)
+    gid, eul = I.voronoi(n, 3, 31)
+    mat = I.material("baseline", tau_c0=250.0, G_crit=7e-4, xi_store=1.0)
+    prog = I.uniaxial_cycle_program(0.006, 24, 2)
+    r = O.RVE(n, H, gid, eul, mat, I.solver_options("parity64"))
+    for Fb, dt in prog[:26]:
+        assert r.run_increment(Fb, dt)[0] == 0
+    phit = r.field("phi").reshape(n[::-1]).copy()
+    s, st = r.run_increment(*prog[26])
+    assert s == 0 and st["stag_it"] >= 5 and st["pf_it_total"] > 0
+    x, y, z = _spectral_freqs(n, H)
+    # equilibrium of the degraded stress
+    P = r.field("P").reshape((9,) + n[::-1])
+    Ph = np.fft.fftn(P, axes=(1, 2, 3))
+    xd = [np.where(np.isclose(np.abs(k), np.pi / H), 0.0, k) for k in (x, y, z)]
+    div = [sum(1j * xd[j] * Ph[3 * i + j] for j in range(3)) for i in range(3)]
+    scale = np.pi / H * np.abs(Ph).max()
+    assert max(np.abs(d).max() for d in div) < 1e-9 * scale
+    # the phase-field equation where phi is not held at phi_t
+    phi = r.field("phi").reshape(n[::-1])
+    S = r.field("drive").reshape(n[::-1])
+    lap = np.real(np.fft.ifftn(-(x ** 2 + y ** 2 + z ** 2) * np.fft.fftn(phi)))
+    res = (1 + 2 * S) * phi - mat["ell"] ** 2 * lap - 2 * S
+    free = phi > phit + 1e-12
+    assert free.sum() > 0 and phi.max() > 0.05
+    assert np.abs(res[free]).max() < 1e-9 * (2 * S).max()
+
+
+def test_staggered_fixed_point_satisfies_both_equations():
+    staggered_fixed_point_check()
+
+
 def test_mixed_cutback_halves_a_changing_stress_target():
     """Cut-back under mixed control when the stress target changes between
     increments: each half takes half of the load change, so the first half
