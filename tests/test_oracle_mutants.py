@@ -89,6 +89,21 @@ MUTANTS_EL = {
 MUTANTS_ALG1 = {
     "stag_single_pass": ("rve.cpp", "r->converged = cF && cP;", "r->converged = true;"),
 }
+# the Green preconditioner contracted over the wrong indices (Eq. precf),
+# and the mixed-control correction with its sign flipped
+MUTANTS_OPS = {
+    "green_wrong_indices": ("rve.cpp", "s += xi[j] * Kbar[9 * (3 * i + j) + 3 * k + l] * xi[l];",
+                            "s += xi[j] * Kbar[9 * (3 * j + i) + 3 * l + k] * xi[l];"),
+    "mixed_correction_sign": ("rve.cpp", "d[a] = -(Pbar[S[a]] - r->Pstar[S[a]]);",
+                              "d[a] = (Pbar[S[a]] - r->Pstar[S[a]]);"),
+}
+
+
+def ops_checks(name):
+    if name.startswith("green"):
+        pins.test_green_operator_identities()
+    else:
+        pins.test_mixed_control_uniaxial_stress_closed_form()
 
 
 def nye_checks():
@@ -111,7 +126,7 @@ def phase_field_checks():
 
 def _build_mutant(tmp, name):
     fname, old, new = {**MUTANTS, **MUTANTS_CP, **MUTANTS_PF, **MUTANTS_NYE,
-                       **MUTANTS_EL, **MUTANTS_ALG1}[name]
+                       **MUTANTS_EL, **MUTANTS_ALG1, **MUTANTS_OPS}[name]
     src = os.path.join(tmp, "src")
     os.makedirs(src, exist_ok=True)
     for f in OB.SOURCES + ["oracle.h", "oracle_internal.hpp"]:
@@ -173,3 +188,11 @@ def test_fixed_point_pin_catches_mutant(name, tmp_path):
     with O.library(path):
         with pytest.raises(AssertionError):
             staggered_fixed_point_check()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_OPS))
+def test_operator_pins_catch_mutant(name, tmp_path):
+    path = _build_mutant(str(tmp_path), name)
+    with O.library(path):
+        with pytest.raises(AssertionError):
+            ops_checks(name)
