@@ -124,10 +124,13 @@ def phase_field_checks():
     pins.test_phase_field_1d_profile_exp()
 
 
+ALL_MUTANTS = {**MUTANTS, **MUTANTS_CP, **MUTANTS_PF, **MUTANTS_NYE, **MUTANTS_EL,
+               **MUTANTS_ALG1, **MUTANTS_OPS}
+
+
 def _build_mutant(tmp, name):
-    fname, old, new = {**MUTANTS, **MUTANTS_CP, **MUTANTS_PF, **MUTANTS_NYE,
-                       **MUTANTS_EL, **MUTANTS_ALG1, **MUTANTS_OPS}[name]
-    src = os.path.join(tmp, "src")
+    fname, old, new = ALL_MUTANTS[name]
+    src = os.path.join(tmp, "src_" + name)
     os.makedirs(src, exist_ok=True)
     for f in OB.SOURCES + ["oracle.h", "oracle_internal.hpp"]:
         shutil.copy(os.path.join(OB.HERE, f), src)
@@ -141,9 +144,20 @@ def _build_mutant(tmp, name):
     return out
 
 
+@pytest.fixture(scope="module")
+def mutant_libs(tmp_path_factory):
+    """Every mutant built once, concurrently (the compiles dominate)."""
+    from concurrent.futures import ThreadPoolExecutor
+    tmp = str(tmp_path_factory.mktemp("mutants"))
+    names = sorted(ALL_MUTANTS)
+    with ThreadPoolExecutor(max_workers=min(len(names), os.cpu_count() or 1)) as ex:
+        paths = list(ex.map(lambda n: _build_mutant(tmp, n), names))
+    return dict(zip(names, paths))
+
+
 @pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_history_pin_catches_mutant(name, tmp_path):
-    path = _build_mutant(str(tmp_path), name)
+def test_history_pin_catches_mutant(name, mutant_libs):
+    path = mutant_libs[name]
     with O.library(path):
         with pytest.raises(AssertionError):
             history_chain_check()
@@ -151,48 +165,48 @@ def test_history_pin_catches_mutant(name, tmp_path):
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS_CP))
-def test_local_solve_pin_catches_mutant(name, tmp_path):
-    path = _build_mutant(str(tmp_path), name)
+def test_local_solve_pin_catches_mutant(name, mutant_libs):
+    path = mutant_libs[name]
     with O.library(path):
         with pytest.raises(AssertionError):
             local_solve_check()
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS_PF))
-def test_phase_field_pins_catch_mutant(name, tmp_path):
-    path = _build_mutant(str(tmp_path), name)
+def test_phase_field_pins_catch_mutant(name, mutant_libs):
+    path = mutant_libs[name]
     with O.library(path):
         with pytest.raises(AssertionError):
             phase_field_checks()
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS_NYE))
-def test_gnd_pins_catch_mutant(name, tmp_path):
-    path = _build_mutant(str(tmp_path), name)
+def test_gnd_pins_catch_mutant(name, mutant_libs):
+    path = mutant_libs[name]
     with O.library(path):
         with pytest.raises(AssertionError):
             nye_checks()
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS_EL))
-def test_elastic_pins_catch_mutant(name, tmp_path):
-    path = _build_mutant(str(tmp_path), name)
+def test_elastic_pins_catch_mutant(name, mutant_libs):
+    path = mutant_libs[name]
     with O.library(path):
         with pytest.raises(AssertionError):
             elastic_checks()
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS_ALG1))
-def test_fixed_point_pin_catches_mutant(name, tmp_path):
-    path = _build_mutant(str(tmp_path), name)
+def test_fixed_point_pin_catches_mutant(name, mutant_libs):
+    path = mutant_libs[name]
     with O.library(path):
         with pytest.raises(AssertionError):
             staggered_fixed_point_check()
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS_OPS))
-def test_operator_pins_catch_mutant(name, tmp_path):
-    path = _build_mutant(str(tmp_path), name)
+def test_operator_pins_catch_mutant(name, mutant_libs):
+    path = mutant_libs[name]
     with O.library(path):
         with pytest.raises(AssertionError):
             ops_checks(name)
