@@ -124,8 +124,30 @@ def phase_field_checks():
     pins.test_phase_field_1d_profile_exp()
 
 
+# the extensions: Willot's rotated derivative without its edge averaging
+# (R33), the cut-back's first half taking the whole step (R28), the Newton
+# damping switched off (R31)
+MUTANTS_EXT = {
+    "willot_unaveraged": ("rve.cpp", "if (l != j) s *= 0.5 * (1.0 + e[l]);",
+                          "if (l != j) s *= 1.0;"),
+    "cutback_full_dt": ("rve.cpp", "int s = attempt(r, mid, Pmid, mask, 0.5 * dt, st);",
+                        "int s = attempt(r, mid, Pmid, mask, dt, st);"),
+    "no_newton_damping": ("rve.cpp", "alpha = std::max(0.5 * alpha, 1.0 / 16);",
+                          "alpha = alpha;"),
+}
+
+
+def ext_checks(name):
+    if name.startswith("willot"):
+        pins.test_willot_matches_real_space_finite_differences("willot")
+    elif name.startswith("cutback"):
+        pins.test_cutback_equals_explicit_halves()
+    else:
+        pins.test_damped_newton_passes_the_yield_plateau()
+
+
 ALL_MUTANTS = {**MUTANTS, **MUTANTS_CP, **MUTANTS_PF, **MUTANTS_NYE, **MUTANTS_EL,
-               **MUTANTS_ALG1, **MUTANTS_OPS}
+               **MUTANTS_ALG1, **MUTANTS_OPS, **MUTANTS_EXT}
 
 
 def _build_mutant(tmp, name):
@@ -210,3 +232,11 @@ def test_operator_pins_catch_mutant(name, mutant_libs):
     with O.library(path):
         with pytest.raises(AssertionError):
             ops_checks(name)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_EXT))
+def test_extension_pins_catch_mutant(name, mutant_libs):
+    path = mutant_libs[name]
+    with O.library(path):
+        with pytest.raises(AssertionError):
+            ext_checks(name)
