@@ -146,8 +146,42 @@ def ext_checks(name):
         pins.test_damped_newton_passes_the_yield_plateau()
 
 
+# further mistakes in the crystal-plasticity point update (Sec. 2.1), each
+# against the pin that restates the step it breaks
+MUTANTS_KIN = {
+    # the Schmid tensor n (x) s in place of s (x) n
+    "schmid_transposed": ("cp.cpp", "sl.P[a] = outer(sl.s[a], sl.n[a]);",
+                          "sl.P[a] = outer(sl.n[a], sl.s[a]);"),
+    # the first Piola-Kirchhoff stress without the pull-back by F_p^-T
+    "pk1_without_fp": ("cp.cpp", "const M3 PL = mul(ev.Fe, mul(S, FpinvT));",
+                       "const M3 PL = mul(ev.Fe, S);"),
+    # F rotated into the lattice frame with Q and Q^T exchanged
+    "lattice_frame_transposed": ("cp.cpp", "const M3 FL = mul(tr(Q), mul(F, Q));",
+                                 "const M3 FL = mul(Q, mul(F, tr(Q)));"),
+    # the SSD increment without the 2/3 of the equivalent plastic strain
+    "ssd_rate_factor": ("cp.cpp", "m.lambda_h * std::sqrt(2.0 / 3.0 * ddot(dL, dL))",
+                        "m.lambda_h * std::sqrt(ddot(dL, dL))"),
+    # the reference slip dt g0 of Eq. flowrule without the time step
+    "rate_without_dt": ("cp.cpp", "tau_c, dt * g0, sT", "tau_c, g0, sT"),
+    # the consistent tangent without the change of F_p^-1 with the slips
+    "tangent_without_slip_term": ("cp.cpp", "mul(mul(Fes, dM), SFpinvT)",
+                                  "scale(mul(mul(Fes, dM), SFpinvT), 0.0)"),
+}
+
+
+def kin_checks(name):
+    if name.startswith("ssd"):
+        pins.test_single_slip_by_bisection(1.0)
+    elif name.startswith("rate"):
+        pins.test_slip_rate_limits()
+    elif name.startswith("tangent"):
+        pins.test_tangent_matches_finite_differences(1)
+    else:
+        local_solve_check()
+
+
 ALL_MUTANTS = {**MUTANTS, **MUTANTS_CP, **MUTANTS_PF, **MUTANTS_NYE, **MUTANTS_EL,
-               **MUTANTS_ALG1, **MUTANTS_OPS, **MUTANTS_EXT}
+               **MUTANTS_ALG1, **MUTANTS_OPS, **MUTANTS_EXT, **MUTANTS_KIN}
 
 
 def _build_mutant(tmp, name):
@@ -240,3 +274,11 @@ def test_extension_pins_catch_mutant(name, mutant_libs):
     with O.library(path):
         with pytest.raises(AssertionError):
             ext_checks(name)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_KIN))
+def test_point_update_pins_catch_mutant(name, mutant_libs):
+    path = mutant_libs[name]
+    with O.library(path):
+        with pytest.raises(AssertionError):
+            kin_checks(name)
