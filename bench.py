@@ -56,6 +56,10 @@ def args_():
                    help="default config: skip the short batched-workload figure")
     p.add_argument("--batch-threads", type=int, default=None,
                    help="--config batch32: host threads driving the handles")
+    p.add_argument("--batch-split", action="store_true",
+                   help="--config batch32 on N GPUs: split the one batch's RVEs over the "
+                        "ranks by estimated cost (strong scaling) instead of giving every "
+                        "rank its own batch of distinct RVEs (weak scaling)")
     p.add_argument("--no-classes", action="store_true",
                    help="--config batch32: no lockstep classes (every handle on its own)")
     p.add_argument("--classes-all", action="store_true",
@@ -249,6 +253,41 @@ def rank_max(x, ws, dev=None):
     t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
     tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_sum(x, ws, dev=None):
+    """x summed over the ranks (units, iterations and launches of the whole
+    job); the reduction tensor lives on dev as in rank_max."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    tdist.all_reduce(t, op=tdist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def rve_cost(n):
+    """Estimated cost of one RVE's increment: every Krylov step runs two
+    9-field transforms (N log N) and passes over the N voxels."""
+    N = int(np.prod(n))
+    return N * max(1.0, float(np.log2(N)))
+
+
+def partition_units(costs, ranks):
+    """Independent RVEs split over ranks by longest processing time first:
+    the costliest unit goes to the least-loaded rank (ties to the lower rank
+    and the lower unit index).  Returns each rank's unit indices, ascending.
+    The largest load is within 4/3 of the best split."""
+    if ranks < 1 or ranks > len(costs):
+        raise ValueError(f"{len(costs)} units cannot fill {ranks} ranks")
+    load = [0.0] * ranks
+    parts = [[] for _ in range(ranks)]
+    for i in sorted(range(len(costs)), key=lambda i: (-costs[i], i)):
+        r = min(range(ranks), key=lambda r: (load[r], r))
+        parts[r].append(i)
+        load[r] += costs[i]
+    return [sorted(p) for p in parts]
 
 
 def dist():
@@ -552,19 +591,37 @@ def run_batch(a, short=False):
     (`batch32`; `batch32x32`: 32 of 32^3) and 20-150 grains, advanced
     together (batch_run_increment: lockstep size classes, other handles on
     their own streams), mixed precision.  A step is one load increment of
-    every RVE."""
+    every RVE.
+
+    On N ranks (one GPU each) the RVEs are independent units and no data
+    crosses ranks: by default rank r advances its own batch of distinct RVEs
+    (the units r*count .. (r+1)*count - 1 of the seeded sequence; weak
+    scaling); with --batch-split the one batch's RVEs are split over the
+    ranks by estimated cost (strong scaling).  The timed steps sit between
+    barriers, the time is the slowest rank's and the units are summed over
+    the ranks."""
     import torch
 
     from paper_2304_01125_gb300 import build as B
     from paper_2304_01125_gb300 import fatiguefft as FF
 
     ws, rank, local = dist()
+    if ws > 1 and not short:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     B.build()
     c = I.CONFIGS[a.config if a.config.startswith("batch") else "batch32"]
-    cfgs = I.batch_configs(seed=c["seed"], count=c["count"], sizes=c["sizes"],
-                           grains=c["grains"])
+    split = ws > 1 and a.batch_split
+    if split:
+        every = I.batch_configs(seed=c["seed"], count=c["count"], sizes=c["sizes"],
+                                grains=c["grains"])
+        part = partition_units([rve_cost(x["n"]) for x in every], ws)
+        cfgs = [every[i] for i in part[rank]]
+    else:
+        cfgs = I.batch_configs(seed=c["seed"] + rank * c["count"], count=c["count"],
+                               sizes=c["sizes"], grains=c["grains"])
     prog = I.uniaxial_cycle_program(c["amplitude"], c["inc_per_cycle"], c["cycles"])
     assert a.warmup + a.steps <= len(prog)
     mat = I.material("baseline")
@@ -598,7 +655,7 @@ def run_batch(a, short=False):
     for r in rves:
         r.profile(["tangent_apply"])
     b.classes(timing=True)
-    torch.cuda.synchronize()
+    rank_barrier(ws, dev)
     clk = Clocks(local)
     clk.start()
     l0 = sum(r.kernel_launches for r in rves)
@@ -615,6 +672,7 @@ def run_batch(a, short=False):
         its += sum(x["lin_it_total"] for x in st)
         vits += sum(nv * x["lin_it_total"] for nv, x in zip(nvox, st))
         cuts += sum(x["cutbacks"] for x in st)
+    rank_barrier(ws, dev)
     clocks = clk.stop()
     launches = sum(r.kernel_launches for r in rves) - l0
     prof = [r.profile_read(reset=True).get("tangent_apply", (0.0, 0, 0.0)) for r in rves]
@@ -623,8 +681,12 @@ def run_batch(a, short=False):
     b.close()
     for r in rves:
         r.close()
-    total_s = sum(ms) / 1e3
-    value = Ntot * a.steps / total_s
+    total_s = rank_max(sum(ms) / 1e3, ws, dev)
+    Njob = int(rank_sum(Ntot, ws, dev))  # voxels of every rank's RVEs
+    its, vits, cuts = (int(rank_sum(x, ws, dev)) for x in (its, vits, cuts))
+    launches = int(rank_sum(launches, ws, dev))
+    Rjob = int(rank_sum(len(cfgs), ws, dev))
+    value = Njob * a.steps / total_s
     hbm, peak_kind = peaks()
     roof = None
     g_ms = sum(c[2] for c in cls)
@@ -660,18 +722,22 @@ def run_batch(a, short=False):
     if short:
         e2e_s = serial_s = None
     else:
-        e2e_s, serial_s = batch_e2e_and_serial(a, make, step, nvox, prog)
+        e2e_s, serial_s = batch_e2e_and_serial(a, make, step, nvox, prog, ws, dev)
     sizes = {}
-    for x in cfgs:
+    for x in (every if split else cfgs):
         sizes[x["n"][0]] = sizes.get(x["n"][0], 0) + 1
-    return batch_line(a, ws, rank, cfgs, sizes, Ntot, ms, value, e2e_s, serial_s, launches, roof,
-                      clocks, its, cuts, cls, variants, vits)
+    line = batch_line(a, ws, rank, Rjob, sizes, Njob, total_s, value, e2e_s, serial_s, launches,
+                      roof, clocks, its, cuts, cls, variants, vits, split)
+    if ws > 1 and not short:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+    return line
 
 
-def batch_e2e_and_serial(a, make, step, nvox, prog):
+def batch_e2e_and_serial(a, make, step, nvox, prog, ws=1, dev=None):
     """End to end (fresh handles, inputs from pinned host memory, every RVE's
     damage field read back each step) and the handles run one after
-    another: wall seconds of the same increments."""
+    another: wall seconds of the same increments (the slowest rank's)."""
     import torch
 
     from paper_2304_01125_gb300 import fatiguefft as FF
@@ -679,14 +745,14 @@ def batch_e2e_and_serial(a, make, step, nvox, prog):
     for k in range(a.warmup):
         step(b, k)
     host_out = [torch.empty(nv, dtype=torch.float64).pin_memory() for nv in nvox]
-    torch.cuda.synchronize()
+    rank_barrier(ws, dev)
     t0 = time.perf_counter()
     for k in range(a.warmup, a.warmup + a.steps):
         step(b, k)
         for r, h in zip(rves, host_out):
             FF.load().fields_out(r._h, FF.FIELDS["phi"][0], h.data_ptr(), h.nbytes, 0)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    rank_barrier(ws, dev)
+    e2e_s = rank_max(time.perf_counter() - t0, ws, dev)
     b.close()
     for r in rves:
         r.close()
@@ -695,31 +761,43 @@ def batch_e2e_and_serial(a, make, step, nvox, prog):
     rves, b = make()
     for k in range(a.warmup):
         step(b, k)
-    torch.cuda.synchronize()
+    rank_barrier(ws, dev)
     t0 = time.perf_counter()
     for k in range(a.warmup, a.warmup + a.steps):
         for r in rves:
             r.run_increment(prog[k][0], prog[k][1])
-    torch.cuda.synchronize()
-    serial_s = time.perf_counter() - t0
+    rank_barrier(ws, dev)
+    serial_s = rank_max(time.perf_counter() - t0, ws, dev)
     b.close()
     for r in rves:
         r.close()
     return e2e_s, serial_s
 
 
-def batch_line(a, ws, rank, cfgs, sizes, Ntot, ms, value, e2e_s, serial_s, launches, roof, clocks,
-               its, cuts, cls, variants, vits):
+def batch_line(a, ws, rank, Rjob, sizes, Ntot, total_s, value, e2e_s, serial_s, launches, roof,
+               clocks, its, cuts, cls, variants, vits, split=False):
+    """The batch's JSON line.  Rjob (RVEs), Ntot (voxels), launches, its,
+    cuts and vits are the whole job's (summed over the ranks), total_s the slowest rank's seconds
+    over the timed steps; sizes counts the grids of the job's RVEs (of the
+    one batch when it is split, of rank 0's batch otherwise)."""
+    names = a.config if a.config.startswith("batch") else "batch32"
+    if ws == 1:
+        who = f"{names}: {sum(sizes.values())} RVEs"
+    elif split:
+        who = f"{names} split over {ws} ranks by estimated cost: {sum(sizes.values())} RVEs"
+    else:
+        who = (f"{names} on each of {ws} ranks (distinct seeded RVEs per rank): "
+               f"{sum(sizes.values())} RVEs per rank, rank 0's")
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "voxel-increments/s",
         "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
-        "ms_per_step": round(sum(ms) / a.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "ms_per_step": round(total_s * 1e3 / a.steps, 3), "higher_is_better": True,
+        "scaling": "strong" if split else "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded periodic Voronoi, uniform SO(3) orientations)",
-        "config": {"workload": f"{a.config if a.config.startswith('batch') else 'batch32'}: "
-                               f"{len(cfgs)} RVEs, grids "
+        "config": {"workload": f"{who}, grids "
                                + ", ".join(f"{k}^3 x{v}" for k, v in sorted(sizes.items()))
-                               + f" ({Ntot} voxels), 20-150 grains, R=-1 uniaxial strain 0.6%, "
+                               + f" ({Ntot} voxels in the job), 20-150 grains, R=-1 uniaxial "
+                                 f"strain 0.6%, "
                                f"30 increments/cycle, increments {a.warmup + 1}-"
                                f"{a.warmup + a.steps}",
                    "tolerances": a.tol, "cutbacks": "on (max_cutbacks 4, max_lin 300)",
@@ -729,13 +807,16 @@ def batch_line(a, ws, rank, cfgs, sizes, Ntot, ms, value, e2e_s, serial_s, launc
                                    "lockstep size classes "
                                    + ", ".join(f"{c[0]} members" for c in cls)
                                    + " (one graph launch per Krylov column per class, batched "
-                                     "9-field transforms); one stream per RVE otherwise")},
+                                     "9-field transforms); one stream per RVE otherwise")
+                                  + ("" if ws == 1 else
+                                     f"; {ws} ranks, one GPU each, no data exchanged between "
+                                     "ranks")},
         "e2e": None if e2e_s is None else {
             "value": round(Ntot * a.steps / e2e_s, 1), "unit": "voxel-increments/s",
-            "h2d_bytes_per_step": 80 * len(cfgs), "d2h_bytes_per_step": 8 * Ntot},
+            "h2d_bytes_per_step": 80 * Rjob, "d2h_bytes_per_step": 8 * Ntot},
         "gpu_launches": int(launches), "roofline": roof, "clocks": clocks,
         "iterations": {"gmres": its, "cutbacks": cuts,
-                       "voxel_gmres_per_s": round(vits / (sum(ms) / 1e3), 1),
+                       "voxel_gmres_per_s": round(vits / total_s, 1),
                        "note": "voxel_gmres_per_s: sum over RVEs of voxels x GMRES iterations "
                                "per second of the timed steps (Krylov throughput independent "
                                "of how many iterations the increments need)"},
