@@ -85,9 +85,17 @@ MUTANTS_EL = {
 }
 
 
-# Algorithm 1: the staggered loop stopped after its first pass
+# Algorithm 1: the staggered loop stopped after its first pass, and two
+# mistakes in the Newton-Krylov solve inside it
 MUTANTS_ALG1 = {
     "stag_single_pass": ("rve.cpp", "r->converged = cF && cP;", "r->converged = true;"),
+    # the Krylov solve of Sec. 3.1 with one Givens rotation applied with the
+    # wrong sign (its residual estimate no longer that of the iterate)
+    "givens_sign": ("rve.cpp", "H[i + 1][k] = -sn[i] * H[i][k] + cs[i] * H[i + 1][k];",
+                    "H[i + 1][k] = sn[i] * H[i][k] + cs[i] * H[i + 1][k];"),
+    # the Newton update of Eq. fdef subtracted instead of added
+    "newton_update_sign": ("rve.cpp", "r->F[(3 * i + j) * N + v] += alpha * g[v];",
+                           "r->F[(3 * i + j) * N + v] -= alpha * g[v];"),
 }
 # the Green preconditioner contracted over the wrong indices (Eq. precf),
 # and the mixed-control correction with its sign flipped
