@@ -188,8 +188,26 @@ def kin_checks(name):
         local_solve_check()
 
 
+# the tensile elastic energy of Eq. decMiehe
+MUTANTS_WE = {
+    # the right stretch F_e^T F_e in place of the left one
+    "we_right_stretch": ("cp.cpp", "const M3 Bdev = sub(mul(Fe, tr(Fe)), eye3());",
+                         "const M3 Bdev = sub(mul(tr(Fe), Fe), eye3());"),
+    # the Green-Lagrange strain in place of the logarithmic one
+    "we_green_strain": ("cp.cpp", "const double e = 0.5 * std::log1p(mu[k]);",
+                        "const double e = 0.5 * mu[k];"),
+    # no split: compressive principal strains kept
+    "we_no_split": ("cp.cpp", "if (e <= 0.0) continue;", "if (e != e) continue;"),
+}
+
+
+def we_checks():
+    pins.test_eigen_split_degenerate_and_rotated()
+    pins.test_we_plus_generic_state_numpy()
+
+
 ALL_MUTANTS = {**MUTANTS, **MUTANTS_CP, **MUTANTS_PF, **MUTANTS_NYE, **MUTANTS_EL,
-               **MUTANTS_ALG1, **MUTANTS_OPS, **MUTANTS_EXT, **MUTANTS_KIN}
+               **MUTANTS_ALG1, **MUTANTS_OPS, **MUTANTS_EXT, **MUTANTS_KIN, **MUTANTS_WE}
 
 
 def _build_mutant(tmp, name):
@@ -290,3 +308,11 @@ def test_point_update_pins_catch_mutant(name, mutant_libs):
     with O.library(path):
         with pytest.raises(AssertionError):
             kin_checks(name)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_WE))
+def test_energy_split_pins_catch_mutant(name, mutant_libs):
+    path = mutant_libs[name]
+    with O.library(path):
+        with pytest.raises(AssertionError):
+            we_checks()

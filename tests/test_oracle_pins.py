@@ -378,6 +378,31 @@ def test_eigen_split_degenerate_and_rotated():
     assert O.we_plus(MAT, np.diag([1 - a, 1 + b, 1 - a])) == 0.0
 
 
+def test_we_plus_generic_state_numpy():
+    """Eq. decMiehe at generic elastic states F_e = R U (a finite lattice
+    rotation R, a stretch U with eigenvalues either side of 1): eps =
+    1/2 ln(F_e F_e^T) from NumPy's eigh, eps+ its positive spectral part and
+    W_e+ = 1/2 eps+ : C : eps+ with the cubic Voigt matrix.  With a finite R
+    the left (F_e F_e^T) and right (F_e^T F_e) stretches give different
+    energies in the anisotropic crystal, so the pin fixes the left one."""
+    rng = np.random.default_rng(11)
+    for _ in range(8):
+        R = O.euler_to_Q(rng.random(3) * 3)
+        W = O.euler_to_Q(rng.random(3) * 3)
+        d = np.array([0.004, -0.002, 0.004 * (2 * rng.random() - 1)])
+        Fe = R @ W @ np.diag(1 + d) @ W.T
+        lam, V = np.linalg.eigh(Fe @ Fe.T)
+        e = 0.5 * np.log(lam)
+        assert e.min() < 0 < e.max()
+        ep = V @ np.diag(np.maximum(e, 0)) @ V.T
+        we = 0.5 * np.sum(ep * cubic_apply_np(MAT, ep))
+        assert abs(O.we_plus(MAT, Fe) - we) < 1e-10 * we
+        # the right stretch's energy differs: the pin tells them apart
+        lam_r, V_r = np.linalg.eigh(Fe.T @ Fe)
+        ep_r = V_r @ np.diag(np.maximum(0.5 * np.log(lam_r), 0)) @ V_r.T
+        assert abs(0.5 * np.sum(ep_r * cubic_apply_np(MAT, ep_r)) - we) > 1e-4 * we
+
+
 # ------------------------------------------------------------------ P5
 def test_green_operator_identities():
     """Eq. precf with Eq. avstiff: M(xi)(xi.K.xi) = I, and the projection
