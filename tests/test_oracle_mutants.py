@@ -206,8 +206,32 @@ def we_checks():
     pins.test_we_plus_generic_state_numpy()
 
 
+# the building blocks: the orientation matrix (Sec. 2.1, Bunge angles), the
+# transform (Sec. 3.1) and the irreversibility clamp (Algorithm 1)
+MUTANTS_BASE = {
+    # g (sample to lattice) returned in place of Q = g^T
+    "euler_not_transposed": ("cp.cpp", "Q[3 * i + j] = g[3 * j + i];",
+                             "Q[3 * i + j] = g[3 * i + j];"),
+    # the twiddle factors off the quarter turns with the opposite sign
+    "fft_twiddle_sign": ("fft.cpp", "const double a = sign * two_pi * (double)t / (double)n;",
+                         "const double a = -sign * two_pi * (double)t / (double)n;"),
+    # the damage no longer held at or above phi_t
+    "pf_clamp_dropped": ("rve.cpp", "phi[v] = std::max(x[v], phi_t[v]);", "phi[v] = x[v];"),
+}
+
+
+def base_checks(name):
+    if name.startswith("euler"):
+        pins.test_euler_rotation_is_bunge()
+    elif name.startswith("fft"):
+        pins.test_fft_matches_numpy_and_naive_dft((6, 6, 6))
+    else:
+        pins.test_phase_field_irreversibility_clamp()
+
+
 ALL_MUTANTS = {**MUTANTS, **MUTANTS_CP, **MUTANTS_PF, **MUTANTS_NYE, **MUTANTS_EL,
-               **MUTANTS_ALG1, **MUTANTS_OPS, **MUTANTS_EXT, **MUTANTS_KIN, **MUTANTS_WE}
+               **MUTANTS_ALG1, **MUTANTS_OPS, **MUTANTS_EXT, **MUTANTS_KIN, **MUTANTS_WE,
+               **MUTANTS_BASE}
 
 
 def _build_mutant(tmp, name):
@@ -316,3 +340,11 @@ def test_energy_split_pins_catch_mutant(name, mutant_libs):
     with O.library(path):
         with pytest.raises(AssertionError):
             we_checks()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_BASE))
+def test_building_block_pins_catch_mutant(name, mutant_libs):
+    path = mutant_libs[name]
+    with O.library(path):
+        with pytest.raises(AssertionError):
+            base_checks(name)
