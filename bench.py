@@ -830,6 +830,26 @@ def batch_line(a, ws, rank, Rjob, sizes, Ntot, total_s, value, e2e_s, serial_s, 
     return line if rank == 0 else None
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the
+    machine type), recorded beside the oracle's timings."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine() or "unknown"
+
+
 def cpu_baseline(cfg, mat, opts, a, budget_s=30.0):
     """The FP64 oracle as it stands, on the host cores: the timed window's
     increments from its first, as many as fit in about budget_s seconds
@@ -854,7 +874,7 @@ def cpu_baseline(cfg, mat, opts, a, budget_s=30.0):
             break
     dt = time.perf_counter() - t0
     return {"value": round(N * increments / dt, 1), "unit": "voxel-increments/s",
-            "cores": threads, "kind": "oracle",
+            "cores": threads, "cpu": cpu_model(), "kind": "oracle",
             "sample": f"{increments} increment(s) of the timed window "
                       f"(increments {a.warmup + 1}-{a.warmup + increments}), {dt:.1f} s"}
 
@@ -895,7 +915,7 @@ def run_reference(a):
         "config": {"workload": f"{workload_desc(a.config, cfg)}, increments {a.warmup + 1}-"
                                f"{a.warmup + a.steps}", "tolerances": a.tol},
         "cpu_baseline": {"value": round(value, 1), "unit": "voxel-increments/s",
-                         "cores": threads, "kind": "oracle",
+                         "cores": threads, "cpu": cpu_model(), "kind": "oracle",
                          "sample": f"{done} full increments of the workload (increments "
                                    f"{a.warmup + 1}-{a.warmup + done}; the run stops timing "
                                    f"after {a.ref_budget_s:.0f} s), {dt:.1f} s"},

@@ -75,3 +75,9 @@ def test_committed_traffic_applies_only_to_its_workload_and_sources(tmp_path, mo
     assert bench.ncu_traffic("gmres_dot", "poly256") is None  # other workload
     assert bench.ncu_traffic("gmres_dot", "poly128") is None  # other kernel sources
     assert bench.ncu_traffic("tangent_apply", "poly64") is None
+
+
+def test_cpu_model_is_a_name():
+    import bench
+    m = bench.cpu_model()
+    assert isinstance(m, str) and m and "\n" not in m
