@@ -68,19 +68,36 @@ def measure(n, prec, variant, stream=None, increments=2):
 
 
 def _load(path):
+    """The cache's entries; an unreadable or malformed file counts as empty."""
     try:
         with open(path) as f:
-            return json.load(f)
+            data = json.load(f)
     except (OSError, ValueError):
         return {}
+    return data if isinstance(data, dict) else {}
+
+
+def _cached(data, key, allowed):
+    """The stored variant for key if it is one of the allowed values, else
+    None (a damaged or outdated entry is measured again)."""
+    e = data.get(key)
+    v = e.get("kernel_variant") if isinstance(e, dict) else None
+    return v if type(v) is int and v in allowed else None
 
 
 def _store(path, data):
-    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
-    fd, tmp = tempfile.mkstemp(dir=os.path.dirname(path) or ".", suffix=".tmp")
-    with os.fdopen(fd, "w") as f:
-        json.dump(data, f, indent=1, sort_keys=True)
-    os.replace(tmp, path)
+    """Write the cache atomically; a cache that cannot be written (a
+    read-only home, a full disk) only costs the measurement next time."""
+    tmp = None
+    try:
+        os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+        fd, tmp = tempfile.mkstemp(dir=os.path.dirname(path) or ".", suffix=".tmp")
+        with os.fdopen(fd, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        if tmp and os.path.exists(tmp):
+            os.unlink(tmp)
 
 
 def best_variant(n, prec, device_name=None, stream=None, path=None, refresh=False,
@@ -95,11 +112,12 @@ def best_variant(n, prec, device_name=None, stream=None, path=None, refresh=Fals
         device_name = torch.cuda.get_device_name()
     path = path or cache_path()
     key = f"{device_name}|{n[0]}x{n[1]}x{n[2]}|{prec}" + ("" if fused else "|unfused")
-    data = _load(path)
-    if key in data and not refresh:
-        return int(data[key]["kernel_variant"])
+    allowed = candidates(n, fused)
+    hit = _cached(_load(path), key, allowed)
+    if hit is not None and not refresh:
+        return hit
     fn = measure_fn or (lambda nn, pp, v: measure(nn, pp, v, stream=stream))
-    times = {v: float(fn(n, prec, v)) for v in candidates(n, fused)}
+    times = {v: float(fn(n, prec, v)) for v in allowed}
     best = min(times, key=lambda v: (times[v], v))
     data = _load(path)  # another process may have written meanwhile
     data[key] = {"kernel_variant": best,

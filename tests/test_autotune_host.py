@@ -53,3 +53,38 @@ def test_unfused_choice_is_cached_apart(tmp_path):
                           fused=False) == 2
     assert sorted(seen) == [0, 0, 1, 2, 2, 3]
     assert A.candidates((64, 64, 64), fused=False) == [0, 2]
+
+
+def test_damaged_cache_entries_are_measured_again(tmp_path):
+    """A malformed file, an entry without a variant, a variant the grid
+    cannot run (the fused pass on 48^3) or a non-integer one: measured
+    again and replaced."""
+    path = tmp_path / "c.json"
+    calls = []
+
+    def fake(n, prec, v):
+        calls.append(v)
+        return {0: 1.0, 1: 0.5, 2: 0.9, 3: 0.6}[v]
+
+    for bad in ("[1, 2]", "{not json",
+                json.dumps({"GPU|48x48x48|mixed": {}}),
+                json.dumps({"GPU|48x48x48|mixed": {"kernel_variant": 1}}),
+                json.dumps({"GPU|48x48x48|mixed": {"kernel_variant": "2"}}),
+                json.dumps({"GPU|48x48x48|mixed": {"kernel_variant": True}})):
+        path.write_text(bad)
+        calls.clear()
+        assert A.best_variant((48, 48, 48), "mixed", "GPU", path=str(path),
+                              measure_fn=fake) == 2
+        assert sorted(calls) == [0, 2]
+        assert json.loads(path.read_text())["GPU|48x48x48|mixed"]["kernel_variant"] == 2
+
+
+def test_unwritable_cache_still_returns_the_choice(tmp_path):
+    """A cache path that cannot be written (its folder is a file): the
+    measured choice is returned all the same."""
+    blocker = tmp_path / "file"
+    blocker.write_text("")
+    path = str(blocker / "sub" / "c.json")
+    got = A.best_variant((64, 64, 64), "mixed", "GPU", path=path,
+                         measure_fn=lambda n, p, v: {0: 1.0, 1: 2.0, 2: 0.5, 3: 3.0}[v])
+    assert got == 2
