@@ -315,8 +315,9 @@ const char* fft_last_error(fft_rve_t r);
 
 /* Batched RVEs (many independent problems of uneven size, one GPU; the
  * paper solves one RVE at a time).  batch_create groups n existing handles,
- * which must be distinct and each created with its own non-default
- * cuda_stream (FFT_ERR_ARG otherwise); the caller keeps ownership of the
+ * which must be distinct, each created with its own non-default
+ * cuda_stream and in no other batch that has not been destroyed
+ * (FFT_ERR_ARG otherwise, with nothing changed); the caller keeps ownership of the
  * handles and must not use them from other threads while the batch runs.
  * n_threads host threads (<= 0: the hardware concurrency; at most n) drive
  * the handles' increments concurrently, largest grid first.  While grouped,

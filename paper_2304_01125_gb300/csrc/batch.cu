@@ -28,6 +28,8 @@ int fatfft_rve_device(fft_rve_t r);
 void* fatfft_rve_stream(fft_rve_t r);
 size_t fatfft_rve_voxels(fft_rve_t r);
 void fatfft_rve_set_poll(fft_rve_t r, bool on);
+bool fatfft_rve_claim(fft_rve_t r, void* batch);
+void fatfft_rve_unclaim(fft_rve_t r, void* batch);
 int fatfft_gang_compatible(fft_rve_t a, fft_rve_t b);
 fft_status fatfft_gang_create(fft_rve_t const* members, int n, void** out);
 fft_status fatfft_gang_run(void* g, const double* const* Fbar, const double* const* Pstar,
@@ -154,6 +156,14 @@ fft_status batch_create_ex(fft_batch_t* out, fft_rve_t const* rves, int n, int n
             return FFT_ERR_ARG;
     }
     fft_batch_s* b = new fft_batch_s();
+    // a handle belongs to one batch at a time (a class takes over its
+    // Arnoldi scratch until the batch is destroyed)
+    for (int i = 0; i < n; ++i)
+        if (!fatfft_rve_claim(rves[i], b)) {
+            for (int j = 0; j < i; ++j) fatfft_rve_unclaim(rves[j], b);
+            delete b;
+            return FFT_ERR_ARG;
+        }
     b->rves.assign(rves, rves + n);
     for (int i = 0; i < n; ++i) fatfft_rve_set_poll(rves[i], true);
     for (int i = 0; i < n; ++i) b->dev.push_back(fatfft_rve_device(rves[i]));
@@ -186,7 +196,10 @@ fft_status batch_create_ex(fft_batch_t* out, fft_rve_t const* rves, int n, int n
             if (s != FFT_OK) {
                 for (Unit& v : b->units)
                     if (v.gang) fatfft_gang_destroy(v.gang);
-                for (int i = 0; i < n; ++i) fatfft_rve_set_poll(rves[i], false);
+                for (int i = 0; i < n; ++i) {
+                    fatfft_rve_set_poll(rves[i], false);
+                    fatfft_rve_unclaim(rves[i], b);
+                }
                 delete b;
                 return s;
             }
@@ -282,7 +295,10 @@ void batch_destroy(fft_batch_t b) {
     for (auto& t : b->pool) t.join();
     for (Unit& u : b->units)
         if (u.gang) fatfft_gang_destroy(u.gang);
-    for (fft_rve_t r : b->rves) fatfft_rve_set_poll(r, false);
+    for (fft_rve_t r : b->rves) {
+        fatfft_rve_set_poll(r, false);
+        fatfft_rve_unclaim(r, b);
+    }
     delete b;
 }
 

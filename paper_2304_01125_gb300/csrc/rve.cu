@@ -3,6 +3,8 @@
 // momentum solve (Eqs. momentum, fdef, newton with the Green preconditioner
 // of Eqs. precf, avstiff) and the phase-field solve (Eqs. phase, precph),
 // all on one CUDA stream.  Only convergence decisions cross to the host.
+#include <mutex>
+
 #include "rve_impl.cuh"
 
 // ------------------------------------------------------- host-side tables
@@ -684,6 +686,18 @@ void* fatfft_rve_stream(fft_rve_t r) { return r ? (void*)r->st : nullptr; }
 size_t fatfft_rve_voxels(fft_rve_t r) { return r ? r->g.N : 0; }
 void fatfft_rve_set_poll(fft_rve_t r, bool on) {
     if (r) r->poll = on;
+}
+// membership of a batch: claim fails if the handle already belongs to one
+static std::mutex g_batch_claim;
+bool fatfft_rve_claim(fft_rve_t r, void* batch) {
+    std::lock_guard<std::mutex> lk(g_batch_claim);
+    if (!r || r->batch) return false;
+    r->batch = batch;
+    return true;
+}
+void fatfft_rve_unclaim(fft_rve_t r, void* batch) {
+    std::lock_guard<std::mutex> lk(g_batch_claim);
+    if (r && r->batch == batch) r->batch = nullptr;
 }
 
 extern "C" {

@@ -95,6 +95,9 @@ struct fft_rve_s {
     // the cores) the event is polled and the core yielded between polls
     cudaEvent_t sync_ev = nullptr;
     bool poll = false;
+    // the batch the handle belongs to (at most one: a lockstep class takes
+    // over the handle's Arnoldi scratch until its batch is destroyed)
+    void* batch = nullptr;
     // one CUDA graph per Arnoldi column j (the step's pointers and grid
     // shapes depend on j only), captured on first use; off on the legacy
     // default stream, while the kernel profiler runs, or with

@@ -367,7 +367,8 @@ class Batch:
         flags = 3 if classes == "all" else (1 if classes else 0)
         s = load().batch_create_ex(C.byref(h), arr, len(self.rves), int(threads or 0), flags)
         if s != FFT_OK:
-            raise FFTError("batch_create", s, "distinct handles, each with its own stream")
+            raise FFTError("batch_create", s, "distinct handles, each with its own stream "
+                                              "and in no other live batch")
         self._h = h
         for r in self.rves:
             r._batches.add(self)

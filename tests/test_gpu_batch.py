@@ -372,6 +372,29 @@ def test_lockstep_class_cuts_back_a_member():
         r.close()
 
 
+def test_a_handle_joins_one_batch_at_a_time():
+    """A lockstep class takes over its members' Arnoldi scratch while its
+    batch exists: a handle in a live batch is refused by another batch
+    (FFT_ERR_ARG, nothing changed) and accepted again once the first batch
+    is closed."""
+    a, c = _make((8, 8, 8), 70, "mixed"), _make((8, 8, 8), 71, "mixed")
+    b1 = FF.Batch([a, c])
+    for group in ([a], [c, a]):
+        with pytest.raises(FF.FFTError):
+            FF.Batch(group)
+    Fb, dt = I.uniaxial_cycle_program(0.004, 8, 1)[0]
+    s, _, _ = b1.run_increment([Fb] * 2, [dt] * 2)
+    assert s == FF.FFT_OK
+    b1.close()
+    b2 = FF.Batch([c, a])
+    Fb, dt = I.uniaxial_cycle_program(0.004, 8, 1)[1]
+    s, _, _ = b2.run_increment([Fb] * 2, [dt] * 2)
+    assert s == FF.FFT_OK
+    b2.close()
+    a.close()
+    c.close()
+
+
 def test_closing_a_class_member_closes_its_batch_first():
     """A lockstep class keeps part of its members' buffers in its arenas:
     closing a member handle closes the batch first (the binding keeps that
