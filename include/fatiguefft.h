@@ -310,6 +310,8 @@ fft_status degraded_average_noalloc(const double* X, int ncomp, const double* ph
 
 /* Size in bytes of the device memory the handle holds. */
 size_t rve_device_bytes(fft_rve_t r);
+/* Release the handle and its device memory.  A handle still in a batch is
+ * left alive (its last error says so): destroy the batch first. */
 void rve_destroy(fft_rve_t r);
 const char* fft_last_error(fft_rve_t r);
 

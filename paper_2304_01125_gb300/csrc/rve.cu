@@ -704,6 +704,15 @@ extern "C" {
 
 void rve_destroy(fft_rve_t r) {
     if (!r) return;
+    {
+        // a handle still in a batch keeps part of its buffers in the
+        // batch's class arenas: it stays alive until the batch is destroyed
+        std::lock_guard<std::mutex> lk(g_batch_claim);
+        if (r->batch) {
+            r->err = "rve_destroy: the handle is still in a batch (destroy the batch first)";
+            return;
+        }
+    }
     cudaStreamSynchronize(r->st);
     release(r);
     delete r;

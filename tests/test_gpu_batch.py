@@ -375,13 +375,16 @@ def test_lockstep_class_cuts_back_a_member():
 def test_a_handle_joins_one_batch_at_a_time():
     """A lockstep class takes over its members' Arnoldi scratch while its
     batch exists: a handle in a live batch is refused by another batch
-    (FFT_ERR_ARG, nothing changed) and accepted again once the first batch
-    is closed."""
+    (FFT_ERR_ARG, nothing changed) and not released by rve_destroy, and is
+    accepted again once the first batch is closed."""
     a, c = _make((8, 8, 8), 70, "mixed"), _make((8, 8, 8), 71, "mixed")
     b1 = FF.Batch([a, c])
     for group in ([a], [c, a]):
         with pytest.raises(FF.FFTError):
             FF.Batch(group)
+    # destroying a handle that is still in a batch leaves it alive
+    FF.load().rve_destroy(a._h)
+    assert b"still in a batch" in FF.load().fft_last_error(a._h)
     Fb, dt = I.uniaxial_cycle_program(0.004, 8, 1)[0]
     s, _, _ = b1.run_increment([Fb] * 2, [dt] * 2)
     assert s == FF.FFT_OK
