@@ -165,3 +165,18 @@ def test_cycle_override_extends_the_loading():
         assert len(more["program"]) == len(base["program"]) + 2 * per
         for (Fa, da), (Fb, db) in zip(base["program"], more["program"]):
             assert np.array_equal(Fa, Fb) and da == db
+
+
+def test_batch_units_are_one_seeded_sequence():
+    """Rank r of a weak-scaled batched run takes units r*count .. (r+1)*count
+    - 1 of one seeded sequence (seed + count*r): the same RVEs as the tail
+    of a batch twice as long, and none shared between ranks."""
+    a = I.batch_configs(seed=2000, count=6, sizes=(8, 12), grains=(2, 5))
+    b = I.batch_configs(seed=2006, count=6, sizes=(8, 12), grains=(2, 5))
+    both = I.batch_configs(seed=2000, count=12, sizes=(8, 12), grains=(2, 5))
+    for x, y in zip(a + b, both):
+        assert x["n"] == y["n"]
+        assert np.array_equal(x["grain_ids"], y["grain_ids"])
+        assert np.array_equal(x["euler"], y["euler"])
+    assert not any(np.array_equal(x["euler"], y["euler"]) for x in a for y in b
+                   if x["euler"].shape == y["euler"].shape)
